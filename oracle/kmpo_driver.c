@@ -1,0 +1,388 @@
+/*
+ * CPU oracle, part 3: balance caps, adaptive imbalance, k-way balancing and
+ * the deep multilevel driver (Algorithm 1 and 2).  Test infrastructure only.
+ *
+ * Readings:
+ *  D1 Coarsening schedule (Section 4.1): k' = max(min(k, floor(n/C)), 1);
+ *     while k' > 1 and n_i <= (k'/2) C, k' is halved; U = max(floor(eps c(V)
+ *     / k'), max_v c(v)) at every level.  Coarsening stops at n_i <= 2C, when
+ *     a clustering contracts nothing, or after a level that shrank by less
+ *     than conv_num/conv_den (Algorithm 1 "has not converged").
+ *  D2 Blocks per level (Algorithm 1, invariant (P)): k_i = k on the input
+ *     graph, else ceil2(n_i / C), clamped to [2, k]; while fewer blocks exist
+ *     every block with final count f_B >= 2 is bipartitioned into
+ *     f = (floor(f_B/2), ceil(f_B/2)) (Section 3, "Handling General k"); new
+ *     ids are handed out in ascending old id, child 0 first.
+ *  D3 Adaptive imbalance (Algorithm 2 generalised by f_B):
+ *     eps' = ((1+eps) c(V) f_B / (k c(B)))^(1/ceil(log2 f_B)) - 1, clamped at
+ *     0; child targets t_j = ceil(c(B) f_j / f_B) and caps
+ *     L_j = floor((1+eps') t_j) (Section 4.2, L_2 = (1+eps') ceil(c(V')/2)).
+ *  D4 Block cap L(b) = floor(max((1+eps) c(V) f_b / k, c(V) f_b / k +
+ *     max_v c(v))) (Section 2, L_max,k, scaled by the block's final count).
+ *  D5 Balancing (Section 4.3): overloaded blocks in ascending id.  Every node
+ *     of the block that has an admissible other block gets d = max over
+ *     admissible blocks of conn - conn(own) and the relative gain d*c(v)
+ *     (d >= 0) or d/c(v) (d < 0), compared exactly.  Nodes are visited in
+ *     (relative gain desc, id asc); at its turn a node moves to the admissible
+ *     block of largest connectivity (ties: lowest id), recomputed then, until
+ *     the block fits.
+ *  D6 Final feasibility uses L_k = floor((1+eps) ceil(c(V)/k)) (Section 2,
+ *     footnote; Section 5).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <time.h>
+
+#include "kmpo.h"
+
+enum { DOM_COARSEN = 1, DOM_IP = 3, DOM_REFINE_LEVEL = 8 };
+
+uint64_t kmpo_step(uint64_t x, uint64_t w);
+
+static int32_t vwt(const int32_t *vw, int32_t v) { return vw ? vw[v] : 1; }
+static int32_t ewt(const int32_t *ew, int64_t e) { return ew ? ew[e] : 1; }
+
+static double now_s(void) {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+void kmpo_config_default(kmpo_config *c) {
+  c->C = 160;
+  c->lp_rounds = 5;
+  c->refine_rounds = 5;
+  c->subrounds = 8;
+  c->two_hop = 1;
+  c->conv_num = 19;
+  c->conv_den = 20;
+  c->ip_C = 16;
+  c->ip_lp_rounds = 5;
+  c->rep_random = 4;
+  c->rep_bfs = 4;
+  c->rep_ggg = 8;
+  c->fm_passes = 8;
+  c->fm_stop = 64;
+}
+
+static int32_t ceil_log2(int32_t f) {
+  int32_t j = 0;
+  while ((1 << j) < f) ++j;
+  return j;
+}
+
+double kmpo_eps_prime(double eps, int64_t cV, int32_t k, int64_t cB, int32_t fB) {
+  double base = ((1.0 + eps) * (double)cV * (double)fB) / ((double)k * (double)cB);
+  return pow(base, 1.0 / (double)ceil_log2(fB)) - 1.0;
+}
+
+void kmpo_split_caps(double eps, int64_t cV, int32_t k, int64_t cB, int32_t fB,
+                     int32_t *target0, int32_t *target1, int32_t *L0, int32_t *L1) {
+  int32_t f0 = fB / 2, f1 = fB - fB / 2;
+  int64_t t0 = (cB * f0 + fB - 1) / fB, t1 = (cB * f1 + fB - 1) / fB;
+  double e = cB > 0 ? kmpo_eps_prime(eps, cV, k, cB, fB) : 0.0;
+  if (e < 0.0) e = 0.0;
+  *target0 = (int32_t)t0;
+  *target1 = (int32_t)t1;
+  *L0 = (int32_t)floor((1.0 + e) * (double)t0);
+  *L1 = (int32_t)floor((1.0 + e) * (double)t1);
+}
+
+int32_t kmpo_block_cap(double eps, int64_t cV, int32_t k, int32_t fb, int32_t maxc) {
+  double a = (1.0 + eps) * (double)cV * (double)fb / (double)k;
+  double b = (double)cV * (double)fb / (double)k + (double)maxc;
+  return (int32_t)floor(a > b ? a : b);
+}
+
+/* ------------------------------------------------------------- balance -- */
+typedef struct {
+  int64_t d, c;
+  int32_t v;
+} rg_t;
+
+/* relative gain order: descending, exact (D5) */
+static int cmp_rg(const void *x, const void *y) {
+  const rg_t *a = (const rg_t *)x, *b = (const rg_t *)y;
+  int sa = a->d >= 0, sb = b->d >= 0;
+  int c;
+  if (sa != sb) c = sa ? -1 : 1;
+  else if (sa) {
+    int64_t p = a->d * a->c, q = b->d * b->c;
+    c = p > q ? -1 : (p < q ? 1 : 0);
+  } else {
+    int64_t p = a->d * b->c, q = b->d * a->c; /* a.d/a.c vs b.d/b.c */
+    c = p > q ? -1 : (p < q ? 1 : 0);
+  }
+  if (c) return c;
+  return a->v < b->v ? -1 : (a->v > b->v);
+}
+
+int64_t kmpo_balance(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
+                     const int32_t *ew, int32_t k, const int32_t *cap, int32_t *part) {
+  int64_t *bw = (int64_t *)calloc((size_t)k, sizeof(int64_t));
+  int64_t *conn = (int64_t *)calloc((size_t)k, sizeof(int64_t));
+  for (int32_t v = 0; v < n; ++v) bw[part[v]] += vwt(vw, v);
+  rg_t *cand = (rg_t *)malloc(sizeof(rg_t) * (size_t)(n > 0 ? n : 1));
+  int64_t moved = 0;
+  for (int32_t B = 0; B < k; ++B) {
+    if (bw[B] <= cap[B]) continue;
+    int32_t nc = 0;
+    for (int32_t v = 0; v < n; ++v) {
+      if (part[v] != B) continue;
+      for (int64_t e = xadj[v]; e < xadj[v + 1]; ++e) conn[part[adj[e]]] += ewt(ew, e);
+      int64_t bestc = -1;
+      for (int32_t b = 0; b < k; ++b) {
+        if (b == B || bw[b] + vwt(vw, v) > cap[b]) continue;
+        if (conn[b] > bestc) bestc = conn[b];
+      }
+      if (bestc >= 0) {
+        cand[nc].d = bestc - conn[B];
+        cand[nc].c = vwt(vw, v);
+        cand[nc].v = v;
+        ++nc;
+      }
+      for (int64_t e = xadj[v]; e < xadj[v + 1]; ++e) conn[part[adj[e]]] = 0;
+      conn[B] = 0;
+    }
+    qsort(cand, (size_t)nc, sizeof(rg_t), cmp_rg);
+    for (int32_t i = 0; i < nc && bw[B] > cap[B]; ++i) {
+      int32_t v = cand[i].v;
+      for (int64_t e = xadj[v]; e < xadj[v + 1]; ++e) conn[part[adj[e]]] += ewt(ew, e);
+      int32_t t = -1;
+      for (int32_t b = 0; b < k; ++b) {
+        if (b == B || bw[b] + vwt(vw, v) > cap[b]) continue;
+        if (t < 0 || conn[b] > conn[t]) t = b;
+      }
+      for (int64_t e = xadj[v]; e < xadj[v + 1]; ++e) conn[part[adj[e]]] = 0;
+      if (t < 0) continue;
+      part[v] = t;
+      bw[B] -= vwt(vw, v);
+      bw[t] += vwt(vw, v);
+      ++moved;
+    }
+  }
+  free(bw); free(conn); free(cand);
+  return moved;
+}
+
+/* --------------------------------------------------------------- driver -- */
+typedef struct {
+  int32_t n;
+  int64_t *xadj;
+  int32_t *adj, *vw, *ew, *map;
+  int32_t owned;
+} glvl_t;
+
+static int32_t max_vw(int32_t n, const int32_t *vw) {
+  int32_t m = 0;
+  for (int32_t v = 0; v < n; ++v)
+    if (vwt(vw, v) > m) m = vwt(vw, v);
+  return m;
+}
+
+/* Algorithm 2: bipartition every block with f >= 2 (one split round) */
+static void bipartition_blocks(const glvl_t *g, int32_t *part, int32_t *nblocks, int32_t *f,
+                               double eps, int64_t cV, int32_t k, uint64_t roundkey,
+                               const kmpo_config *cfg) {
+  int32_t nb = *nblocks;
+  int32_t *newid = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
+  int32_t *nf = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * nb));
+  int32_t nn = 0;
+  for (int32_t b = 0; b < nb; ++b) {
+    newid[b] = nn;
+    if (f[b] >= 2) {
+      nf[nn] = f[b] / 2;
+      nf[nn + 1] = f[b] - f[b] / 2;
+      nn += 2;
+    } else {
+      nf[nn] = f[b];
+      nn += 1;
+    }
+  }
+  /* members of each block in ascending id */
+  int32_t *cnt = (int32_t *)calloc((size_t)nb + 1, sizeof(int32_t));
+  for (int32_t v = 0; v < g->n; ++v) cnt[part[v] + 1]++;
+  for (int32_t b = 0; b < nb; ++b) cnt[b + 1] += cnt[b];
+  int32_t *mem = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->n > 0 ? g->n : 1));
+  int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
+  for (int32_t b = 0; b < nb; ++b) pos[b] = cnt[b];
+  for (int32_t v = 0; v < g->n; ++v) mem[pos[part[v]]++] = v;
+  int32_t *loc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->n > 0 ? g->n : 1));
+  int32_t *newpart = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->n > 0 ? g->n : 1));
+  for (int32_t b = 0; b < nb; ++b)
+    for (int32_t i = cnt[b]; i < cnt[b + 1]; ++i) loc[mem[i]] = i - cnt[b];
+  for (int32_t b = 0; b < nb; ++b) {
+    int32_t nbv = cnt[b + 1] - cnt[b];
+    if (f[b] < 2) {
+      for (int32_t i = cnt[b]; i < cnt[b + 1]; ++i) newpart[mem[i]] = newid[b];
+      continue;
+    }
+    /* induced subgraph G[V_b] with local ids in ascending global id */
+    int64_t *sx = (int64_t *)calloc((size_t)nbv + 1, sizeof(int64_t));
+    int64_t tot = 0;
+    for (int32_t i = 0; i < nbv; ++i) {
+      int32_t v = mem[cnt[b] + i];
+      for (int64_t e = g->xadj[v]; e < g->xadj[v + 1]; ++e)
+        if (part[g->adj[e]] == b) ++tot;
+    }
+    int32_t *sa = (int32_t *)malloc(sizeof(int32_t) * (size_t)(tot > 0 ? tot : 1));
+    int32_t *se = (int32_t *)malloc(sizeof(int32_t) * (size_t)(tot > 0 ? tot : 1));
+    int32_t *sv = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nbv > 0 ? nbv : 1));
+    int64_t m = 0, cB = 0;
+    for (int32_t i = 0; i < nbv; ++i) {
+      int32_t v = mem[cnt[b] + i];
+      sv[i] = vwt(g->vw, v);
+      cB += sv[i];
+      for (int64_t e = g->xadj[v]; e < g->xadj[v + 1]; ++e)
+        if (part[g->adj[e]] == b) {
+          sa[m] = loc[g->adj[e]];
+          se[m] = ewt(g->ew, e);
+          ++m;
+        }
+      sx[i + 1] = m;
+    }
+    int32_t t0, t1, L0, L1;
+    kmpo_split_caps(eps, cV, k, cB, f[b], &t0, &t1, &L0, &L1);
+    int32_t *side = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nbv > 0 ? nbv : 1));
+    kmpo_bipartition(nbv, sx, sa, sv, se, L0, L1, t0, t1, kmpo_step(roundkey, (uint64_t)b),
+                     cfg, side);
+    for (int32_t i = 0; i < nbv; ++i) newpart[mem[cnt[b] + i]] = newid[b] + side[i];
+    free(sx); free(sa); free(se); free(sv); free(side);
+  }
+  memcpy(part, newpart, sizeof(int32_t) * (size_t)g->n);
+  memcpy(f, nf, sizeof(int32_t) * (size_t)nn);
+  *nblocks = nn;
+  free(newid); free(nf); free(cnt); free(mem); free(pos); free(loc); free(newpart);
+}
+
+int32_t kmpo_partition(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
+                       const int32_t *ew, int32_t k, double eps, uint64_t seed,
+                       const kmpo_config *cfg, int32_t *part_out, kmpo_stats *st) {
+  double t0 = now_s();
+  kmpo_stats dummy;
+  if (!st) st = &dummy;
+  memset(st, 0, sizeof(*st));
+  if (k <= 1) {
+    for (int32_t v = 0; v < n; ++v) part_out[v] = 0;
+    st->feasible = 1;
+    return 0;
+  }
+  int64_t cV = 0;
+  for (int32_t v = 0; v < n; ++v) cV += vwt(vw, v);
+  glvl_t lv[64];
+  int32_t nl = 1;
+  lv[0].n = n;
+  lv[0].xadj = (int64_t *)xadj;
+  lv[0].adj = (int32_t *)adj;
+  lv[0].vw = (int32_t *)vw;
+  lv[0].ew = (int32_t *)ew;
+  lv[0].map = NULL;
+  lv[0].owned = 0;
+  int64_t kp = n / cfg->C;
+  if (kp > k) kp = k;
+  if (kp < 1) kp = 1;
+  /* D1: coarsening */
+  while (nl < 63 && lv[nl - 1].n > 2 * cfg->C) {
+    glvl_t *g = &lv[nl - 1];
+    while (kp > 1 && 2 * (int64_t)g->n <= kp * cfg->C) kp /= 2;
+    int64_t U = (int64_t)floor(eps * (double)cV / (double)kp);
+    int32_t maxc = max_vw(g->n, g->vw);
+    if (U < maxc) U = maxc;
+    if (U < 1) U = 1;
+    int32_t *label = (int32_t *)malloc(sizeof(int32_t) * (size_t)g->n);
+    kmpo_lp_stats ls;
+    int32_t nc = kmpo_cluster(g->n, g->xadj, g->adj, g->vw, g->ew, (int32_t)U, cfg->lp_rounds,
+                              seed, nl - 1, cfg, 1, cfg->two_hop, label, NULL, &ls);
+    for (int32_t r = 0; r < ls.rounds && r < 16; ++r) st->lp_scanned += ls.scanned[r];
+    if (nc == g->n) {
+      free(label);
+      break;
+    }
+    g->map = (int32_t *)malloc(sizeof(int32_t) * (size_t)g->n);
+    kmpo_graph cg;
+    kmpo_contract(g->n, g->xadj, g->adj, g->vw, g->ew, label, g->map, &cg);
+    free(label);
+    lv[nl].n = cg.n;
+    lv[nl].xadj = cg.xadj;
+    lv[nl].adj = cg.adj;
+    lv[nl].vw = cg.vw;
+    lv[nl].ew = cg.ew;
+    lv[nl].map = NULL;
+    lv[nl].owned = 1;
+    ++nl;
+    if ((int64_t)cfg->conv_den * cg.n > (int64_t)cfg->conv_num * g->n) break;
+  }
+  double t1 = now_s();
+  st->t_coarsen = t1 - t0;
+  st->levels = nl;
+  for (int32_t l = 0; l < nl && l < 64; ++l) {
+    st->level_n[l] = lv[l].n;
+    st->level_m[l] = lv[l].xadj[lv[l].n];
+  }
+  /* D2: uncoarsening with recursive bipartitioning, balancing, refinement */
+  int32_t *f = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * k + 2));
+  int32_t *cap = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * k + 2));
+  int32_t nblocks = 1;
+  f[0] = k;
+  int32_t *part = (int32_t *)calloc((size_t)lv[nl - 1].n, sizeof(int32_t));
+  double tip = 0, tref = 0;
+  for (int32_t l = nl - 1; l >= 0; --l) {
+    glvl_t *g = &lv[l];
+    if (l < nl - 1) {
+      int32_t *fine = (int32_t *)malloc(sizeof(int32_t) * (size_t)g->n);
+      for (int32_t v = 0; v < g->n; ++v) fine[v] = part[g->map[v]];
+      free(part);
+      part = fine;
+    }
+    int64_t ki;
+    if (l == 0) {
+      ki = k;
+    } else {
+      ki = 1;
+      while (ki * cfg->C < g->n) ki *= 2;
+    }
+    if (ki > k) ki = k;
+    if (ki < 2) ki = 2;
+    double a = now_s();
+    for (int32_t j = 0; nblocks < ki; ++j) {
+      uint64_t w[3] = {DOM_IP, (uint64_t)l, (uint64_t)j};
+      bipartition_blocks(g, part, &nblocks, f, eps, cV, k, kmpo_key(seed, 3, w), cfg);
+    }
+    double b = now_s();
+    tip += b - a;
+    int32_t maxc = max_vw(g->n, g->vw);
+    for (int32_t i = 0; i < nblocks; ++i) cap[i] = kmpo_block_cap(eps, cV, k, f[i], maxc);
+    kmpo_balance(g->n, g->xadj, g->adj, g->vw, g->ew, nblocks, cap, part);
+    uint64_t w2[2] = {DOM_REFINE_LEVEL, (uint64_t)l};
+    kmpo_lp_stats ls;
+    kmpo_refine(g->n, g->xadj, g->adj, g->vw, g->ew, nblocks, cap, cfg->refine_rounds,
+                kmpo_key(seed, 2, w2), cfg, part, &ls);
+    for (int32_t r = 0; r < ls.rounds && r < 16; ++r) st->refine_scanned += ls.scanned[r];
+    tref += now_s() - b;
+  }
+  memcpy(part_out, part, sizeof(int32_t) * (size_t)n);
+  free(part);
+  free(f);
+  free(cap);
+  for (int32_t l = 0; l < nl; ++l) {
+    free(lv[l].map);
+    if (lv[l].owned) {
+      free(lv[l].xadj); free(lv[l].adj); free(lv[l].vw); free(lv[l].ew);
+    }
+  }
+  /* D6 */
+  int64_t Lk = (int64_t)floor((1.0 + eps) * (double)((cV + k - 1) / k));
+  int64_t *bw = (int64_t *)calloc((size_t)k, sizeof(int64_t));
+  for (int32_t v = 0; v < n; ++v) bw[part_out[v]] += vwt(vw, v);
+  int32_t feas = 1;
+  for (int32_t b = 0; b < k; ++b)
+    if (bw[b] > Lk) feas = 0;
+  free(bw);
+  st->cut = kmpo_cut(n, xadj, adj, ew, part_out);
+  st->feasible = feas;
+  st->t_ip = tip;
+  st->t_refine = tref;
+  st->t_total = now_s() - t0;
+  return feas ? 0 : -5;
+}

@@ -1,0 +1,391 @@
+"""Pins for the CPU oracle: checks against facts the paper and the mathematics
+fix (closed forms, invariants, brute force, hand-derived cases), never against
+the oracle's own formulas retyped.  CPU only."""
+import itertools
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from paper_2105_02022_gb300 import graphgen as gg
+
+
+def adjacency(g):
+    rows = np.repeat(np.arange(g.n), np.diff(g.xadj))
+    return sp.csr_matrix((g.ew().astype(np.int64), (rows, g.adjncy)), shape=(g.n, g.n))
+
+
+def cut_by_matrix(g, part):
+    """Cut via an independent formula: 1/2 * sum of A[u,v] over u,v in different blocks."""
+    A = adjacency(g).tocoo()
+    return int(A.data[part[A.row] != part[A.col]].sum() // 2)
+
+
+# ----------------------------------------------------------------- keys --
+def test_splitmix64_reference_value():
+    # SplitMix64 seeded with 0: first output 0xE220A8397B1DCDAF (published value)
+    assert O.key(0, []) == 0xE220A8397B1DCDAF
+
+
+def test_fmix32_reference_value_and_bijection():
+    # MurmurHash3 fmix32(1) = 0x514E28B7 (published), fmix32(0) = 0
+    assert O.lib().kmpo_perm32(0, 1) == 0x514E28B7
+    assert O.lib().kmpo_perm32(0, 0) == 0
+    rk = O.key(7, [1, 2, 3])
+    vals = {O.lib().kmpo_perm32(rk, i) for i in range(20000)}
+    assert len(vals) == 20000
+
+
+def test_subround_balanced():
+    rk = O.key(3, [1, 0, 0])
+    S = 8
+    counts = np.bincount([O.lib().kmpo_subround(rk, v, S) for v in range(16000)], minlength=S)
+    assert counts.min() > 1800 and counts.max() < 2200
+
+
+# ------------------------------------------------------------------ cut --
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_cut_matches_matrix_formula(seed):
+    g = gg.with_weights(gg.random_graph(60, 200, seed), 5, 9, seed)
+    rng = np.random.default_rng(seed)
+    part = rng.integers(0, 4, g.n).astype(np.int32)
+    assert O.cut(g, part) == cut_by_matrix(g, part)
+
+
+def test_hand_cuts():
+    # path P_n bisection cut 1, cycle C_n cut 2, K4 cut 4, a x b grid cut a
+    assert O.cut(gg.path(10), np.array([0] * 5 + [1] * 5, np.int32)) == 1
+    cyc = gg.from_edges(8, [(i, (i + 1) % 8) for i in range(8)])
+    assert O.cut(cyc, np.array([0] * 4 + [1] * 4, np.int32)) == 2
+    k4 = gg.from_edges(4, list(itertools.combinations(range(4), 2)))
+    assert O.cut(k4, np.array([0, 0, 1, 1], np.int32)) == 4
+    g = gg.grid(3, 6)
+    part = np.array([0 if j < 3 else 1 for i in range(3) for j in range(6)], np.int32)
+    assert O.cut(g, part) == 3
+
+
+# ------------------------------------------------------ brute bisection --
+@pytest.mark.parametrize("a,b", [(2, 4), (3, 4), (3, 6), (4, 4)])
+def test_brute_grid_bisection(a, b):
+    g = gg.grid(a, b)
+    half = a * b // 2
+    c, side = O.brute_bisection(g, half, half)
+    assert c == a
+    assert O.cut(g, side) == c
+
+
+def test_brute_small_families():
+    assert O.brute_bisection(gg.path(12), 6, 6)[0] == 1
+    cyc = gg.from_edges(10, [(i, (i + 1) % 10) for i in range(10)])
+    assert O.brute_bisection(cyc, 5, 5)[0] == 2
+    k4 = gg.from_edges(4, list(itertools.combinations(range(4), 2)))
+    assert O.brute_bisection(k4, 2, 2)[0] == 4
+
+
+# --------------------------------------------------------------- LP core --
+def _weights_of(g, label):
+    return np.bincount(label, weights=g.vw(), minlength=g.n).astype(np.int64)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+@pytest.mark.parametrize("U", [1, 3, 7, 40])
+def test_lp_cap_and_conservation(seed, U):
+    g = gg.with_weights(gg.random_graph(120, 360, seed), 3, 5, seed)
+    U = max(U, int(g.vw().max()))
+    label = O.cluster(g, U, 5, seed, 0, isolated=True, two_hop=False)
+    w = _weights_of(g, label)
+    assert w.max() <= U                       # size constraint c(K) <= U (Section 2)
+    assert w.sum() == g.vw().sum()            # weights conserved
+    assert np.all((label >= 0) & (label < g.n))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 5])
+def test_lp_converged_is_local_optimum_without_cap(seed):
+    """With U >= c(V) and a final round without moves, no node has a neighbouring
+    cluster of strictly larger rating than its own (Raghavan et al. fixpoint)."""
+    g = gg.with_weights(gg.random_graph(80, 200, seed), 1, 7, seed)
+    U = int(g.vw().sum())
+    cfg = O.config()
+    label, fav, st = O.cluster(g, U, 12, seed, 0, cfg=cfg, isolated=False, two_hop=False, stats=True)
+    assert st.rounds < 12 or st.moved[st.rounds - 1] == 0
+    A = adjacency(g)
+    for u in range(g.n):
+        s, e = g.xadj[u], g.xadj[u + 1]
+        r = {}
+        for v, w in zip(g.adjncy[s:e], g.ew()[s:e]):
+            r[label[v]] = r.get(label[v], 0) + int(w)
+        own = r.get(label[u], 0)
+        assert all(val <= own for val in r.values()), (u, r, own)
+    assert A.nnz == g.m_directed
+
+
+def test_lp_determinism_and_seed_dependence():
+    g = gg.workload_rgg_small(3)
+    a = O.cluster(g, 122, 5, 11, 0)
+    b = O.cluster(g, 122, 5, 11, 0)
+    c = O.cluster(g, 122, 5, 12, 0)
+    assert np.array_equal(a, b)
+    assert not np.array_equal(a, c)
+
+
+def test_isolated_packing_hand_case():
+    # no edges; weights 2 with U = 3: prefixes 0,2,4,6,8,... (hand derived)
+    n = 8
+    g = gg.Graph(n, np.zeros(n + 1, np.int64), np.zeros(0, np.int32), np.full(n, 2, np.int32), None)
+    label = O.cluster(g, 3, 5, 1, 0, two_hop=False)
+    # P=0 chunk0 (label0); P=2 straddles (alone); P=4 chunk1 (label2); P=6 chunk2 (label3);
+    # P=8 straddles; P=10 chunk3 (label5); P=12 chunk4 (label6); P=14 straddles
+    assert label.tolist() == [0, 1, 2, 3, 4, 5, 6, 7]
+    g1 = gg.Graph(n, np.zeros(n + 1, np.int64), np.zeros(0, np.int32), None, None)
+    assert O.cluster(g1, 3, 5, 1, 0, two_hop=False).tolist() == [0, 0, 0, 3, 3, 3, 6, 6]
+
+
+def test_two_hop_star_forced():
+    """Heavy centre (weight U) joined to L unit leaves: no LP move is admissible,
+    every leaf favours the centre's cluster, two-hop pairs leaves (1,2),(3,4),..."""
+    L, U = 9, 2
+    n = L + 1
+    g = gg.from_edges(n, [(0, i) for i in range(1, n)], vwgt=[U] + [1] * L)
+    label, fav, st = O.cluster(g, U, 5, 3, 0, isolated=True, two_hop=True, stats=True)
+    assert st.moved[0] == 0
+    assert fav[1:].tolist() == [0] * L
+    need = n - n // 2
+    pairs = min(need, L // 2)
+    exp = list(range(n))
+    for p in range(pairs):
+        a, b = 1 + 2 * p, 2 + 2 * p
+        exp[b] = a
+    assert label.tolist() == exp
+    assert len(set(label.tolist())) == n - pairs
+
+
+def test_two_triangles():
+    """Two triangles joined by one edge, unit weights, U = 3: every cluster
+    stays within the cap and the cap forbids any cluster spanning both sides
+    with more than 3 nodes."""
+    g = gg.from_edges(6, [(0, 1), (1, 2), (0, 2), (3, 4), (4, 5), (3, 5), (2, 3)])
+    for seed in range(1, 30):
+        label = O.cluster(g, 3, 5, seed, 0, two_hop=False)
+        assert np.bincount(label, minlength=6).max() <= 3
+
+
+# ---------------------------------------------------------- contraction --
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_contraction_is_PtAP(seed):
+    g = gg.with_weights(gg.random_graph(150, 500, seed), 4, 6, seed)
+    label = O.cluster(g, 12, 5, seed, 0)
+    cg, mp = O.contract(g, label)
+    # P: n x n' assignment; coarse adjacency = P^T A P without the diagonal
+    P = sp.csr_matrix((np.ones(g.n, np.int64), (np.arange(g.n), mp)), shape=(g.n, cg.n))
+    Ac = (P.T @ adjacency(g) @ P).tolil()
+    Ac.setdiag(0)
+    Ac = Ac.tocsr()
+    Ac.eliminate_zeros()
+    mine = adjacency(cg)
+    assert (Ac != mine).nnz == 0
+    assert np.array_equal(np.bincount(mp, weights=g.vw(), minlength=cg.n).astype(np.int64),
+                          cg.vw().astype(np.int64))
+    # canonical form: rows sorted, symmetric, no self-loops; ids follow label order
+    for x in range(cg.n):
+        row = cg.adjncy[cg.xadj[x]:cg.xadj[x + 1]]
+        assert np.all(np.diff(row) > 0) and not np.any(row == x)
+    firsts = [label[np.where(mp == x)[0][0]] for x in range(cg.n)]
+    assert firsts == sorted(firsts)
+
+
+@pytest.mark.parametrize("seed", [1, 4])
+def test_projection_preserves_cut(seed):
+    """A coarse partition projected to the fine graph has the same cut (Section 1)."""
+    g = gg.with_weights(gg.rgg(2000, 8, seed), 0, 5, seed)
+    label = O.cluster(g, 30, 5, seed, 0)
+    cg, mp = O.contract(g, label)
+    part_c = np.random.default_rng(seed).integers(0, 5, cg.n).astype(np.int32)
+    assert O.cut(cg, part_c) == O.cut(g, part_c[mp])
+
+
+def test_weight_conservation_across_levels():
+    g = gg.workload_rgg_small(2)
+    tot_v, cur = int(g.vw().sum()), g
+    tot_e = int(g.ew().sum())
+    for lvl in range(3):
+        label = O.cluster(cur, 122, 5, 1, lvl)
+        intra = sum(int(w) for u in range(cur.n)
+                    for v, w in zip(cur.adjncy[cur.xadj[u]:cur.xadj[u + 1]],
+                                    cur.ew()[cur.xadj[u]:cur.xadj[u + 1]]) if label[u] == label[v])
+        nxt, _ = O.contract(cur, label)
+        assert int(nxt.vw().sum()) == tot_v
+        assert int(nxt.ew().sum()) == int(cur.ew().sum()) - intra
+        cur = nxt
+    assert int(cur.ew().sum()) < tot_e
+
+
+# ------------------------------------------------------------ refinement --
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_refine_caps_and_reported_cut(seed):
+    g = gg.with_weights(gg.rgg(3000, 8, seed), 3, 4, seed)
+    k = 6
+    part = np.random.default_rng(seed).integers(0, k, g.n).astype(np.int32)
+    bw = np.bincount(part, weights=g.vw(), minlength=k)
+    caps = (np.maximum(bw, bw.mean() * 1.05) + 2).astype(np.int32)
+    out, c = O.refine(g, k, caps, 5, seed, part)
+    bw2 = np.bincount(out, weights=g.vw(), minlength=k)
+    assert np.all(bw2 <= caps)
+    assert c == cut_by_matrix(g, out)
+    assert c < cut_by_matrix(g, part)
+
+
+def test_refine_uncapped_fixpoint():
+    g = gg.with_weights(gg.random_graph(100, 300, 9), 1, 5, 9)
+    k = 4
+    part = (np.arange(g.n) % k).astype(np.int32)
+    caps = np.full(k, int(g.vw().sum()), np.int32)
+    out, c, st = O.refine(g, k, caps, 30, 5, part, stats=True)
+    if st.moved[st.rounds - 1] == 0:
+        for u in range(g.n):
+            s, e = g.xadj[u], g.xadj[u + 1]
+            conn = np.bincount(out[g.adjncy[s:e]], weights=g.ew()[s:e], minlength=k)
+            assert conn.max() <= conn[out[u]]
+
+
+# ----------------------------------------------------------- FM / initial --
+@pytest.mark.parametrize("seed", range(1, 9))
+def test_fm_cut_bookkeeping_and_rollback(seed):
+    g = gg.with_weights(gg.random_graph(40, 120, seed), 3, 9, seed)
+    c = int(g.vw().sum())
+    L = int(np.ceil(c / 2) * 1.1)
+    side0 = np.random.default_rng(seed).integers(0, 2, g.n).astype(np.int32)
+    side, cut = O.fm(g, L, L, side0)
+    assert cut == O.cut(g, side)                      # incremental gains agree with recount
+    W = np.bincount(side, weights=g.vw(), minlength=2)
+    W0 = np.bincount(side0, weights=g.vw(), minlength=2)
+    ov = lambda w: max(w[0] - L, w[1] - L)
+    key = lambda w, ct: (ov(w) > 0, max(ov(w), 0), ct)
+    assert key(W, cut) <= key(W0, O.cut(g, side0))    # a pass never ends worse
+
+
+@pytest.mark.parametrize("algo", [0, 1, 2])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_initial_first_fit_maximal(algo, seed):
+    g = gg.with_weights(gg.random_graph(50, 100, seed), 6, 3, seed)
+    t0 = int(g.vw().sum()) // 2
+    side = O.initial(algo, g, t0, O.key(seed, [5, algo]))
+    W0 = int(g.vw()[side == 0].sum())
+    assert W0 <= t0
+    assert np.all(g.vw()[side == 1] > t0 - W0)
+
+
+def test_bfs_on_path_is_interval():
+    g = gg.path(40)
+    for s in range(1, 6):
+        side = O.initial(1, g, 13, O.key(s, [6]))
+        idx = np.where(side == 0)[0]
+        assert len(idx) == 13 and idx.max() - idx.min() == 12
+
+
+@pytest.mark.parametrize("seed", range(1, 13))
+def test_bipartition_vs_brute_force(seed):
+    n = 12 + seed % 7
+    g = gg.with_weights(gg.random_graph(n, 3 * n, seed), 4, 8, seed)
+    c = int(g.vw().sum())
+    t0 = (c + 1) // 2
+    L = int(np.floor(1.1 * t0))
+    t1 = c - t0
+    side, cut = O.bipartition(g, L, L, t0, t1, O.key(seed, [3, 0, 0, 0]))
+    # caps on the finest level: max(L, t + max c(v)) (Fiduccia-Mattheyses slack)
+    Lf = max(L, t0 + int(g.vw().max()))
+    opt, _ = O.brute_bisection(g, Lf, Lf)
+    assert cut == O.cut(g, side)
+    W = np.bincount(side, weights=g.vw(), minlength=2)
+    assert opt >= 0
+    assert W.max() <= Lf
+    assert cut >= opt
+
+
+@pytest.mark.parametrize("n", [20, 64, 200, 320])
+def test_bipartition_path_finds_optimum(n):
+    g = gg.path(n)
+    L = int(1.03 * n / 2)
+    side, cut = O.bipartition(g, L, L, n // 2, n - n // 2, O.key(1, [3]))
+    assert cut == 1
+    assert np.bincount(side).max() <= max(L, n // 2 + 1)
+
+
+# ----------------------------------------------------- imbalance / caps --
+def test_eps_prime_closed_forms():
+    eps = 0.03
+    # root bipartition for k = 2: eps' = eps
+    assert abs(O.eps_prime(eps, 1000, 2, 1000, 2) - eps) < 1e-12
+    # product over the recursion: (1+eps')^log2(f) = (1+eps) when c(B) = c(V) f/k
+    for k, f in [(4, 4), (16, 16), (64, 8), (1024, 2)]:
+        cV = 1 << 20
+        e = O.eps_prime(eps, cV, k, cV * f // k, f)
+        assert abs((1 + e) ** int(np.log2(f)) - (1 + eps)) < 1e-12
+    # general f: exponent is 1/ceil(log2 f)
+    e = O.eps_prime(eps, 3000, 3, 3000, 3)
+    assert abs((1 + e) ** 2 - (1 + eps)) < 1e-12
+
+
+def test_split_caps_match_L2():
+    # f = 2: target ceil(c/2), L = floor((1+eps') ceil(c/2)) (Section 4.2)
+    t0, t1, L0, L1 = O.split_caps(0.03, 1001, 2, 1001, 2)
+    assert t0 == 501 and t1 == 501 and L0 == int(np.floor(1.03 * 501)) and L1 == L0
+    # f = 3: weight split 1:2
+    t0, t1, L0, L1 = O.split_caps(0.03, 3000, 3, 3000, 3)
+    assert t0 == 1000 and t1 == 2000 and L1 >= 2000 and L0 >= 1000
+
+
+def test_block_cap_is_Lmax():
+    # L_max,k = max{(1+eps) c(V)/k, c(V)/k + max c(v)} (Section 2)
+    assert O.block_cap(0.03, 32768, 8, 1, 1) == int(np.floor(1.03 * 4096))
+    assert O.block_cap(0.03, 1000, 10, 1, 50) == 150
+    assert O.block_cap(0.03, 32768, 8, 2, 1) == int(np.floor(1.03 * 8192))
+
+
+def test_balance_removes_overload():
+    g = gg.with_weights(gg.rgg(2000, 8, 3), 0, 3, 3)
+    k = 4
+    part = (np.arange(g.n) * k // g.n).astype(np.int32)
+    part[500:700] = 0
+    caps = np.full(k, int(1.03 * g.n / k), np.int32)
+    out, mv = O.balance(g, k, caps, part)
+    bw = np.bincount(out, minlength=k)
+    assert np.all(bw <= caps) and mv > 0
+    # nodes only leave overloaded blocks
+    assert np.all((out == part) | (np.bincount(part, minlength=k)[part] > caps[part]))
+
+
+# ------------------------------------------------------------- driver --
+@pytest.mark.parametrize("k", [2, 3, 5, 8, 13])
+def test_partition_feasible_and_valid(k):
+    g = gg.rgg(4000, 8, k)
+    part, rc, st = O.partition(g, k, 0.03, 1)
+    assert rc == 0 and st.feasible
+    Lk = int(np.floor(1.03 * np.ceil(g.n / k)))
+    bw = np.bincount(part, minlength=k)
+    assert len(bw) == k and bw.max() <= Lk and bw.sum() == g.n
+    assert st.cut == O.cut(g, part)
+
+
+def test_partition_weighted_feasible():
+    g = gg.with_weights(gg.rgg(3000, 8, 5), 9, 20, 5)
+    part, rc, st = O.partition(g, 7, 0.05, 2)
+    cV = int(g.vw().sum())
+    Lk = int(np.floor(1.05 * np.ceil(cV / 7)))
+    assert np.bincount(part, weights=g.vw(), minlength=7).max() <= Lk or rc == -5
+
+
+def test_partition_k1_and_grid_bound():
+    g = gg.grid(16, 32)
+    part, rc, st = O.partition(g, 1, 0.03, 1)
+    assert rc == 0 and not part.any()
+    part, rc, st = O.partition(g, 2, 0.03, 1)
+    assert st.cut >= 16          # optimal bisection of a 16 x 32 grid cuts 16 edges
+    assert st.cut <= 24
+
+
+def test_partition_deterministic():
+    g = gg.rgg(3000, 8, 9)
+    a = O.partition(g, 8, 0.03, 3)[0]
+    b = O.partition(g, 8, 0.03, 3)[0]
+    assert np.array_equal(a, b)
