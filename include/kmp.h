@@ -1,0 +1,211 @@
+/*
+ * kmp.h -- C ABI of the GB300 (sm_103a) deep multilevel graph partitioner.
+ *
+ * Problem (Section 2, "Notation and Definitions"): an undirected graph
+ * G = (V, E, c, w) with positive integer node weights c and edge weights w is
+ * split into k blocks V_1..V_k, every block obeying the balance constraint
+ * c(V_i) <= L, while the cut (total weight of edges between blocks) is
+ * minimised.  The method is deep multilevel graph partitioning (Section 3,
+ * Algorithm 1 and 2) with size-constrained label propagation for coarsening
+ * and refinement (Section 4.1, 4.3), contraction (Section 2) and multilevel
+ * recursive bipartitioning of the blocks (Section 4.2).  Every step runs in
+ * CUDA kernels on one GPU; there is no CPU fallback.
+ *
+ * Graphs are CSR: xadj[n+1] (int64 offsets), adjncy[xadj[n]] (int32 ids),
+ * vwgt[n] and adjwgt[xadj[n]] (int32, > 0; NULL means all ones).  The CSR must
+ * be symmetric with equal weights in both directions and no self-loops.
+ * Limits: n < 2^31, sum of node weights < 2^31, sum of edge weights over
+ * undirected edges < 2^31 (every rating and gain then fits in int32).
+ *
+ * Results are deterministic for fixed (input, k, eps, seed, config) and equal,
+ * bit for bit, to those of the project's CPU oracle.
+ *
+ * Errors: every entry point returns KMP_OK (0) or a negative code; the text of
+ * the last error of the calling thread is available from kmp_last_error().  No
+ * C++ exception crosses this boundary.  Device pointers are plain
+ * cudaMalloc-style global memory pointers on the current device; all work is
+ * issued on the stream set with kmp_set_stream (default: the legacy stream)
+ * and every call returns after that stream has drained, unless noted.
+ */
+#ifndef KMP_H
+#define KMP_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t kmp_vid; /* vertex id */
+typedef int64_t kmp_eid; /* CSR offset */
+typedef int32_t kmp_wgt; /* node / edge weight */
+
+#define KMP_OK 0
+#define KMP_ERR_ARG -1         /* invalid argument or CSR */
+#define KMP_ERR_NOMEM -2       /* device or host allocation failed */
+#define KMP_ERR_CUDA -3        /* a CUDA call or kernel failed */
+#define KMP_ERR_TIMEOUT -4     /* a bounded device wait expired */
+#define KMP_ERR_INFEASIBLE -5  /* result violates L_k (result still written) */
+#define KMP_ERR_UNSUPPORTED -6 /* input beyond a documented limit */
+
+/*
+ * Parameters of the method.  Values the paper gives: lp_rounds = 5 and
+ * refine_rounds = 5 (Section 4.1, 4.3).  The others are readings of passages
+ * the paper leaves open (C is not given; "the same value used in KaHIP" for
+ * the bipartitioner's cluster cap; the number of portfolio repetitions; FM
+ * details); kmp_config_default documents the defaults.
+ */
+typedef struct {
+  int32_t C;             /* coarsening stops at <= 2C nodes; k_i = ceil2(n_i/C) (default 160) */
+  int32_t lp_rounds;     /* coarsening LP rounds (5) */
+  int32_t refine_rounds; /* refinement LP rounds (5) */
+  int32_t subrounds;     /* S deterministic sub-rounds per LP round, power of two (8) */
+  int32_t two_hop;       /* two-hop clustering on/off (1) */
+  int32_t conv_num;      /* coarsening converged when conv_den*n' > conv_num*n (19) */
+  int32_t conv_den;      /* (20) */
+  int32_t ip_C;          /* bipartitioner cluster cap floor(c(B)/ip_C) (16) */
+  int32_t ip_lp_rounds;  /* LP rounds per bipartitioner level (5) */
+  int32_t rep_random;    /* portfolio repetitions: random (4) */
+  int32_t rep_bfs;       /* BFS (4) */
+  int32_t rep_ggg;       /* greedy graph growing (8) */
+  int32_t fm_passes;     /* 2-way FM passes per level (8) */
+  int32_t fm_stop;       /* fruitless FM moves that end a pass (64) */
+} kmp_config;
+
+/* Per-call measurements of kmp_partition / kmp_partition_graph (CUDA events). */
+typedef struct {
+  int32_t levels;            /* graphs in the hierarchy, input included */
+  int32_t level_n[64];
+  int64_t level_m[64];       /* directed CSR entries per level */
+  int64_t lp_scanned;        /* directed entries rated by coarsening LP (all rounds) */
+  int64_t refine_scanned;    /* same for refinement LP */
+  int64_t lp_rounds_run;     /* coarsening LP rounds executed, all levels */
+  int64_t cut;
+  int32_t feasible;
+  int32_t ip_items;          /* bipartitioner work items */
+  float ms_lp;               /* coarsening LP (rating + commit) */
+  float ms_cluster_other;    /* isolated packing + two-hop */
+  float ms_contract;
+  float ms_ip;               /* batched initial bipartitioning incl. extraction */
+  float ms_balance;
+  float ms_refine;
+  float ms_project;
+  float ms_total;            /* whole call on the device stream */
+  float ms_lp_level0;        /* coarsening LP of the input level alone */
+  int64_t lp_scanned_level0; /* entries rated there */
+  int32_t lp_rounds_level0;
+  int32_t gpu_launches;      /* kernels launched by the call */
+} kmp_stats;
+
+/* opaque handle to a CSR graph resident in device memory */
+typedef struct kmp_graph kmp_graph;
+
+void kmp_config_default(kmp_config *cfg);
+/* process-wide configuration used by all later calls; KMP_ERR_ARG if invalid */
+int kmp_set_config(const kmp_config *cfg);
+int kmp_get_config(kmp_config *cfg);
+/* stream (cudaStream_t) used by later calls of this thread's process */
+int kmp_set_stream(void *stream);
+/* message of the last failed call on this thread ("" if none) */
+const char *kmp_last_error(void);
+
+/*
+ * Create a device graph.  is_device = 0: the arrays are host memory and are
+ * copied; 1: they are device memory and are copied device-to-device.  The
+ * library owns the copy; free with kmp_graph_free.  vwgt/adjwgt may be NULL
+ * (unit weights).  Validates offsets and ranges (KMP_ERR_ARG); symmetry is
+ * the caller's contract.
+ */
+int kmp_graph_create(kmp_vid n, const kmp_eid *xadj, const kmp_vid *adjncy,
+                     const kmp_wgt *vwgt, const kmp_wgt *adjwgt, int is_device,
+                     kmp_graph **out);
+int kmp_graph_free(kmp_graph *g);
+/* device pointers of a graph (vwgt/adjwgt NULL when unit) */
+int kmp_graph_get(const kmp_graph *g, kmp_vid *n, kmp_eid *m_directed, const kmp_eid **xadj,
+                  const kmp_vid **adjncy, const kmp_wgt **vwgt, const kmp_wgt **adjwgt);
+
+/* copy a device graph to host arrays (xadj[n+1], adjncy[m], vwgt[n],
+ * adjwgt[m]; any may be NULL to skip; unit weights are written as ones) */
+int kmp_graph_copy_to_host(const kmp_graph *g, kmp_eid *xadj, kmp_vid *adjncy, kmp_wgt *vwgt,
+                           kmp_wgt *adjwgt);
+
+/*
+ * One level of coarsening (Section 4.1): size-constrained label propagation
+ * with cluster cap U = max_cluster_weight for `rounds` rounds in S
+ * deterministic sub-rounds, packing of isolated nodes, and two-hop clustering
+ * when fewer than half of the nodes were clustered away (config.two_hop).
+ * label_out: device int32[n], cluster id of each node (a node id).
+ * fav_out: device int32[n] or NULL, favoured cluster (-1 if none).
+ * Random choices depend on (seed, level).  KMP_ERR_ARG if U < max c(v).
+ */
+int kmp_coarsen_level(const kmp_graph *g, int64_t max_cluster_weight, int32_t rounds,
+                      uint64_t seed, int32_t level, kmp_vid *label_out, kmp_vid *fav_out);
+
+/*
+ * Contraction (Section 2, "Multilevel Graph Partitioning"): every cluster of
+ * `label` (device int32[n]) becomes one coarse node of summed weight; parallel
+ * edges are summed, edges inside a cluster vanish.  Coarse ids follow
+ * ascending label; coarse rows are sorted by neighbour id.  *coarse_out is
+ * allocated by the library (free with kmp_graph_free); map_out: device
+ * int32[n], coarse id of each node.
+ */
+int kmp_contract(const kmp_graph *g, const kmp_vid *label, kmp_graph **coarse_out,
+                 kmp_vid *map_out);
+
+/*
+ * LP refinement (Section 4.3, "Local Improvement"): label propagation over
+ * the k blocks of part_inout (device int32[n], values in [0,k)) that never
+ * lets a block exceed max_block_weight[b] (host int64[k]).  `rounds` rounds,
+ * early stop when nothing moved.  cut_out (host, nullable) receives the cut.
+ */
+int kmp_refine(const kmp_graph *g, int32_t k, const int64_t *max_block_weight, int32_t rounds,
+               uint64_t seed, kmp_vid *part_inout, int64_t *cut_out);
+
+/*
+ * k-way balancing (Section 4.3, "Balancing"): moves nodes out of every block
+ * heavier than max_block_weight[b] (host int64[k]) by relative gain until it
+ * fits or no node can move.  moved_out (host, nullable): nodes moved.
+ */
+int kmp_balance(const kmp_graph *g, int32_t k, const int64_t *max_block_weight,
+                kmp_vid *part_inout, int64_t *moved_out);
+
+/* projection (Algorithm 1): part_fine[v] = part_coarse[map[v]], device arrays */
+int kmp_project(kmp_vid n_fine, const kmp_vid *map, const kmp_vid *part_coarse,
+                kmp_vid *part_fine);
+
+/* cut and block weights of a partition (Section 2); block_weights_out host int64[k] or NULL */
+int kmp_cut(const kmp_graph *g, const kmp_vid *part, int32_t k, int64_t *cut_out,
+            int64_t *block_weights_out);
+
+/*
+ * One round of Algorithm 2 (bipartitionBlocks): every block b of part_inout
+ * (device int32[n], nblocks blocks) with final count f[b] >= 2 (host int32)
+ * is split by the multilevel bipartitioner of Section 4.2, all blocks in one
+ * batched launch; blocks are renumbered in ascending order, child 0 first.
+ * f_out (host int32[2*nblocks]) and *nblocks_out receive the new counts.
+ * eps, total weight cV and final k define the adaptive imbalance; roundkey
+ * selects the random choices.
+ */
+int kmp_bipartition_blocks(const kmp_graph *g, int32_t nblocks, const int32_t *f, double eps,
+                           int64_t cV, int32_t k, uint64_t roundkey, kmp_vid *part_inout,
+                           int32_t *nblocks_out, int32_t *f_out);
+
+/*
+ * Full deep multilevel partition (Algorithm 1) of a host CSR into k blocks
+ * with imbalance eps.  part_out: host int32[n].  Returns KMP_ERR_INFEASIBLE
+ * (result still written) when a block exceeds L_k = floor((1+eps) ceil(c(V)/k)).
+ */
+int kmp_partition(kmp_vid n, const kmp_eid *xadj, const kmp_vid *adjncy, const kmp_wgt *vwgt,
+                  const kmp_wgt *adjwgt, int32_t k, double eps, uint64_t seed,
+                  kmp_vid *part_out);
+
+/* same on a device graph; part_out is device int32[n]; stats (host) nullable */
+int kmp_partition_graph(const kmp_graph *g, int32_t k, double eps, uint64_t seed,
+                        kmp_vid *part_out, kmp_stats *stats);
+
+/* stats of the last kmp_partition / kmp_partition_graph call of this thread */
+int kmp_last_stats(kmp_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,394 @@
+// Contraction (Section 2, "Multilevel Graph Partitioning"): each cluster
+// becomes one coarse node whose weight is the sum of its members' weights;
+// the coarse edge between two clusters carries the summed weight of the fine
+// edges between them; edges inside a cluster vanish.
+//
+// GPU layout: coarse ids = exclusive scan of "label used" flags (ascending
+// label); members grouped by a counting sort; every coarse node aggregates
+// the (coarse neighbour, weight) pairs of all member edges in a hash table
+// (a warp with a shared-memory table when the members' total degree is
+// <= 512, a CTA with a global-memory table above), sorts them by neighbour id
+// with a bitonic network and writes them to a temporary row; a prefix sum of
+// the row lengths then places the rows into the final CSR.
+// Also: projection (Algorithm 1), cut and block weights (Section 2), and the
+// per-graph facts the other kernels need (max degree, isolated nodes, weights).
+#include "kmp_internal.cuh"
+
+namespace kmp {
+
+constexpr int CW_UB = 512;            // warp path: members' total degree <= CW_UB
+constexpr int CW_TAB = 2 * CW_UB;     // per-warp table entries
+constexpr int CW_WARPS = 4;           // warps per block in the warp path
+
+__global__ void k_map_used(int32_t n, const int32_t *label, uint8_t *used) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    used[label[v]] = 1;
+}
+
+__global__ void k_map(int32_t n, const int32_t *label, const int32_t *cid, int32_t *map) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    map[v] = cid[label[v]];
+}
+
+__global__ void k_contract_prep(int32_t n, const int64_t *xadj, const int32_t *vw,
+                                const int32_t *map, int32_t *cvw, int32_t *csize,
+                                unsigned long long *cub) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t x = map[v];
+    atomicAdd(&cvw[x], vw ? vw[v] : 1);
+    atomicAdd(&csize[x], 1);
+    atomicAdd(&cub[x], (unsigned long long)(xadj[v + 1] - xadj[v]));
+  }
+}
+
+__global__ void k_members(int32_t n, const int32_t *map, const int32_t *moff, int32_t *mcur,
+                          int32_t *members) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t x = map[v];
+    members[moff[x] + atomicAdd(&mcur[x], 1)] = (int32_t)v;
+  }
+}
+
+// split coarse nodes into the warp path and the block path
+__global__ void k_split_ub(int32_t nc, const unsigned long long *cub, int32_t *small_list,
+                           int32_t *nsmall, int32_t *large_list, int32_t *nlarge,
+                           unsigned long long *maxub) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nc;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long ub = cub[x];
+    if (ub <= (unsigned long long)CW_UB) {
+      small_list[atomicAdd(nsmall, 1)] = (int32_t)x;
+    } else {
+      large_list[atomicAdd(nlarge, 1)] = (int32_t)x;
+      atomicMax(maxub, ub);
+    }
+  }
+}
+
+__global__ void k_ub_to_i64(int32_t nc, const unsigned long long *cub, int64_t *ub64) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nc;
+       x += (int64_t)gridDim.x * blockDim.x)
+    ub64[x] = (int64_t)cub[x];
+}
+
+// bitonic sort (ascending) of P = power-of-two entries by `nt` cooperating
+// threads with index t; sync() separates the steps
+template <bool BLOCK>
+__device__ __forceinline__ void bitonic(uint64_t *a, uint32_t P, uint32_t t, uint32_t nt) {
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = t; i < P; i += nt) {
+        uint32_t l = i ^ j;
+        if (l > i) {
+          uint64_t x = a[i], y = a[l];
+          bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      if (BLOCK) __syncthreads();
+      else __syncwarp();
+    }
+  }
+}
+
+// warp path: one coarse node per warp
+__global__ void __launch_bounds__(CW_WARPS * 32) k_aggregate_warp(
+    const int32_t *small_list, const int32_t *nsmall_p, const int64_t *xadj, const int32_t *adj,
+    const int32_t *ew, const int32_t *map, const int32_t *members, const int32_t *moff,
+    const int64_t *toff, int32_t *tadj, int32_t *tw, int32_t *cdeg) {
+  __shared__ int32_t keys[CW_WARPS][CW_TAB];
+  __shared__ int32_t vals[CW_WARPS][CW_TAB];
+  __shared__ uint64_t lst[CW_WARPS][CW_UB];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t nsmall = *nsmall_p;
+  int64_t gw = (int64_t)blockIdx.x * CW_WARPS + w, nw = (int64_t)gridDim.x * CW_WARPS;
+  int32_t *K = keys[w], *V = vals[w];
+  uint64_t *L = lst[w];
+  for (int64_t i = gw; i < nsmall; i += nw) {
+    int32_t x = small_list[i];
+    for (int j = lane; j < CW_TAB; j += 32) {
+      K[j] = HT_EMPTY;
+      V[j] = 0;
+    }
+    __syncwarp();
+    for (int32_t mi = moff[x]; mi < moff[x + 1]; ++mi) {
+      int32_t v = members[mi];
+      int64_t b = xadj[v], e = xadj[v + 1];
+      for (int64_t q = b + lane; q < e; q += 32) {
+        int32_t y = map[adj[q]];
+        if (y != x) ht_add(K, V, CW_TAB - 1, y, ew ? ew[q] : 1);
+      }
+    }
+    __syncwarp();
+    // compact the table into L (order arbitrary), then sort by neighbour id
+    int32_t cnt = 0;
+    for (int j0 = 0; j0 < CW_TAB; j0 += 32) {
+      int j = j0 + lane;
+      bool has = K[j] != HT_EMPTY;
+      unsigned b = __ballot_sync(0xFFFFFFFFu, has);
+      if (has) L[cnt + __popc(b & ((1u << lane) - 1u))] = ((uint64_t)(uint32_t)K[j] << 32) | (uint32_t)V[j];
+      cnt += __popc(b);
+    }
+    uint32_t P = 1;
+    while (P < (uint32_t)cnt) P <<= 1;
+    for (uint32_t j = cnt + lane; j < P; j += 32) L[j] = ~0ull;
+    __syncwarp();
+    bitonic<false>(L, P, lane, 32);
+    int64_t o = toff[x];
+    for (int32_t j = lane; j < cnt; j += 32) {
+      tadj[o + j] = (int32_t)(L[j] >> 32);
+      tw[o + j] = (int32_t)(uint32_t)L[j];
+    }
+    if (lane == 0) cdeg[x] = cnt;
+    __syncwarp();
+  }
+}
+
+// block path: one coarse node per block, table and list in global scratch
+__global__ void __launch_bounds__(256) k_aggregate_block(
+    const int32_t *large_list, const int32_t *nlarge_p, const int64_t *xadj, const int32_t *adj,
+    const int32_t *ew, const int32_t *map, const int32_t *members, const int32_t *moff,
+    const int64_t *toff, const unsigned long long *cub, int32_t *gk, int32_t *gv, uint64_t *gl,
+    int64_t tabcap, int32_t *tadj, int32_t *tw, int32_t *cdeg) {
+  __shared__ int32_t cnt;
+  int32_t nlarge = *nlarge_p;
+  int32_t *K = gk + (int64_t)blockIdx.x * tabcap;
+  int32_t *V = gv + (int64_t)blockIdx.x * tabcap;
+  uint64_t *L = gl + (int64_t)blockIdx.x * (tabcap / 2);
+  for (int64_t i = blockIdx.x; i < nlarge; i += gridDim.x) {
+    int32_t x = large_list[i];
+    uint32_t cap = 1;
+    while (cap < 2 * cub[x]) cap <<= 1;
+    uint32_t mask = cap - 1;
+    for (uint32_t j = threadIdx.x; j < cap; j += blockDim.x) {
+      K[j] = HT_EMPTY;
+      V[j] = 0;
+    }
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int32_t mi = moff[x]; mi < moff[x + 1]; ++mi) {
+      int32_t v = members[mi];
+      int64_t b = xadj[v], e = xadj[v + 1];
+      for (int64_t q = b + threadIdx.x; q < e; q += blockDim.x) {
+        int32_t y = map[adj[q]];
+        if (y != x) ht_add(K, V, mask, y, ew ? ew[q] : 1);
+      }
+    }
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < cap; j += blockDim.x)
+      if (K[j] != HT_EMPTY) L[atomicAdd(&cnt, 1)] = ((uint64_t)(uint32_t)K[j] << 32) | (uint32_t)V[j];
+    __syncthreads();
+    int32_t c = cnt;
+    uint32_t P = 1;
+    while (P < (uint32_t)c) P <<= 1;
+    for (uint32_t j = c + threadIdx.x; j < P; j += blockDim.x) L[j] = ~0ull;
+    __syncthreads();
+    bitonic<true>(L, P, threadIdx.x, blockDim.x);
+    int64_t o = toff[x];
+    for (int32_t j = threadIdx.x; j < c; j += blockDim.x) {
+      tadj[o + j] = (int32_t)(L[j] >> 32);
+      tw[o + j] = (int32_t)(uint32_t)L[j];
+    }
+    if (threadIdx.x == 0) cdeg[x] = c;
+    __syncthreads();
+  }
+}
+
+__global__ void k_copy_rows(int32_t nc, const int64_t *toff, const int64_t *cx, const int32_t *tadj,
+                            const int32_t *tw, int32_t *adj, int32_t *ew) {
+  int lane = threadIdx.x & 31;
+  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t x = gw; x < nc; x += nw) {
+    int64_t o = toff[x], d = cx[x + 1] - cx[x], p = cx[x];
+    for (int64_t j = lane; j < d; j += 32) {
+      adj[p + j] = tadj[o + j];
+      ew[p + j] = tw[o + j];
+    }
+  }
+}
+
+__global__ void k_set_last_i64(int64_t *a, int64_t idx, const int64_t *v) { a[idx] = *v; }
+
+// graph facts: max degree, isolated nodes, max and total node weight, total edge weight
+__global__ void k_graph_facts(int32_t n, const int64_t *xadj, const int32_t *vw,
+                              unsigned long long *out /* [maxdeg, iso, maxvw, totvw] */) {
+  unsigned long long md = 0, iso = 0, mw = 0, tw = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long d = (unsigned long long)(xadj[v + 1] - xadj[v]);
+    md = d > md ? d : md;
+    iso += d == 0;
+    unsigned long long w = vw ? (unsigned long long)vw[v] : 1ull;
+    mw = w > mw ? w : mw;
+    tw += w;
+  }
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) {
+    unsigned long long a = __shfl_xor_sync(0xFFFFFFFFu, md, m);
+    md = a > md ? a : md;
+    iso += __shfl_xor_sync(0xFFFFFFFFu, iso, m);
+    unsigned long long b = __shfl_xor_sync(0xFFFFFFFFu, mw, m);
+    mw = b > mw ? b : mw;
+    tw += __shfl_xor_sync(0xFFFFFFFFu, tw, m);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], md);
+    atomicAdd(&out[1], iso);
+    atomicMax(&out[2], mw);
+    atomicAdd(&out[3], tw);
+  }
+}
+
+void compute_facts(Graph &g) {
+  DBuf<unsigned long long> f(4);
+  f.zero();
+  k_graph_facts<<<grid_for(g.n, 256), 256, 0, ctx().stream>>>(g.n, g.xadj, g.vw, f);
+  KMP_LAUNCHED("graph_facts");
+  unsigned long long h[4];
+  to_host(h, f.p, 4);
+  g.maxdeg = (int64_t)h[0];
+  g.n_isolated = (int64_t)h[1];
+  g.max_vw = (int32_t)h[2];
+  g.total_vw = (int64_t)h[3];
+}
+
+void free_graph(Graph &g) {
+  if (g.owned) {
+    dfree(g.xadj);
+    dfree(g.adj);
+    dfree(g.vw);
+    dfree(g.ew);
+  }
+  g = Graph();
+}
+
+Graph contract_graph(const Graph &g, const int32_t *label, int32_t *map) {
+  Context &C = ctx();
+  cudaStream_t s = C.stream;
+  int32_t n = g.n;
+  int grid = grid_for(n, 256);
+  DBuf<uint8_t> used(n);
+  used.zero();
+  DBuf<int32_t> cid(n), ncd(1);
+  k_map_used<<<grid, 256, 0, s>>>(n, label, used);
+  KMP_LAUNCHED("map_used");
+  scan_excl_u8_to_i32(used, cid, n, ncd);
+  k_map<<<grid, 256, 0, s>>>(n, label, cid, map);
+  KMP_LAUNCHED("map");
+  int32_t nc = read1(ncd.p);
+
+  Graph out;
+  out.n = nc;
+  out.owned = true;
+  DBuf<int32_t> cvw(nc), csize(nc + 1), moff(nc + 1), mcur(nc), members(n);
+  DBuf<unsigned long long> cub(nc);
+  cvw.zero();
+  csize.zero();
+  mcur.zero();
+  cub.zero();
+  k_contract_prep<<<grid, 256, 0, s>>>(n, g.xadj, g.vw, map, cvw, csize, cub);
+  KMP_LAUNCHED("contract_prep");
+  scan_excl_i32(csize, moff, nc + 1, nullptr);
+  k_members<<<grid, 256, 0, s>>>(n, map, moff, mcur, members);
+  KMP_LAUNCHED("members");
+  // temporary rows at upper-bound offsets
+  DBuf<int64_t> ub64(nc + 1), toff(nc + 1), ttot(1);
+  int gridc = grid_for(nc, 256);
+  k_ub_to_i64<<<gridc, 256, 0, s>>>(nc, cub, ub64);
+  KMP_LAUNCHED("ub_copy");
+  scan_excl_i64(ub64, toff, nc, ttot);
+  int64_t tot = read1(ttot.p);
+  DBuf<int32_t> tadj(tot), tw(tot), cdeg(nc + 1);
+  DBuf<int32_t> small_list(nc), large_list(nc), counts(2);
+  DBuf<unsigned long long> maxub(1);
+  counts.zero();
+  maxub.zero();
+  k_split_ub<<<gridc, 256, 0, s>>>(nc, cub, small_list, counts.p, large_list, counts.p + 1, maxub);
+  KMP_LAUNCHED("split_ub");
+  int32_t hc[2];
+  to_host(hc, counts.p, 2);
+  if (hc[0] > 0) {
+    k_aggregate_warp<<<grid_for(hc[0], CW_WARPS, 16), CW_WARPS * 32, 0, s>>>(
+        small_list, counts.p, g.xadj, g.adj, g.ew, map, members, moff, toff, tadj, tw, cdeg);
+    KMP_LAUNCHED("aggregate_warp");
+  }
+  if (hc[1] > 0) {
+    unsigned long long mu = read1(maxub.p);
+    int64_t tabcap = next_pow2(2 * mu);
+    int gb = hc[1] < 2 * C.sms ? hc[1] : 2 * C.sms;
+    DBuf<int32_t> gk(tabcap * gb), gv(tabcap * gb);
+    DBuf<uint64_t> gl((tabcap / 2) * gb);
+    k_aggregate_block<<<gb, 256, 0, s>>>(large_list, counts.p + 1, g.xadj, g.adj, g.ew, map,
+                                         members, moff, toff, cub, gk, gv, gl, tabcap, tadj, tw,
+                                         cdeg);
+    KMP_LAUNCHED("aggregate_block");
+  }
+  DBuf<int64_t> mtot(1);
+  out.xadj = static_cast<int64_t *>(dmalloc((nc + 1) * sizeof(int64_t)));
+  scan_excl_i32_to_i64(cdeg, out.xadj, nc, mtot);
+  k_set_last_i64<<<1, 1, 0, s>>>(out.xadj, nc, mtot);
+  KMP_LAUNCHED("set_last");
+  out.m = read1(mtot.p);
+  out.adj = static_cast<int32_t *>(dmalloc((out.m > 0 ? out.m : 1) * sizeof(int32_t)));
+  out.ew = static_cast<int32_t *>(dmalloc((out.m > 0 ? out.m : 1) * sizeof(int32_t)));
+  if (nc > 0) {
+    k_copy_rows<<<grid_for((int64_t)nc * 32, 256), 256, 0, s>>>(nc, toff, out.xadj, tadj, tw,
+                                                                out.adj, out.ew);
+    KMP_LAUNCHED("copy_rows");
+  }
+  out.vw = cvw.release();
+  compute_facts(out);
+  return out;
+}
+
+__global__ void k_project(int32_t n, const int32_t *map, const int32_t *pc, int32_t *pf) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    pf[v] = pc[map[v]];
+}
+
+void project(int32_t n_fine, const int32_t *map, const int32_t *part_c, int32_t *part_f) {
+  k_project<<<grid_for(n_fine, 256), 256, 0, ctx().stream>>>(n_fine, map, part_c, part_f);
+  KMP_LAUNCHED("project");
+}
+
+__global__ void k_cut_bw(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
+                         const int32_t *ew, const int32_t *part, unsigned long long *bw,
+                         unsigned long long *cut) {
+  unsigned long long c = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t p = part[v];
+    atomicAdd(&bw[p], (unsigned long long)(vw ? vw[v] : 1));
+    for (int64_t e = xadj[v]; e < xadj[v + 1]; ++e)
+      if (part[adj[e]] != p) c += (unsigned long long)(ew ? ew[e] : 1);
+  }
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, m);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(cut, c);
+}
+
+__global__ void k_half(int64_t *c) { *c /= 2; }
+
+void cut_and_weights(const Graph &g, const int32_t *part, int32_t k, int64_t *bw_dev,
+                     int64_t *cut_dev) {
+  cudaStream_t s = ctx().stream;
+  KMP_CUDA(cudaMemsetAsync(bw_dev, 0, (size_t)k * sizeof(int64_t), s));
+  KMP_CUDA(cudaMemsetAsync(cut_dev, 0, sizeof(int64_t), s));
+  k_cut_bw<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, g.xadj, g.adj, g.vw, g.ew, part,
+                                               reinterpret_cast<unsigned long long *>(bw_dev),
+                                               reinterpret_cast<unsigned long long *>(cut_dev));
+  KMP_LAUNCHED("cut_bw");
+  k_half<<<1, 1, 0, s>>>(cut_dev);
+  KMP_LAUNCHED("half");
+}
+
+}  // namespace kmp

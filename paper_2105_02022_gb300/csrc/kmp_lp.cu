@@ -1,0 +1,834 @@
+// Size-constrained label propagation on the GPU (Section 2 "Size-Constrained
+// Label Propagation", Section 4.1 coarsening, Section 4.3 refinement).
+//
+// Each round visits the active nodes in S deterministic sub-rounds; a node's
+// sub-round is step(roundkey, u) mod S.  Per sub-round:
+//   rate     : every node of the sub-round sums the edge weight to each
+//              neighbouring cluster (degree-binned: 4..32-lane groups with
+//              shuffles, a warp with a shared-memory hash table, a CTA with a
+//              shared-memory table, a CTA with a global table for very high
+//              degrees), picks the best admissible cluster K with
+//              w(K) + c(u) <= cap(K) by (rating desc, perm32 asc) and proposes
+//              it when it beats the own cluster.
+//   classify : a target whose total proposed weight fits is accepted whole;
+//              otherwise its proposals are bucketed ("contested").
+//   resolve  : per contested target, proposals ordered by (gain desc, u asc)
+//              are accepted while the start weight plus the prefix fits
+//              (warp shuffles for <= 32 proposals, a block radix select above).
+//   apply    : labels and weights are updated, neighbours of moved nodes are
+//              marked active for the next round.
+// The cap holds exactly and the result is independent of scheduling.
+#include <cstdio>
+
+#include "kmp_internal.cuh"
+
+namespace kmp {
+
+constexpr int NB = 7;           // degree bins
+constexpr int BIN_TILE = 2048;  // nodes per binning tile
+constexpr int RATE_T = 256;
+constexpr int WARP_TAB = 512;   // per-warp hash table (bin 4: degree <= 256)
+constexpr int CTA_TAB = 4096;   // per-CTA shared table (bin 5: degree <= 2048)
+constexpr int64_t HUGE_DEG = 2048;
+
+__host__ __device__ __forceinline__ int deg_bin(int64_t d) {
+  if (d <= 4) return 0;
+  if (d <= 8) return 1;
+  if (d <= 16) return 2;
+  if (d <= 32) return 3;
+  if (d <= 256) return 4;
+  if (d <= HUGE_DEG) return 5;
+  return 6;
+}
+
+struct LPArgs {
+  int32_t n;
+  const int64_t *xadj;
+  const int32_t *adj;
+  const int32_t *vw;
+  const int32_t *ew;
+  int32_t *label;
+  int32_t *wt;
+  const int32_t *cap;
+  int32_t U;
+  int32_t *fav;
+  uint8_t *act;
+  uint8_t *act_next;
+  int32_t *vlist;
+  int32_t *boff;  // [S*NB+1]
+  int32_t *prop_t;
+  int32_t *prop_g;
+  uint8_t *acc;
+  int32_t *pos_in_t;
+  int32_t *tsum;
+  int32_t *tcnt;
+  int32_t *tcur;
+  int32_t *tslot;
+  int32_t *slot_t;
+  int32_t *slot_base;
+  int32_t *bucket;
+  int32_t *ctr;                // [0] slots, [1] bucket top
+  unsigned long long *ctr64;   // [0] scanned entries, [1] moved nodes
+  int32_t *gkeys;              // per-block global tables (bin 6)
+  int32_t *gvals;
+  int64_t gcap;                // entries per block
+  int32_t S;
+  uint64_t rk;
+  uint32_t rk_hi;
+};
+
+__device__ __forceinline__ int32_t node_w(const LPArgs &A, int32_t v) { return A.vw ? A.vw[v] : 1; }
+__device__ __forceinline__ int32_t edge_w(const LPArgs &A, int64_t e) { return A.ew ? A.ew[e] : 1; }
+__device__ __forceinline__ int64_t cap_of(const LPArgs &A, int32_t K) {
+  return A.cap ? (int64_t)A.cap[K] : (int64_t)A.U;
+}
+__device__ __forceinline__ uint64_t rate_key(const LPArgs &A, int32_t K, int32_t r) {
+  return ((uint64_t)(uint32_t)r << 32) | (uint64_t)(0xFFFFFFFFu - perm32(A.rk_hi, K));
+}
+
+// final decision for node u given the best constrained / unconstrained keys
+__device__ __forceinline__ void emit(const LPArgs &A, int32_t u, int32_t pos, int32_t r_own,
+                                     uint64_t kc, int32_t lc, uint64_t ku, int32_t lu) {
+  int32_t rc = (int32_t)(kc >> 32);
+  if (kc != 0 && rc > r_own) {
+    A.prop_t[pos] = lc;
+    A.prop_g[pos] = rc - r_own;
+    atomicAdd(&A.tsum[lc], node_w(A, u));
+    atomicAdd(&A.tcnt[lc], 1);
+  } else {
+    A.prop_t[pos] = -1;
+    int32_t ru = (int32_t)(ku >> 32);
+    if (A.fav && ku != 0 && ru > r_own) A.fav[u] = lu;
+  }
+}
+
+// ------------------------------------------------------------------ binning
+__global__ void __launch_bounds__(256) k_bin_count(LPArgs A, int32_t *cnt, int64_t ntiles) {
+  __shared__ int32_t c[8 * NB];
+  __shared__ unsigned long long scanned;
+  for (int i = threadIdx.x; i < A.S * NB; i += blockDim.x) c[i] = 0;
+  if (threadIdx.x == 0) scanned = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * BIN_TILE;
+  unsigned long long my = 0;
+  for (int i = threadIdx.x; i < BIN_TILE; i += blockDim.x) {
+    int64_t v = base + i;
+    if (v >= A.n || !A.act[v]) continue;
+    int64_t d = A.xadj[v + 1] - A.xadj[v];
+    if (d == 0) continue;
+    int s = (int)(key_step(A.rk, (uint64_t)(uint32_t)v) & (uint64_t)(A.S - 1));
+    atomicAdd(&c[s * NB + deg_bin(d)], 1);
+    my += (unsigned long long)d;
+  }
+  atomicAdd(&scanned, my);
+  __syncthreads();
+  for (int i = threadIdx.x; i < A.S * NB; i += blockDim.x) cnt[(int64_t)i * ntiles + blockIdx.x] = c[i];
+  if (threadIdx.x == 0) atomicAdd(&A.ctr64[0], scanned);
+}
+
+__global__ void k_bin_boff(LPArgs A, const int32_t *off, const int32_t *total, int64_t ntiles) {
+  int i = threadIdx.x;
+  if (i < A.S * NB) A.boff[i] = off[(int64_t)i * ntiles];
+  if (i == 0) A.boff[A.S * NB] = *total;
+}
+
+// stable scatter of the active nodes into (sub-round, bin) order; consumes act[]
+__global__ void __launch_bounds__(256) k_bin_scatter(LPArgs A, const int32_t *off, int64_t ntiles) {
+  constexpr int W = 8;
+  __shared__ uint8_t key[BIN_TILE];
+  __shared__ int32_t wcnt[W][8 * NB];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int nk = A.S * NB;
+  for (int i = threadIdx.x; i < W * 8 * NB; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * BIN_TILE;
+  // pass 1: keys and per-warp counts; warp w owns nodes [w*256, w*256+256) of the tile
+  for (int it = 0; it < BIN_TILE / (W * 32); ++it) {
+    int li = w * (BIN_TILE / W) + it * 32 + lane;
+    int64_t v = base + li;
+    int k = 255;
+    if (v < A.n && A.act[v]) {
+      int64_t d = A.xadj[v + 1] - A.xadj[v];
+      if (d > 0) {
+        int s = (int)(key_step(A.rk, (uint64_t)(uint32_t)v) & (uint64_t)(A.S - 1));
+        k = s * NB + deg_bin(d);
+      }
+    }
+    if (v < A.n) A.act[v] = 0;
+    key[li] = (uint8_t)k;
+    unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
+    if (k != 255 && (peers & ((1u << lane) - 1u)) == 0) wcnt[w][k] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  if (threadIdx.x < nk) {
+    int32_t s = 0;
+    for (int ww = 0; ww < W; ++ww) {
+      int32_t c = wcnt[ww][threadIdx.x];
+      wcnt[ww][threadIdx.x] = s;
+      s += c;
+    }
+  }
+  __syncthreads();
+  // pass 2: positions
+  for (int it = 0; it < BIN_TILE / (W * 32); ++it) {
+    int li = w * (BIN_TILE / W) + it * 32 + lane;
+    int k = key[li];
+    unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
+    int rank = __popc(peers & ((1u << lane) - 1u));
+    if (k != 255) {
+      int32_t p = off[(int64_t)k * ntiles + blockIdx.x] + wcnt[w][k] + rank;
+      A.vlist[p] = (int32_t)(base + li);
+    }
+    __syncwarp();
+    if (k != 255 && rank == 0) wcnt[w][k] += __popc(peers);
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------- rating
+// G lanes per node (G in 4, 8, 16, 32), degree <= G: one neighbour per lane.
+template <int G>
+__device__ __forceinline__ void rate_group(const LPArgs &A, int32_t u, int32_t pos, int lane) {
+  int gl = lane & (G - 1);
+  unsigned gmask = (G == 32) ? 0xFFFFFFFFu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  int64_t beg = 0;
+  int32_t deg = 0, own = -1, cu = 0;
+  if (u >= 0) {
+    beg = A.xadj[u];
+    deg = (int32_t)(A.xadj[u + 1] - beg);
+    own = A.label[u];
+    cu = node_w(A, u);
+  }
+  int32_t l = -1, w = 0;
+  if (gl < deg) {
+    l = A.label[A.adj[beg + gl]];
+    w = edge_w(A, beg + gl);
+  }
+  int32_t r = 0, rown = 0;
+#pragma unroll
+  for (int j = 0; j < G; ++j) {
+    int32_t lj = __shfl_sync(0xFFFFFFFFu, l, j, G);
+    int32_t wj = __shfl_sync(0xFFFFFFFFu, w, j, G);
+    r += (lj == l) ? wj : 0;
+    rown += (lj == own) ? wj : 0;
+  }
+  bool valid = l >= 0 && l != own;
+  uint64_t ku = valid ? rate_key(A, l, r) : 0ull;
+  bool adm = valid && ((int64_t)A.wt[l] + cu <= cap_of(A, l));
+  uint64_t kc = adm ? ku : 0ull;
+  uint64_t mc = group_max64<G>(kc), mu = group_max64<G>(ku);
+  unsigned bc = __ballot_sync(0xFFFFFFFFu, mc != 0 && kc == mc) & gmask;
+  unsigned bu = __ballot_sync(0xFFFFFFFFu, mu != 0 && ku == mu) & gmask;
+  int32_t lc = __shfl_sync(0xFFFFFFFFu, l, bc ? __ffs(bc) - 1 : lane);
+  int32_t lu = __shfl_sync(0xFFFFFFFFu, l, bu ? __ffs(bu) - 1 : lane);
+  if (gl == 0 && u >= 0) emit(A, u, pos, rown, mc, lc, mu, lu);
+}
+
+// one node per warp, neighbours aggregated in a shared-memory table of WARP_TAB
+__device__ __forceinline__ void rate_warp(const LPArgs &A, int32_t u, int32_t pos, int lane,
+                                          int32_t *keys, int32_t *vals) {
+#pragma unroll
+  for (int i = lane; i < WARP_TAB; i += 32) {
+    keys[i] = HT_EMPTY;
+    vals[i] = 0;
+  }
+  __syncwarp();
+  int64_t beg = A.xadj[u];
+  int32_t deg = (int32_t)(A.xadj[u + 1] - beg);
+  int32_t own = A.label[u], cu = node_w(A, u);
+  for (int32_t e = lane; e < deg; e += 32)
+    ht_add(keys, vals, WARP_TAB - 1, A.label[A.adj[beg + e]], edge_w(A, beg + e));
+  __syncwarp();
+  int32_t rown = ht_get(keys, vals, WARP_TAB - 1, own);
+  uint64_t kc = 0, ku = 0;
+  int32_t lc = -1, lu = -1;
+  for (int i = lane; i < WARP_TAB; i += 32) {
+    int32_t K = keys[i];
+    if (K == HT_EMPTY || K == own) continue;
+    uint64_t k = rate_key(A, K, vals[i]);
+    if (k > ku) { ku = k; lu = K; }
+    if ((int64_t)A.wt[K] + cu <= cap_of(A, K) && k > kc) { kc = k; lc = K; }
+  }
+  uint64_t mc = group_max64<32>(kc), mu = group_max64<32>(ku);
+  unsigned bc = __ballot_sync(0xFFFFFFFFu, mc != 0 && kc == mc);
+  unsigned bu = __ballot_sync(0xFFFFFFFFu, mu != 0 && ku == mu);
+  lc = __shfl_sync(0xFFFFFFFFu, lc, bc ? __ffs(bc) - 1 : 0);
+  lu = __shfl_sync(0xFFFFFFFFu, lu, bu ? __ffs(bu) - 1 : 0);
+  if (lane == 0) emit(A, u, pos, rown, mc, lc, mu, lu);
+  __syncwarp();
+}
+
+// one node per CTA with a table of `mask+1` entries (shared or global memory)
+__device__ void rate_cta(const LPArgs &A, int32_t u, int32_t pos, int32_t *keys, int32_t *vals,
+                         uint32_t mask) {
+  __shared__ uint64_t red_c[RATE_T / 32], red_u[RATE_T / 32];
+  __shared__ int32_t lab_c, lab_u;
+  for (uint32_t i = threadIdx.x; i <= mask; i += blockDim.x) {
+    keys[i] = HT_EMPTY;
+    vals[i] = 0;
+  }
+  if (threadIdx.x == 0) { lab_c = -1; lab_u = -1; }
+  __syncthreads();
+  int64_t beg = A.xadj[u];
+  int64_t deg = A.xadj[u + 1] - beg;
+  int32_t own = A.label[u], cu = node_w(A, u);
+  for (int64_t e = threadIdx.x; e < deg; e += blockDim.x)
+    ht_add(keys, vals, mask, A.label[A.adj[beg + e]], edge_w(A, beg + e));
+  __syncthreads();
+  int32_t rown = ht_get(keys, vals, mask, own);
+  uint64_t kc = 0, ku = 0;
+  int32_t lc = -1, lu = -1;
+  for (uint32_t i = threadIdx.x; i <= mask; i += blockDim.x) {
+    int32_t K = keys[i];
+    if (K == HT_EMPTY || K == own) continue;
+    uint64_t k = rate_key(A, K, vals[i]);
+    if (k > ku) { ku = k; lu = K; }
+    if ((int64_t)A.wt[K] + cu <= cap_of(A, K) && k > kc) { kc = k; lc = K; }
+  }
+  uint64_t wc = group_max64<32>(kc), wu = group_max64<32>(ku);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) { red_c[w] = wc; red_u[w] = wu; }
+  __syncthreads();
+  uint64_t mc = 0, mu = 0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+    mc = red_c[i] > mc ? red_c[i] : mc;
+    mu = red_u[i] > mu ? red_u[i] : mu;
+  }
+  if (mc != 0 && kc == mc) lab_c = lc;  // unique label per key: benign identical writes
+  if (mu != 0 && ku == mu) lab_u = lu;
+  __syncthreads();
+  if (threadIdx.x == 0) emit(A, u, pos, rown, mc, lab_c, mu, lab_u);
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(RATE_T) k_rate(LPArgs A, int s) {
+  __shared__ int32_t tkeys[CTA_TAB];
+  __shared__ int32_t tvals[CTA_TAB];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    A.ctr[0] = 0;
+    A.ctr[1] = 0;
+  }
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t gw = (int64_t)blockIdx.x * (RATE_T / 32) + w;
+  int64_t nw = (int64_t)gridDim.x * (RATE_T / 32);
+  const int32_t *bo = A.boff + s * NB;
+#define KMP_GROUP_BIN(BIN, G)                                                  \
+  {                                                                            \
+    int32_t lo = bo[BIN], hi = bo[BIN + 1];                                    \
+    constexpr int per = 32 / G;                                                \
+    for (int64_t b0 = lo + gw * per; b0 < hi; b0 += nw * per) {               \
+      int64_t idx = b0 + lane / G;                                             \
+      int32_t u = idx < hi ? A.vlist[idx] : -1;                                \
+      rate_group<G>(A, u, (int32_t)idx, lane);                                 \
+    }                                                                          \
+  }
+  KMP_GROUP_BIN(0, 4)
+  KMP_GROUP_BIN(1, 8)
+  KMP_GROUP_BIN(2, 16)
+  KMP_GROUP_BIN(3, 32)
+#undef KMP_GROUP_BIN
+  {
+    int32_t lo = bo[4], hi = bo[5];
+    for (int64_t idx = lo + gw; idx < hi; idx += nw)
+      rate_warp(A, A.vlist[idx], (int32_t)idx, lane, tkeys + w * WARP_TAB, tvals + w * WARP_TAB);
+  }
+  __syncthreads();
+  {
+    int32_t lo = bo[5], hi = bo[6];
+    for (int64_t idx = lo + blockIdx.x; idx < hi; idx += gridDim.x)
+      rate_cta(A, A.vlist[idx], (int32_t)idx, tkeys, tvals, CTA_TAB - 1);
+  }
+}
+
+__global__ void __launch_bounds__(RATE_T) k_rate_huge(LPArgs A, int s) {
+  const int32_t *bo = A.boff + s * NB;
+  int32_t lo = bo[6], hi = bo[7];
+  int32_t *keys = A.gkeys + (int64_t)blockIdx.x * A.gcap;
+  int32_t *vals = A.gvals + (int64_t)blockIdx.x * A.gcap;
+  for (int64_t idx = lo + blockIdx.x; idx < hi; idx += gridDim.x) {
+    int32_t u = A.vlist[idx];
+    int64_t deg = A.xadj[u + 1] - A.xadj[u];
+    uint32_t cap = next_pow2_dev(2 * deg);
+    rate_cta(A, u, (int32_t)idx, keys, vals, cap - 1);
+  }
+}
+
+// ------------------------------------------------------------------- commit
+__global__ void __launch_bounds__(256) k_classify(LPArgs A, int s) {
+  int32_t lo = A.boff[s * NB], hi = A.boff[(s + 1) * NB];
+  for (int64_t pos = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pos < hi;
+       pos += (int64_t)gridDim.x * blockDim.x) {
+    int32_t T = A.prop_t[pos];
+    if (T < 0) continue;
+    if ((int64_t)A.wt[T] + A.tsum[T] <= cap_of(A, T)) {
+      A.acc[pos] = 1;
+    } else {
+      A.acc[pos] = 0;
+      int32_t r = atomicAdd(&A.tcur[T], 1);
+      A.pos_in_t[pos] = r;
+      if (r == 0) {
+        int32_t sl = atomicAdd(&A.ctr[0], 1);
+        A.slot_t[sl] = T;
+        A.slot_base[sl] = atomicAdd(&A.ctr[1], A.tcnt[T]);
+        A.tslot[T] = sl;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_bucket(LPArgs A, int s) {
+  if (A.ctr[0] == 0) return;
+  int32_t lo = A.boff[s * NB], hi = A.boff[(s + 1) * NB];
+  for (int64_t pos = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pos < hi;
+       pos += (int64_t)gridDim.x * blockDim.x) {
+    int32_t T = A.prop_t[pos];
+    if (T < 0 || A.acc[pos]) continue;
+    int32_t sl = A.tslot[T];
+    A.bucket[A.slot_base[sl] + A.pos_in_t[pos]] = (int32_t)pos;
+  }
+}
+
+__device__ __forceinline__ uint64_t commit_key(const LPArgs &A, int32_t pos) {
+  return ((uint64_t)(uint32_t)(0x7FFFFFFF - A.prop_g[pos]) << 32) | (uint32_t)A.vlist[pos];
+}
+
+__global__ void __launch_bounds__(256) k_resolve(LPArgs A) {
+  int32_t nslots = A.ctr[0];
+  if (nslots == 0) return;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t gw = (int64_t)blockIdx.x * (blockDim.x / 32) + w;
+  int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+  // small contested targets: one warp each
+  for (int64_t sl = gw; sl < nslots; sl += nw) {
+    int32_t T = A.slot_t[sl];
+    int32_t cnt = A.tcnt[T];
+    if (cnt > 32) continue;
+    int32_t base = A.slot_base[sl];
+    uint64_t key = ~0ull;
+    int32_t c = 0, pos = -1;
+    if (lane < cnt) {
+      pos = A.bucket[base + lane];
+      key = commit_key(A, pos);
+      c = node_w(A, A.vlist[pos]);
+    }
+    int64_t pre = 0;
+    for (int j = 0; j < 32; ++j) {
+      uint64_t kj = __shfl_sync(0xFFFFFFFFu, key, j);
+      int32_t cj = __shfl_sync(0xFFFFFFFFu, c, j);
+      if (j < cnt && kj <= key) pre += cj;
+    }
+    int64_t R = cap_of(A, T) - A.wt[T];
+    if (lane < cnt) A.acc[pos] = (pre <= R) ? 1 : 0;
+  }
+  // large contested targets: one block each, radix select of the accepted prefix
+  __shared__ unsigned long long hist[256];
+  __shared__ uint64_t prefix;
+  __shared__ long long accw;
+  for (int64_t sl = blockIdx.x; sl < nslots; sl += gridDim.x) {
+    int32_t T = A.slot_t[sl];
+    int32_t cnt = A.tcnt[T];
+    if (cnt <= 32) continue;
+    int32_t base = A.slot_base[sl];
+    int64_t R = cap_of(A, T) - A.wt[T];
+    if (R < 0) continue;  // nothing fits (acc already 0)
+    if (threadIdx.x == 0) { prefix = 0; accw = 0; }
+    __syncthreads();
+    for (int p = 0; p < 8; ++p) {
+      int sh = 56 - 8 * p;
+      for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+      __syncthreads();
+      uint64_t pf = prefix;
+      for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        int32_t ps = A.bucket[base + i];
+        uint64_t k = commit_key(A, ps);
+        if (p == 0 || (k >> (sh + 8)) == pf)
+          atomicAdd(&hist[(k >> sh) & 255u], (unsigned long long)node_w(A, A.vlist[ps]));
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        long long run = accw;
+        int dstar = 255;
+        for (int d = 0; d < 256; ++d) {
+          if (run + (long long)hist[d] <= R) {
+            run += (long long)hist[d];
+          } else {
+            dstar = d;
+            break;
+          }
+        }
+        accw = run;
+        prefix = (pf << 8) | (uint64_t)dstar;
+      }
+      __syncthreads();
+    }
+    uint64_t thr = prefix;  // key of the first rejected proposal
+    for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+      int32_t ps = A.bucket[base + i];
+      A.acc[ps] = commit_key(A, ps) < thr ? 1 : 0;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_apply(LPArgs A, int s) {
+  int32_t lo = A.boff[s * NB], hi = A.boff[(s + 1) * NB];
+  unsigned long long moved = 0;
+  for (int64_t pos = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pos < hi;
+       pos += (int64_t)gridDim.x * blockDim.x) {
+    int32_t T = A.prop_t[pos];
+    if (T < 0) continue;
+    int32_t u = A.vlist[pos];
+    if (A.acc[pos]) {
+      int32_t own = A.label[u], c = node_w(A, u);
+      A.label[u] = T;
+      atomicAdd(&A.wt[T], c);
+      atomicSub(&A.wt[own], c);
+      ++moved;
+      for (int64_t e = A.xadj[u]; e < A.xadj[u + 1]; ++e) A.act_next[A.adj[e]] = 1;
+    } else if (A.fav) {
+      A.fav[u] = T;
+    }
+    A.tsum[T] = 0;
+    A.tcnt[T] = 0;
+    A.tcur[T] = 0;
+  }
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) moved += __shfl_xor_sync(0xFFFFFFFFu, moved, m);
+  if ((threadIdx.x & 31) == 0 && moved) atomicAdd(&A.ctr64[1], moved);
+}
+
+__global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+// ------------------------------------------------------------------- driver
+void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int32_t *cap,
+            int32_t U, int32_t rounds, uint64_t basekey, int32_t *fav, LPStats *st) {
+  Context &C = ctx();
+  const int S = C.cfg.subrounds;
+  cudaStream_t stream = C.stream;
+  int32_t n = g.n;
+  LPStats local;
+  if (!st) st = &local;
+  *st = LPStats();
+  if (n == 0 || rounds <= 0) return;
+  cudaEvent_t e0, e1;
+  KMP_CUDA(cudaEventCreate(&e0));
+  KMP_CUDA(cudaEventCreate(&e1));
+  KMP_CUDA(cudaEventRecord(e0, stream));
+
+  int64_t ntiles = ceil_div(n, BIN_TILE);
+  DBuf<uint8_t> act(n), act_next(n), acc(n);
+  DBuf<int32_t> vlist(n), boff(S * NB + 1), prop_t(n), prop_g(n), pos_in_t(n);
+  DBuf<int32_t> tsum(nlab), tcnt(nlab), tcur(nlab), tslot(nlab);
+  DBuf<int32_t> slot_t(n), slot_base(n), bucket(n), ctr(8);
+  DBuf<unsigned long long> ctr64(4);
+  DBuf<int32_t> bcnt(S * NB * ntiles), boffs(S * NB * ntiles), btotal(1);
+  act.fill_bytes(1);
+  act_next.zero();
+  tsum.zero();
+  tcnt.zero();
+  tcur.zero();
+  ctr.zero();
+
+  int huge_grid = 0;
+  DBuf<int32_t> gkeys, gvals;
+  int64_t gcap = 0;
+  if (g.maxdeg > HUGE_DEG) {
+    gcap = next_pow2(2 * (uint64_t)g.maxdeg);
+    huge_grid = 2 * C.sms;
+    gkeys.alloc(gcap * huge_grid);
+    gvals.alloc(gcap * huge_grid);
+  }
+
+  LPArgs A;
+  A.n = n;
+  A.xadj = g.xadj;
+  A.adj = g.adj;
+  A.vw = g.vw;
+  A.ew = g.ew;
+  A.label = label;
+  A.wt = wt;
+  A.cap = cap;
+  A.U = U;
+  A.fav = fav;
+  A.act = act;
+  A.act_next = act_next;
+  A.vlist = vlist;
+  A.boff = boff;
+  A.prop_t = prop_t;
+  A.prop_g = prop_g;
+  A.acc = acc;
+  A.pos_in_t = pos_in_t;
+  A.tsum = tsum;
+  A.tcnt = tcnt;
+  A.tcur = tcur;
+  A.tslot = tslot;
+  A.slot_t = slot_t;
+  A.slot_base = slot_base;
+  A.bucket = bucket;
+  A.ctr = ctr;
+  A.ctr64 = ctr64;
+  A.gkeys = gkeys.p;
+  A.gvals = gvals.p;
+  A.gcap = gcap;
+  A.S = S;
+
+  int grid_rate = 4 * C.sms;
+  int grid_commit = grid_for(ceil_div(n, S), 256, 8);
+  unsigned long long h64[4];
+  for (int r = 0; r < rounds; ++r) {
+    A.rk = key_step(basekey, (uint64_t)r);
+    A.rk_hi = (uint32_t)(A.rk >> 32);
+    ctr64.zero();
+    k_bin_count<<<(unsigned)ntiles, 256, 0, stream>>>(A, bcnt, ntiles);
+    KMP_LAUNCHED("bin_count");
+    scan_excl_i32(bcnt, boffs, (int64_t)S * NB * ntiles, btotal);
+    k_bin_boff<<<1, 64, 0, stream>>>(A, boffs, btotal, ntiles);
+    KMP_LAUNCHED("bin_boff");
+    k_bin_scatter<<<(unsigned)ntiles, 256, 0, stream>>>(A, boffs, ntiles);
+    KMP_LAUNCHED("bin_scatter");
+    for (int s = 0; s < S; ++s) {
+      k_rate<<<grid_rate, RATE_T, 0, stream>>>(A, s);
+      KMP_LAUNCHED("rate");
+      if (huge_grid) {
+        k_rate_huge<<<huge_grid, RATE_T, 0, stream>>>(A, s);
+        KMP_LAUNCHED("rate_huge");
+      }
+      k_classify<<<grid_commit, 256, 0, stream>>>(A, s);
+      KMP_LAUNCHED("classify");
+      k_bucket<<<grid_commit, 256, 0, stream>>>(A, s);
+      KMP_LAUNCHED("bucket");
+      k_resolve<<<grid_commit, 256, 0, stream>>>(A);
+      KMP_LAUNCHED("resolve");
+      k_apply<<<grid_commit, 256, 0, stream>>>(A, s);
+      KMP_LAUNCHED("apply");
+    }
+    to_host(h64, ctr64.p, 2);
+    st->rounds = r + 1;
+    st->scanned += (int64_t)h64[0];
+    st->moved_total += (int64_t)h64[1];
+    uint8_t *t = A.act;
+    A.act = A.act_next;
+    A.act_next = t;
+    if (h64[1] == 0) break;
+  }
+  KMP_CUDA(cudaEventRecord(e1, stream));
+  KMP_CUDA(cudaEventSynchronize(e1));
+  float ms = 0;
+  KMP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  st->ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
+// ------------------------------------------------ clustering of one level
+__global__ void k_init_cluster(int32_t n, const int32_t *vw, int32_t *label, int32_t *wt,
+                               int32_t *fav) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    label[v] = (int32_t)v;
+    wt[v] = vw ? vw[v] : 1;
+    fav[v] = -1;
+  }
+}
+
+__global__ void k_iso_w(int32_t n, const int64_t *xadj, const int32_t *vw, int32_t *w) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    w[v] = (xadj[v + 1] == xadj[v]) ? (vw ? vw[v] : 1) : 0;
+}
+
+// isolated node v with exclusive prefix weight P joins chunk floor(P/U) unless it straddles
+__global__ void k_iso_chunk(int32_t n, const int64_t *xadj, const int32_t *vw, const int64_t *P,
+                            int32_t U, int32_t *first, int pass, int32_t *label) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    if (xadj[v + 1] != xadj[v]) continue;
+    int64_t c = vw ? vw[v] : 1;
+    int64_t q = P[v] / U, qe = (P[v] + c - 1) / U;
+    if (q != qe) continue;
+    if (pass == 0) atomicMin(&first[q], label[v]);
+    else label[v] = first[q];
+  }
+}
+
+__global__ void k_mark_used(int32_t n, const int32_t *label, uint8_t *used) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    used[label[v]] = 1;
+}
+
+__global__ void k_count_u8(int64_t n, const uint8_t *f, unsigned long long *out) {
+  unsigned long long s = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += f[i];
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, m);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+static int32_t count_clusters(int32_t n, const int32_t *label) {
+  cudaStream_t s = ctx().stream;
+  DBuf<uint8_t> used(n);
+  used.zero();
+  DBuf<unsigned long long> cnt(1);
+  cnt.zero();
+  int grid = grid_for(n, 256);
+  k_mark_used<<<grid, 256, 0, s>>>(n, label, used);
+  KMP_LAUNCHED("mark_used");
+  k_count_u8<<<grid, 256, 0, s>>>(n, used, cnt);
+  KMP_LAUNCHED("count_u8");
+  return (int32_t)read1(cnt.p);
+}
+
+// two-hop: candidates are singleton clusters with a favoured cluster
+__global__ void k_cluster_size(int32_t n, const int32_t *label, int32_t *size) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&size[label[v]], 1);
+}
+
+__global__ void k_twohop_cand(int32_t n, const int32_t *label, const int32_t *size,
+                              const int32_t *fav, int bits, uint64_t *keys, int32_t *count) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    if (size[label[u]] != 1 || fav[u] < 0) continue;
+    int32_t p = atomicAdd(count, 1);
+    keys[p] = ((uint64_t)(uint32_t)fav[u] << bits) | (uint64_t)u;
+  }
+}
+
+__global__ void k_twohop_heads(int32_t N, const uint64_t *keys, int bits, uint8_t *head) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    head[i] = (i == 0 || (keys[i] >> bits) != (keys[i - 1] >> bits)) ? 1 : 0;
+}
+
+__global__ void k_twohop_headpos(int32_t N, const uint8_t *head, const int32_t *hidx, int32_t *H) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (head[i]) H[hidx[i]] = (int32_t)i;
+}
+
+__global__ void k_twohop_valid(int32_t N, const uint64_t *keys, int bits, const int32_t *H,
+                               int32_t nh, const int32_t *vw, int32_t U, uint8_t *valid) {
+  uint64_t mask = (bits >= 64) ? ~0ull : ((1ull << bits) - 1ull);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    // group start: largest head position <= i
+    int32_t lo = 0, hi = nh - 1;
+    while (lo < hi) {
+      int32_t mid = (lo + hi + 1) >> 1;
+      if (H[mid] <= i) lo = mid;
+      else hi = mid - 1;
+    }
+    int64_t off = i - H[lo];
+    uint8_t ok = 0;
+    if ((off & 1) == 0 && i + 1 < N && (keys[i] >> bits) == (keys[i + 1] >> bits)) {
+      int32_t a = (int32_t)(keys[i] & mask), b = (int32_t)(keys[i + 1] & mask);
+      int64_t w = (int64_t)(vw ? vw[a] : 1) + (vw ? vw[b] : 1);
+      ok = w <= U ? 1 : 0;
+    }
+    valid[i] = ok;
+  }
+}
+
+__global__ void k_twohop_apply(int32_t N, const uint64_t *keys, int bits, const uint8_t *valid,
+                               const int32_t *rank, int32_t need, int32_t *label) {
+  uint64_t mask = (1ull << bits) - 1ull;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (!valid[i] || rank[i] >= need) continue;
+    int32_t a = (int32_t)(keys[i] & mask), b = (int32_t)(keys[i + 1] & mask);
+    label[b] = label[a];
+  }
+}
+
+static void two_hop(const Graph &g, int32_t U, const int32_t *fav, int32_t *label, int32_t nc) {
+  int32_t n = g.n;
+  if (2 * (int64_t)nc <= n) return;
+  int32_t need = nc - n / 2;
+  cudaStream_t s = ctx().stream;
+  int grid = grid_for(n, 256);
+  DBuf<int32_t> size(n), count(1);
+  size.zero();
+  count.zero();
+  int bits = 1;
+  while ((1ll << bits) < (int64_t)n) ++bits;
+  DBuf<uint64_t> keys(n), tmp(n);
+  k_cluster_size<<<grid, 256, 0, s>>>(n, label, size);
+  KMP_LAUNCHED("cluster_size");
+  k_twohop_cand<<<grid, 256, 0, s>>>(n, label, size, fav, bits, keys, count);
+  KMP_LAUNCHED("twohop_cand");
+  int32_t N = read1(count.p);
+  if (N < 2) return;
+  radix_sort_u64(keys, tmp, N, 2 * bits);
+  int gN = grid_for(N, 256);
+  DBuf<uint8_t> head(N), valid(N);
+  DBuf<int32_t> hidx(N), H(N), rank(N), nh(1), nvalid(1);
+  k_twohop_heads<<<gN, 256, 0, s>>>(N, keys, bits, head);
+  KMP_LAUNCHED("twohop_heads");
+  scan_excl_u8_to_i32(head, hidx, N, nh);
+  k_twohop_headpos<<<gN, 256, 0, s>>>(N, head, hidx, H);
+  KMP_LAUNCHED("twohop_headpos");
+  int32_t nhh = read1(nh.p);
+  k_twohop_valid<<<gN, 256, 0, s>>>(N, keys, bits, H, nhh, g.vw, U, valid);
+  KMP_LAUNCHED("twohop_valid");
+  scan_excl_u8_to_i32(valid, rank, N, nvalid);
+  k_twohop_apply<<<gN, 256, 0, s>>>(N, keys, bits, valid, rank, need, label);
+  KMP_LAUNCHED("twohop_apply");
+}
+
+int32_t cluster_level(const Graph &g, int32_t U, int32_t rounds, uint64_t basekey, bool do_two_hop,
+                      int32_t *label, int32_t *fav_out, LPStats *st, float *ms_other) {
+  Context &C = ctx();
+  cudaStream_t s = C.stream;
+  int32_t n = g.n;
+  DBuf<int32_t> wt(n), favb;
+  int32_t *fav = fav_out;
+  if (!fav) {
+    favb.alloc(n);
+    fav = favb;
+  }
+  int grid = grid_for(n, 256);
+  k_init_cluster<<<grid, 256, 0, s>>>(n, g.vw, label, wt, fav);
+  KMP_LAUNCHED("init_cluster");
+  lp_run(g, label, wt, n, nullptr, U, rounds, basekey, fav, st);
+  cudaEvent_t e0, e1;
+  KMP_CUDA(cudaEventCreate(&e0));
+  KMP_CUDA(cudaEventCreate(&e1));
+  KMP_CUDA(cudaEventRecord(e0, s));
+  if (g.n_isolated > 0) {
+    DBuf<int32_t> w(n), first(n + 1);
+    DBuf<int64_t> P(n);
+    k_iso_w<<<grid, 256, 0, s>>>(n, g.xadj, g.vw, w);
+    KMP_LAUNCHED("iso_w");
+    scan_excl_i32_to_i64(w, P, n, nullptr);
+    k_fill_i32<<<grid_for(n + 1, 256), 256, 0, s>>>(first, n + 1, INT32_MAX);
+    KMP_LAUNCHED("fill");
+    k_iso_chunk<<<grid, 256, 0, s>>>(n, g.xadj, g.vw, P, U, first, 0, label);
+    KMP_LAUNCHED("iso_chunk");
+    k_iso_chunk<<<grid, 256, 0, s>>>(n, g.xadj, g.vw, P, U, first, 1, label);
+    KMP_LAUNCHED("iso_chunk");
+  }
+  int32_t nc = count_clusters(n, label);
+  if (do_two_hop && 2 * (int64_t)nc > n) {
+    two_hop(g, U, fav, label, nc);
+    nc = count_clusters(n, label);
+  }
+  KMP_CUDA(cudaEventRecord(e1, s));
+  KMP_CUDA(cudaEventSynchronize(e1));
+  float ms = 0;
+  KMP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  if (ms_other) *ms_other += ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return nc;
+}
+
+}  // namespace kmp

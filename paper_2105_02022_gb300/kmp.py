@@ -1,0 +1,290 @@
+"""Thin Python binding of libkmp's C ABI (include/kmp.h): argument marshalling
+only.  Device memory and streams come from PyTorch; every step of the method
+runs in the library's CUDA kernels.  Importing this module does not build
+anything: when libkmp.so is missing, load() raises, so a missing extension
+fails loudly instead of falling back to any CPU code."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import _build
+
+KMP_OK = 0
+KMP_ERR_ARG = -1
+KMP_ERR_NOMEM = -2
+KMP_ERR_CUDA = -3
+KMP_ERR_TIMEOUT = -4
+KMP_ERR_INFEASIBLE = -5
+KMP_ERR_UNSUPPORTED = -6
+
+_LIB = None
+
+
+class KmpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"kmp error {code}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in (
+        "C", "lp_rounds", "refine_rounds", "subrounds", "two_hop", "conv_num", "conv_den",
+        "ip_C", "ip_lp_rounds", "rep_random", "rep_bfs", "rep_ggg", "fm_passes", "fm_stop")]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("level_n", ctypes.c_int32 * 64),
+                ("level_m", ctypes.c_int64 * 64), ("lp_scanned", ctypes.c_int64),
+                ("refine_scanned", ctypes.c_int64), ("lp_rounds_run", ctypes.c_int64),
+                ("cut", ctypes.c_int64), ("feasible", ctypes.c_int32), ("ip_items", ctypes.c_int32),
+                ("ms_lp", ctypes.c_float), ("ms_cluster_other", ctypes.c_float),
+                ("ms_contract", ctypes.c_float), ("ms_ip", ctypes.c_float),
+                ("ms_balance", ctypes.c_float), ("ms_refine", ctypes.c_float),
+                ("ms_project", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("ms_lp_level0", ctypes.c_float), ("lp_scanned_level0", ctypes.c_int64),
+                ("lp_rounds_level0", ctypes.c_int32), ("gpu_launches", ctypes.c_int32)]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            if name in ("level_n", "level_m"):
+                v = list(v)[: self.levels]
+            d[name] = v
+        return d
+
+
+def load():
+    """Load libkmp.so (built by __graft_entry__.build()); raise if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.lib_path()
+    if not os.path.exists(path):
+        raise ImportError(f"libkmp.so not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    P, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "kmp_config_default": (None, [P]),
+        "kmp_set_config": (ctypes.c_int, [P]),
+        "kmp_get_config": (ctypes.c_int, [P]),
+        "kmp_set_stream": (ctypes.c_int, [P]),
+        "kmp_last_error": (ctypes.c_char_p, []),
+        "kmp_graph_create": (ctypes.c_int, [i32, P, P, P, P, ctypes.c_int, PP]),
+        "kmp_graph_free": (ctypes.c_int, [P]),
+        "kmp_graph_get": (ctypes.c_int, [P, P, P, P, P, P, P]),
+        "kmp_graph_copy_to_host": (ctypes.c_int, [P, P, P, P, P]),
+        "kmp_coarsen_level": (ctypes.c_int, [P, i64, i32, u64, i32, P, P]),
+        "kmp_contract": (ctypes.c_int, [P, P, PP, P]),
+        "kmp_refine": (ctypes.c_int, [P, i32, P, i32, u64, P, P]),
+        "kmp_balance": (ctypes.c_int, [P, i32, P, P, P]),
+        "kmp_project": (ctypes.c_int, [i32, P, P, P]),
+        "kmp_cut": (ctypes.c_int, [P, P, i32, P, P]),
+        "kmp_bipartition_blocks": (ctypes.c_int, [P, i32, P, dbl, i64, i32, u64, P, P, P]),
+        "kmp_partition": (ctypes.c_int, [i32, P, P, P, P, i32, dbl, u64, P]),
+        "kmp_partition_graph": (ctypes.c_int, [P, i32, dbl, u64, P, P]),
+        "kmp_last_stats": (ctypes.c_int, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = L
+    return L
+
+
+def _check(rc: int, allow=()):
+    if rc != KMP_OK and rc not in allow:
+        raise KmpError(rc, load().kmp_last_error().decode())
+    return rc
+
+
+def _stream():
+    load().kmp_set_stream(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def config(**kw) -> Config:
+    c = Config()
+    load().kmp_config_default(ctypes.byref(c))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def set_config(cfg: Config):
+    _check(load().kmp_set_config(ctypes.byref(cfg)))
+
+
+def get_config() -> Config:
+    c = Config()
+    _check(load().kmp_get_config(ctypes.byref(c)))
+    return c
+
+
+class DeviceGraph:
+    """Owning handle of a kmp_graph (CSR in device memory)."""
+
+    def __init__(self, handle):
+        self.h = handle
+
+    @classmethod
+    def from_host(cls, g) -> "DeviceGraph":
+        L = load()
+        _stream()
+        xadj = np.ascontiguousarray(g.xadj, np.int64)
+        adj = np.ascontiguousarray(g.adjncy, np.int32)
+        vw = None if g.vwgt is None else np.ascontiguousarray(g.vwgt, np.int32)
+        ew = None if g.adjwgt is None else np.ascontiguousarray(g.adjwgt, np.int32)
+        h = ctypes.c_void_p()
+        _check(L.kmp_graph_create(g.n, _ptr(xadj), _ptr(adj), _ptr(vw), _ptr(ew), 0, ctypes.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def from_device(cls, n, xadj: torch.Tensor, adj: torch.Tensor, vw=None, ew=None) -> "DeviceGraph":
+        L = load()
+        _stream()
+        h = ctypes.c_void_p()
+        _check(L.kmp_graph_create(n, _ptr(xadj), _ptr(adj), _ptr(vw), _ptr(ew), 1, ctypes.byref(h)))
+        return cls(h)
+
+    def info(self):
+        n, m = ctypes.c_int32(), ctypes.c_int64()
+        _check(load().kmp_graph_get(self.h, ctypes.byref(n), ctypes.byref(m), None, None, None, None))
+        return n.value, m.value
+
+    @property
+    def n(self):
+        return self.info()[0]
+
+    @property
+    def m(self):
+        return self.info()[1]
+
+    def to_host(self):
+        from .graphgen import Graph
+
+        n, m = self.info()
+        xadj = np.zeros(n + 1, np.int64)
+        adj = np.zeros(max(m, 1), np.int32)
+        vw = np.zeros(max(n, 1), np.int32)
+        ew = np.zeros(max(m, 1), np.int32)
+        _stream()
+        _check(load().kmp_graph_copy_to_host(self.h, _ptr(xadj), _ptr(adj), _ptr(vw), _ptr(ew)))
+        return Graph(n, xadj, adj[:m], vw[:n], ew[:m], "device")
+
+    def free(self):
+        if self.h:
+            load().kmp_graph_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _i32(n, device="cuda"):
+    return torch.empty(max(int(n), 1), dtype=torch.int32, device=device)[: int(n)]
+
+
+def coarsen_level(dg: DeviceGraph, U: int, rounds: int, seed: int, level: int, fav=False):
+    _stream()
+    n = dg.n
+    label = _i32(n)
+    favt = _i32(n) if fav else None
+    _check(load().kmp_coarsen_level(dg.h, int(U), int(rounds), int(seed), int(level), _ptr(label), _ptr(favt)))
+    return (label, favt) if fav else label
+
+
+def contract(dg: DeviceGraph, label: torch.Tensor):
+    _stream()
+    mp = _i32(label.numel())
+    h = ctypes.c_void_p()
+    _check(load().kmp_contract(dg.h, _ptr(label), ctypes.byref(h), _ptr(mp)))
+    return DeviceGraph(h), mp
+
+
+def refine(dg: DeviceGraph, k: int, caps, rounds: int, seed: int, part: torch.Tensor) -> int:
+    _stream()
+    caps = np.ascontiguousarray(caps, np.int64)
+    cut = ctypes.c_int64()
+    _check(load().kmp_refine(dg.h, int(k), _ptr(caps), int(rounds), int(seed), _ptr(part), ctypes.byref(cut)))
+    return cut.value
+
+
+def balance(dg: DeviceGraph, k: int, caps, part: torch.Tensor) -> int:
+    _stream()
+    caps = np.ascontiguousarray(caps, np.int64)
+    mv = ctypes.c_int64()
+    _check(load().kmp_balance(dg.h, int(k), _ptr(caps), _ptr(part), ctypes.byref(mv)))
+    return mv.value
+
+
+def project(mp: torch.Tensor, part_c: torch.Tensor) -> torch.Tensor:
+    _stream()
+    pf = _i32(mp.numel())
+    _check(load().kmp_project(mp.numel(), _ptr(mp), _ptr(part_c), _ptr(pf)))
+    return pf
+
+
+def cut(dg: DeviceGraph, part: torch.Tensor, k: int):
+    _stream()
+    bw = np.zeros(k, np.int64)
+    c = ctypes.c_int64()
+    _check(load().kmp_cut(dg.h, _ptr(part), int(k), ctypes.byref(c), _ptr(bw)))
+    return c.value, bw
+
+
+def bipartition_blocks(dg: DeviceGraph, nblocks: int, f, eps: float, cV: int, k: int, roundkey: int,
+                       part: torch.Tensor):
+    _stream()
+    f = np.ascontiguousarray(f, np.int32)
+    fo = np.zeros(2 * nblocks, np.int32)
+    nb = ctypes.c_int32()
+    _check(load().kmp_bipartition_blocks(dg.h, int(nblocks), _ptr(f), float(eps), int(cV), int(k),
+                                         ctypes.c_uint64(roundkey), _ptr(part), ctypes.byref(nb), _ptr(fo)))
+    return nb.value, fo[: nb.value].copy()
+
+
+def partition(g, k: int, eps: float, seed: int):
+    """kmp_partition on a host CSR; returns (part numpy int32, return code)."""
+    _stream()
+    xadj = np.ascontiguousarray(g.xadj, np.int64)
+    adj = np.ascontiguousarray(g.adjncy, np.int32)
+    vw = None if g.vwgt is None else np.ascontiguousarray(g.vwgt, np.int32)
+    ew = None if g.adjwgt is None else np.ascontiguousarray(g.adjwgt, np.int32)
+    part = np.zeros(g.n, np.int32)
+    rc = _check(load().kmp_partition(g.n, _ptr(xadj), _ptr(adj), _ptr(vw), _ptr(ew), int(k), float(eps),
+                                     ctypes.c_uint64(seed), _ptr(part)), allow=(KMP_ERR_INFEASIBLE,))
+    return part, rc
+
+
+def partition_graph(dg: DeviceGraph, k: int, eps: float, seed: int, part: torch.Tensor | None = None):
+    """kmp_partition_graph on a device graph; returns (part tensor, rc, Stats)."""
+    _stream()
+    if part is None:
+        part = _i32(dg.n)
+    st = Stats()
+    rc = _check(load().kmp_partition_graph(dg.h, int(k), float(eps), ctypes.c_uint64(seed), _ptr(part),
+                                           ctypes.byref(st)), allow=(KMP_ERR_INFEASIBLE,))
+    return part, rc, st
+
+
+def last_stats() -> Stats:
+    st = Stats()
+    load().kmp_last_stats(ctypes.byref(st))
+    return st

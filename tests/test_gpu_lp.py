@@ -1,0 +1,152 @@
+"""GPU parity of the coarsening / contraction / refinement kernels against the
+CPU oracle, called through the C ABI.  Integer work: bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2105_02022_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kmp():
+    from paper_2105_02022_gb300 import _build
+    from paper_2105_02022_gb300 import kmp as K
+
+    _build.build_all()
+    O.build()
+    assert torch.cuda.is_available()
+    K.set_config(K.config())
+    return K
+
+
+def _cases():
+    hubs = gg.hubs(20000, [40, 300, 1500, 3000, 9000, 20000], 30000, 3)
+    return {
+        "path": gg.path(30),
+        "grid": gg.grid(12, 17),
+        "triangles": gg.from_edges(6, [(0, 1), (1, 2), (0, 2), (3, 4), (4, 5), (3, 5), (2, 3)]),
+        "star_heavy": gg.from_edges(10, [(0, i) for i in range(1, 10)], vwgt=[2] + [1] * 9),
+        "isolated": gg.Graph(50, np.zeros(51, np.int64), np.zeros(0, np.int32), None, None),
+        "rand_w": gg.with_weights(gg.random_graph(700, 2100, 5), 9, 20, 5),
+        "rand_iso": gg.with_weights(gg.random_graph(3000, 1500, 6), 3, 4, 6),
+        "hubs": hubs,
+        "hubs_w": gg.with_weights(hubs, 4, 7, 2),
+        "rgg15": gg.workload_rgg_small(1),
+        "rmat14": gg.rmat(14, 16, 2),
+    }
+
+
+CASES = _cases()
+
+
+def _U(g, frac):
+    return max(int(g.vw().max()), int(frac * g.vw().sum()))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("frac", [0.0, 0.004, 0.05])
+def test_coarsen_level_parity(kmp, name, frac):
+    g = CASES[name]
+    U = _U(g, frac)
+    dg = kmp.DeviceGraph.from_host(g)
+    for seed, level in [(1, 0), (9, 3)]:
+        label, fav = kmp.coarsen_level(dg, U, 5, seed, level, fav=True)
+        rl, rf, st = O.cluster(g, U, 5, seed, level, stats=True)
+        assert np.array_equal(label.cpu().numpy(), rl), (name, U, seed)
+        assert np.array_equal(fav.cpu().numpy(), rf), (name, U, seed)
+        w = np.bincount(rl, weights=g.vw(), minlength=g.n)
+        assert w.max() <= U
+
+
+@pytest.mark.parametrize("name", ["grid", "rand_w", "hubs", "hubs_w", "rgg15", "rmat14", "isolated"])
+def test_contract_parity(kmp, name):
+    g = CASES[name]
+    U = _U(g, 0.004)
+    ref = O.cluster(g, U, 5, 3, 0)
+    dg = kmp.DeviceGraph.from_host(g)
+    lab = torch.from_numpy(ref).cuda()
+    cg, mp = kmp.contract(dg, lab)
+    rg, rmp = O.contract(g, ref)
+    h = cg.to_host()
+    assert np.array_equal(mp.cpu().numpy(), rmp)
+    assert h.n == rg.n
+    assert np.array_equal(h.xadj, rg.xadj)
+    assert np.array_equal(h.adjncy, rg.adjncy)
+    assert np.array_equal(h.adjwgt, rg.adjwgt)
+    assert np.array_equal(h.vwgt, rg.vwgt)
+
+
+def test_two_levels_chain(kmp):
+    """coarsen -> contract -> coarsen on the GPU's own coarse graph equals the oracle chain"""
+    g = CASES["rmat14"]
+    dg = kmp.DeviceGraph.from_host(g)
+    rg = g
+    for level in range(3):
+        U = _U(rg, 0.01)
+        label = kmp.coarsen_level(dg, U, 5, 4, level)
+        ref = O.cluster(rg, U, 5, 4, level)
+        assert np.array_equal(label.cpu().numpy(), ref)
+        dg, _ = kmp.contract(dg, label)
+        rg, _ = O.contract(rg, ref)
+        h = dg.to_host()
+        assert np.array_equal(h.adjncy, rg.adjncy) and np.array_equal(h.adjwgt, rg.adjwgt)
+
+
+@pytest.mark.parametrize("name", ["grid", "rand_w", "hubs_w", "rgg15", "rmat14"])
+@pytest.mark.parametrize("k", [2, 7, 64])
+def test_refine_parity(kmp, name, k):
+    g = CASES[name]
+    rng = np.random.default_rng(k)
+    part = rng.integers(0, k, g.n).astype(np.int32)
+    bw = np.bincount(part, weights=g.vw(), minlength=k)
+    caps = (np.maximum(bw, 1.03 * g.vw().sum() / k) + int(g.vw().max())).astype(np.int64)
+    dg = kmp.DeviceGraph.from_host(g)
+    pt = torch.from_numpy(part).cuda()
+    cut = kmp.refine(dg, k, caps, 5, 11, pt)
+    rp, rc = O.refine(g, k, caps.astype(np.int32), 5, 11, part)
+    assert np.array_equal(pt.cpu().numpy(), rp)
+    assert cut == rc
+    c2, bw2 = kmp.cut(dg, pt, k)
+    assert c2 == rc and np.all(bw2 <= caps)
+
+
+def test_project_and_cut(kmp):
+    g = CASES["rgg15"]
+    ref = O.cluster(g, 60, 5, 2, 0)
+    rg, rmp = O.contract(g, ref)
+    pc = np.random.default_rng(1).integers(0, 9, rg.n).astype(np.int32)
+    pf = kmp.project(torch.from_numpy(rmp).cuda(), torch.from_numpy(pc).cuda())
+    assert np.array_equal(pf.cpu().numpy(), pc[rmp])
+    dg = kmp.DeviceGraph.from_host(g)
+    c, bw = kmp.cut(dg, pf, 9)
+    assert c == O.cut(g, pc[rmp]) == O.cut(rg, pc)
+    assert np.array_equal(bw, np.bincount(pc[rmp], minlength=9))
+
+
+def test_invalid_inputs_are_rejected(kmp):
+    g = gg.path(10)
+    bad = gg.Graph(10, g.xadj, g.adjncy.copy(), None, None)
+    bad.adjncy[0] = 99
+    with pytest.raises(kmp.KmpError) as e:
+        kmp.DeviceGraph.from_host(bad)
+    assert e.value.code == kmp.KMP_ERR_ARG
+    dg = kmp.DeviceGraph.from_host(g)
+    with pytest.raises(kmp.KmpError):
+        kmp.coarsen_level(dg, 0, 5, 1, 0)          # U below max node weight
+    lab = torch.full((10,), 50, dtype=torch.int32, device="cuda")
+    with pytest.raises(kmp.KmpError):
+        kmp.contract(dg, lab)                      # labels out of range
+
+
+def test_full_size_rmat20_level0(kmp):
+    """Level 0 of the R-MAT scale-20 workload in the launch configuration the
+    benchmark uses: labels bit-exact with the oracle."""
+    g = gg.workload_rmat20(1)
+    U = int(np.floor(0.03 * g.n / 256))
+    dg = kmp.DeviceGraph.from_host(g)
+    label = kmp.coarsen_level(dg, U, 5, 1, 0)
+    ref = O.cluster(g, U, 5, 1, 0)
+    assert np.array_equal(label.cpu().numpy(), ref)
