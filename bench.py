@@ -1,0 +1,286 @@
+"""Benchmark: deep multilevel partitioning of the R-MAT scale-20 workload
+(edge factor 16, a,b,c,d = 0.57,0.19,0.19,0.05, symmetrised, deduplicated,
+self-loops removed, unit weights; k = 256, eps = 0.03) on one GB300.
+
+One step = one full kmp_partition_graph call: coarsening (size-constrained LP
+rating + deterministic commit, isolated packing, two-hop, contraction),
+batched initial bipartitioning, balancing, LP refinement, projection, cut.
+
+value    = LP edges/s per round: directed CSR entries rated by all LP rounds
+           (coarsening and refinement) / device time of those rounds.
+e2e      = the same quantity through kmp_partition with host buffers: entries
+           rated / wall time of the call (CSR upload and partition download
+           included).
+roofline = the LP rating kernel: algorithmic bytes / summed launch time (CUDA
+           events on the library stream, live in the timed region) against the
+           measured HBM copy bandwidth.
+cpu_baseline = the CPU oracle (single thread) on a bounded sample: level-0
+           coarsening LP of the same graph.
+
+--impl reference times the CPU oracle itself (the reference arm of this
+project) on the same workload, one bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LP edges/s per round (HBM GB/s vs peak); end-to-end s at k; cut vs plain"
+UNIT = "edges/s"
+K_BLOCKS = 256
+EPS = 0.03
+SEED = 1
+WORKLOAD = "rmat_scale20_ef16_k256"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.proc:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=reasons, samples=len(rows))
+        return out
+
+
+def cpu_baseline(g):
+    """The oracle as it stands: level-0 coarsening LP (5 rounds, 8 sub-rounds,
+    isolated packing, two-hop) of the workload graph, single thread."""
+    import oracle as O
+
+    U = int(EPS * g.n / K_BLOCKS)
+    t = time.perf_counter()
+    _, _, st = O.cluster(g, U, 5, SEED, 0, stats=True)
+    dt = time.perf_counter() - t
+    scanned = sum(st.scanned[r] for r in range(st.rounds))
+    return {"value": scanned / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"level-0 coarsening LP of {WORKLOAD}: {st.rounds} rounds, {scanned} entries rated, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    import oracle as O
+    from paper_2105_02022_gb300 import graphgen as gg
+
+    if rank != 0:
+        return
+    O.build()
+    g = gg.workload_rmat20(SEED)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; samples are independent
+    vals, secs = [], []
+    base = None
+    for _ in range(args.steps):
+        b = cpu_baseline(g)
+        vals.append(b["value"])
+        base = b
+    v = statistics.mean(vals)
+    base["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "k": K_BLOCKS, "eps": EPS, "n": g.n, "m_directed": g.m_directed},
+            "cpu_baseline": base, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                           "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2105_02022_gb300 import graphgen as gg
+    from paper_2105_02022_gb300 import kmp
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    kmp.load()
+    kmp.set_config(kmp.config())
+    g = gg.workload_rmat20(SEED)
+    dg = kmp.DeviceGraph.from_host(g)
+    part = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 3)):
+        kmp.partition_graph(dg, K_BLOCKS, EPS, SEED, part)
+    torch.cuda.synchronize()
+
+    kmp.set_profiling(True)
+    kmp.profile_read(reset=True)
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms, lp_ms, scanned, launches, cuts, feas, e2e_s = [], [], 0, 0, [], [], []
+    stats = None
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, rc, st = kmp.partition_graph(dg, K_BLOCKS, EPS, SEED, part)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        lp_ms.append(st.ms_lp + st.ms_refine)
+        scanned += st.lp_scanned + st.refine_scanned
+        launches += st.gpu_launches
+        cuts.append(st.cut)
+        feas.append(st.feasible)
+        stats = st
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    kmp.set_profiling(False)
+    rate_ms, rate_bytes, rate_launches = kmp.profile_read(reset=True)
+
+    total_lp_s = sum(lp_ms) / 1e3
+    total_step_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_lp_s, total_step_ms, float(scanned)], device="cuda", dtype=torch.float64)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        total_lp_s, total_step_ms, scanned_all = float(mx[0]), float(mx[1]), float(sm[2])
+    else:
+        scanned_all = float(scanned)
+    value = scanned_all / total_lp_s
+
+    # end to end through the host-buffer entry point (upload + partition + download)
+    e2e_vals = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hp, rc = kmp.partition(g, K_BLOCKS, EPS, SEED)
+        t1 = time.perf_counter()
+        st2 = kmp.last_stats()
+        e2e_vals.append((st2.lp_scanned + st2.refine_scanned) / (t1 - t0))
+        e2e_s.append(t1 - t0)
+    e2e_value = statistics.median(e2e_vals) * (world if world > 1 else 1)
+    h2d = g.xadj.nbytes + g.adjncy.nbytes
+    d2h = g.n * 4
+
+    peak, peak_kind = _peaks()
+    achieved = (rate_bytes / (rate_ms / 1e3)) / 1e9 if rate_ms > 0 else 0.0
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "lp_rate_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_step_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": g.n, "m_directed": g.m_directed, "k": K_BLOCKS, "eps": EPS,
+                   "seed": SEED, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between steps (256 MB write)"},
+        "end_to_end_s": (total_step_ms / args.steps) / 1e3,
+        "end_to_end_s_host_api": statistics.median(e2e_s),
+        "lp_scanned_per_step": (scanned_all / max(world, 1)) / args.steps,
+        "lp_s_per_step": total_lp_s / args.steps,
+        "cut": cuts[-1], "feasible": all(feas), "levels": stats.levels,
+        "phase_ms": {"lp": stats.ms_lp, "cluster_other": stats.ms_cluster_other,
+                     "contract": stats.ms_contract, "ip": stats.ms_ip, "balance": stats.ms_balance,
+                     "refine": stats.ms_refine, "project": stats.ms_project, "total": stats.ms_total},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "LP rating (k_rate)", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak if peak else None,
+                     "traffic": traffic, "launches": int(rate_launches),
+                     "algorithmic_bytes": rate_bytes, "ms": rate_ms},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(g)
+    elif not args.no_cpu_baseline and rank == 0:
+        line["cpu_baseline"] = cpu_baseline(g)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

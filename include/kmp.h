@@ -205,6 +205,17 @@ int kmp_partition_graph(const kmp_graph *g, int32_t k, double eps, uint64_t seed
 /* stats of the last kmp_partition / kmp_partition_graph call of this thread */
 int kmp_last_stats(kmp_stats *stats);
 
+/*
+ * Live profiling of the LP rating kernel (the dominant kernel of coarsening
+ * and refinement): when on, every rating launch is bracketed by CUDA events on
+ * the library's stream and its algorithmic bytes are counted (per directed
+ * entry rated: adjncy 4 + neighbour label 4 (+ edge weight 4 when weighted);
+ * per rated node: xadj 8 + list entry 4 + own label 4 + proposal 8 (+ node
+ * weight 4)).  kmp_profile_read returns the sums since the last reset.
+ */
+int kmp_set_profiling(int on);
+int kmp_profile_read(double *rate_ms, double *rate_bytes, int64_t *rate_launches, int reset);
+
 #ifdef __cplusplus
 }
 #endif

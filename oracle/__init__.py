@@ -82,6 +82,7 @@ def lib():
             "kmpo_split_caps": (None, [dbl, i64, i32, i64, i32, P, P, P, P]),
             "kmpo_block_cap": (i32, [dbl, i64, i32, i32, i32]),
             "kmpo_partition": (i32, [i32, P, P, P, P, i32, dbl, u64, P, P, P]),
+            "kmpo_bipartition_blocks": (i32, [i32, P, P, P, P, i32, P, dbl, i64, i32, u64, P, P, P]),
             "kmpo_brute_bisection": (i64, [i32, P, P, P, P, i64, i64, P]),
             "kmpo_async_cluster": (i32, [i32, P, P, P, P, i32, i32, P]),
         }
@@ -232,6 +233,18 @@ def partition(g, k, eps, seed, cfg=None):
     rc = lib().kmpo_partition(n, _p(xadj), _p(adj), _p(vw), _p(ew), k, eps, seed,
                               ctypes.byref(cfg), _p(part), ctypes.byref(st))
     return part, int(rc), st
+
+
+def bipartition_blocks(g, nblocks, f, eps, cV, k, roundkey, part, cfg=None):
+    """One split round of Algorithm 2; returns (new part, new f)."""
+    cfg = cfg or config()
+    n, xadj, adj, vw, ew = _g(g)
+    part = np.array(part, np.int32, copy=True)
+    f = np.ascontiguousarray(f, np.int32)
+    fo = np.zeros(2 * nblocks + 2, np.int32)
+    nb = lib().kmpo_bipartition_blocks(n, _p(xadj), _p(adj), _p(vw), _p(ew), nblocks, _p(f), eps, cV, k,
+                                       roundkey, ctypes.byref(cfg), _p(part), _p(fo))
+    return part, fo[:nb].copy()
 
 
 def brute_bisection(g, L0, L1):

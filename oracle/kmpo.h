@@ -126,6 +126,15 @@ void kmpo_split_caps(double eps, int64_t cV, int32_t k, int64_t cB, int32_t fB,
 /* per-block cap L(b) = floor(max((1+eps) cV f/k, cV f/k + maxc)) */
 int32_t kmpo_block_cap(double eps, int64_t cV, int32_t k, int32_t fb, int32_t maxc);
 
+/* one split round of Algorithm 2: every block b with f_in[b] >= 2 is
+ * bipartitioned; blocks renumbered in ascending order, child 0 first;
+ * returns the new block count, f_out receives the new final counts */
+int32_t kmpo_bipartition_blocks(int32_t n, const int64_t *xadj, const int32_t *adj,
+                                const int32_t *vw, const int32_t *ew, int32_t nblocks,
+                                const int32_t *f_in, double eps, int64_t cV, int32_t k,
+                                uint64_t roundkey, const kmpo_config *cfg, int32_t *part,
+                                int32_t *f_out);
+
 /* full deep multilevel partition (Algorithm 1).  Returns 0, or -5 when the
  * result violates L_k = floor((1+eps) ceil(c(V)/k)) (result still written). */
 int32_t kmpo_partition(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,

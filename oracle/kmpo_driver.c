@@ -256,6 +256,28 @@ static void bipartition_blocks(const glvl_t *g, int32_t *part, int32_t *nblocks,
   free(newid); free(nf); free(cnt); free(mem); free(pos); free(loc); free(newpart);
 }
 
+int32_t kmpo_bipartition_blocks(int32_t n, const int64_t *xadj, const int32_t *adj,
+                                const int32_t *vw, const int32_t *ew, int32_t nblocks,
+                                const int32_t *f_in, double eps, int64_t cV, int32_t k,
+                                uint64_t roundkey, const kmpo_config *cfg, int32_t *part,
+                                int32_t *f_out) {
+  glvl_t g;
+  g.n = n;
+  g.xadj = (int64_t *)xadj;
+  g.adj = (int32_t *)adj;
+  g.vw = (int32_t *)vw;
+  g.ew = (int32_t *)ew;
+  g.map = NULL;
+  g.owned = 0;
+  int32_t *f = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * nblocks + 2));
+  memcpy(f, f_in, sizeof(int32_t) * (size_t)nblocks);
+  int32_t nb = nblocks;
+  bipartition_blocks(&g, part, &nb, f, eps, cV, k, roundkey, cfg);
+  memcpy(f_out, f, sizeof(int32_t) * (size_t)nb);
+  free(f);
+  return nb;
+}
+
 int32_t kmpo_partition(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
                        const int32_t *ew, int32_t k, double eps, uint64_t seed,
                        const kmpo_config *cfg, int32_t *part_out, kmpo_stats *st) {

@@ -602,4 +602,22 @@ int kmp_last_stats(kmp_stats *stats) {
   return KMP_OK;
 }
 
+int kmp_set_profiling(int on) {
+  return guarded([&] { ctx().profile = on != 0; });
+}
+
+int kmp_profile_read(double *rate_ms, double *rate_bytes, int64_t *rate_launches, int reset) {
+  return guarded([&] {
+    Context &C = ctx();
+    if (rate_ms) *rate_ms = C.prof_rate_ms;
+    if (rate_bytes) *rate_bytes = C.prof_rate_bytes;
+    if (rate_launches) *rate_launches = C.prof_rate_launches;
+    if (reset) {
+      C.prof_rate_ms = 0;
+      C.prof_rate_bytes = 0;
+      C.prof_rate_launches = 0;
+    }
+  });
+}
+
 }  // extern "C"

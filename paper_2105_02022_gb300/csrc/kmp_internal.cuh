@@ -37,6 +37,10 @@ struct Context {
   int device = 0;
   int64_t launches = 0;
   int *d_status = nullptr;  // device status word: 0 ok, else KMP_ERR_* set by kernels
+  // live profiling of the LP rating launches (CUDA events on `stream`)
+  bool profile = false;
+  double prof_rate_ms = 0, prof_rate_bytes = 0;
+  int64_t prof_rate_launches = 0;
 };
 Context &ctx();
 void ensure_init();

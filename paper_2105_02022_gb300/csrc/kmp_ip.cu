@@ -1,16 +1,1365 @@
-// Batched multilevel initial bipartitioning (Section 4.2) and k-way balancing
-// (Section 4.3).
+// Batched multilevel initial bipartitioning (Section 4.2) for Algorithm 2
+// (bipartitionBlocks): every block that must be split becomes one work item;
+// all items of a split round run in ONE persistent launch whose CTAs take
+// items from a device work queue (largest first).  Per item, one CTA:
+//   1. coarsens the induced subgraph G[B] with the deterministic sub-round LP
+//      (CTA-parallel rating with per-warp hash tables, commit by a bitonic
+//      sort of (target, gain desc, node) keys and a segmented prefix sum),
+//      packs isolated nodes, and contracts (sort of (cu, cv) pairs, run sums),
+//      level after level until nothing contracts or the shrink stalls;
+//   2. runs the portfolio -- random, BFS and greedy graph growing starts, each
+//      refined by 2-way FM -- with one warp per repetition;
+//   3. projects the best bipartition up the item's hierarchy and runs 2-way FM
+//      (one warp) on every level.
+// Scratch comes from a per-item region through a bump allocator; if a region
+// is too small the launch reports it and the host repeats the round with
+// larger regions, so results never depend on scratch sizes.
+// Also: k-way balancing (Section 4.3, "Balancing") in a single-CTA kernel.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
 #include "kmp_internal.cuh"
 
 namespace kmp {
 
+constexpr int IPT = 256;
+constexpr int IPW = IPT / 32;
+constexpr int IP_WTAB = 512;       // per-warp shared table: degree <= 256
+constexpr int IP_MAXL = 63;
+constexpr int32_t IP_MAX_N = 65535;
+
+struct ItemDesc {
+  int64_t vbase;  // first member position
+  int64_t ebase;  // first induced edge
+  int64_t sbase;  // scratch region (int32 units)
+  int64_t ssize;
+  uint64_t key;
+  int32_t n, m;
+  int32_t t0, t1, L0, L1;
+  int32_t pad0, pad1;
+};
+
+struct IPArgs {
+  const ItemDesc *items;
+  const int32_t *order;   // item processing order
+  int32_t nitems;
+  int32_t *queue;         // work counter
+  int32_t *oom;           // set when a scratch region was too small
+  const int64_t *gx;      // induced CSR offsets over all members (n+1)
+  const int32_t *sadj;    // local neighbour ids
+  const int32_t *sew;
+  const int32_t *svw;
+  int32_t *side_out;      // per member position
+  int32_t *scratch;
+  // configuration
+  int32_t S, ip_C, ip_lp_rounds, rep_random, rep_bfs, rep_ggg, fm_passes, fm_stop;
+  int32_t conv_num, conv_den;
+};
+
+struct LG {
+  int32_t n, m;
+  int32_t *xadj, *adj, *ew, *vw;
+  int32_t maxdeg, maxc;
+};
+
+struct Bump {
+  int32_t *base;
+  int64_t cap, top;
+  bool oom;
+  __device__ int32_t *take(int64_t cnt) {
+    int64_t t = (top + 1) & ~1ll;
+    if (oom || t + cnt > cap) {
+      oom = true;
+      return base;  // never dereferenced: callers check oom
+    }
+    top = t + cnt;
+    return base + t;
+  }
+};
+
+// ------------------------------------------------------- block helpers
+__device__ int64_t block_sum64(int64_t v) {
+  __shared__ int64_t red[IPW];
+  v = warp_sum64(v);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  int64_t s = 0;
+  for (int i = 0; i < IPW; ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+__device__ int32_t block_max32(int32_t v) {
+  __shared__ int32_t red[IPW];
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v = max(v, __shfl_xor_sync(0xFFFFFFFFu, v, m));
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  int32_t s = red[0];
+  for (int i = 1; i < IPW; ++i) s = max(s, red[i]);
+  __syncthreads();
+  return s;
+}
+
+// exclusive scan of in[0..n) into out (may alias), returns total
+template <class T>
+__device__ T block_scan_excl(const T *in, T *out, int32_t n) {
+  __shared__ T wsum[IPW];
+  __shared__ T carry;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int32_t base = 0; base < n; base += IPT) {
+    int32_t i = base + threadIdx.x;
+    T v = i < n ? in[i] : T(0);
+    T x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      T y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+      if (lane >= d) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    T pre = carry;
+    for (int k = 0; k < w; ++k) pre += wsum[k];
+    T tot = 0;
+    for (int k = 0; k < IPW; ++k) tot += wsum[k];
+    if (i < n) out[i] = pre + x - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  T r = carry;
+  __syncthreads();
+  return r;
+}
+
+// bitonic sort of P (power of two) keys ascending, optional values; block-wide
+__device__ void block_bitonic(uint64_t *key, int32_t *val, int32_t P) {
+  for (int32_t k = 2; k <= P; k <<= 1)
+    for (int32_t j = k >> 1; j > 0; j >>= 1) {
+      for (int32_t i = threadIdx.x; i < P; i += IPT) {
+        int32_t l = i ^ j;
+        if (l > i) {
+          uint64_t x = key[i], y = key[l];
+          bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            key[i] = y;
+            key[l] = x;
+            if (val) {
+              int32_t t = val[i];
+              val[i] = val[l];
+              val[l] = t;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+// warp bitonic of P pairs (h, v) ascending by (h, v)
+__device__ void warp_bitonic_hv(uint64_t *h, int32_t *v, int32_t P) {
+  int lane = threadIdx.x & 31;
+  for (int32_t k = 2; k <= P; k <<= 1)
+    for (int32_t j = k >> 1; j > 0; j >>= 1) {
+      for (int32_t i = lane; i < P; i += 32) {
+        int32_t l = i ^ j;
+        if (l > i) {
+          uint64_t a = h[i], b = h[l];
+          int32_t va = v[i], vb = v[l];
+          bool gt = a > b || (a == b && va > vb);
+          bool up = (i & k) == 0;
+          if (gt == up) {
+            h[i] = b; h[l] = a;
+            v[i] = vb; v[l] = va;
+          }
+        }
+      }
+      __syncwarp();
+    }
+}
+
+__device__ __forceinline__ int32_t pow2_at_least(int32_t x) {
+  int32_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// ------------------------------------------------------ item clustering
+// rating of node u by one warp; returns (via lane 0) proposal target or -1
+__device__ void item_rate(const LG &g, int32_t u, const int32_t *label, const int32_t *wt, int32_t U,
+                          uint32_t rk_hi, int32_t *keys, int32_t *vals, int32_t *out_t,
+                          int32_t *out_g) {
+  int lane = threadIdx.x & 31;
+  int32_t b = g.xadj[u], e = g.xadj[u + 1], deg = e - b;
+  uint32_t cap = 32;
+  while ((int64_t)cap < 2ll * deg) cap <<= 1;
+  uint32_t mask = cap - 1;
+  for (uint32_t i = lane; i < cap; i += 32) {
+    keys[i] = HT_EMPTY;
+    vals[i] = 0;
+  }
+  __syncwarp();
+  for (int32_t q = b + lane; q < e; q += 32) ht_add(keys, vals, mask, label[g.adj[q]], g.ew[q]);
+  __syncwarp();
+  int32_t own = label[u], cu = g.vw[u];
+  int32_t rown = ht_get(keys, vals, mask, own);
+  uint64_t kc = 0;
+  int32_t lc = -1;
+  for (uint32_t i = lane; i < cap; i += 32) {
+    int32_t K = keys[i];
+    if (K == HT_EMPTY || K == own) continue;
+    if ((int64_t)wt[K] + cu > U) continue;
+    uint64_t k = ((uint64_t)(uint32_t)vals[i] << 32) | (uint64_t)(0xFFFFFFFFu - perm32(rk_hi, K));
+    if (k > kc) { kc = k; lc = K; }
+  }
+  uint64_t mc = group_max64<32>(kc);
+  unsigned bc = __ballot_sync(0xFFFFFFFFu, mc != 0 && kc == mc);
+  lc = __shfl_sync(0xFFFFFFFFu, lc, bc ? __ffs(bc) - 1 : 0);
+  if (lane == 0) {
+    int32_t rc = (int32_t)(mc >> 32);
+    if (mc != 0 && rc > rown) {
+      *out_t = lc;
+      *out_g = rc - rown;
+    } else {
+      *out_t = -1;
+    }
+  }
+  __syncwarp();
+}
+
+// segmented inclusive scan in shared memory (one element per thread)
+__device__ int64_t block_seg_scan(int64_t x, bool head) {
+  __shared__ int64_t sv[IPT];
+  __shared__ int32_t sf[IPT];
+  int t = threadIdx.x;
+  sv[t] = x;
+  sf[t] = head ? 1 : 0;
+  __syncthreads();
+  for (int d = 1; d < IPT; d <<= 1) {
+    int64_t v = sv[t];
+    int32_t f = sf[t];
+    if (t >= d && !f) {
+      v += sv[t - d];
+      f |= sf[t - d];
+    }
+    __syncthreads();
+    sv[t] = v;
+    sf[t] = f;
+    __syncthreads();
+  }
+  int64_t r = sv[t];
+  __syncthreads();
+  return r;
+}
+
+// LP clustering of one item level + isolated packing; returns #clusters
+__device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_t basekey,
+                                int32_t *label, Bump &B, int32_t *wkeys, int32_t *wvals) {
+  __shared__ int32_t s_cnt;
+  __shared__ int32_t s_moved;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t n = g.n;
+  int64_t mark = B.top;
+  int32_t *wt = B.take(n);
+  int32_t *act = B.take(n);
+  int32_t *act2 = B.take(n);
+  int32_t *pt = B.take(n);
+  int32_t *pg = B.take(n);
+  int32_t P = pow2_at_least(n > 1 ? n : 2);
+  uint64_t *pl = reinterpret_cast<uint64_t *>(B.take(2ll * P));
+  int32_t *gtab = nullptr;
+  uint32_t gcap = 0;
+  if (g.maxdeg > IP_WTAB / 2) {
+    gcap = 32;
+    while ((int64_t)gcap < 2ll * g.maxdeg) gcap <<= 1;
+    gtab = B.take(2ll * gcap * IPW);
+  }
+  if (B.oom) return -1;
+  for (int32_t v = threadIdx.x; v < n; v += IPT) {
+    label[v] = v;
+    wt[v] = g.vw[v];
+    act[v] = 1;
+  }
+  __syncthreads();
+  int32_t *mk = wkeys + w * IP_WTAB, *mv = wvals + w * IP_WTAB;
+  if (gtab) {
+    mk = gtab + (int64_t)w * 2 * gcap;
+    mv = mk + gcap;
+  }
+  for (int32_t r = 0; r < A.ip_lp_rounds; ++r) {
+    uint64_t rk = key_step(basekey, (uint64_t)r);
+    uint32_t rk_hi = (uint32_t)(rk >> 32);
+    for (int32_t v = threadIdx.x; v < n; v += IPT) act2[v] = 0;
+    if (threadIdx.x == 0) s_moved = 0;
+    __syncthreads();
+    for (int32_t s = 0; s < A.S; ++s) {
+      // rating
+      for (int32_t u = w; u < n; u += IPW) {
+        bool rate = act[u] && g.xadj[u + 1] > g.xadj[u] &&
+                    (int32_t)(key_step(rk, (uint64_t)(uint32_t)u) & (uint64_t)(A.S - 1)) == s;
+        if (rate) item_rate(g, u, label, wt, U, rk_hi, mk, mv, &pt[u], &pg[u]);
+        else if (lane == 0) pt[u] = -1;
+      }
+      if (threadIdx.x == 0) s_cnt = 0;
+      __syncthreads();
+      // collect (target, gain desc, node) keys
+      for (int32_t u = threadIdx.x; u < n; u += IPT) {
+        int32_t T = pt[u];
+        if (T < 0) continue;
+        int32_t p = atomicAdd(&s_cnt, 1);
+        pl[p] = ((uint64_t)(uint32_t)T << 47) | ((uint64_t)(uint32_t)(0x7FFFFFFF - pg[u]) << 16) |
+                (uint64_t)(uint32_t)u;
+      }
+      __syncthreads();
+      int32_t np = s_cnt;
+      if (np > 0) {
+        int32_t Pp = pow2_at_least(np);
+        for (int32_t i = np + threadIdx.x; i < Pp; i += IPT) pl[i] = ~0ull;
+        __syncthreads();
+        block_bitonic(pl, nullptr, Pp);
+        // accepted prefix per target: start weight + segmented prefix <= U
+        __shared__ int64_t carry;
+        __shared__ int32_t carryT;
+        if (threadIdx.x == 0) { carry = 0; carryT = -1; }
+        __syncthreads();
+        for (int32_t base = 0; base < np; base += IPT) {
+          int32_t i = base + threadIdx.x;
+          bool ok = i < np;
+          uint64_t k = ok ? pl[i] : 0;
+          int32_t T = ok ? (int32_t)(k >> 47) : -1;
+          int32_t u = ok ? (int32_t)(k & 0xFFFF) : 0;
+          int32_t Tprev = (i == 0) ? -1 : (int32_t)((pl[i - 1] >> 47) & 0xFFFF);
+          bool head = !ok || i == 0 || T != Tprev;
+          int64_t c = ok ? g.vw[u] : 0;
+          int64_t pre = block_seg_scan(c, head || threadIdx.x == 0);
+          // the chunk's first segment continues the previous chunk's last one
+          bool cont = ok && base > 0 && T == carryT;
+          __shared__ int32_t firsthead;
+          if (threadIdx.x == 0) firsthead = IPT;
+          __syncthreads();
+          if (ok && threadIdx.x > 0 && head) atomicMin(&firsthead, (int32_t)threadIdx.x);
+          __syncthreads();
+          if (cont && (int32_t)threadIdx.x < firsthead) pre += carry;
+          if (ok) {
+            bool acc = (int64_t)wt[T] + pre <= U;
+            if (acc) pl[i] = k | (1ull << 63);
+          }
+          __syncthreads();
+          int32_t last = min(IPT, np - base) - 1;
+          if ((int32_t)threadIdx.x == last) {
+            carry = pre;
+            carryT = T;
+          }
+          __syncthreads();
+        }
+        // apply
+        int32_t mv_local = 0;
+        for (int32_t i = threadIdx.x; i < np; i += IPT) {
+          uint64_t k = pl[i];
+          if (!(k >> 63)) continue;
+          int32_t T = (int32_t)((k >> 47) & 0xFFFF);
+          int32_t u = (int32_t)(k & 0xFFFF);
+          int32_t own = label[u], c = g.vw[u];
+          label[u] = T;
+          atomicAdd(&wt[T], c);
+          atomicSub(&wt[own], c);
+          ++mv_local;
+          for (int32_t q = g.xadj[u]; q < g.xadj[u + 1]; ++q) act2[g.adj[q]] = 1;
+        }
+        if (mv_local) atomicAdd(&s_moved, mv_local);
+      }
+      __syncthreads();
+    }
+    int32_t moved = s_moved;
+    int32_t *t = act;
+    act = act2;
+    act2 = t;
+    __syncthreads();
+    if (moved == 0) break;
+  }
+  // isolated packing in id order
+  int32_t *iw = act2;  // reuse: weights of isolated nodes, then prefix
+  for (int32_t v = threadIdx.x; v < n; v += IPT) iw[v] = (g.xadj[v + 1] == g.xadj[v]) ? g.vw[v] : 0;
+  __syncthreads();
+  block_scan_excl<int32_t>(iw, iw, n);
+  int32_t *first = act;
+  for (int32_t v = threadIdx.x; v < n; v += IPT) first[v] = INT32_MAX;
+  __syncthreads();
+  for (int32_t v = threadIdx.x; v < n; v += IPT) {
+    if (g.xadj[v + 1] != g.xadj[v]) continue;
+    int64_t P0 = iw[v], c = g.vw[v];
+    int64_t q = P0 / U, qe = (P0 + c - 1) / U;
+    if (q == qe) atomicMin(&first[q], label[v]);
+  }
+  __syncthreads();
+  for (int32_t v = threadIdx.x; v < n; v += IPT) {
+    if (g.xadj[v + 1] != g.xadj[v]) continue;
+    int64_t P0 = iw[v], c = g.vw[v];
+    int64_t q = P0 / U, qe = (P0 + c - 1) / U;
+    if (q == qe) label[v] = first[q];
+  }
+  __syncthreads();
+  // count clusters
+  int32_t *used = pt;
+  for (int32_t v = threadIdx.x; v < n; v += IPT) used[v] = 0;
+  __syncthreads();
+  for (int32_t v = threadIdx.x; v < n; v += IPT) used[label[v]] = 1;
+  __syncthreads();
+  int64_t c = 0;
+  for (int32_t v = threadIdx.x; v < n; v += IPT) c += used[v];
+  int32_t nc = (int32_t)block_sum64(c);
+  B.top = mark;
+  return nc;
+}
+
+// contraction of one item level; fills *out (arrays allocated from B)
+__device__ void item_contract(const LG &g, const int32_t *label, int32_t *map, LG *out, Bump &B) {
+  __shared__ int32_t s_cnt;
+  int32_t n = g.n;
+  int32_t *cid = B.take(n + 1);
+  if (B.oom) return;
+  for (int32_t v = threadIdx.x; v < n; v += IPT) cid[v] = 0;
+  __syncthreads();
+  for (int32_t v = threadIdx.x; v < n; v += IPT) cid[label[v]] = 1;
+  __syncthreads();
+  int32_t nc = block_scan_excl<int32_t>(cid, cid, n);
+  for (int32_t v = threadIdx.x; v < n; v += IPT) map[v] = cid[label[v]];
+  __syncthreads();
+  // coarse arrays (kept)
+  int32_t *cvw = B.take(nc);
+  int32_t *cx = B.take(nc + 1);
+  // pair count
+  int64_t cnt = 0;
+  for (int32_t v = threadIdx.x; v < n; v += IPT)
+    for (int32_t q = g.xadj[v]; q < g.xadj[v + 1]; ++q) cnt += (map[v] != map[g.adj[q]]);
+  int32_t np = (int32_t)block_sum64(cnt);
+  int32_t *cadj = B.take(np);
+  int32_t *cew = B.take(np);
+  int64_t mark = B.top;
+  int32_t P = pow2_at_least(np > 1 ? np : 2);
+  uint64_t *key = reinterpret_cast<uint64_t *>(B.take(2ll * P));
+  int32_t *val = B.take(P);
+  int32_t *head = B.take(P + 1);
+  if (B.oom) return;
+  for (int32_t x = threadIdx.x; x < nc; x += IPT) {
+    cvw[x] = 0;
+    cx[x] = 0;
+  }
+  if (threadIdx.x == 0) {
+    s_cnt = 0;
+    cx[nc] = 0;
+  }
+  __syncthreads();
+  for (int32_t v = threadIdx.x; v < n; v += IPT) {
+    atomicAdd(&cvw[map[v]], g.vw[v]);
+    int32_t a = map[v];
+    for (int32_t q = g.xadj[v]; q < g.xadj[v + 1]; ++q) {
+      int32_t b = map[g.adj[q]];
+      if (a == b) continue;
+      int32_t p = atomicAdd(&s_cnt, 1);
+      key[p] = ((uint64_t)(uint32_t)a << 32) | (uint32_t)b;
+      val[p] = g.ew[q];
+    }
+  }
+  for (int32_t i = np + threadIdx.x; i < P; i += IPT) {
+    key[i] = ~0ull;
+    val[i] = 0;
+  }
+  __syncthreads();
+  block_bitonic(key, val, P);
+  for (int32_t i = threadIdx.x; i < np; i += IPT) head[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
+  __syncthreads();
+  int32_t m2 = block_scan_excl<int32_t>(head, head, np);  // head[i] -> exclusive rank
+  // run sums: each run head sums its run
+  for (int32_t i = threadIdx.x; i < np; i += IPT) {
+    bool h = (i == 0 || key[i] != key[i - 1]);
+    if (!h) continue;
+    int64_t s = 0;
+    int32_t j = i;
+    while (j < np && key[j] == key[i]) s += val[j++];
+    int32_t r = head[i];
+    cadj[r] = (int32_t)(uint32_t)key[i];
+    cew[r] = (int32_t)s;
+    atomicAdd(&cx[(int32_t)(key[i] >> 32)], 1);
+  }
+  __syncthreads();
+  block_scan_excl<int32_t>(cx, cx, nc + 1);
+  B.top = mark;
+  out->n = nc;
+  out->m = m2;
+  out->xadj = cx;
+  out->adj = cadj;
+  out->ew = cew;
+  out->vw = cvw;
+  __syncthreads();
+}
+
+// ------------------------------------------------------------ warp FM
+struct FMBuf {
+  int32_t *gain, *locked, *moves;
+};
+
+__device__ __forceinline__ bool fm_less(int32_t ia, int64_t oa, int64_t ca, int32_t ib, int64_t ob,
+                                        int64_t cb) {
+  if (ia != ib) return ia < ib;
+  if (oa != ob) return oa < ob;
+  return ca < cb;
+}
+
+// 2-way FM by one warp (same decisions as the oracle); returns the final cut
+__device__ int64_t warp_fm(const IPArgs &A, const LG &g, int32_t *side, int64_t L0, int64_t L1,
+                           FMBuf fb) {
+  int lane = threadIdx.x & 31;
+  int32_t n = g.n;
+  int64_t cut = 0;
+  for (int32_t v = lane; v < n; v += 32)
+    for (int32_t q = g.xadj[v]; q < g.xadj[v + 1]; ++q)
+      if (side[g.adj[q]] != side[v]) cut += g.ew[q];
+  cut = warp_sum64(cut) / 2;
+  for (int32_t pass = 0; pass < A.fm_passes; ++pass) {
+    int64_t W0 = 0, W1 = 0;
+    for (int32_t v = lane; v < n; v += 32) {
+      if (side[v] == 0) W0 += g.vw[v];
+      else W1 += g.vw[v];
+      int32_t gsum = 0;
+      for (int32_t q = g.xadj[v]; q < g.xadj[v + 1]; ++q)
+        gsum += (side[g.adj[q]] != side[v]) ? g.ew[q] : -g.ew[q];
+      fb.gain[v] = gsum;
+      fb.locked[v] = 0;
+    }
+    W0 = warp_sum64(W0);
+    W1 = warp_sum64(W1);
+    __syncwarp();
+    auto mk = [&](int32_t &inf, int64_t &ov) {
+      int64_t o0 = W0 - L0, o1 = W1 - L1;
+      int64_t o = o0 > o1 ? o0 : o1;
+      inf = o > 0;
+      ov = inf ? o : 0;
+    };
+    int32_t binf;
+    int64_t bov;
+    mk(binf, bov);
+    int64_t bcut = cut;
+    int32_t best_step = 0, nsteps = 0;
+    for (;;) {
+      uint64_t t0 = 0, t1 = 0;  // (gain biased, ~id): larger is better; 0 = none
+      for (int32_t v = lane; v < n; v += 32) {
+        if (fb.locked[v]) continue;
+        uint64_t k = ((uint64_t)((uint32_t)fb.gain[v] ^ 0x80000000u) << 32) | (0xFFFFFFFFu - (uint32_t)v);
+        if (side[v] == 0) t0 = k > t0 ? k : t0;
+        else t1 = k > t1 ? k : t1;
+      }
+      t0 = group_max64<32>(t0);
+      t1 = group_max64<32>(t1);
+      if (t0 == 0 && t1 == 0) break;
+      int32_t v0 = t0 ? (int32_t)(0xFFFFFFFFu - (uint32_t)t0) : -1;
+      int32_t v1 = t1 ? (int32_t)(0xFFFFFFFFu - (uint32_t)t1) : -1;
+      bool f0 = v0 >= 0 && W1 + g.vw[v0] <= L1;
+      bool f1 = v1 >= 0 && W0 + g.vw[v1] <= L0;
+      int32_t v;
+      if (f0 && f1) v = (t0 > t1) ? v0 : v1;
+      else if (f0) v = v0;
+      else if (f1) v = v1;
+      else {
+        if (lane == 0) {
+          if (v0 >= 0) fb.locked[v0] = 1;
+          if (v1 >= 0) fb.locked[v1] = 1;
+        }
+        __syncwarp();
+        continue;
+      }
+      int32_t from = side[v], to = 1 - from;
+      int32_t gv = fb.gain[v];
+      __syncwarp();
+      if (lane == 0) {
+        side[v] = to;
+        fb.locked[v] = 1;
+      }
+      int32_t c = g.vw[v];
+      if (from == 0) { W0 -= c; W1 += c; } else { W1 -= c; W0 += c; }
+      cut -= gv;
+      for (int32_t q = g.xadj[v] + lane; q < g.xadj[v + 1]; q += 32) {
+        int32_t x = g.adj[q];
+        if (side[x] == to) fb.gain[x] -= 2 * g.ew[q];
+        else fb.gain[x] += 2 * g.ew[q];
+      }
+      __syncwarp();
+      if (lane == 0) {
+        fb.gain[v] = -gv;
+        fb.moves[nsteps] = v;
+      }
+      ++nsteps;
+      __syncwarp();
+      int32_t inf;
+      int64_t ov;
+      mk(inf, ov);
+      if (fm_less(inf, ov, cut, binf, bov, bcut)) {
+        binf = inf;
+        bov = ov;
+        bcut = cut;
+        best_step = nsteps;
+      }
+      if (nsteps - best_step >= A.fm_stop) break;
+    }
+    for (int32_t i = best_step + lane; i < nsteps; i += 32) side[fb.moves[i]] ^= 1;
+    __syncwarp();
+    cut = bcut;
+    if (best_step == 0) break;
+  }
+  return cut;
+}
+
+// portfolio initial bipartition by one warp: algo 0 random, 1 BFS, 2 GGG
+__device__ void warp_initial(int algo, const LG &g, int32_t t0, uint64_t key, int32_t *side,
+                             uint64_t *oh, int32_t *ov, int32_t *gain, int32_t *vis, int32_t *queue) {
+  int lane = threadIdx.x & 31;
+  int32_t n = g.n;
+  int32_t P = pow2_at_least(n > 1 ? n : 2);
+  for (int32_t i = lane; i < P; i += 32) {
+    if (i < n) {
+      oh[i] = key_step(key, (uint64_t)(uint32_t)i);
+      ov[i] = i;
+    } else {
+      oh[i] = ~0ull;
+      ov[i] = INT32_MAX;
+    }
+  }
+  for (int32_t v = lane; v < n; v += 32) side[v] = 1;
+  __syncwarp();
+  warp_bitonic_hv(oh, ov, P);
+  if (algo == 0) {
+    if (lane == 0) {
+      int64_t W0 = 0;
+      for (int32_t i = 0; i < n; ++i) {
+        int32_t v = ov[i];
+        if (W0 + g.vw[v] <= t0) {
+          side[v] = 0;
+          W0 += g.vw[v];
+        }
+      }
+    }
+  } else if (algo == 1) {
+    for (int32_t v = lane; v < n; v += 32) vis[v] = 0;
+    __syncwarp();
+    if (lane == 0) {
+      int64_t W0 = 0;
+      int32_t qh = 0, qt = 0, nr = 0;
+      while (qh < n) {
+        if (qh == qt) {
+          while (vis[ov[nr]]) ++nr;
+          vis[ov[nr]] = 1;
+          queue[qt++] = ov[nr];
+        }
+        int32_t v = queue[qh++];
+        if (W0 + g.vw[v] <= t0) {
+          side[v] = 0;
+          W0 += g.vw[v];
+        }
+        for (int32_t q = g.xadj[v]; q < g.xadj[v + 1]; ++q) {
+          int32_t x = g.adj[q];
+          if (!vis[x]) {
+            vis[x] = 1;
+            queue[qt++] = x;
+          }
+        }
+      }
+    }
+  } else {
+    for (int32_t v = lane; v < n; v += 32) {
+      int32_t s = 0;
+      for (int32_t q = g.xadj[v]; q < g.xadj[v + 1]; ++q) s -= g.ew[q];
+      gain[v] = s;
+    }
+    __syncwarp();
+    int64_t W0 = 0;
+    int32_t v = (n > 0 && g.vw[ov[0]] <= t0) ? ov[0] : -1;
+    for (;;) {
+      if (v >= 0) {
+        if (lane == 0) side[v] = 0;
+        W0 += g.vw[v];
+        for (int32_t q = g.xadj[v] + lane; q < g.xadj[v + 1]; q += 32) gain[g.adj[q]] += 2 * g.ew[q];
+        __syncwarp();
+      }
+      uint64_t best = 0;
+      for (int32_t x = lane; x < n; x += 32) {
+        if (side[x] == 0 || W0 + g.vw[x] > t0) continue;
+        uint64_t k = ((uint64_t)((uint32_t)gain[x] ^ 0x80000000u) << 32) | (0xFFFFFFFFu - (uint32_t)x);
+        best = k > best ? k : best;
+      }
+      best = group_max64<32>(best);
+      if (best == 0) break;
+      v = (int32_t)(0xFFFFFFFFu - (uint32_t)best);
+    }
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ int32_t level_cap(int32_t L, int32_t t, int32_t maxc) {
+  int64_t b = (int64_t)t + maxc;
+  return b > L ? (int32_t)b : L;
+}
+
+__device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *wvals) {
+  __shared__ LG lv[IP_MAXL + 1];
+  __shared__ int32_t *maps[IP_MAXL + 1];
+  __shared__ int32_t s_nl;
+  __shared__ int64_t s_wk[IPW][3];
+  __shared__ int32_t s_wrep[IPW];
+  const ItemDesc D = A.items[it];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (D.n == 0) return;
+  Bump B{A.scratch + D.sbase, D.ssize, 0, false};
+  int32_t n0 = D.n;
+  int32_t *x0 = B.take(n0 + 1);
+  if (B.oom) {
+    if (threadIdx.x == 0) atomicExch(A.oom, 1);
+    return;
+  }
+  const int64_t eb = A.gx[D.vbase];
+  for (int32_t v = threadIdx.x; v <= n0; v += IPT) x0[v] = (int32_t)(A.gx[D.vbase + v] - eb);
+  int64_t cB = 0;
+  int32_t md = 0, mc = 0;
+  for (int32_t v = threadIdx.x; v < n0; v += IPT) {
+    cB += A.svw[D.vbase + v];
+    md = max(md, (int32_t)(A.gx[D.vbase + v + 1] - A.gx[D.vbase + v]));
+    mc = max(mc, A.svw[D.vbase + v]);
+  }
+  cB = block_sum64(cB);
+  md = block_max32(md);
+  mc = block_max32(mc);
+  if (threadIdx.x == 0) {
+    LG g0;
+    g0.n = n0;
+    g0.m = D.m;
+    g0.xadj = x0;
+    g0.adj = const_cast<int32_t *>(A.sadj + eb);
+    g0.ew = const_cast<int32_t *>(A.sew + eb);
+    g0.vw = const_cast<int32_t *>(A.svw + D.vbase);
+    g0.maxdeg = md;
+    g0.maxc = mc;
+    lv[0] = g0;
+    s_nl = 1;
+  }
+  __syncthreads();
+  // 1. coarsen
+  uint64_t lpkey = key_step(D.key, DOM_IP_LP);
+  int32_t nl = 1;
+  while (nl < IP_MAXL) {
+    LG g = lv[nl - 1];
+    if (g.n <= 1) break;
+    int64_t UB = cB / A.ip_C;
+    if (UB < g.maxc) UB = g.maxc;
+    if (UB < 1) UB = 1;
+    int32_t *label = B.take(g.n);
+    if (B.oom) break;
+    int32_t nc = item_cluster(A, g, (int32_t)UB, key_step(lpkey, (uint64_t)(nl - 1)), label, B, wkeys, wvals);
+    if (B.oom) break;
+    if (nc == g.n) break;
+    int32_t *map = B.take(g.n);
+    LG c;
+    item_contract(g, label, map, &c, B);
+    if (B.oom) break;
+    int32_t cmd = 0, cmc = 0;
+    for (int32_t x = threadIdx.x; x < c.n; x += IPT) {
+      cmd = max(cmd, c.xadj[x + 1] - c.xadj[x]);
+      cmc = max(cmc, c.vw[x]);
+    }
+    cmd = block_max32(cmd);
+    cmc = block_max32(cmc);
+    c.maxdeg = cmd;
+    c.maxc = cmc;
+    if (threadIdx.x == 0) {
+      lv[nl] = c;
+      maps[nl - 1] = map;
+    }
+    __syncthreads();
+    ++nl;
+    if ((int64_t)A.conv_den * c.n > (int64_t)A.conv_num * g.n) break;
+  }
+  if (B.oom) {
+    if (threadIdx.x == 0) atomicExch(A.oom, 1);
+    return;
+  }
+  // 2. portfolio on the coarsest level, one warp per repetition
+  LG h = lv[nl - 1];
+  int32_t nH = h.n;
+  int32_t PH = pow2_at_least(nH > 1 ? nH : 2);
+  int32_t hL0 = level_cap(D.L0, D.t0, h.maxc), hL1 = level_cap(D.L1, D.t1, h.maxc);
+  int64_t per_warp = 8ll * nH + 3ll * PH + 16;  // even: keeps every warp's 64-bit area aligned
+  int32_t *wbuf = B.take(per_warp * IPW);
+  int32_t *fin = B.take(nH);
+  if (B.oom) {
+    if (threadIdx.x == 0) atomicExch(A.oom, 1);
+    return;
+  }
+  {
+    int32_t *base = wbuf + per_warp * w;
+    int32_t *side = base;
+    int32_t *best = side + nH;
+    int32_t *gain = best + nH;
+    int32_t *locked = gain + nH;
+    int32_t *moves = locked + nH;
+    int32_t *queue = moves + nH;
+    int32_t *ov = queue + nH;
+    uint64_t *oh = reinterpret_cast<uint64_t *>(ov + PH);  // offset 6 nH + PH: even
+    int32_t reps[3] = {A.rep_random, A.rep_bfs, A.rep_ggg};
+    uint64_t doms[3] = {DOM_RANDOM, DOM_BFS, DOM_GGG};
+    int32_t R = reps[0] + reps[1] + reps[2];
+    bool have = false;
+    int32_t binf = 0, brep = -1;
+    int64_t bov = 0, bcut = 0;
+    for (int32_t q = w; q < R; q += IPW) {
+      int a = q < reps[0] ? 0 : (q < reps[0] + reps[1] ? 1 : 2);
+      int32_t r = a == 0 ? q : (a == 1 ? q - reps[0] : q - reps[0] - reps[1]);
+      uint64_t key = key_step(key_step(D.key, doms[a]), (uint64_t)r);
+      warp_initial(a, h, D.t0, key, side, oh, ov, gain, locked, queue);
+      FMBuf fb{gain, locked, moves};
+      int64_t cut = warp_fm(A, h, side, hL0, hL1, fb);
+      int64_t W0 = 0, W1 = 0;
+      for (int32_t v = lane; v < nH; v += 32) {
+        if (side[v] == 0) W0 += h.vw[v];
+        else W1 += h.vw[v];
+      }
+      W0 = warp_sum64(W0);
+      W1 = warp_sum64(W1);
+      int64_t o0 = W0 - hL0, o1 = W1 - hL1;
+      int64_t o = o0 > o1 ? o0 : o1;
+      int32_t inf = o > 0;
+      int64_t ovv = inf ? o : 0;
+      if (!have || fm_less(inf, ovv, cut, binf, bov, bcut)) {
+        have = true;
+        binf = inf;
+        bov = ovv;
+        bcut = cut;
+        brep = q;
+        for (int32_t v = lane; v < nH; v += 32) best[v] = side[v];
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      s_wk[w][0] = have ? binf : 2;
+      s_wk[w][1] = bov;
+      s_wk[w][2] = bcut;
+      s_wrep[w] = have ? brep : INT32_MAX;
+    }
+  }
+  __syncthreads();
+  __shared__ int32_t s_bw;
+  if (threadIdx.x == 0) {
+    int32_t bw_ = 0;
+    for (int32_t x = 1; x < IPW; ++x) {
+      bool better = fm_less((int32_t)s_wk[x][0], s_wk[x][1], s_wk[x][2], (int32_t)s_wk[bw_][0],
+                            s_wk[bw_][1], s_wk[bw_][2]);
+      bool tie = !better && !fm_less((int32_t)s_wk[bw_][0], s_wk[bw_][1], s_wk[bw_][2],
+                                     (int32_t)s_wk[x][0], s_wk[x][1], s_wk[x][2]);
+      if (better || (tie && s_wrep[x] < s_wrep[bw_])) bw_ = x;
+    }
+    s_bw = bw_;
+  }
+  __syncthreads();
+  {
+    int32_t *bsrc = wbuf + per_warp * s_bw + nH;
+    for (int32_t v = threadIdx.x; v < nH; v += IPT) fin[v] = bsrc[v];
+  }
+  __syncthreads();
+  // 3. uncoarsen with FM on every level (warp 0)
+  int32_t *cur = fin;
+  int32_t *fmbuf = B.take(3ll * n0);
+  if (B.oom) {
+    if (threadIdx.x == 0) atomicExch(A.oom, 1);
+    return;
+  }
+  FMBuf fb{fmbuf, fmbuf + n0, fmbuf + 2ll * n0};
+  for (int32_t l = nl - 2; l >= 0; --l) {
+    LG g = lv[l];
+    int32_t *fine = B.take(g.n);
+    if (B.oom) {
+      if (threadIdx.x == 0) atomicExch(A.oom, 1);
+      return;
+    }
+    const int32_t *map = maps[l];
+    for (int32_t v = threadIdx.x; v < g.n; v += IPT) fine[v] = cur[map[v]];
+    __syncthreads();
+    if (w == 0) warp_fm(A, g, fine, level_cap(D.L0, D.t0, g.maxc), level_cap(D.L1, D.t1, g.maxc), fb);
+    __syncthreads();
+    cur = fine;
+  }
+  for (int32_t v = threadIdx.x; v < n0; v += IPT) A.side_out[D.vbase + v] = cur[v];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(IPT) k_ip_items(IPArgs A) {
+  __shared__ int32_t wkeys[IPW * IP_WTAB];
+  __shared__ int32_t wvals[IPW * IP_WTAB];
+  __shared__ int32_t s_it;
+  for (;;) {
+    if (threadIdx.x == 0) s_it = atomicAdd(A.queue, 1);
+    __syncthreads();
+    int32_t q = s_it;
+    __syncthreads();
+    if (q >= A.nitems) break;
+    run_item(A, A.order[q], wkeys, wvals);
+  }
+}
+
+// ------------------------------------------------------ extraction (host side kernels)
+__global__ void k_block_keys(int32_t n, const int32_t *part, int bits, uint64_t *keys) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    keys[v] = ((uint64_t)(uint32_t)part[v] << bits) | (uint64_t)v;
+}
+
+__global__ void k_block_stats(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
+                              const int32_t *part, const uint64_t *keys, uint64_t mask, int32_t *members,
+                              int32_t *bcount, unsigned long long *bweight, int32_t *ideg,
+                              unsigned long long *becount) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v = (int32_t)(keys[i] & mask);
+    members[i] = v;
+    int32_t b = part[v];
+    atomicAdd(&bcount[b], 1);
+    atomicAdd(&bweight[b], (unsigned long long)(vw ? vw[v] : 1));
+    int32_t d = 0;
+    for (int64_t q = xadj[v]; q < xadj[v + 1]; ++q) d += (part[adj[q]] == b);
+    ideg[i] = d;
+    atomicAdd(&becount[b], (unsigned long long)d);
+  }
+}
+
+__global__ void k_local_ids(int32_t n, const int32_t *members, const int32_t *part, const int32_t *boff,
+                            int32_t *loc) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v = members[i];
+    loc[v] = (int32_t)(i - boff[part[v]]);
+  }
+}
+
+__global__ void k_fill_sub(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
+                           const int32_t *ew, const int32_t *part, const int32_t *members,
+                           const int32_t *loc, const int64_t *gx, int32_t *sadj, int32_t *sew,
+                           int32_t *svw) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v = members[i];
+    int32_t b = part[v];
+    svw[i] = vw ? vw[v] : 1;
+    int64_t o = gx[i];
+    for (int64_t q = xadj[v]; q < xadj[v + 1]; ++q) {
+      int32_t u = adj[q];
+      if (part[u] != b) continue;
+      sadj[o] = loc[u];
+      sew[o] = ew ? ew[q] : 1;
+      ++o;
+    }
+  }
+}
+
+__global__ void k_set_last(int64_t *a, int64_t idx, const int64_t *v) { a[idx] = *v; }
+
+__global__ void k_write_parts(int32_t n, const int32_t *members, const int32_t *part_old,
+                              const int32_t *newid, const int32_t *split, const int32_t *side,
+                              int32_t *part) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v = members[i];
+    int32_t b = part_old[v];
+    part[v] = newid[b] + (split[b] ? side[i] : 0);
+  }
+}
+
 int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::vector<int32_t> &f,
                            double eps, int64_t cV, int32_t k, uint64_t roundkey, int32_t *items_out) {
-  fail(KMP_ERR_UNSUPPORTED, "bipartitioner not built yet");
+  Context &C = ctx();
+  const kmp_config &cfg = C.cfg;
+  cudaStream_t s = C.stream;
+  int32_t n = g.n;
+  // new ids, child final counts
+  std::vector<int32_t> newid(nblocks), split(nblocks), nf;
+  int32_t nn = 0;
+  for (int32_t b = 0; b < nblocks; ++b) {
+    newid[b] = nn;
+    if (f[b] >= 2) {
+      split[b] = 1;
+      nf.push_back(f[b] / 2);
+      nf.push_back(f[b] - f[b] / 2);
+      nn += 2;
+    } else {
+      split[b] = 0;
+      nf.push_back(f[b]);
+      nn += 1;
+    }
+  }
+  if (items_out) *items_out = 0;
+  if (n == 0) {
+    f = nf;
+    return nn;
+  }
+  int bitsN = 1;
+  while ((1ll << bitsN) < (int64_t)n) ++bitsN;
+  int bitsB = 1;
+  while ((1ll << bitsB) < (int64_t)nblocks) ++bitsB;
+  int grid = grid_for(n, 256);
+  DBuf<uint64_t> keys(n), tmp(n);
+  k_block_keys<<<grid, 256, 0, s>>>(n, part, bitsN, keys);
+  KMP_LAUNCHED("block_keys");
+  radix_sort_u64(keys, tmp, n, bitsN + bitsB);
+  DBuf<int32_t> members(n), bcount(nblocks + 1), ideg(n), boff(nblocks + 1), loc(n);
+  DBuf<unsigned long long> bweight(nblocks), becount(nblocks);
+  bcount.zero();
+  bweight.zero();
+  becount.zero();
+  k_block_stats<<<grid, 256, 0, s>>>(n, g.xadj, g.adj, g.vw, part, keys, (1ull << bitsN) - 1ull, members,
+                                     bcount, bweight, ideg, becount);
+  KMP_LAUNCHED("block_stats");
+  scan_excl_i32(bcount, boff, nblocks + 1, nullptr);
+  k_local_ids<<<grid, 256, 0, s>>>(n, members, part, boff, loc);
+  KMP_LAUNCHED("local_ids");
+  DBuf<int64_t> gx(n + 1), etot(1);
+  scan_excl_i32_to_i64(ideg, gx, n, etot);
+  k_set_last<<<1, 1, 0, s>>>(gx, n, etot);
+  KMP_LAUNCHED("set_last");
+  int64_t E = read1(etot.p);
+  DBuf<int32_t> sadj(E), sew(E), svw(n);
+  k_fill_sub<<<grid, 256, 0, s>>>(n, g.xadj, g.adj, g.vw, g.ew, part, members, loc, gx, sadj, sew, svw);
+  KMP_LAUNCHED("fill_sub");
+  std::vector<int32_t> hcount(nblocks + 1), hoff(nblocks + 1);
+  std::vector<unsigned long long> hw(nblocks), he(nblocks);
+  to_host(hcount.data(), bcount.p, nblocks);
+  to_host(hoff.data(), boff.p, nblocks + 1);
+  to_host(hw.data(), bweight.p, nblocks);
+  to_host(he.data(), becount.p, nblocks);
+  // item descriptors
+  std::vector<ItemDesc> items;
+  int64_t ebase = 0;
+  for (int32_t b = 0; b < nblocks; ++b) {
+    int64_t eb = ebase;
+    ebase += (int64_t)he[b];
+    if (!split[b] || hcount[b] == 0) continue;
+    if (hcount[b] > IP_MAX_N)
+      fail(KMP_ERR_UNSUPPORTED, "block of " + std::to_string(hcount[b]) +
+                                    " nodes exceeds the bipartitioner's item limit");
+    ItemDesc d{};
+    d.vbase = hoff[b];
+    d.ebase = eb;
+    d.n = hcount[b];
+    d.m = (int32_t)he[b];
+    split_caps(eps, cV, k, (int64_t)hw[b], f[b], &d.t0, &d.t1, &d.L0, &d.L1);
+    d.key = key_step(roundkey, (uint64_t)b);
+    items.push_back(d);
+  }
+  if (items_out) *items_out = (int32_t)items.size();
+  DBuf<int32_t> side(n);
+  side.zero();
+  if (!items.empty()) {
+    // largest items first (work queue order does not change results)
+    std::vector<int32_t> order(items.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b2) {
+      return (int64_t)items[a].n + items[a].m > (int64_t)items[b2].n + items[b2].m;
+    });
+    DBuf<int32_t> dorder(items.size()), q(2);
+    to_dev(dorder.p, order.data(), order.size());
+    int64_t mult = 1;
+    for (int attempt = 0; attempt < 6; ++attempt, mult *= 4) {
+      int64_t total = 0;
+      for (auto &d : items) {
+        int64_t nP = next_pow2((uint64_t)std::max(d.n, 2));
+        int64_t mP = next_pow2((uint64_t)std::max(d.m, 2));
+        d.sbase = total;
+        d.ssize = mult * (96ll * d.n + 64ll * nP + 16ll * d.m + 8ll * mP + 2048);
+        total += d.ssize;
+      }
+      DBuf<ItemDesc> ditems(items.size());
+      DBuf<int32_t> scratch(total);
+      to_dev(ditems.p, items.data(), items.size());
+      q.zero();
+      IPArgs A;
+      A.items = ditems;
+      A.order = dorder;
+      A.nitems = (int32_t)items.size();
+      A.queue = q.p;
+      A.oom = q.p + 1;
+      A.gx = gx;
+      A.sadj = sadj;
+      A.sew = sew;
+      A.svw = svw;
+      A.side_out = side;
+      A.scratch = scratch;
+      A.S = cfg.subrounds;
+      A.ip_C = cfg.ip_C;
+      A.ip_lp_rounds = cfg.ip_lp_rounds;
+      A.rep_random = cfg.rep_random;
+      A.rep_bfs = cfg.rep_bfs;
+      A.rep_ggg = cfg.rep_ggg;
+      A.fm_passes = cfg.fm_passes;
+      A.fm_stop = cfg.fm_stop;
+      A.conv_num = cfg.conv_num;
+      A.conv_den = cfg.conv_den;
+      int gridip = (int)std::min<int64_t>((int64_t)items.size(), (int64_t)C.sms * 4);
+      k_ip_items<<<gridip, IPT, 0, s>>>(A);
+      KMP_LAUNCHED("ip_items");
+      int32_t oom = 0;
+      to_host(&oom, q.p + 1, 1);
+      if (!oom) break;
+      if (attempt == 5) fail(KMP_ERR_NOMEM, "bipartitioner scratch could not be sized");
+    }
+  }
+  DBuf<int32_t> dnew(nblocks), dsplit(nblocks), old(n);
+  to_dev(dnew.p, newid.data(), nblocks);
+  to_dev(dsplit.p, split.data(), nblocks);
+  KMP_CUDA(cudaMemcpyAsync(old.p, part, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  k_write_parts<<<grid, 256, 0, s>>>(n, members, old, dnew, dsplit, side, part);
+  KMP_LAUNCHED("write_parts");
+  f = nf;
+  return nn;
+}
+
+// ================================================================ balance
+// Section 4.3 "Balancing", deterministic reading: overloaded blocks in
+// ascending id; candidates ordered by exact relative gain (d*c if d >= 0,
+// d/c if d < 0; d = best admissible connectivity minus own connectivity),
+// ties by id; at its turn a node moves to the admissible block of largest
+// connectivity (ties lowest id), recomputed then, until the block fits.
+constexpr int BT = 1024;
+constexpr int BW = BT / 32;
+
+struct BalArgs {
+  int32_t n, k;
+  const int64_t *xadj;
+  const int32_t *adj;
+  const int32_t *vw;
+  const int32_t *ew;
+  int32_t *part;
+  int64_t *bw;
+  const int32_t *cap;
+  int32_t *cand_v;     // [n]
+  int64_t *cand_d;     // [n]
+  int32_t *cand_c;     // [n]
+  int32_t *slack;      // [k] sorted scratch
+  int32_t *tabk;       // per-warp global tables
+  int32_t *tabv;
+  uint32_t tcap;
+  unsigned long long *moved;
+};
+
+// connectivity aggregation of v by one warp into its table; returns conn(own)
+__device__ int64_t bal_conn(const BalArgs &A, int32_t v, int32_t *K, int32_t *V, uint32_t &mask) {
+  int lane = threadIdx.x & 31;
+  int64_t b = A.xadj[v], e = A.xadj[v + 1];
+  uint32_t cap = 32;
+  while ((int64_t)cap < 2 * (e - b)) cap <<= 1;
+  mask = cap - 1;
+  for (uint32_t i = lane; i < cap; i += 32) {
+    K[i] = HT_EMPTY;
+    V[i] = 0;
+  }
+  __syncwarp();
+  for (int64_t q = b + lane; q < e; q += 32) ht_add(K, V, mask, A.part[A.adj[q]], A.ew ? A.ew[q] : 1);
+  __syncwarp();
+  return ht_get(K, V, mask, A.part[v]);
+}
+
+// number of blocks (other than B) whose slack >= c, using sorted slacks
+__device__ int32_t count_fit(const BalArgs &A, int64_t c) {
+  int32_t lo = 0, hi = A.k;  // first index with slack >= c
+  while (lo < hi) {
+    int32_t mid = (lo + hi) >> 1;
+    if ((int64_t)A.slack[mid] >= c) hi = mid;
+    else lo = mid + 1;
+  }
+  return A.k - lo;
+}
+
+__device__ bool rg_before(int64_t d1, int64_t c1, int32_t v1, int64_t d2, int64_t c2, int32_t v2) {
+  bool s1 = d1 >= 0, s2 = d2 >= 0;
+  if (s1 != s2) return s1;
+  if (s1) {
+    int64_t p = d1 * c1, q = d2 * c2;
+    if (p != q) return p > q;
+  } else {
+    int64_t p = d1 * c2, q = d2 * c1;
+    if (p != q) return p > q;
+  }
+  return v1 < v2;
+}
+
+__global__ void __launch_bounds__(BT) k_balance(BalArgs A) {
+  __shared__ int32_t s_nc;
+  __shared__ int32_t s_target;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t *K = A.tabk + (int64_t)w * A.tcap, *V = A.tabv + (int64_t)w * A.tcap;
+  for (int32_t B = 0; B < A.k; ++B) {
+    if (A.bw[B] <= A.cap[B]) continue;
+    // sorted slacks (cap - weight) of all blocks; B itself is overloaded (negative)
+    int32_t Pk = 1;
+    while (Pk < A.k) Pk <<= 1;
+    for (int32_t i = threadIdx.x; i < Pk; i += BT)
+      A.slack[i] = i < A.k ? (int32_t)((int64_t)A.cap[i] - A.bw[i] < INT32_MIN ? INT32_MIN : (int64_t)A.cap[i] - A.bw[i]) : INT32_MAX;
+    __syncthreads();
+    for (int32_t kk = 2; kk <= Pk; kk <<= 1)
+      for (int32_t j = kk >> 1; j > 0; j >>= 1) {
+        for (int32_t i = threadIdx.x; i < Pk; i += BT) {
+          int32_t l = i ^ j;
+          if (l > i) {
+            int32_t x = A.slack[i], y = A.slack[l];
+            if ((x > y) == ((i & kk) == 0)) {
+              A.slack[i] = y;
+              A.slack[l] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    // candidates
+    if (threadIdx.x == 0) s_nc = 0;
+    __syncthreads();
+    for (int32_t v = w; v < A.n; v += BW) {
+      if (A.part[v] != B) continue;
+      uint32_t mask;
+      int64_t cown = bal_conn(A, v, K, V, mask);
+      int64_t c = A.vw ? A.vw[v] : 1;
+      int64_t best = -1;
+      int32_t nadj = 0;
+      for (uint32_t i = lane; i <= mask; i += 32) {
+        int32_t b = K[i];
+        if (b == HT_EMPTY || b == B) continue;
+        if (A.bw[b] + c > A.cap[b]) continue;
+        ++nadj;
+        if (V[i] > best) best = V[i];
+      }
+#pragma unroll
+      for (int m = 16; m > 0; m >>= 1) {
+        int64_t o = (int64_t)shfl_xor64((uint64_t)best, m);
+        best = o > best ? o : best;
+        nadj += __shfl_xor_sync(0xFFFFFFFFu, nadj, m);
+      }
+      if (count_fit(A, c) > nadj && best < 0) best = 0;  // a non-adjacent admissible block
+      if (lane == 0 && best >= 0) {
+        int32_t p = atomicAdd(&s_nc, 1);
+        A.cand_v[p] = v;
+        A.cand_d[p] = best - cown;
+        A.cand_c[p] = (int32_t)c;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    int32_t nc = s_nc;
+    int32_t P = 1;
+    while (P < nc) P <<= 1;
+    for (int32_t i = nc + threadIdx.x; i < P; i += BT) {
+      A.cand_v[i] = INT32_MAX;
+      A.cand_d[i] = (int64_t)INT32_MIN;  // sorts after every real candidate; products stay < 2^63
+      A.cand_c[i] = 1;
+    }
+    __syncthreads();
+    for (int32_t kk = 2; kk <= P; kk <<= 1)
+      for (int32_t j = kk >> 1; j > 0; j >>= 1) {
+        for (int32_t i = threadIdx.x; i < P; i += BT) {
+          int32_t l = i ^ j;
+          if (l > i) {
+            bool before = rg_before(A.cand_d[l], A.cand_c[l], A.cand_v[l], A.cand_d[i], A.cand_c[i], A.cand_v[i]);
+            if (before == ((i & kk) == 0)) {
+              int32_t tv = A.cand_v[i]; A.cand_v[i] = A.cand_v[l]; A.cand_v[l] = tv;
+              int64_t td = A.cand_d[i]; A.cand_d[i] = A.cand_d[l]; A.cand_d[l] = td;
+              int32_t tc = A.cand_c[i]; A.cand_c[i] = A.cand_c[l]; A.cand_c[l] = tc;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    // moves in order (warp 0); fallback scan for the lowest admissible block uses all warps
+    for (int32_t i = 0; i < nc; ++i) {
+      if (A.bw[B] <= A.cap[B]) break;
+      int32_t v = A.cand_v[i];
+      int64_t c = A.cand_c[i];
+      if (w == 0) {
+        uint32_t mask;
+        bal_conn(A, v, K, V, mask);
+        uint64_t bestk = 0;  // (conn, ~block)
+        for (uint32_t x = lane; x <= mask; x += 32) {
+          int32_t b = K[x];
+          if (b == HT_EMPTY || b == B) continue;
+          if (A.bw[b] + c > A.cap[b]) continue;
+          uint64_t kk2 = ((uint64_t)(uint32_t)V[x] << 32) | (0xFFFFFFFFu - (uint32_t)b);
+          bestk = kk2 > bestk ? kk2 : bestk;
+        }
+        bestk = group_max64<32>(bestk);
+        if (lane == 0) s_target = bestk ? (int32_t)(0xFFFFFFFFu - (uint32_t)bestk) : -1;
+      }
+      __syncthreads();
+      if (s_target < 0) {
+        // no admissible adjacent block: lowest-id admissible block overall
+        __shared__ int32_t s_low;
+        if (threadIdx.x == 0) s_low = INT32_MAX;
+        __syncthreads();
+        for (int32_t b = threadIdx.x; b < A.k; b += BT)
+          if (b != B && A.bw[b] + c <= A.cap[b]) atomicMin(&s_low, b);
+        __syncthreads();
+        if (threadIdx.x == 0) s_target = s_low == INT32_MAX ? -1 : s_low;
+        __syncthreads();
+      }
+      int32_t t = s_target;
+      if (threadIdx.x == 0 && t >= 0) {
+        A.part[v] = t;
+        A.bw[B] -= c;
+        A.bw[t] += c;
+        atomicAdd(A.moved, 1ull);
+      }
+      __syncthreads();
+    }
+  }
 }
 
 int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *part) {
-  fail(KMP_ERR_UNSUPPORTED, "balancer not built yet");
+  cudaStream_t s = ctx().stream;
+  DBuf<int64_t> bw(k), cut(1);
+  cut_and_weights(g, part, k, bw, cut);
+  std::vector<int64_t> hbw(k);
+  to_host(hbw.data(), bw.p, k);
+  bool over = false;
+  for (int32_t b = 0; b < k; ++b)
+    if (hbw[b] > caps_host[b]) over = true;
+  if (!over) return 0;
+  int32_t Pk = (int32_t)next_pow2((uint64_t)std::max(k, 1));
+  int64_t P = (int64_t)next_pow2((uint64_t)std::max(g.n, 1));
+  DBuf<int32_t> cap(k), cand_v(P), cand_c(P), slack(Pk);
+  DBuf<int64_t> cand_d(P);
+  uint32_t tcap = 32;
+  while ((int64_t)tcap < 2 * g.maxdeg) tcap <<= 1;
+  DBuf<int32_t> tk((int64_t)tcap * BW), tv((int64_t)tcap * BW);
+  DBuf<unsigned long long> moved(1);
+  moved.zero();
+  to_dev(cap.p, caps_host, k);
+  BalArgs A;
+  A.n = g.n;
+  A.k = k;
+  A.xadj = g.xadj;
+  A.adj = g.adj;
+  A.vw = g.vw;
+  A.ew = g.ew;
+  A.part = part;
+  A.bw = bw;
+  A.cap = cap;
+  A.cand_v = cand_v;
+  A.cand_d = cand_d;
+  A.cand_c = cand_c;
+  A.slack = slack;
+  A.tabk = tk;
+  A.tabv = tv;
+  A.tcap = tcap;
+  A.moved = moved;
+  k_balance<<<1, BT, 0, s>>>(A);
+  KMP_LAUNCHED("balance");
+  return (int64_t)read1(moved.p);
 }
 
 }  // namespace kmp

@@ -111,6 +111,9 @@ __global__ void __launch_bounds__(256) k_bin_count(LPArgs A, int32_t *cnt, int64
   __syncthreads();
   int64_t base = (int64_t)blockIdx.x * BIN_TILE;
   unsigned long long my = 0;
+  __shared__ unsigned long long sdeg[8];
+  if (threadIdx.x < 8) sdeg[threadIdx.x] = 0;
+  __syncthreads();
   for (int i = threadIdx.x; i < BIN_TILE; i += blockDim.x) {
     int64_t v = base + i;
     if (v >= A.n || !A.act[v]) continue;
@@ -118,12 +121,14 @@ __global__ void __launch_bounds__(256) k_bin_count(LPArgs A, int32_t *cnt, int64
     if (d == 0) continue;
     int s = (int)(key_step(A.rk, (uint64_t)(uint32_t)v) & (uint64_t)(A.S - 1));
     atomicAdd(&c[s * NB + deg_bin(d)], 1);
+    atomicAdd(&sdeg[s], (unsigned long long)d);
     my += (unsigned long long)d;
   }
   atomicAdd(&scanned, my);
   __syncthreads();
   for (int i = threadIdx.x; i < A.S * NB; i += blockDim.x) cnt[(int64_t)i * ntiles + blockIdx.x] = c[i];
   if (threadIdx.x == 0) atomicAdd(&A.ctr64[0], scanned);
+  if (threadIdx.x < A.S && sdeg[threadIdx.x]) atomicAdd(&A.ctr64[2 + threadIdx.x], sdeg[threadIdx.x]);
 }
 
 __global__ void k_bin_boff(LPArgs A, const int32_t *off, const int32_t *total, int64_t ntiles) {
@@ -525,7 +530,7 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   DBuf<int32_t> vlist(n), boff(S * NB + 1), prop_t(n), prop_g(n), pos_in_t(n);
   DBuf<int32_t> tsum(nlab), tcnt(nlab), tcur(nlab), tslot(nlab);
   DBuf<int32_t> slot_t(n), slot_base(n), bucket(n), ctr(8);
-  DBuf<unsigned long long> ctr64(4);
+  DBuf<unsigned long long> ctr64(2 + 8);  // scanned, moved, per-sub-round degree sums
   DBuf<int32_t> bcnt(S * NB * ntiles), boffs(S * NB * ntiles), btotal(1);
   act.fill_bytes(1);
   act_next.zero();
@@ -579,7 +584,10 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
 
   int grid_rate = 4 * C.sms;
   int grid_commit = grid_for(ceil_div(n, S), 256, 8);
-  unsigned long long h64[4];
+  unsigned long long h64[10];
+  int32_t hboff[8 * NB + 1];
+  std::vector<cudaEvent_t> ev;  // profiling: event pairs around every rating launch
+  std::vector<double> ev_bytes;
   for (int r = 0; r < rounds; ++r) {
     A.rk = key_step(basekey, (uint64_t)r);
     A.rk_hi = (uint32_t)(A.rk >> 32);
@@ -591,13 +599,23 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
     KMP_LAUNCHED("bin_boff");
     k_bin_scatter<<<(unsigned)ntiles, 256, 0, stream>>>(A, boffs, ntiles);
     KMP_LAUNCHED("bin_scatter");
+    size_t ev0 = ev.size();
     for (int s = 0; s < S; ++s) {
+      if (C.profile) {
+        cudaEvent_t a, b;
+        KMP_CUDA(cudaEventCreate(&a));
+        KMP_CUDA(cudaEventCreate(&b));
+        ev.push_back(a);
+        ev.push_back(b);
+        KMP_CUDA(cudaEventRecord(a, stream));
+      }
       k_rate<<<grid_rate, RATE_T, 0, stream>>>(A, s);
       KMP_LAUNCHED("rate");
       if (huge_grid) {
         k_rate_huge<<<huge_grid, RATE_T, 0, stream>>>(A, s);
         KMP_LAUNCHED("rate_huge");
       }
+      if (C.profile) KMP_CUDA(cudaEventRecord(ev.back(), stream));
       k_classify<<<grid_commit, 256, 0, stream>>>(A, s);
       KMP_LAUNCHED("classify");
       k_bucket<<<grid_commit, 256, 0, stream>>>(A, s);
@@ -607,7 +625,19 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
       k_apply<<<grid_commit, 256, 0, stream>>>(A, s);
       KMP_LAUNCHED("apply");
     }
-    to_host(h64, ctr64.p, 2);
+    to_host(h64, ctr64.p, 2 + S);
+    if (C.profile) {
+      // algorithmic bytes of each rating launch: per edge visit adjncy + neighbour
+      // label (+ edge weight); per rated node xadj, list entry, own label,
+      // proposal (target, gain) (+ node weight)
+      to_host(hboff, boff.p, S * NB + 1);
+      for (int s = 0; s < S; ++s) {
+        double V = (double)(hboff[(s + 1) * NB] - hboff[s * NB]);
+        double D = (double)h64[2 + s];
+        ev_bytes.push_back(D * (8.0 + (g.ew ? 4.0 : 0.0)) + V * (24.0 + (g.vw ? 4.0 : 0.0)));
+      }
+      (void)ev0;
+    }
     st->rounds = r + 1;
     st->scanned += (int64_t)h64[0];
     st->moved_total += (int64_t)h64[1];
@@ -623,6 +653,15 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   st->ms = ms;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+    float t = 0;
+    KMP_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+    C.prof_rate_ms += t;
+    C.prof_rate_launches += 1;
+    C.prof_rate_bytes += ev_bytes[i / 2];
+    cudaEventDestroy(ev[i]);
+    cudaEventDestroy(ev[i + 1]);
+  }
 }
 
 // ------------------------------------------------ clustering of one level

@@ -89,6 +89,8 @@ def load():
         "kmp_partition": (ctypes.c_int, [i32, P, P, P, P, i32, dbl, u64, P]),
         "kmp_partition_graph": (ctypes.c_int, [P, i32, dbl, u64, P, P]),
         "kmp_last_stats": (ctypes.c_int, [P]),
+        "kmp_set_profiling": (ctypes.c_int, [ctypes.c_int]),
+        "kmp_profile_read": (ctypes.c_int, [P, P, P, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -288,3 +290,14 @@ def last_stats() -> Stats:
     st = Stats()
     load().kmp_last_stats(ctypes.byref(st))
     return st
+
+
+def set_profiling(on: bool):
+    _check(load().kmp_set_profiling(1 if on else 0))
+
+
+def profile_read(reset: bool = False):
+    """Rating-kernel launch sums since the last reset: (ms, algorithmic bytes, launches)."""
+    ms, by, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    _check(load().kmp_profile_read(ctypes.byref(ms), ctypes.byref(by), ctypes.byref(n), 1 if reset else 0))
+    return ms.value, by.value, n.value

@@ -1,0 +1,168 @@
+"""GPU parity of the batched initial bipartitioner (Algorithm 2 split round),
+k-way balancing and the full deep multilevel partition (Algorithm 1) against
+the CPU oracle, through the C ABI.  Integer outputs: bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2105_02022_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kmp():
+    from paper_2105_02022_gb300 import _build
+    from paper_2105_02022_gb300 import kmp as K
+
+    _build.build_all()
+    O.build()
+    assert torch.cuda.is_available()
+    K.set_config(K.config())
+    return K
+
+
+def _split_case(name):
+    if name == "rgg_root":
+        g = gg.rgg(4096, 8, 3)
+        return g, np.zeros(g.n, np.int32), [8], 8
+    if name == "rgg_16blocks":
+        g = gg.rgg(20000, 8, 4)
+        return g, (np.arange(g.n) * 16 // g.n).astype(np.int32), [2] * 16, 32
+    if name == "weighted_generalk":
+        g = gg.with_weights(gg.rgg(6000, 10, 5), 7, 30, 5)
+        return g, (np.arange(g.n) * 4 // g.n).astype(np.int32), [3, 2, 1, 5], 11
+    if name == "hubs_items":
+        g = gg.hubs(8000, [500, 900], 16000, 7)
+        return g, (np.arange(g.n) % 3).astype(np.int32), [2, 4, 2], 8
+    if name == "tiny_blocks":
+        g = gg.rgg(300, 6, 9)
+        part = np.zeros(g.n, np.int32)
+        part[0] = 1          # a one-node block
+        part[1:3] = 2        # a two-node block; block 3 stays empty
+        return g, part, [2, 2, 2, 2], 8
+    if name == "rmat_blocks":
+        g = gg.rmat(13, 8, 3)
+        rng = np.random.default_rng(3)
+        return g, rng.integers(0, 6, g.n).astype(np.int32), [2, 2, 3, 1, 2, 6], 16
+    raise KeyError(name)
+
+
+SPLITS = ["rgg_root", "rgg_16blocks", "weighted_generalk", "hubs_items", "tiny_blocks", "rmat_blocks"]
+
+
+@pytest.mark.parametrize("name", SPLITS)
+def test_bipartition_blocks_parity(kmp, name):
+    g, part, f, k = _split_case(name)
+    cV = int(g.vw().sum())
+    rk = O.key(5, [3, 1, 0])
+    dg = kmp.DeviceGraph.from_host(g)
+    pt = torch.from_numpy(part).cuda()
+    nb, fo = kmp.bipartition_blocks(dg, len(f), f, 0.03, cV, k, rk, pt)
+    rp, rf = O.bipartition_blocks(g, len(f), f, 0.03, cV, k, rk, part)
+    assert nb == len(rf) and np.array_equal(fo, rf)
+    assert np.array_equal(pt.cpu().numpy(), rp)
+
+
+@pytest.mark.parametrize("cfgkw", [dict(rep_random=1, rep_bfs=0, rep_ggg=0), dict(fm_passes=0),
+                                   dict(ip_lp_rounds=1, subrounds=2), dict(rep_ggg=17, fm_stop=3)])
+def test_bipartition_config_variants(kmp, cfgkw):
+    g, part, f, k = _split_case("rgg_16blocks")
+    kmp.set_config(kmp.config(**cfgkw))
+    try:
+        cV = int(g.vw().sum())
+        dg = kmp.DeviceGraph.from_host(g)
+        pt = torch.from_numpy(part).cuda()
+        kmp.bipartition_blocks(dg, len(f), f, 0.03, cV, k, 77, pt)
+        rp, _ = O.bipartition_blocks(g, len(f), f, 0.03, cV, k, 77, part, cfg=O.config(**cfgkw))
+        assert np.array_equal(pt.cpu().numpy(), rp)
+    finally:
+        kmp.set_config(kmp.config())
+
+
+@pytest.mark.parametrize("case", ["rgg", "weighted", "rmat"])
+def test_balance_parity(kmp, case):
+    if case == "rgg":
+        g = gg.rgg(5000, 8, 3)
+    elif case == "weighted":
+        g = gg.with_weights(gg.rgg(5000, 8, 4), 9, 5, 4)
+    else:
+        g = gg.rmat(13, 8, 5)
+    k = 6
+    part = (np.arange(g.n) * k // g.n).astype(np.int32)
+    part[g.n // 6: g.n // 3] = 0
+    part[g.n // 2: g.n // 2 + 300] = 5
+    cap = np.full(k, int(1.03 * g.vw().sum() / k), np.int64)
+    dg = kmp.DeviceGraph.from_host(g)
+    pt = torch.from_numpy(part).cuda()
+    mv = kmp.balance(dg, k, cap, pt)
+    rp, rmv = O.balance(g, k, cap.astype(np.int32), part)
+    assert mv == rmv and mv > 0
+    assert np.array_equal(pt.cpu().numpy(), rp)
+
+
+PARTS = [
+    ("path", lambda: gg.path(700), [2, 5]),
+    ("grid", lambda: gg.grid(40, 60), [2, 4, 7]),
+    ("rgg15", lambda: gg.workload_rgg_small(1), [8, 3, 64]),
+    ("rgg_w", lambda: gg.with_weights(gg.rgg(12000, 8, 6), 5, 9, 6), [7, 16]),
+    ("rmat14", lambda: gg.rmat(14, 16, 2), [32, 5]),
+    ("hubs", lambda: gg.hubs(30000, [3000, 12000], 60000, 8), [16]),
+]
+
+
+@pytest.mark.parametrize("name,make,ks", PARTS, ids=[p[0] for p in PARTS])
+def test_partition_parity(kmp, name, make, ks):
+    g = make()
+    dg = kmp.DeviceGraph.from_host(g)
+    for k in ks:
+        for seed in (1, 2):
+            part, rc, st = kmp.partition_graph(dg, k, 0.03, seed)
+            rp, rrc, rst = O.partition(g, k, 0.03, seed)
+            got = part.cpu().numpy()
+            assert np.array_equal(got, rp), (name, k, seed)
+            assert rc == rrc and st.cut == rst.cut and st.feasible == rst.feasible
+            assert st.levels == rst.levels
+            assert list(st.level_n[: st.levels]) == list(rst.level_n[: rst.levels])
+
+
+def test_host_partition_entry(kmp):
+    g = gg.rgg(6000, 8, 11)
+    part, rc = kmp.partition(g, 12, 0.05, 4)
+    rp, rrc, _ = O.partition(g, 12, 0.05, 4)
+    assert np.array_equal(part, rp) and rc == rrc == 0
+
+
+def test_partition_edge_cases(kmp):
+    g = gg.rgg(2000, 8, 1)
+    dg = kmp.DeviceGraph.from_host(g)
+    part, rc, st = kmp.partition_graph(dg, 1, 0.03, 1)
+    assert rc == 0 and not part.any().item()
+    # more blocks than nodes
+    small = gg.rgg(40, 6, 2)
+    ds = kmp.DeviceGraph.from_host(small)
+    part, rc, st = kmp.partition_graph(ds, 64, 0.03, 1)
+    rp, rrc, _ = O.partition(small, 64, 0.03, 1)
+    assert np.array_equal(part.cpu().numpy(), rp) and rc == rrc
+    # isolated nodes only
+    iso = gg.Graph(500, np.zeros(501, np.int64), np.zeros(0, np.int32), None, None)
+    di = kmp.DeviceGraph.from_host(iso)
+    part, rc, st = kmp.partition_graph(di, 4, 0.03, 1)
+    rp, rrc, _ = O.partition(iso, 4, 0.03, 1)
+    assert np.array_equal(part.cpu().numpy(), rp) and rc == rrc
+    with pytest.raises(kmp.KmpError):
+        kmp.partition_graph(dg, 0, 0.03, 1)
+    with pytest.raises(kmp.KmpError):
+        kmp.partition_graph(dg, 4, 0.0, 1)
+
+
+def test_full_size_rmat20_k256(kmp):
+    """The R-MAT scale-20, k = 256 workload exactly as the benchmark runs it:
+    partition, cut and balance bit-exact with the oracle."""
+    g = gg.workload_rmat20(1)
+    dg = kmp.DeviceGraph.from_host(g)
+    part, rc, st = kmp.partition_graph(dg, 256, 0.03, 1)
+    rp, rrc, rst = O.partition(g, 256, 0.03, 1)
+    assert np.array_equal(part.cpu().numpy(), rp)
+    assert rc == rrc == 0 and st.cut == rst.cut and st.feasible == 1
