@@ -19,13 +19,15 @@
  *     L_j = floor((1+eps') t_j) (Section 4.2, L_2 = (1+eps') ceil(c(V')/2)).
  *  D4 Block cap L(b) = floor(max((1+eps) c(V) f_b / k, c(V) f_b / k +
  *     max_v c(v))) (Section 2, L_max,k, scaled by the block's final count).
- *  D5 Balancing (Section 4.3): overloaded blocks in ascending id.  Every node
- *     of the block that has an admissible other block gets d = max over
- *     admissible blocks of conn - conn(own) and the relative gain d*c(v)
- *     (d >= 0) or d/c(v) (d < 0), compared exactly.  Nodes are visited in
- *     (relative gain desc, id asc); at its turn a node moves to the admissible
- *     block of largest connectivity (ties: lowest id), recomputed then, until
- *     the block fits.
+ *  D5 Balancing (Section 4.3): one pass over the starting state initialises
+ *     the candidates (the paper's priority-queue initialisation): every node
+ *     of an initially overloaded block that has an admissible other block gets
+ *     d = max over admissible blocks of conn - conn(own) and the relative gain
+ *     d*c(v) (d >= 0) or d/c(v) (d < 0), compared exactly.  Then the
+ *     overloaded blocks are emptied one after the other in ascending id: nodes
+ *     in (relative gain desc, id asc) order, each moved at its turn to the
+ *     admissible block of largest current connectivity (ties: lowest id)
+ *     until the block fits.
  *  D6 Final feasibility uses L_k = floor((1+eps) ceil(c(V)/k)) (Section 2,
  *     footnote; Section 5).
  */
@@ -122,47 +124,69 @@ int64_t kmpo_balance(int32_t n, const int64_t *xadj, const int32_t *adj, const i
                      const int32_t *ew, int32_t k, const int32_t *cap, int32_t *part) {
   int64_t *bw = (int64_t *)calloc((size_t)k, sizeof(int64_t));
   int64_t *conn = (int64_t *)calloc((size_t)k, sizeof(int64_t));
+  char *over = (char *)calloc((size_t)k, 1);
   for (int32_t v = 0; v < n; ++v) bw[part[v]] += vwt(vw, v);
+  int32_t nover = 0;
+  for (int32_t b = 0; b < k; ++b)
+    if (bw[b] > cap[b]) { over[b] = 1; ++nover; }
   rg_t *cand = (rg_t *)malloc(sizeof(rg_t) * (size_t)(n > 0 ? n : 1));
+  int32_t *cb = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
   int64_t moved = 0;
-  for (int32_t B = 0; B < k; ++B) {
-    if (bw[B] <= cap[B]) continue;
-    int32_t nc = 0;
-    for (int32_t v = 0; v < n; ++v) {
-      if (part[v] != B) continue;
-      for (int64_t e = xadj[v]; e < xadj[v + 1]; ++e) conn[part[adj[e]]] += ewt(ew, e);
-      int64_t bestc = -1;
-      for (int32_t b = 0; b < k; ++b) {
-        if (b == B || bw[b] + vwt(vw, v) > cap[b]) continue;
-        if (conn[b] > bestc) bestc = conn[b];
-      }
-      if (bestc >= 0) {
-        cand[nc].d = bestc - conn[B];
-        cand[nc].c = vwt(vw, v);
-        cand[nc].v = v;
-        ++nc;
-      }
-      for (int64_t e = xadj[v]; e < xadj[v + 1]; ++e) conn[part[adj[e]]] = 0;
-      conn[B] = 0;
+  if (nover == 0) goto done;
+  /* initialisation from the starting state: every node of an overloaded block
+   * with an admissible other block becomes a candidate of its block */
+  int32_t nc = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    int32_t B = part[v];
+    if (!over[B]) continue;
+    for (int64_t e = xadj[v]; e < xadj[v + 1]; ++e) conn[part[adj[e]]] += ewt(ew, e);
+    int64_t bestc = -1;
+    for (int32_t b = 0; b < k; ++b) {
+      if (b == B || bw[b] + vwt(vw, v) > cap[b]) continue;
+      if (conn[b] > bestc) bestc = conn[b];
     }
-    qsort(cand, (size_t)nc, sizeof(rg_t), cmp_rg);
-    for (int32_t i = 0; i < nc && bw[B] > cap[B]; ++i) {
-      int32_t v = cand[i].v;
-      for (int64_t e = xadj[v]; e < xadj[v + 1]; ++e) conn[part[adj[e]]] += ewt(ew, e);
-      int32_t t = -1;
-      for (int32_t b = 0; b < k; ++b) {
-        if (b == B || bw[b] + vwt(vw, v) > cap[b]) continue;
-        if (t < 0 || conn[b] > conn[t]) t = b;
-      }
-      for (int64_t e = xadj[v]; e < xadj[v + 1]; ++e) conn[part[adj[e]]] = 0;
-      if (t < 0) continue;
-      part[v] = t;
-      bw[B] -= vwt(vw, v);
-      bw[t] += vwt(vw, v);
-      ++moved;
+    if (bestc >= 0) {
+      cand[nc].d = bestc - conn[B];
+      cand[nc].c = vwt(vw, v);
+      cand[nc].v = v;
+      ++nc;
     }
+    for (int64_t e = xadj[v]; e < xadj[v + 1]; ++e) conn[part[adj[e]]] = 0;
+    conn[B] = 0;
   }
-  free(bw); free(conn); free(cand);
+  /* group by block (stable in id order), then order each group by relative gain */
+  {
+    int32_t *cnt = (int32_t *)calloc((size_t)k + 1, sizeof(int32_t));
+    for (int32_t i = 0; i < nc; ++i) cnt[part[cand[i].v] + 1]++;
+    for (int32_t b = 0; b < k; ++b) cnt[b + 1] += cnt[b];
+    rg_t *tmp = (rg_t *)malloc(sizeof(rg_t) * (size_t)(nc > 0 ? nc : 1));
+    int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+    for (int32_t b = 0; b < k; ++b) pos[b] = cnt[b];
+    for (int32_t i = 0; i < nc; ++i) tmp[pos[part[cand[i].v]]++] = cand[i];
+    for (int32_t B = 0; B < k; ++B) {
+      if (!over[B]) continue;
+      int32_t lo = cnt[B], hi = cnt[B + 1];
+      qsort(tmp + lo, (size_t)(hi - lo), sizeof(rg_t), cmp_rg);
+      for (int32_t i = lo; i < hi && bw[B] > cap[B]; ++i) {
+        int32_t v = tmp[i].v;
+        for (int64_t e = xadj[v]; e < xadj[v + 1]; ++e) conn[part[adj[e]]] += ewt(ew, e);
+        int32_t t = -1;
+        for (int32_t b = 0; b < k; ++b) {
+          if (b == B || bw[b] + vwt(vw, v) > cap[b]) continue;
+          if (t < 0 || conn[b] > conn[t]) t = b;
+        }
+        for (int64_t e = xadj[v]; e < xadj[v + 1]; ++e) conn[part[adj[e]]] = 0;
+        if (t < 0) continue;
+        part[v] = t;
+        bw[B] -= vwt(vw, v);
+        bw[t] += vwt(vw, v);
+        ++moved;
+      }
+    }
+    free(cnt); free(tmp); free(pos);
+  }
+done:
+  free(bw); free(conn); free(cand); free(cb); free(over);
   return moved;
 }
 

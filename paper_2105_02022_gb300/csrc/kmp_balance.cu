@@ -1,0 +1,335 @@
+// k-way balancing (Section 4.3, "Balancing").
+//
+// Deterministic reading: the starting state initialises the candidates of
+// every overloaded block at once (the paper's priority-queue initialisation):
+// a node v of an overloaded block B with some admissible other block gets
+// d = max over admissible blocks of conn(v, b) - conn(v, B) and the relative
+// gain d*c(v) (d >= 0) or d/c(v) (d < 0).  Then the overloaded blocks are
+// emptied in ascending id, candidates in (relative gain desc, id asc) order,
+// each moved at its turn to the admissible block of largest current
+// connectivity (ties: lowest id) until the block fits.
+//
+// GPU mapping: candidates of all overloaded blocks in one full-GPU pass (one
+// warp per node, connectivity in a per-warp hash table); grouping by block
+// with a radix sort of (block, node) keys; one CTA per overloaded block sorts
+// its candidates by the exact rational order; one warp performs the moves in
+// order (each move depends on the weights left by the previous ones).
+#include <algorithm>
+
+#include "kmp_internal.cuh"
+
+namespace kmp {
+
+constexpr int BAL_T = 256;
+constexpr int BAL_W = BAL_T / 32;
+constexpr int BAL_STAB = 512;  // per-warp shared table entries
+
+struct BalArgs {
+  int32_t n, k;
+  const int64_t *xadj;
+  const int32_t *adj;
+  const int32_t *vw;
+  const int32_t *ew;
+  int32_t *part;
+  int64_t *bw;
+  const int32_t *cap;
+  const uint8_t *over;
+  int32_t *slack;        // sorted cap - weight of all blocks (Pk entries)
+  int64_t *cand_d;       // [n] d of candidate nodes
+  uint64_t *keys;        // (block << bitsN | node) of candidates
+  int32_t *ncand;
+  int bitsN;
+  int32_t *seg_lo;       // [k] candidate segment of each block
+  int32_t *seg_hi;
+  uint64_t *sortbuf;     // per-block sort space (2 * ncand)
+  int32_t *gtab;         // per-warp global tables when labels do not fit shared memory
+  uint32_t gcap;
+  unsigned long long *moved;
+};
+
+__device__ __forceinline__ int32_t bw_node(const BalArgs &A, int32_t v) { return A.vw ? A.vw[v] : 1; }
+
+// connectivity of v to the blocks of its neighbours, aggregated by one warp
+__device__ int64_t conn_table(const BalArgs &A, int32_t v, int32_t *K, int32_t *V, uint32_t &mask) {
+  int lane = threadIdx.x & 31;
+  int64_t b = A.xadj[v], e = A.xadj[v + 1];
+  int64_t d = e - b < A.k ? e - b : A.k;
+  uint32_t cap = 32;
+  while ((int64_t)cap < 2 * d) cap <<= 1;
+  mask = cap - 1;
+  for (uint32_t i = lane; i < cap; i += 32) {
+    K[i] = HT_EMPTY;
+    V[i] = 0;
+  }
+  __syncwarp();
+  for (int64_t q = b + lane; q < e; q += 32) ht_add(K, V, mask, A.part[A.adj[q]], A.ew ? A.ew[q] : 1);
+  __syncwarp();
+  return ht_get(K, V, mask, A.part[v]);
+}
+
+// blocks whose slack is at least c (B itself has negative slack)
+__device__ int32_t count_fit(const BalArgs &A, int64_t c) {
+  int32_t lo = 0, hi = A.k;
+  while (lo < hi) {
+    int32_t mid = (lo + hi) >> 1;
+    if ((int64_t)A.slack[mid] >= c) hi = mid;
+    else lo = mid + 1;
+  }
+  return A.k - lo;
+}
+
+__global__ void __launch_bounds__(1024) k_bal_slack(BalArgs A, int32_t Pk) {
+  for (int32_t i = threadIdx.x; i < Pk; i += blockDim.x) {
+    int64_t s = i < A.k ? (int64_t)A.cap[i] - A.bw[i] : (int64_t)INT32_MAX;
+    A.slack[i] = (int32_t)(s < INT32_MIN ? INT32_MIN : (s > INT32_MAX ? INT32_MAX : s));
+  }
+  __syncthreads();
+  for (int32_t kk = 2; kk <= Pk; kk <<= 1)
+    for (int32_t j = kk >> 1; j > 0; j >>= 1) {
+      for (int32_t i = threadIdx.x; i < Pk; i += blockDim.x) {
+        int32_t l = i ^ j;
+        if (l > i) {
+          int32_t x = A.slack[i], y = A.slack[l];
+          if ((x > y) == ((i & kk) == 0)) {
+            A.slack[i] = y;
+            A.slack[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(BAL_T) k_bal_cand(BalArgs A) {
+  __shared__ int32_t sk[BAL_W][BAL_STAB], sv[BAL_W][BAL_STAB];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t gw = (int64_t)blockIdx.x * BAL_W + w, nw = (int64_t)gridDim.x * BAL_W;
+  int32_t *K = sk[w], *V = sv[w];
+  if (A.gtab) {
+    K = A.gtab + gw * 2ll * A.gcap;
+    V = K + A.gcap;
+  }
+  for (int64_t v = gw; v < A.n; v += nw) {
+    int32_t B = A.part[v];
+    if (!A.over[B]) continue;
+    uint32_t mask;
+    int64_t cown = conn_table(A, (int32_t)v, K, V, mask);
+    int64_t c = bw_node(A, (int32_t)v);
+    int64_t best = -1;
+    int32_t nadj = 0;
+    for (uint32_t i = lane; i <= mask; i += 32) {
+      int32_t b = K[i];
+      if (b == HT_EMPTY || b == B) continue;
+      if (A.bw[b] + c > A.cap[b]) continue;
+      ++nadj;
+      if (V[i] > best) best = V[i];
+    }
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+      int64_t o = (int64_t)shfl_xor64((uint64_t)best, m);
+      best = o > best ? o : best;
+      nadj += __shfl_xor_sync(0xFFFFFFFFu, nadj, m);
+    }
+    if (best < 0 && count_fit(A, c) > nadj) best = 0;  // an admissible block without neighbours
+    if (lane == 0 && best >= 0) {
+      A.cand_d[v] = best - cown;
+      int32_t p = atomicAdd(A.ncand, 1);
+      A.keys[p] = ((uint64_t)(uint32_t)B << A.bitsN) | (uint64_t)v;
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void k_bal_segments(BalArgs A, int32_t N) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t B = (int32_t)(A.keys[i] >> A.bitsN);
+    if (i == 0 || (int32_t)(A.keys[i - 1] >> A.bitsN) != B) A.seg_lo[B] = (int32_t)i;
+    if (i == N - 1 || (int32_t)(A.keys[i + 1] >> A.bitsN) != B) A.seg_hi[B] = (int32_t)i + 1;
+  }
+}
+
+// "a before b" in (relative gain desc, node asc); exact with 64-bit products
+__device__ __forceinline__ bool rg_before(int64_t d1, int64_t c1, int32_t v1, int64_t d2, int64_t c2,
+                                          int32_t v2) {
+  bool s1 = d1 >= 0, s2 = d2 >= 0;
+  if (s1 != s2) return s1;
+  int64_t p = s1 ? d1 * c1 : d1 * c2, q = s1 ? d2 * c2 : d2 * c1;
+  if (p != q) return p > q;
+  return v1 < v2;
+}
+
+// one CTA per overloaded block: bitonic sort of its candidates
+__global__ void __launch_bounds__(BAL_T) k_bal_sort(BalArgs A) {
+  int32_t B = blockIdx.x;
+  if (!A.over[B]) return;
+  int32_t lo = A.seg_lo[B], hi = A.seg_hi[B];
+  int32_t len = hi - lo;
+  if (len <= 1) return;
+  int32_t P = 1;
+  while (P < len) P <<= 1;
+  uint64_t mask = (1ull << A.bitsN) - 1ull;
+  int32_t *vv = reinterpret_cast<int32_t *>(A.sortbuf + 2ll * lo);  // 2*len >= P slots
+  for (int32_t i = threadIdx.x; i < P; i += blockDim.x)
+    vv[i] = i < len ? (int32_t)(A.keys[lo + i] & mask) : -1;
+  __syncthreads();
+  for (int32_t kk = 2; kk <= P; kk <<= 1)
+    for (int32_t j = kk >> 1; j > 0; j >>= 1) {
+      for (int32_t i = threadIdx.x; i < P; i += blockDim.x) {
+        int32_t l = i ^ j;
+        if (l > i) {
+          int32_t a = vv[i], b = vv[l];
+          // padding (-1) sorts last
+          bool b_first;
+          if (a < 0) b_first = b >= 0;
+          else if (b < 0) b_first = false;
+          else b_first = rg_before(A.cand_d[b], bw_node(A, b), b, A.cand_d[a], bw_node(A, a), a);
+          if (b_first == ((i & kk) == 0)) {
+            vv[i] = b;
+            vv[l] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int32_t i = threadIdx.x; i < len; i += blockDim.x)
+    A.keys[lo + i] = ((uint64_t)(uint32_t)B << A.bitsN) | (uint64_t)(uint32_t)vv[i];
+}
+
+// sequential moves by one warp
+__global__ void __launch_bounds__(32) k_bal_moves(BalArgs A) {
+  __shared__ int32_t sk[BAL_STAB], sv[BAL_STAB];
+  int lane = threadIdx.x & 31;
+  int32_t *K = sk, *V = sv;
+  if (A.gtab) {
+    K = A.gtab;
+    V = K + A.gcap;
+  }
+  uint64_t mask = (1ull << A.bitsN) - 1ull;
+  for (int32_t B = 0; B < A.k; ++B) {
+    if (!A.over[B]) continue;
+    int32_t lo = A.seg_lo[B], hi = A.seg_hi[B];
+    for (int32_t i = lo; i < hi; ++i) {
+      if (A.bw[B] <= A.cap[B]) break;
+      int32_t v = (int32_t)(A.keys[i] & mask);
+      int64_t c = bw_node(A, v);
+      uint32_t tm;
+      conn_table(A, v, K, V, tm);
+      uint64_t bestk = 0;  // (conn, ~block): largest connectivity, then lowest id
+      for (uint32_t x = lane; x <= tm; x += 32) {
+        int32_t b = K[x];
+        if (b == HT_EMPTY || b == B) continue;
+        if (A.bw[b] + c > A.cap[b]) continue;
+        uint64_t key = ((uint64_t)(uint32_t)V[x] << 32) | (0xFFFFFFFFu - (uint32_t)b);
+        bestk = key > bestk ? key : bestk;
+      }
+      bestk = group_max64<32>(bestk);
+      int32_t t = bestk ? (int32_t)(0xFFFFFFFFu - (uint32_t)bestk) : -1;
+      if (t < 0) {
+        int32_t low = INT32_MAX;
+        for (int32_t b = lane; b < A.k; b += 32)
+          if (b != B && A.bw[b] + c <= A.cap[b]) { low = b; break; }
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) low = min(low, __shfl_xor_sync(0xFFFFFFFFu, low, m));
+        t = low == INT32_MAX ? -1 : low;
+      }
+      if (t >= 0 && lane == 0) {
+        A.part[v] = t;
+        A.bw[B] -= c;
+        A.bw[t] += c;
+        atomicAdd(A.moved, 1ull);
+      }
+      __syncwarp();
+    }
+  }
+}
+
+int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *part) {
+  Context &C = ctx();
+  cudaStream_t s = C.stream;
+  int32_t n = g.n;
+  DBuf<int64_t> bw(k), cut(1);
+  cut_and_weights(g, part, k, bw, cut);
+  std::vector<int64_t> hbw(k);
+  to_host(hbw.data(), bw.p, k);
+  std::vector<uint8_t> hover(k, 0);
+  bool any = false;
+  for (int32_t b = 0; b < k; ++b)
+    if (hbw[b] > caps_host[b]) {
+      hover[b] = 1;
+      any = true;
+    }
+  if (!any || n == 0) return 0;
+  int32_t Pk = (int32_t)next_pow2((uint64_t)std::max(k, 2));
+  int bitsN = 1;
+  while ((1ll << bitsN) < (int64_t)n) ++bitsN;
+  int bitsK = 1;
+  while ((1ll << bitsK) < (int64_t)k) ++bitsK;
+  DBuf<int32_t> cap(k), slack(Pk), ncand(1), seg_lo(k), seg_hi(k);
+  DBuf<uint8_t> over(k);
+  DBuf<int64_t> cand_d(n);
+  DBuf<uint64_t> keys(n), tmp(n), sortbuf(2ll * n);
+  DBuf<unsigned long long> moved(1);
+  to_dev(cap.p, caps_host, k);
+  to_dev(over.p, hover.data(), k);
+  ncand.zero();
+  moved.zero();
+  seg_lo.zero();
+  seg_hi.zero();
+  int64_t dmax = std::min<int64_t>(g.maxdeg, k);
+  uint32_t gcap = 32;
+  while ((int64_t)gcap < 2 * dmax) gcap <<= 1;
+  int grid = grid_for((int64_t)n * 32, BAL_T, 8);
+  DBuf<int32_t> gtab;
+  BalArgs A;
+  A.n = n;
+  A.k = k;
+  A.xadj = g.xadj;
+  A.adj = g.adj;
+  A.vw = g.vw;
+  A.ew = g.ew;
+  A.part = part;
+  A.bw = bw;
+  A.cap = cap;
+  A.over = over;
+  A.slack = slack;
+  A.cand_d = cand_d;
+  A.keys = keys;
+  A.ncand = ncand;
+  A.bitsN = bitsN;
+  A.seg_lo = seg_lo;
+  A.seg_hi = seg_hi;
+  A.sortbuf = sortbuf;
+  A.gtab = nullptr;
+  A.gcap = gcap;
+  A.moved = moved;
+  if (gcap > BAL_STAB) {
+    // bound the per-warp tables to about 256 MB
+    int64_t per_block = 2ll * gcap * BAL_W * (int64_t)sizeof(int32_t);
+    int64_t gmax = std::max<int64_t>(1, (256ll << 20) / per_block);
+    grid = (int)std::min<int64_t>(grid, gmax);
+    gtab.alloc(2ll * gcap * (int64_t)grid * BAL_W);
+    A.gtab = gtab;
+  }
+  k_bal_slack<<<1, 1024, 0, s>>>(A, Pk);
+  KMP_LAUNCHED("bal_slack");
+  k_bal_cand<<<grid, BAL_T, 0, s>>>(A);
+  KMP_LAUNCHED("bal_cand");
+  int32_t N = read1(ncand.p);
+  if (N == 0) return 0;
+  radix_sort_u64(keys, tmp, N, bitsN + bitsK);
+  k_bal_segments<<<grid_for(N, 256), 256, 0, s>>>(A, N);
+  KMP_LAUNCHED("bal_segments");
+  k_bal_sort<<<k, BAL_T, 0, s>>>(A);
+  KMP_LAUNCHED("bal_sort");
+  DBuf<int32_t> gtab1;
+  if (gcap > BAL_STAB) {
+    gtab1.alloc(2ll * gcap);
+    A.gtab = gtab1;
+  }
+  k_bal_moves<<<1, 32, 0, s>>>(A);
+  KMP_LAUNCHED("bal_moves");
+  return (int64_t)read1(moved.p);
+}
+
+}  // namespace kmp

@@ -4,12 +4,13 @@
 // edges between them; edges inside a cluster vanish.
 //
 // GPU layout: coarse ids = exclusive scan of "label used" flags (ascending
-// label); members grouped by a counting sort; every coarse node aggregates
-// the (coarse neighbour, weight) pairs of all member edges in a hash table
-// (a warp with a shared-memory table when the members' total degree is
-// <= 512, a CTA with a global-memory table above), sorts them by neighbour id
-// with a bitonic network and writes them to a temporary row; a prefix sum of
-// the row lengths then places the rows into the final CSR.
+// label); members grouped by a counting sort.  A coarse node whose members'
+// total degree is <= 512 is aggregated by one warp in a shared-memory hash
+// table and sorted by a warp bitonic network; larger rows are aggregated by
+// all their members' warps in parallel into global tables, and the distinct
+// entries of all large rows are ordered by one GPU-wide key-value radix sort
+// of (row, neighbour).  Rows go to temporary space at upper-bound offsets; a
+// prefix sum of the row lengths then places them into the final CSR.
 // Also: projection (Algorithm 1), cut and block weights (Section 2), and the
 // per-graph facts the other kernels need (max degree, isolated nodes, weights).
 #include "kmp_internal.cuh"
@@ -151,53 +152,99 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_aggregate_warp(
   }
 }
 
-// block path: one coarse node per block, table and list in global scratch
-__global__ void __launch_bounds__(256) k_aggregate_block(
-    const int32_t *large_list, const int32_t *nlarge_p, const int64_t *xadj, const int32_t *adj,
-    const int32_t *ew, const int32_t *map, const int32_t *members, const int32_t *moff,
-    const int64_t *toff, const unsigned long long *cub, int32_t *gk, int32_t *gv, uint64_t *gl,
-    int64_t tabcap, int32_t *tadj, int32_t *tw, int32_t *cdeg) {
-  __shared__ int32_t cnt;
-  int32_t nlarge = *nlarge_p;
-  int32_t *K = gk + (int64_t)blockIdx.x * tabcap;
-  int32_t *V = gv + (int64_t)blockIdx.x * tabcap;
-  uint64_t *L = gl + (int64_t)blockIdx.x * (tabcap / 2);
-  for (int64_t i = blockIdx.x; i < nlarge; i += gridDim.x) {
-    int32_t x = large_list[i];
-    uint32_t cap = 1;
-    while (cap < 2 * cub[x]) cap <<= 1;
-    uint32_t mask = cap - 1;
-    for (uint32_t j = threadIdx.x; j < cap; j += blockDim.x) {
-      K[j] = HT_EMPTY;
-      V[j] = 0;
+// ---- large rows (members' total degree > CW_UB)
+__global__ void k_large_sizes(int32_t nc, const unsigned long long *cub, int64_t *tsz) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nc;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long ub = cub[x];
+    if (ub <= (unsigned long long)CW_UB) {
+      tsz[x] = 0;
+    } else {
+      int64_t d = (int64_t)ub < nc ? (int64_t)ub : nc;  // distinct neighbours < nc
+      int64_t c = 32;
+      while (c < 2 * d) c <<= 1;
+      tsz[x] = c;
     }
-    if (threadIdx.x == 0) cnt = 0;
-    __syncthreads();
-    for (int32_t mi = moff[x]; mi < moff[x + 1]; ++mi) {
-      int32_t v = members[mi];
-      int64_t b = xadj[v], e = xadj[v + 1];
-      for (int64_t q = b + threadIdx.x; q < e; q += blockDim.x) {
-        int32_t y = map[adj[q]];
-        if (y != x) ht_add(K, V, mask, y, ew ? ew[q] : 1);
-      }
+  }
+}
+
+// one warp per member position; members of small rows are skipped
+__global__ void __launch_bounds__(256) k_large_insert(int32_t n, const int64_t *xadj, const int32_t *adj,
+                                                      const int32_t *ew, const int32_t *map,
+                                                      const int32_t *members,
+                                                      const unsigned long long *cub, const int64_t *ltoff,
+                                                      const int64_t *tsz, int32_t *lk, int32_t *lv) {
+  int lane = threadIdx.x & 31;
+  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = gw; i < n; i += nw) {
+    int32_t v = members[i];
+    int32_t x = map[v];
+    if (cub[x] <= (unsigned long long)CW_UB) continue;
+    int32_t *K = lk + ltoff[x], *V = lv + ltoff[x];
+    uint32_t mask = (uint32_t)(tsz[x] - 1);
+    for (int64_t q = xadj[v] + lane; q < xadj[v + 1]; q += 32) {
+      int32_t y = map[adj[q]];
+      if (y != x) ht_add(K, V, mask, y, ew ? ew[q] : 1);
     }
-    __syncthreads();
-    for (uint32_t j = threadIdx.x; j < cap; j += blockDim.x)
-      if (K[j] != HT_EMPTY) L[atomicAdd(&cnt, 1)] = ((uint64_t)(uint32_t)K[j] << 32) | (uint32_t)V[j];
-    __syncthreads();
-    int32_t c = cnt;
-    uint32_t P = 1;
-    while (P < (uint32_t)c) P <<= 1;
-    for (uint32_t j = c + threadIdx.x; j < P; j += blockDim.x) L[j] = ~0ull;
-    __syncthreads();
-    bitonic<true>(L, P, threadIdx.x, blockDim.x);
-    int64_t o = toff[x];
-    for (int32_t j = threadIdx.x; j < c; j += blockDim.x) {
-      tadj[o + j] = (int32_t)(L[j] >> 32);
-      tw[o + j] = (int32_t)(uint32_t)L[j];
+  }
+}
+
+// distinct entries of all large rows into one (row << bits | neighbour, weight) list
+// Tables are powers of two >= 32 laid out back to back, so every aligned tile
+// of 32 entries belongs to one row: a warp per tile finds its row by binary
+// search (the last row whose offset is <= the tile start owns it).
+__global__ void __launch_bounds__(256) k_large_compact(int32_t nc, int64_t LT, const int64_t *ltoff,
+                                                       const int32_t *lk, const int32_t *lv, int bits,
+                                                       uint64_t *ek, int32_t *ev, int32_t *cnt,
+                                                       int32_t *cdeg) {
+  int lane = threadIdx.x & 31;
+  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = gw; t * 32 < LT; t += nw) {
+    int64_t e = t * 32;
+    int32_t lo = 0, hi = nc - 1;
+    while (lo < hi) {
+      int32_t mid = (lo + hi + 1) >> 1;
+      if (ltoff[mid] <= e) lo = mid;
+      else hi = mid - 1;
     }
-    if (threadIdx.x == 0) cdeg[x] = c;
-    __syncthreads();
+    int32_t x = lo;
+    int32_t y = lk[e + lane];
+    bool has = y != HT_EMPTY;
+    unsigned bal = __ballot_sync(0xFFFFFFFFu, has);
+    if (bal == 0) continue;
+    int32_t p0 = 0;
+    if (lane == 0) {
+      p0 = atomicAdd(cnt, __popc(bal));
+      atomicAdd(&cdeg[x], __popc(bal));
+    }
+    p0 = __shfl_sync(0xFFFFFFFFu, p0, 0);
+    if (has) {
+      int32_t p = p0 + __popc(bal & ((1u << lane) - 1u));
+      ek[p] = ((uint64_t)(uint32_t)x << bits) | (uint64_t)(uint32_t)y;
+      ev[p] = lv[e + lane];
+    }
+  }
+}
+
+__global__ void k_large_seg(int32_t N, const uint64_t *ek, int bits, int32_t *seglo) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t x = ek[i] >> bits;
+    if (i == 0 || (ek[i - 1] >> bits) != x) seglo[x] = (int32_t)i;
+  }
+}
+
+__global__ void k_large_place(int32_t N, const uint64_t *ek, const int32_t *ev, int bits,
+                              const int32_t *seglo, const int64_t *toff, int32_t *tadj, int32_t *tw) {
+  uint64_t mask = (1ull << bits) - 1ull;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t x = (int32_t)(ek[i] >> bits);
+    int64_t p = toff[x] + (i - seglo[x]);
+    tadj[p] = (int32_t)(ek[i] & mask);
+    tw[p] = ev[i];
   }
 }
 
@@ -307,6 +354,7 @@ Graph contract_graph(const Graph &g, const int32_t *label, int32_t *map) {
   scan_excl_i64(ub64, toff, nc, ttot);
   int64_t tot = read1(ttot.p);
   DBuf<int32_t> tadj(tot), tw(tot), cdeg(nc + 1);
+  cdeg.zero();
   DBuf<int32_t> small_list(nc), large_list(nc), counts(2);
   DBuf<unsigned long long> maxub(1);
   counts.zero();
@@ -321,15 +369,34 @@ Graph contract_graph(const Graph &g, const int32_t *label, int32_t *map) {
     KMP_LAUNCHED("aggregate_warp");
   }
   if (hc[1] > 0) {
-    unsigned long long mu = read1(maxub.p);
-    int64_t tabcap = next_pow2(2 * mu);
-    int gb = hc[1] < 2 * C.sms ? hc[1] : 2 * C.sms;
-    DBuf<int32_t> gk(tabcap * gb), gv(tabcap * gb);
-    DBuf<uint64_t> gl((tabcap / 2) * gb);
-    k_aggregate_block<<<gb, 256, 0, s>>>(large_list, counts.p + 1, g.xadj, g.adj, g.ew, map,
-                                         members, moff, toff, cub, gk, gv, gl, tabcap, tadj, tw,
-                                         cdeg);
-    KMP_LAUNCHED("aggregate_block");
+    // large rows: every member inserts in parallel into its coarse node's global
+    // table; the distinct entries of all large rows are then ordered by one
+    // key-value radix sort of (row, neighbour) and placed into their rows
+    int bits = 1;
+    while ((1ll << bits) < (int64_t)nc) ++bits;
+    DBuf<int64_t> tsz(nc), ltoff(nc), ltot(1);
+    k_large_sizes<<<gridc, 256, 0, s>>>(nc, cub, tsz);
+    KMP_LAUNCHED("large_sizes");
+    scan_excl_i64(tsz, ltoff, nc, ltot);
+    int64_t LT = read1(ltot.p);
+    DBuf<int32_t> lk(LT), lv(LT), lcnt(1);
+    lk.fill_bytes(0xFF);
+    lv.zero();
+    lcnt.zero();
+    k_large_insert<<<grid_for((int64_t)n * 32, 256, 8), 256, 0, s>>>(
+        n, g.xadj, g.adj, g.ew, map, members, cub, ltoff, tsz, lk, lv);
+    KMP_LAUNCHED("large_insert");
+    int64_t cap_entries = LT / 2 + 1;
+    DBuf<uint64_t> ek(cap_entries), ektmp(cap_entries);
+    DBuf<int32_t> ev(cap_entries), evtmp(cap_entries), seglo(nc);
+    k_large_compact<<<grid_for(LT, 256, 8), 256, 0, s>>>(nc, LT, ltoff, lk, lv, bits, ek, ev, lcnt, cdeg);
+    KMP_LAUNCHED("large_compact");
+    int32_t NE = read1(lcnt.p);
+    radix_sort_kv(ek, ev, ektmp, evtmp, NE, 2 * bits);
+    k_large_seg<<<grid_for(NE, 256), 256, 0, s>>>(NE, ek, bits, seglo);
+    KMP_LAUNCHED("large_seg");
+    k_large_place<<<grid_for(NE, 256), 256, 0, s>>>(NE, ek, ev, bits, seglo, toff, tadj, tw);
+    KMP_LAUNCHED("large_place");
   }
   DBuf<int64_t> mtot(1);
   out.xadj = static_cast<int64_t *>(dmalloc((nc + 1) * sizeof(int64_t)));
@@ -360,20 +427,46 @@ void project(int32_t n_fine, const int32_t *map, const int32_t *part_c, int32_t 
   KMP_LAUNCHED("project");
 }
 
-__global__ void k_cut_bw(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
-                         const int32_t *ew, const int32_t *part, unsigned long long *bw,
-                         unsigned long long *cut) {
+// Each warp takes 32 consecutive nodes and walks their rows one after the
+// other with its lanes over the entries (balanced for any degree mix); block
+// weights are accumulated in shared memory when k is small.
+constexpr int CUT_SBW = 2048;
+__global__ void __launch_bounds__(256) k_cut_bw(int32_t n, int32_t k, const int64_t *xadj,
+                                                const int32_t *adj, const int32_t *vw, const int32_t *ew,
+                                                const int32_t *part, unsigned long long *bw,
+                                                unsigned long long *cut) {
+  __shared__ unsigned long long sbw[CUT_SBW];
+  bool local = k <= CUT_SBW;
+  if (local)
+    for (int i = threadIdx.x; i < k; i += blockDim.x) sbw[i] = 0;
+  __syncthreads();
+  int lane = threadIdx.x & 31;
+  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long c = 0;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    int32_t p = part[v];
-    atomicAdd(&bw[p], (unsigned long long)(vw ? vw[v] : 1));
-    for (int64_t e = xadj[v]; e < xadj[v + 1]; ++e)
-      if (part[adj[e]] != p) c += (unsigned long long)(ew ? ew[e] : 1);
+  for (int64_t base = gw * 32; base < n; base += nw * 32) {
+    int64_t my = base + lane;
+    int32_t p = my < n ? part[my] : -1;
+    if (p >= 0) {
+      unsigned long long w = (unsigned long long)(vw ? vw[my] : 1);
+      if (local) atomicAdd(&sbw[p], w);
+      else atomicAdd(&bw[p], w);
+    }
+    int jmax = (int)(n - base < 32 ? n - base : 32);
+    for (int j = 0; j < jmax; ++j) {
+      int64_t v = base + j;
+      int32_t pv = __shfl_sync(0xFFFFFFFFu, p, j);
+      for (int64_t q = xadj[v] + lane; q < xadj[v + 1]; q += 32)
+        if (part[adj[q]] != pv) c += (unsigned long long)(ew ? ew[q] : 1);
+    }
   }
 #pragma unroll
   for (int m = 16; m > 0; m >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, m);
-  if ((threadIdx.x & 31) == 0 && c) atomicAdd(cut, c);
+  if (lane == 0 && c) atomicAdd(cut, c);
+  __syncthreads();
+  if (local)
+    for (int i = threadIdx.x; i < k; i += blockDim.x)
+      if (sbw[i]) atomicAdd(&bw[i], sbw[i]);
 }
 
 __global__ void k_half(int64_t *c) { *c /= 2; }
@@ -383,9 +476,9 @@ void cut_and_weights(const Graph &g, const int32_t *part, int32_t k, int64_t *bw
   cudaStream_t s = ctx().stream;
   KMP_CUDA(cudaMemsetAsync(bw_dev, 0, (size_t)k * sizeof(int64_t), s));
   KMP_CUDA(cudaMemsetAsync(cut_dev, 0, sizeof(int64_t), s));
-  k_cut_bw<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, g.xadj, g.adj, g.vw, g.ew, part,
-                                               reinterpret_cast<unsigned long long *>(bw_dev),
-                                               reinterpret_cast<unsigned long long *>(cut_dev));
+  k_cut_bw<<<grid_for((int64_t)g.n, 256, 8), 256, 0, s>>>(
+      g.n, k, g.xadj, g.adj, g.vw, g.ew, part, reinterpret_cast<unsigned long long *>(bw_dev),
+      reinterpret_cast<unsigned long long *>(cut_dev));
   KMP_LAUNCHED("cut_bw");
   k_half<<<1, 1, 0, s>>>(cut_dev);
   KMP_LAUNCHED("half");

@@ -222,7 +222,8 @@ __global__ void __launch_bounds__(RS_T) k_rs_hist(const uint64_t *keys, int64_t 
 
 __global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t *keys, uint64_t *out,
                                                      int64_t n, int sh, const int32_t *off,
-                                                     int64_t ntiles) {
+                                                     int64_t ntiles, const int32_t *vin = nullptr,
+                                                     int32_t *vout = nullptr) {
   __shared__ int32_t wc[RS_T / 32][256];
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < (RS_T / 32) * 256; i += RS_T) (&wc[0][0])[i] = 0;
@@ -246,7 +247,11 @@ __global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t *keys, uint6
     }
   }
   __syncthreads();
-  if (ok) out[off[(int64_t)d * ntiles + blockIdx.x] + wc[w][d] + rank] = k;
+  if (ok) {
+    int64_t p = off[(int64_t)d * ntiles + blockIdx.x] + wc[w][d] + rank;
+    out[p] = k;
+    if (vin) vout[p] = vin[j];
+  }
 }
 
 void radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t n, int bits) {
@@ -266,6 +271,30 @@ void radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t n, int bits) {
     uint64_t *t = a; a = b; b = t;
   }
   if (a != keys) KMP_CUDA(cudaMemcpyAsync(keys, a, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+}
+
+void radix_sort_kv(uint64_t *keys, int32_t *vals, uint64_t *tmpk, int32_t *tmpv, int64_t n, int bits) {
+  if (n <= 1 || bits <= 0) return;
+  int64_t ntiles = ceil_div(n, RS_T);
+  DBuf<int32_t> cnt(256 * ntiles), off(256 * ntiles);
+  cudaStream_t s = ctx().stream;
+  uint64_t *a = keys, *b = tmpk;
+  int32_t *va = vals, *vb = tmpv;
+  int passes = (bits + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    int sh = 8 * p;
+    k_rs_hist<<<(unsigned)ntiles, RS_T, 0, s>>>(a, n, sh, cnt, ntiles);
+    KMP_LAUNCHED("rs_hist");
+    scan_excl_i32(cnt, off, 256 * ntiles, nullptr);
+    k_rs_scatter<<<(unsigned)ntiles, RS_T, 0, s>>>(a, b, n, sh, off, ntiles, va, vb);
+    KMP_LAUNCHED("rs_scatter");
+    uint64_t *t = a; a = b; b = t;
+    int32_t *tv = va; va = vb; vb = tv;
+  }
+  if (a != keys) {
+    KMP_CUDA(cudaMemcpyAsync(keys, a, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    KMP_CUDA(cudaMemcpyAsync(vals, va, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  }
 }
 
 }  // namespace kmp

@@ -231,6 +231,8 @@ void scan_excl_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_de
 void scan_excl_u8_to_i32(const uint8_t *in, int32_t *out, int64_t n, int32_t *total_dev);
 // stable LSD radix sort of 64-bit keys over the low `bits` bits (in place via tmp)
 void radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t n, int bits);
+// same with an int32 payload moved along with each key
+void radix_sort_kv(uint64_t *keys, int32_t *vals, uint64_t *tmpk, int32_t *tmpv, int64_t n, int bits);
 int grid_for(int64_t work, int per_block, int max_blocks_per_sm = 8);
 
 // -------------------------------------------------------------- components

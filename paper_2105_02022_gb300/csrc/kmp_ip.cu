@@ -14,7 +14,6 @@
 // Scratch comes from a per-item region through a bump allocator; if a region
 // is too small the launch reports it and the host repeats the round with
 // larger regions, so results never depend on scratch sizes.
-// Also: k-way balancing (Section 4.3, "Balancing") in a single-CTA kernel.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -920,17 +919,33 @@ __global__ void k_block_stats(int32_t n, const int64_t *xadj, const int32_t *adj
                               const int32_t *part, const uint64_t *keys, uint64_t mask, int32_t *members,
                               int32_t *bcount, unsigned long long *bweight, int32_t *ideg,
                               unsigned long long *becount) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int32_t v = (int32_t)(keys[i] & mask);
-    members[i] = v;
-    int32_t b = part[v];
-    atomicAdd(&bcount[b], 1);
-    atomicAdd(&bweight[b], (unsigned long long)(vw ? vw[v] : 1));
-    int32_t d = 0;
-    for (int64_t q = xadj[v]; q < xadj[v + 1]; ++q) d += (part[adj[q]] == b);
-    ideg[i] = d;
-    atomicAdd(&becount[b], (unsigned long long)d);
+  // a warp takes 32 consecutive positions and walks their rows one by one
+  int lane = threadIdx.x & 31;
+  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = gw * 32; base < n; base += nw * 32) {
+    int64_t i = base + lane;
+    int32_t v = -1, b = -1;
+    if (i < n) {
+      v = (int32_t)(keys[i] & mask);
+      members[i] = v;
+      b = part[v];
+    }
+    int32_t myd = 0;
+    int jmax = (int)(n - base < 32 ? n - base : 32);
+    for (int j = 0; j < jmax; ++j) {
+      int32_t vj = __shfl_sync(0xFFFFFFFFu, v, j), bj = __shfl_sync(0xFFFFFFFFu, b, j);
+      int32_t d = 0;
+      for (int64_t q = xadj[vj] + lane; q < xadj[vj + 1]; q += 32) d += (part[adj[q]] == bj);
+      d = warp_sum32(d);
+      if (lane == j) myd = d;
+    }
+    if (i < n) {
+      atomicAdd(&bcount[b], 1);
+      atomicAdd(&bweight[b], (unsigned long long)(vw ? vw[v] : 1));
+      ideg[i] = myd;
+      atomicAdd(&becount[b], (unsigned long long)myd);
+    }
   }
 }
 
@@ -947,18 +962,30 @@ __global__ void k_fill_sub(int32_t n, const int64_t *xadj, const int32_t *adj, c
                            const int32_t *ew, const int32_t *part, const int32_t *members,
                            const int32_t *loc, const int64_t *gx, int32_t *sadj, int32_t *sew,
                            int32_t *svw) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  // a warp per row, order-preserving compaction of the entries inside the block
+  int lane = threadIdx.x & 31;
+  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = gw; i < n; i += nw) {
     int32_t v = members[i];
     int32_t b = part[v];
-    svw[i] = vw ? vw[v] : 1;
+    if (lane == 0) svw[i] = vw ? vw[v] : 1;
     int64_t o = gx[i];
-    for (int64_t q = xadj[v]; q < xadj[v + 1]; ++q) {
-      int32_t u = adj[q];
-      if (part[u] != b) continue;
-      sadj[o] = loc[u];
-      sew[o] = ew ? ew[q] : 1;
-      ++o;
+    for (int64_t q0 = xadj[v]; q0 < xadj[v + 1]; q0 += 32) {
+      int64_t q = q0 + lane;
+      bool keep = false;
+      int32_t u = 0;
+      if (q < xadj[v + 1]) {
+        u = adj[q];
+        keep = part[u] == b;
+      }
+      unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+      if (keep) {
+        int64_t p = o + __popc(bal & ((1u << lane) - 1u));
+        sadj[p] = loc[u];
+        sew[p] = ew ? ew[q] : 1;
+      }
+      o += __popc(bal);
     }
   }
 }
@@ -1121,245 +1148,6 @@ int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::
   KMP_LAUNCHED("write_parts");
   f = nf;
   return nn;
-}
-
-// ================================================================ balance
-// Section 4.3 "Balancing", deterministic reading: overloaded blocks in
-// ascending id; candidates ordered by exact relative gain (d*c if d >= 0,
-// d/c if d < 0; d = best admissible connectivity minus own connectivity),
-// ties by id; at its turn a node moves to the admissible block of largest
-// connectivity (ties lowest id), recomputed then, until the block fits.
-constexpr int BT = 1024;
-constexpr int BW = BT / 32;
-
-struct BalArgs {
-  int32_t n, k;
-  const int64_t *xadj;
-  const int32_t *adj;
-  const int32_t *vw;
-  const int32_t *ew;
-  int32_t *part;
-  int64_t *bw;
-  const int32_t *cap;
-  int32_t *cand_v;     // [n]
-  int64_t *cand_d;     // [n]
-  int32_t *cand_c;     // [n]
-  int32_t *slack;      // [k] sorted scratch
-  int32_t *tabk;       // per-warp global tables
-  int32_t *tabv;
-  uint32_t tcap;
-  unsigned long long *moved;
-};
-
-// connectivity aggregation of v by one warp into its table; returns conn(own)
-__device__ int64_t bal_conn(const BalArgs &A, int32_t v, int32_t *K, int32_t *V, uint32_t &mask) {
-  int lane = threadIdx.x & 31;
-  int64_t b = A.xadj[v], e = A.xadj[v + 1];
-  uint32_t cap = 32;
-  while ((int64_t)cap < 2 * (e - b)) cap <<= 1;
-  mask = cap - 1;
-  for (uint32_t i = lane; i < cap; i += 32) {
-    K[i] = HT_EMPTY;
-    V[i] = 0;
-  }
-  __syncwarp();
-  for (int64_t q = b + lane; q < e; q += 32) ht_add(K, V, mask, A.part[A.adj[q]], A.ew ? A.ew[q] : 1);
-  __syncwarp();
-  return ht_get(K, V, mask, A.part[v]);
-}
-
-// number of blocks (other than B) whose slack >= c, using sorted slacks
-__device__ int32_t count_fit(const BalArgs &A, int64_t c) {
-  int32_t lo = 0, hi = A.k;  // first index with slack >= c
-  while (lo < hi) {
-    int32_t mid = (lo + hi) >> 1;
-    if ((int64_t)A.slack[mid] >= c) hi = mid;
-    else lo = mid + 1;
-  }
-  return A.k - lo;
-}
-
-__device__ bool rg_before(int64_t d1, int64_t c1, int32_t v1, int64_t d2, int64_t c2, int32_t v2) {
-  bool s1 = d1 >= 0, s2 = d2 >= 0;
-  if (s1 != s2) return s1;
-  if (s1) {
-    int64_t p = d1 * c1, q = d2 * c2;
-    if (p != q) return p > q;
-  } else {
-    int64_t p = d1 * c2, q = d2 * c1;
-    if (p != q) return p > q;
-  }
-  return v1 < v2;
-}
-
-__global__ void __launch_bounds__(BT) k_balance(BalArgs A) {
-  __shared__ int32_t s_nc;
-  __shared__ int32_t s_target;
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int32_t *K = A.tabk + (int64_t)w * A.tcap, *V = A.tabv + (int64_t)w * A.tcap;
-  for (int32_t B = 0; B < A.k; ++B) {
-    if (A.bw[B] <= A.cap[B]) continue;
-    // sorted slacks (cap - weight) of all blocks; B itself is overloaded (negative)
-    int32_t Pk = 1;
-    while (Pk < A.k) Pk <<= 1;
-    for (int32_t i = threadIdx.x; i < Pk; i += BT)
-      A.slack[i] = i < A.k ? (int32_t)((int64_t)A.cap[i] - A.bw[i] < INT32_MIN ? INT32_MIN : (int64_t)A.cap[i] - A.bw[i]) : INT32_MAX;
-    __syncthreads();
-    for (int32_t kk = 2; kk <= Pk; kk <<= 1)
-      for (int32_t j = kk >> 1; j > 0; j >>= 1) {
-        for (int32_t i = threadIdx.x; i < Pk; i += BT) {
-          int32_t l = i ^ j;
-          if (l > i) {
-            int32_t x = A.slack[i], y = A.slack[l];
-            if ((x > y) == ((i & kk) == 0)) {
-              A.slack[i] = y;
-              A.slack[l] = x;
-            }
-          }
-        }
-        __syncthreads();
-      }
-    // candidates
-    if (threadIdx.x == 0) s_nc = 0;
-    __syncthreads();
-    for (int32_t v = w; v < A.n; v += BW) {
-      if (A.part[v] != B) continue;
-      uint32_t mask;
-      int64_t cown = bal_conn(A, v, K, V, mask);
-      int64_t c = A.vw ? A.vw[v] : 1;
-      int64_t best = -1;
-      int32_t nadj = 0;
-      for (uint32_t i = lane; i <= mask; i += 32) {
-        int32_t b = K[i];
-        if (b == HT_EMPTY || b == B) continue;
-        if (A.bw[b] + c > A.cap[b]) continue;
-        ++nadj;
-        if (V[i] > best) best = V[i];
-      }
-#pragma unroll
-      for (int m = 16; m > 0; m >>= 1) {
-        int64_t o = (int64_t)shfl_xor64((uint64_t)best, m);
-        best = o > best ? o : best;
-        nadj += __shfl_xor_sync(0xFFFFFFFFu, nadj, m);
-      }
-      if (count_fit(A, c) > nadj && best < 0) best = 0;  // a non-adjacent admissible block
-      if (lane == 0 && best >= 0) {
-        int32_t p = atomicAdd(&s_nc, 1);
-        A.cand_v[p] = v;
-        A.cand_d[p] = best - cown;
-        A.cand_c[p] = (int32_t)c;
-      }
-      __syncwarp();
-    }
-    __syncthreads();
-    int32_t nc = s_nc;
-    int32_t P = 1;
-    while (P < nc) P <<= 1;
-    for (int32_t i = nc + threadIdx.x; i < P; i += BT) {
-      A.cand_v[i] = INT32_MAX;
-      A.cand_d[i] = (int64_t)INT32_MIN;  // sorts after every real candidate; products stay < 2^63
-      A.cand_c[i] = 1;
-    }
-    __syncthreads();
-    for (int32_t kk = 2; kk <= P; kk <<= 1)
-      for (int32_t j = kk >> 1; j > 0; j >>= 1) {
-        for (int32_t i = threadIdx.x; i < P; i += BT) {
-          int32_t l = i ^ j;
-          if (l > i) {
-            bool before = rg_before(A.cand_d[l], A.cand_c[l], A.cand_v[l], A.cand_d[i], A.cand_c[i], A.cand_v[i]);
-            if (before == ((i & kk) == 0)) {
-              int32_t tv = A.cand_v[i]; A.cand_v[i] = A.cand_v[l]; A.cand_v[l] = tv;
-              int64_t td = A.cand_d[i]; A.cand_d[i] = A.cand_d[l]; A.cand_d[l] = td;
-              int32_t tc = A.cand_c[i]; A.cand_c[i] = A.cand_c[l]; A.cand_c[l] = tc;
-            }
-          }
-        }
-        __syncthreads();
-      }
-    // moves in order (warp 0); fallback scan for the lowest admissible block uses all warps
-    for (int32_t i = 0; i < nc; ++i) {
-      if (A.bw[B] <= A.cap[B]) break;
-      int32_t v = A.cand_v[i];
-      int64_t c = A.cand_c[i];
-      if (w == 0) {
-        uint32_t mask;
-        bal_conn(A, v, K, V, mask);
-        uint64_t bestk = 0;  // (conn, ~block)
-        for (uint32_t x = lane; x <= mask; x += 32) {
-          int32_t b = K[x];
-          if (b == HT_EMPTY || b == B) continue;
-          if (A.bw[b] + c > A.cap[b]) continue;
-          uint64_t kk2 = ((uint64_t)(uint32_t)V[x] << 32) | (0xFFFFFFFFu - (uint32_t)b);
-          bestk = kk2 > bestk ? kk2 : bestk;
-        }
-        bestk = group_max64<32>(bestk);
-        if (lane == 0) s_target = bestk ? (int32_t)(0xFFFFFFFFu - (uint32_t)bestk) : -1;
-      }
-      __syncthreads();
-      if (s_target < 0) {
-        // no admissible adjacent block: lowest-id admissible block overall
-        __shared__ int32_t s_low;
-        if (threadIdx.x == 0) s_low = INT32_MAX;
-        __syncthreads();
-        for (int32_t b = threadIdx.x; b < A.k; b += BT)
-          if (b != B && A.bw[b] + c <= A.cap[b]) atomicMin(&s_low, b);
-        __syncthreads();
-        if (threadIdx.x == 0) s_target = s_low == INT32_MAX ? -1 : s_low;
-        __syncthreads();
-      }
-      int32_t t = s_target;
-      if (threadIdx.x == 0 && t >= 0) {
-        A.part[v] = t;
-        A.bw[B] -= c;
-        A.bw[t] += c;
-        atomicAdd(A.moved, 1ull);
-      }
-      __syncthreads();
-    }
-  }
-}
-
-int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *part) {
-  cudaStream_t s = ctx().stream;
-  DBuf<int64_t> bw(k), cut(1);
-  cut_and_weights(g, part, k, bw, cut);
-  std::vector<int64_t> hbw(k);
-  to_host(hbw.data(), bw.p, k);
-  bool over = false;
-  for (int32_t b = 0; b < k; ++b)
-    if (hbw[b] > caps_host[b]) over = true;
-  if (!over) return 0;
-  int32_t Pk = (int32_t)next_pow2((uint64_t)std::max(k, 1));
-  int64_t P = (int64_t)next_pow2((uint64_t)std::max(g.n, 1));
-  DBuf<int32_t> cap(k), cand_v(P), cand_c(P), slack(Pk);
-  DBuf<int64_t> cand_d(P);
-  uint32_t tcap = 32;
-  while ((int64_t)tcap < 2 * g.maxdeg) tcap <<= 1;
-  DBuf<int32_t> tk((int64_t)tcap * BW), tv((int64_t)tcap * BW);
-  DBuf<unsigned long long> moved(1);
-  moved.zero();
-  to_dev(cap.p, caps_host, k);
-  BalArgs A;
-  A.n = g.n;
-  A.k = k;
-  A.xadj = g.xadj;
-  A.adj = g.adj;
-  A.vw = g.vw;
-  A.ew = g.ew;
-  A.part = part;
-  A.bw = bw;
-  A.cap = cap;
-  A.cand_v = cand_v;
-  A.cand_d = cand_d;
-  A.cand_c = cand_c;
-  A.slack = slack;
-  A.tabk = tk;
-  A.tabv = tv;
-  A.tcap = tcap;
-  A.moved = moved;
-  k_balance<<<1, BT, 0, s>>>(A);
-  KMP_LAUNCHED("balance");
-  return (int64_t)read1(moved.p);
 }
 
 }  // namespace kmp

@@ -67,15 +67,50 @@ struct LPArgs {
   int32_t *slot_t;
   int32_t *slot_base;
   int32_t *bucket;
-  int32_t *ctr;                // [0] slots, [1] bucket top
+  int32_t *ctr;                // [0] slots, [1] bucket top, [2] big movers
+  int32_t *bigmove;            // high-degree nodes that moved in this sub-round
   unsigned long long *ctr64;   // [0] scanned entries, [1] moved nodes
-  int32_t *gkeys;              // per-block global tables (bin 6)
-  int32_t *gvals;
-  int64_t gcap;                // entries per block
+  // bin 6 (degree > HUGE_DEG) with many labels: per-hub global tables filled
+  // by many CTAs in parallel
+  const int32_t *hubs;         // hub node ids, ascending
+  int32_t nhubs;
+  const int64_t *hoff;         // table offset of each hub
+  int32_t *hkeys;
+  int32_t *hvals;
+  unsigned long long *hkc;     // best admissible key per hub
+  unsigned long long *hku;     // best key per hub
+  int32_t *hrown;              // rating of the hub's own cluster
+  int32_t *hstamp;             // per hub: stamp of the sub-round it is rated in
+  const int64_t *hechunk;      // per hub: first edge chunk (exclusive prefix)
+  const int64_t *htchunk;      // per hub: first table chunk
+  int64_t hchunks_total, htchunks_total;
+  int32_t stamp;               // stamp of the current sub-round (round * S + s + 1)
+  int32_t small_labels;        // all labels fit a CTA table: bin 6 handled like bin 5
+  int32_t nlab;
   int32_t S;
   uint64_t rk;
   uint32_t rk_hi;
 };
+
+// inverse of perm32: the label whose tie-break rank is p
+__device__ __forceinline__ int32_t perm32_inv(uint32_t rk_hi, uint32_t p) {
+  uint32_t h = p;
+  h ^= h >> 16;
+  h *= 0x7ED1B41Du;  // inverse of 0xC2B2AE35 modulo 2^32
+  h ^= (h >> 13) ^ (h >> 26);
+  h *= 0xA5CB9243u;  // inverse of 0x85EBCA6B modulo 2^32
+  h ^= h >> 16;
+  return (int32_t)(h ^ rk_hi);
+}
+__device__ __forceinline__ int32_t label_of_key(uint32_t rk_hi, uint64_t key) {
+  return perm32_inv(rk_hi, 0xFFFFFFFFu - (uint32_t)key);
+}
+__device__ __forceinline__ uint32_t table_cap(int64_t deg, int32_t nlab) {
+  int64_t d = deg < nlab ? deg : nlab;
+  uint32_t c = 32;
+  while ((int64_t)c < 2 * d) c <<= 1;
+  return c;
+}
 
 __device__ __forceinline__ int32_t node_w(const LPArgs &A, int32_t v) { return A.vw ? A.vw[v] : 1; }
 __device__ __forceinline__ int32_t edge_w(const LPArgs &A, int64_t e) { return A.ew ? A.ew[e] : 1; }
@@ -307,17 +342,26 @@ __device__ void rate_cta(const LPArgs &A, int32_t u, int32_t pos, int32_t *keys,
   __syncthreads();
 }
 
+__device__ __forceinline__ int32_t hub_index(const LPArgs &A, int32_t u);
+
 __global__ void __launch_bounds__(RATE_T) k_rate(LPArgs A, int s) {
   __shared__ int32_t tkeys[CTA_TAB];
   __shared__ int32_t tvals[CTA_TAB];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     A.ctr[0] = 0;
     A.ctr[1] = 0;
+    A.ctr[2] = 0;
   }
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int64_t gw = (int64_t)blockIdx.x * (RATE_T / 32) + w;
   int64_t nw = (int64_t)gridDim.x * (RATE_T / 32);
   const int32_t *bo = A.boff + s * NB;
+  if (!A.small_labels && A.nhubs > 0) {
+    // stamp the hubs rated in this sub-round for the hub kernels
+    for (int64_t p = bo[6] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < bo[7];
+         p += (int64_t)gridDim.x * blockDim.x)
+      A.hstamp[hub_index(A, A.vlist[p])] = A.stamp;
+  }
 #define KMP_GROUP_BIN(BIN, G)                                                  \
   {                                                                            \
     int32_t lo = bo[BIN], hi = bo[BIN + 1];                                    \
@@ -340,23 +384,146 @@ __global__ void __launch_bounds__(RATE_T) k_rate(LPArgs A, int s) {
   }
   __syncthreads();
   {
-    int32_t lo = bo[5], hi = bo[6];
-    for (int64_t idx = lo + blockIdx.x; idx < hi; idx += gridDim.x)
-      rate_cta(A, A.vlist[idx], (int32_t)idx, tkeys, tvals, CTA_TAB - 1);
+    // bin 5, and bin 6 as well when every label set fits a shared table
+    int32_t lo = bo[5], hi = A.small_labels ? bo[7] : bo[6];
+    for (int64_t idx = lo + blockIdx.x; idx < hi; idx += gridDim.x) {
+      int32_t u = A.vlist[idx];
+      uint32_t cap = table_cap(A.xadj[u + 1] - A.xadj[u], A.nlab);
+      rate_cta(A, u, (int32_t)idx, tkeys, tvals, cap - 1);
+    }
   }
 }
 
-__global__ void __launch_bounds__(RATE_T) k_rate_huge(LPArgs A, int s) {
+// ---- hubs (bin 6) with many labels: insert / reduce / emit
+constexpr int64_t HUB_CHUNK = 2048;   // edges per insert work unit
+constexpr int64_t HUB_RCHUNK = 4096;  // table entries per reduce work unit
+
+__device__ __forceinline__ int32_t hub_index(const LPArgs &A, int32_t u) {
+  int32_t lo = 0, hi = A.nhubs - 1;
+  while (lo < hi) {
+    int32_t mid = (lo + hi) >> 1;
+    if (A.hubs[mid] < u) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// the hubs of the current sub-round carry its stamp (set by k_rate)
+__device__ __forceinline__ int32_t find_seg(const int64_t *off, int32_t cnt, int64_t x) {
+  int32_t lo = 0, hi = cnt - 1;  // last index with off[idx] <= x
+  while (lo < hi) {
+    int32_t mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// work units: edge chunks of all hubs (global index space, fixed per run)
+__global__ void __launch_bounds__(256) k_hub_insert(LPArgs A, int32_t stamp) {
+  for (int64_t c = blockIdx.x; c < A.hchunks_total; c += gridDim.x) {
+    int32_t h = find_seg(A.hechunk, A.nhubs, c);
+    if (A.hstamp[h] != stamp) continue;
+    int32_t u = A.hubs[h];
+    int64_t b = A.xadj[u], deg = A.xadj[u + 1] - b;
+    uint32_t mask = next_pow2_dev(2 * deg) - 1;
+    int32_t *keys = A.hkeys + A.hoff[h], *vals = A.hvals + A.hoff[h];
+    int64_t cc = c - A.hechunk[h];
+    int64_t e0 = b + cc * HUB_CHUNK, e1 = e0 + HUB_CHUNK < b + deg ? e0 + HUB_CHUNK : b + deg;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x)
+      ht_add(keys, vals, mask, A.label[A.adj[e]], edge_w(A, e));
+  }
+}
+
+// work units: table chunks of all hubs
+__global__ void __launch_bounds__(256) k_hub_reduce(LPArgs A, int32_t stamp) {
+  __shared__ unsigned long long red_c[8], red_u[8];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t c = blockIdx.x; c < A.htchunks_total; c += gridDim.x) {
+    int32_t h = find_seg(A.htchunk, A.nhubs, c);
+    if (A.hstamp[h] != stamp) continue;
+    int32_t u = A.hubs[h];
+    int64_t deg = A.xadj[u + 1] - A.xadj[u];
+    int64_t cap = next_pow2_dev(2 * deg);
+    int32_t own = A.label[u], cu = node_w(A, u);
+    int32_t *keys = A.hkeys + A.hoff[h], *vals = A.hvals + A.hoff[h];
+    int64_t cc = c - A.htchunk[h];
+    {
+      uint64_t kc = 0, ku = 0;
+      int64_t e1 = (cc + 1) * HUB_RCHUNK < cap ? (cc + 1) * HUB_RCHUNK : cap;
+      for (int64_t i = cc * HUB_RCHUNK + threadIdx.x; i < e1; i += blockDim.x) {
+        int32_t K = keys[i];
+        if (K == HT_EMPTY) continue;
+        int32_t r = vals[i];
+        keys[i] = HT_EMPTY;  // leave the table empty for its next use
+        vals[i] = 0;
+        if (K == own) {
+          A.hrown[h] = r;
+          continue;
+        }
+        uint64_t k = rate_key(A, K, r);
+        ku = k > ku ? k : ku;
+        if ((int64_t)A.wt[K] + cu <= cap_of(A, K) && k > kc) kc = k;
+      }
+      kc = group_max64<32>(kc);
+      ku = group_max64<32>(ku);
+      if (lane == 0) { red_c[w] = kc; red_u[w] = ku; }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+          kc = red_c[i] > kc ? red_c[i] : kc;
+          ku = red_u[i] > ku ? red_u[i] : ku;
+        }
+        if (kc) atomicMax(&A.hkc[h], kc);
+        if (ku) atomicMax(&A.hku[h], ku);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// hub ids, table offsets and chunk offsets of one run
+__global__ void k_hub_chunks(int32_t nh, const int32_t *hubs, const int64_t *xadj, int64_t *ech,
+                             int64_t *tch) {
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nh;
+       h += (int64_t)gridDim.x * blockDim.x) {
+    int64_t deg = xadj[hubs[h] + 1] - xadj[hubs[h]];
+    ech[h] = ceil_div(deg, HUB_CHUNK);
+    tch[h] = ceil_div((int64_t)next_pow2_dev(2 * deg), HUB_RCHUNK);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_hub_emit(LPArgs A, int s) {
   const int32_t *bo = A.boff + s * NB;
   int32_t lo = bo[6], hi = bo[7];
-  int32_t *keys = A.gkeys + (int64_t)blockIdx.x * A.gcap;
-  int32_t *vals = A.gvals + (int64_t)blockIdx.x * A.gcap;
-  for (int64_t idx = lo + blockIdx.x; idx < hi; idx += gridDim.x) {
-    int32_t u = A.vlist[idx];
-    int64_t deg = A.xadj[u + 1] - A.xadj[u];
-    uint32_t cap = next_pow2_dev(2 * deg);
-    rate_cta(A, u, (int32_t)idx, keys, vals, cap - 1);
+  for (int64_t p = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < hi;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int32_t u = A.vlist[p];
+    int32_t h = hub_index(A, u);
+    uint64_t kc = A.hkc[h], ku = A.hku[h];
+    int32_t rown = A.hrown[h];
+    emit(A, u, (int32_t)p, rown, kc, kc ? label_of_key(A.rk_hi, kc) : -1, ku,
+         ku ? label_of_key(A.rk_hi, ku) : -1);
+    A.hkc[h] = 0;
+    A.hku[h] = 0;
+    A.hrown[h] = 0;
   }
+}
+
+__global__ void k_hub_flags(int32_t n, const int64_t *xadj, uint8_t *flag) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    flag[v] = (xadj[v + 1] - xadj[v]) > HUGE_DEG ? 1 : 0;
+}
+
+__global__ void k_hub_list(int32_t n, const int64_t *xadj, const uint8_t *flag, const int32_t *pos,
+                           int32_t *hubs, int64_t *hsz) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    if (flag[v]) {
+      hubs[pos[v]] = (int32_t)v;
+      hsz[pos[v]] = (int64_t)next_pow2_dev(2 * (xadj[v + 1] - xadj[v]));
+    }
 }
 
 // ------------------------------------------------------------------- commit
@@ -437,18 +604,59 @@ __global__ void __launch_bounds__(256) k_resolve(LPArgs A) {
     int32_t base = A.slot_base[sl];
     int64_t R = cap_of(A, T) - A.wt[T];
     if (R < 0) continue;  // nothing fits (acc already 0)
-    if (threadIdx.x == 0) { prefix = 0; accw = 0; }
+    // skip the leading digits that every key shares (all gains of a target
+    // are usually small, so the top bytes agree): common prefix of min..max
+    __shared__ unsigned long long kmin, kmax;
+    if (threadIdx.x == 0) { kmin = ~0ull; kmax = 0; }
     __syncthreads();
-    for (int p = 0; p < 8; ++p) {
+    {
+      unsigned long long lmin = ~0ull, lmax = 0;
+      for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        unsigned long long k = commit_key(A, A.bucket[base + i]);
+        lmin = k < lmin ? k : lmin;
+        lmax = k > lmax ? k : lmax;
+      }
+      atomicMin(&kmin, lmin);
+      atomicMax(&kmax, lmax);
+    }
+    __syncthreads();
+    int p0 = 0;
+    {
+      unsigned long long diff = kmin ^ kmax;  // != 0: keys are distinct and cnt > 32
+      int top = 63 - __clzll((long long)diff);
+      p0 = (63 - top) / 8;                     // first byte (from the top) that differs
+    }
+    if (threadIdx.x == 0) {
+      prefix = p0 > 0 ? (kmin >> (64 - 8 * p0)) : 0;
+      accw = 0;
+    }
+    __syncthreads();
+    for (int p = p0; p < 8; ++p) {
       int sh = 56 - 8 * p;
       for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
       __syncthreads();
       uint64_t pf = prefix;
-      for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        int32_t ps = A.bucket[base + i];
-        uint64_t k = commit_key(A, ps);
-        if (p == 0 || (k >> (sh + 8)) == pf)
-          atomicAdd(&hist[(k >> sh) & 255u], (unsigned long long)node_w(A, A.vlist[ps]));
+      int lane2 = threadIdx.x & 31;
+      for (int32_t i0 = 0; i0 < cnt; i0 += blockDim.x) {
+        int32_t i = i0 + threadIdx.x;
+        int d = 256 + lane2;  // unique per lane when not counted
+        unsigned long long wgt = 0;
+        if (i < cnt) {
+          int32_t ps = A.bucket[base + i];
+          uint64_t k = commit_key(A, ps);
+          if (p == 0 || (k >> (sh + 8)) == pf) {
+            d = (int)((k >> sh) & 255u);
+            wgt = (unsigned long long)node_w(A, A.vlist[ps]);
+          }
+        }
+        // lanes with the same digit add their weights first: one atomic per digit and warp
+        unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+        unsigned long long sum = 0;
+        for (int j = 0; j < 32; ++j) {
+          unsigned long long wj = __shfl_sync(0xFFFFFFFFu, wgt, j);
+          if ((peers >> j) & 1u) sum += wj;
+        }
+        if (d < 256 && (peers & ((1u << lane2) - 1u)) == 0) atomicAdd(&hist[d], sum);
       }
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -490,7 +698,12 @@ __global__ void __launch_bounds__(256) k_apply(LPArgs A, int s) {
       atomicAdd(&A.wt[T], c);
       atomicSub(&A.wt[own], c);
       ++moved;
-      for (int64_t e = A.xadj[u]; e < A.xadj[u + 1]; ++e) A.act_next[A.adj[e]] = 1;
+      int64_t b = A.xadj[u], e1 = A.xadj[u + 1];
+      if (e1 - b > 64) {
+        A.bigmove[atomicAdd(&A.ctr[2], 1)] = u;  // neighbours marked by k_scatter_big
+      } else {
+        for (int64_t e = b; e < e1; ++e) A.act_next[A.adj[e]] = 1;
+      }
     } else if (A.fav) {
       A.fav[u] = T;
     }
@@ -501,6 +714,15 @@ __global__ void __launch_bounds__(256) k_apply(LPArgs A, int s) {
 #pragma unroll
   for (int m = 16; m > 0; m >>= 1) moved += __shfl_xor_sync(0xFFFFFFFFu, moved, m);
   if ((threadIdx.x & 31) == 0 && moved) atomicAdd(&A.ctr64[1], moved);
+}
+
+// neighbours of high-degree nodes that moved become active: one block per node
+__global__ void __launch_bounds__(256) k_scatter_big(LPArgs A) {
+  int32_t nb = A.ctr[2];
+  for (int32_t i = blockIdx.x; i < nb; i += gridDim.x) {
+    int32_t u = A.bigmove[i];
+    for (int64_t e = A.xadj[u] + threadIdx.x; e < A.xadj[u + 1]; e += blockDim.x) A.act_next[A.adj[e]] = 1;
+  }
 }
 
 __global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
@@ -529,7 +751,7 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   DBuf<uint8_t> act(n), act_next(n), acc(n);
   DBuf<int32_t> vlist(n), boff(S * NB + 1), prop_t(n), prop_g(n), pos_in_t(n);
   DBuf<int32_t> tsum(nlab), tcnt(nlab), tcur(nlab), tslot(nlab);
-  DBuf<int32_t> slot_t(n), slot_base(n), bucket(n), ctr(8);
+  DBuf<int32_t> slot_t(n), slot_base(n), bucket(n), ctr(8), bigmove(n);
   DBuf<unsigned long long> ctr64(2 + 8);  // scanned, moved, per-sub-round degree sums
   DBuf<int32_t> bcnt(S * NB * ntiles), boffs(S * NB * ntiles), btotal(1);
   act.fill_bytes(1);
@@ -539,14 +761,52 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   tcur.zero();
   ctr.zero();
 
-  int huge_grid = 0;
-  DBuf<int32_t> gkeys, gvals;
-  int64_t gcap = 0;
-  if (g.maxdeg > HUGE_DEG) {
-    gcap = next_pow2(2 * (uint64_t)g.maxdeg);
-    huge_grid = 2 * C.sms;
-    gkeys.alloc(gcap * huge_grid);
-    gvals.alloc(gcap * huge_grid);
+  // hubs: with few labels (refinement) a shared-memory table always fits;
+  // otherwise every hub gets its own global table region for the whole run
+  bool small_labels = 2 * (int64_t)nlab <= CTA_TAB;
+  bool hub_path = !small_labels && g.maxdeg > HUGE_DEG;
+  int32_t nhubs = 0;
+  DBuf<int32_t> hubs, hkeys, hvals, hrown, hstamp;
+  DBuf<int64_t> hoff, hechunk, htchunk;
+  int64_t hchunks_total = 0, htchunks_total = 0;
+  DBuf<unsigned long long> hkc, hku;
+  if (hub_path) {
+    DBuf<uint8_t> flag(n);
+    DBuf<int32_t> pos(n), cnt(1);
+    k_hub_flags<<<grid_for(n, 256), 256, 0, stream>>>(n, g.xadj, flag);
+    KMP_LAUNCHED("hub_flags");
+    scan_excl_u8_to_i32(flag, pos, n, cnt);
+    nhubs = read1(cnt.p);
+    hubs.alloc(nhubs);
+    DBuf<int64_t> hsz(nhubs), tot(1);
+    hoff.alloc(nhubs);
+    k_hub_list<<<grid_for(n, 256), 256, 0, stream>>>(n, g.xadj, flag, pos, hubs, hsz);
+    KMP_LAUNCHED("hub_list");
+    scan_excl_i64(hsz, hoff, nhubs, tot);
+    int64_t T = read1(tot.p);
+    hkeys.alloc(T);
+    hvals.alloc(T);
+    hkeys.fill_bytes(0xFF);
+    hvals.zero();
+    hkc.alloc(nhubs);
+    hku.alloc(nhubs);
+    hrown.alloc(nhubs);
+    hstamp.alloc(nhubs);
+    hkc.zero();
+    hku.zero();
+    hrown.zero();
+    hstamp.zero();
+    DBuf<int64_t> ech(nhubs), tch(nhubs), tots(2);
+    hechunk.alloc(nhubs);
+    htchunk.alloc(nhubs);
+    k_hub_chunks<<<grid_for(nhubs, 256), 256, 0, stream>>>(nhubs, hubs, g.xadj, ech, tch);
+    KMP_LAUNCHED("hub_chunks");
+    scan_excl_i64(ech, hechunk, nhubs, tots.p);
+    scan_excl_i64(tch, htchunk, nhubs, tots.p + 1);
+    int64_t ht[2];
+    to_host(ht, tots.p, 2);
+    hchunks_total = ht[0];
+    htchunks_total = ht[1];
   }
 
   LPArgs A;
@@ -576,13 +836,28 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   A.slot_base = slot_base;
   A.bucket = bucket;
   A.ctr = ctr;
+  A.bigmove = bigmove;
   A.ctr64 = ctr64;
-  A.gkeys = gkeys.p;
-  A.gvals = gvals.p;
-  A.gcap = gcap;
+  A.hubs = hubs.p;
+  A.nhubs = nhubs;
+  A.hoff = hoff.p;
+  A.hkeys = hkeys.p;
+  A.hvals = hvals.p;
+  A.hkc = hkc.p;
+  A.hku = hku.p;
+  A.hrown = hrown.p;
+  A.hstamp = hstamp.p;
+  A.hechunk = hechunk.p;
+  A.htchunk = htchunk.p;
+  A.hchunks_total = hchunks_total;
+  A.htchunks_total = htchunks_total;
+  A.stamp = 0;
+  A.small_labels = small_labels ? 1 : 0;
+  A.nlab = nlab;
   A.S = S;
 
-  int grid_rate = 4 * C.sms;
+  int grid_rate = 6 * C.sms;
+  int grid_hub = 4 * C.sms;
   int grid_commit = grid_for(ceil_div(n, S), 256, 8);
   unsigned long long h64[10];
   int32_t hboff[8 * NB + 1];
@@ -609,11 +884,16 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
         ev.push_back(b);
         KMP_CUDA(cudaEventRecord(a, stream));
       }
+      A.stamp = r * S + s + 1;
       k_rate<<<grid_rate, RATE_T, 0, stream>>>(A, s);
       KMP_LAUNCHED("rate");
-      if (huge_grid) {
-        k_rate_huge<<<huge_grid, RATE_T, 0, stream>>>(A, s);
-        KMP_LAUNCHED("rate_huge");
+      if (hub_path) {
+        k_hub_insert<<<grid_hub, 256, 0, stream>>>(A, A.stamp);
+        KMP_LAUNCHED("hub_insert");
+        k_hub_reduce<<<grid_hub, 256, 0, stream>>>(A, A.stamp);
+        KMP_LAUNCHED("hub_reduce");
+        k_hub_emit<<<grid_for(nhubs, 256), 256, 0, stream>>>(A, s);
+        KMP_LAUNCHED("hub_emit");
       }
       if (C.profile) KMP_CUDA(cudaEventRecord(ev.back(), stream));
       k_classify<<<grid_commit, 256, 0, stream>>>(A, s);
@@ -624,6 +904,10 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
       KMP_LAUNCHED("resolve");
       k_apply<<<grid_commit, 256, 0, stream>>>(A, s);
       KMP_LAUNCHED("apply");
+      if (g.maxdeg > 64) {
+        k_scatter_big<<<2 * C.sms, 256, 0, stream>>>(A);
+        KMP_LAUNCHED("scatter_big");
+      }
     }
     to_host(h64, ctr64.p, 2 + S);
     if (C.profile) {
