@@ -148,9 +148,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="partition", choices=["partition", "coarsen1"],
+    ap.add_argument("--mode", default="partition", choices=["partition", "coarsen1", "launchlist"],
                     help="coarsen1: one level-0 coarsening (LP) of the workload graph only; "
-                         "used for kernel profiles")
+                         "launchlist: one warm-up partition and one partition inside the NVTX "
+                         "range kmp_step (for ncu launch lists); both are used for kernel profiles")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -193,6 +194,16 @@ def main():
                           "rate_gbs": by / (ms / 1e3) / 1e9 if ms else None, "peak": peak, "peak_kind": kind}))
         return
     part = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    if args.mode == "launchlist":
+        kmp.partition_graph(dg, K_BLOCKS, EPS, SEED, part)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("kmp_step")
+        _, rc, st = kmp.partition_graph(dg, K_BLOCKS, EPS, SEED, part)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"mode": "launchlist", "workload": WORKLOAD, "gpu_launches": st.gpu_launches,
+                          "ms_total": st.ms_total, "cut": st.cut}))
+        return
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 

@@ -216,6 +216,30 @@ int kmp_last_stats(kmp_stats *stats);
 int kmp_set_profiling(int on);
 int kmp_profile_read(double *rate_ms, double *rate_bytes, int64_t *rate_launches, int reset);
 
+/*
+ * Schedule parameters of the GPU kernels.  They decide which kernel variant
+ * handles a node or work item and how grids are sized; they never change a
+ * result (the parity tests run every setting against the CPU oracle).
+ */
+typedef struct {
+  int32_t rate_blocks_per_sm; /* LP rating grid = this * SMs (2..16) */
+  int32_t hub_degree;         /* degree above which coarsening rates a node with the
+                                 multi-CTA hub kernels (256..2048) */
+  int32_t hub_chunk;          /* edges per hub work unit (256..65536, power of two) */
+  int32_t ip_blocks_per_sm;   /* bipartitioner CTAs per SM (1..8) */
+} kmp_tuning;
+
+int kmp_set_tuning(const kmp_tuning *t);
+int kmp_get_tuning(kmp_tuning *t);
+/*
+ * Autotuner: times candidate schedules on the level-0 coarsening LP of `g`
+ * (one run per candidate, cap derived from k and eps as the partitioner
+ * does), keeps the fastest with kmp_set_tuning and returns it in *best.
+ * Candidates: rating grid {4, 6, 8} x SMs, hub degree {1024, 2048}, hub chunk
+ * {1024, 4096}.
+ */
+int kmp_autotune(const kmp_graph *g, int32_t k, double eps, uint64_t seed, kmp_tuning *best);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,12 @@ def lib():
             "kmpo_bipartition_blocks": (i32, [i32, P, P, P, P, i32, P, dbl, i64, i32, u64, P, P, P]),
             "kmpo_brute_bisection": (i64, [i32, P, P, P, P, i64, i64, P]),
             "kmpo_async_cluster": (i32, [i32, P, P, P, P, i32, i32, P]),
+            "kmpo_mpnn_num_params": (i32, []),
+            "kmpo_mpnn_features": (None, [i32, P, P, P, P, u64, P]),
+            "kmpo_mpnn_forward": (None, [i32, P, P, P, P, P, P, P]),
+            "kmpo_mpnn_loss": (dbl, [i32, P, P, P]),
+            "kmpo_mpnn_backward": (None, [i32, P, P, P, P, P, P, P]),
+            "kmpo_mpnn_propose": (None, [i32, P, P, i32, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -252,6 +258,56 @@ def brute_bisection(g, L0, L1):
     side = np.zeros(n, np.int32)
     c = lib().kmpo_brute_bisection(n, _p(xadj), _p(adj), _p(vw), _p(ew), L0, L1, _p(side))
     return int(c), side
+
+
+MPNN_F, MPNN_H = 8, 64
+
+
+def mpnn_num_params() -> int:
+    return int(lib().kmpo_mpnn_num_params())
+
+
+def mpnn_features(g, key_):
+    n, xadj, adj, vw, ew = _g(g)
+    X = np.zeros((n, MPNN_F), np.float64)
+    lib().kmpo_mpnn_features(n, _p(xadj), _p(adj), _p(vw), _p(ew), key_, _p(X))
+    return X
+
+
+def mpnn_forward(g, X, P):
+    n, xadj, adj, vw, ew = _g(g)
+    X = np.ascontiguousarray(X, np.float64)
+    P = np.ascontiguousarray(P, np.float64)
+    S = np.zeros(n, np.float64)
+    lib().kmpo_mpnn_forward(n, _p(xadj), _p(adj), _p(ew), _p(X), _p(P), _p(S), None)
+    return S
+
+
+def mpnn_loss(S, side):
+    S = np.ascontiguousarray(S, np.float64)
+    side = np.ascontiguousarray(side, np.int32)
+    gS = np.zeros(len(S), np.float64)
+    L = lib().kmpo_mpnn_loss(len(S), _p(S), _p(side), _p(gS))
+    return float(L), gS
+
+
+def mpnn_backward(g, X, P, gS):
+    n, xadj, adj, vw, ew = _g(g)
+    X = np.ascontiguousarray(X, np.float64)
+    P = np.ascontiguousarray(P, np.float64)
+    gS = np.ascontiguousarray(gS, np.float64)
+    gP = np.zeros(mpnn_num_params(), np.float64)
+    lib().kmpo_mpnn_backward(n, _p(xadj), _p(adj), _p(ew), _p(X), _p(P), _p(gS), _p(gP))
+    return gP
+
+
+def mpnn_propose(g, S, target0):
+    n = g.n
+    vw = None if g.vwgt is None else np.ascontiguousarray(g.vwgt, np.int32)
+    S = np.ascontiguousarray(S, np.float64)
+    side = np.zeros(n, np.int32)
+    lib().kmpo_mpnn_propose(n, _p(vw), _p(S), int(target0), _p(side))
+    return side
 
 
 def async_cluster(g, U, rounds):

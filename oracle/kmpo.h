@@ -153,6 +153,18 @@ int32_t kmpo_async_cluster(int32_t n, const int64_t *xadj, const int32_t *adj,
                            const int32_t *vw, const int32_t *ew, int32_t U, int32_t rounds,
                            int32_t *label_out);
 
+/* learned seed proposer (kmpo_mpnn.c): parameters in fp64, layout documented there */
+int32_t kmpo_mpnn_num_params(void);
+void kmpo_mpnn_features(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
+                        const int32_t *ew, uint64_t key, double *X);
+void kmpo_mpnn_forward(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *ew,
+                       const double *X, const double *P, double *S, double *cache);
+double kmpo_mpnn_loss(int32_t n, const double *S, const int32_t *side, double *gS);
+void kmpo_mpnn_backward(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *ew,
+                        const double *X, const double *P, const double *gS, double *gP);
+void kmpo_mpnn_propose(int32_t n, const int32_t *vw, const double *S, int32_t target0,
+                       int32_t *side);
+
 #ifdef __cplusplus
 }
 #endif

@@ -176,15 +176,17 @@ __global__ void k_bw_to_i32(int32_t k, const int64_t *bw64, int32_t *bw) {
 }
 
 int64_t refine(const Graph &g, int32_t k, const int32_t *caps_host, int32_t rounds, uint64_t seed,
-               int32_t *part, LPStats *st) {
+               int32_t *part, LPStats *st, bool want_cut) {
   cudaStream_t s = ctx().stream;
-  DBuf<int64_t> bw64(k), cut(1);
+  DBuf<int64_t> bw64(k);
   DBuf<int32_t> bw(k), cap(k);
   to_dev(cap.p, caps_host, k);
-  cut_and_weights(g, part, k, bw64, cut);
+  block_weights(g, part, k, bw64);
   k_bw_to_i32<<<grid_for(k, 256), 256, 0, s>>>(k, bw64, bw);
   KMP_LAUNCHED("bw_to_i32");
   lp_run(g, part, bw, k, cap, 0, rounds, key_of(seed, {DOM_REFINE}), nullptr, st);
+  if (!want_cut) return 0;
+  DBuf<int64_t> cut(1);
   cut_and_weights(g, part, k, bw64, cut);
   return read1(cut.p);
 }
@@ -324,7 +326,7 @@ static void partition_graph(const Graph &g0, int32_t k, double eps, uint64_t see
     }
     LPStats rs;
     refine(g, nblocks, caps.data(), cfg.refine_rounds, key_of(seed, {DOM_REFINE_LEVEL, (uint64_t)l}),
-           part, &rs);
+           part, &rs, false);
     st->refine_scanned += rs.scanned;
     st->ms_refine += rs.ms;
   }
@@ -600,6 +602,61 @@ int kmp_last_stats(kmp_stats *stats) {
   if (!stats) return KMP_ERR_ARG;
   *stats = g_last_stats;
   return KMP_OK;
+}
+
+int kmp_set_tuning(const kmp_tuning *t) {
+  return guarded([&] {
+    if (!t) fail(KMP_ERR_ARG, "tuning is NULL");
+    bool pow2 = t->hub_chunk > 0 && (t->hub_chunk & (t->hub_chunk - 1)) == 0;
+    if (t->rate_blocks_per_sm < 2 || t->rate_blocks_per_sm > 16 || t->hub_degree < 256 ||
+        t->hub_degree > 2048 || !pow2 || t->hub_chunk < 256 || t->hub_chunk > 65536 ||
+        t->ip_blocks_per_sm < 1 || t->ip_blocks_per_sm > 8)
+      fail(KMP_ERR_ARG, "invalid tuning");
+    ctx().tune = *t;
+  });
+}
+
+int kmp_get_tuning(kmp_tuning *t) {
+  return guarded([&] {
+    if (!t) fail(KMP_ERR_ARG, "tuning is NULL");
+    *t = ctx().tune;
+  });
+}
+
+int kmp_autotune(const kmp_graph *g, int32_t k, double eps, uint64_t seed, kmp_tuning *best) {
+  return guarded([&] {
+    if (!g || !best) fail(KMP_ERR_ARG, "NULL argument");
+    if (k < 1 || !(eps > 0.0)) fail(KMP_ERR_ARG, "invalid k or eps");
+    Context &C = ctx();
+    const Graph &G = g->g;
+    kmp_tuning keep = C.tune, bestt = C.tune;
+    float bestms = -1.f;
+    int64_t kp = G.n / C.cfg.C;
+    if (kp > k) kp = k;
+    if (kp < 1) kp = 1;
+    int64_t U = (int64_t)std::floor(eps * (double)G.total_vw / (double)kp);
+    if (U < G.max_vw) U = G.max_vw;
+    if (U < 1) U = 1;
+    DBuf<int32_t> label(G.n > 0 ? G.n : 1);
+    const int grids[3] = {4, 6, 8};
+    const int hubs[2] = {1024, 2048};
+    const int chunks[2] = {1024, 4096};
+    for (int gi : grids)
+      for (int hd : hubs)
+        for (int hc : chunks) {
+          C.tune = kmp_tuning{gi, hd, hc, keep.ip_blocks_per_sm};
+          LPStats st;
+          cluster_level(G, (int32_t)U, C.cfg.lp_rounds, key_of(seed, {DOM_COARSEN, 0}), false, label,
+                        nullptr, &st, nullptr);
+          if (bestms < 0 || st.ms < bestms) {
+            bestms = st.ms;
+            bestt = C.tune;
+          }
+        }
+    C.tune = bestt;
+    sync_and_check("autotune");
+    *best = bestt;
+  });
 }
 
 int kmp_set_profiling(int on) {

@@ -196,50 +196,106 @@ __global__ void __launch_bounds__(BAL_T) k_bal_sort(BalArgs A) {
     A.keys[lo + i] = ((uint64_t)(uint32_t)B << A.bitsN) | (uint64_t)(uint32_t)vv[i];
 }
 
-// sequential moves by one warp
-__global__ void __launch_bounds__(32) k_bal_moves(BalArgs A) {
-  __shared__ int32_t sk[BAL_STAB], sv[BAL_STAB];
-  int lane = threadIdx.x & 31;
-  int32_t *K = sk, *V = sv;
-  if (A.gtab) {
-    K = A.gtab;
-    V = K + A.gcap;
-  }
+// Moves in candidate order, evaluated 32 at a time.  Warp j computes the
+// target of candidate i+j from the state at the start of the batch; thread 0
+// then commits them in order.  While a block is emptied, every other block
+// only gains weight, so a target that is still admissible is still the best
+// (or still the lowest-id admissible one), and "no admissible target" stays
+// true; only a move of a neighbour changes connectivity.  A candidate passes
+// iff its target still fits and no earlier move of the batch was its
+// neighbour; at the first one that does not, the next batch starts there (its
+// first candidate always passes).  The result equals one move at a time.
+constexpr int BM_T = 1024;
+constexpr int BM_W = BM_T / 32;
+
+__global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch) {
+  __shared__ int32_t s_v[BM_W], s_t[BM_W];
+  __shared__ int64_t s_c[BM_W];
+  __shared__ uint32_t s_adj[BM_W];
+  __shared__ int32_t s_next, s_stop;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t *K = A.gtab + (int64_t)w * 2 * A.gcap, *V = K + A.gcap;
   uint64_t mask = (1ull << A.bitsN) - 1ull;
   for (int32_t B = 0; B < A.k; ++B) {
     if (!A.over[B]) continue;
     int32_t lo = A.seg_lo[B], hi = A.seg_hi[B];
-    for (int32_t i = lo; i < hi; ++i) {
+    int32_t i = lo;
+    while (i < hi) {
       if (A.bw[B] <= A.cap[B]) break;
-      int32_t v = (int32_t)(A.keys[i] & mask);
-      int64_t c = bw_node(A, v);
-      uint32_t tm;
-      conn_table(A, v, K, V, tm);
-      uint64_t bestk = 0;  // (conn, ~block): largest connectivity, then lowest id
-      for (uint32_t x = lane; x <= tm; x += 32) {
-        int32_t b = K[x];
-        if (b == HT_EMPTY || b == B) continue;
-        if (A.bw[b] + c > A.cap[b]) continue;
-        uint64_t key = ((uint64_t)(uint32_t)V[x] << 32) | (0xFFFFFFFFu - (uint32_t)b);
-        bestk = key > bestk ? key : bestk;
+      int32_t nb = hi - i < BM_W ? hi - i : BM_W;
+      if (w < nb) {
+        int32_t v = (int32_t)(A.keys[i + w] & mask);
+        if (lane == 0) {
+          s_v[w] = v;
+          inbatch[v] = w + 1;
+        }
       }
-      bestk = group_max64<32>(bestk);
-      int32_t t = bestk ? (int32_t)(0xFFFFFFFFu - (uint32_t)bestk) : -1;
-      if (t < 0) {
-        int32_t low = INT32_MAX;
-        for (int32_t b = lane; b < A.k; b += 32)
-          if (b != B && A.bw[b] + c <= A.cap[b]) { low = b; break; }
+      __syncthreads();
+      if (w < nb) {
+        int32_t v = s_v[w];
+        int64_t c = bw_node(A, v);
+        uint32_t tm;
+        conn_table(A, v, K, V, tm);
+        uint64_t bestk = 0;  // (conn, ~block): largest connectivity, then lowest id
+        for (uint32_t x = lane; x <= tm; x += 32) {
+          int32_t b = K[x];
+          if (b == HT_EMPTY || b == B) continue;
+          if (A.bw[b] + c > A.cap[b]) continue;
+          uint64_t key = ((uint64_t)(uint32_t)V[x] << 32) | (0xFFFFFFFFu - (uint32_t)b);
+          bestk = key > bestk ? key : bestk;
+        }
+        bestk = group_max64<32>(bestk);
+        int32_t t = bestk ? (int32_t)(0xFFFFFFFFu - (uint32_t)bestk) : -1;
+        if (t < 0) {
+          int32_t low = INT32_MAX;
+          for (int32_t b = lane; b < A.k; b += 32)
+            if (b != B && A.bw[b] + c <= A.cap[b]) { low = b; break; }
 #pragma unroll
-        for (int m = 16; m > 0; m >>= 1) low = min(low, __shfl_xor_sync(0xFFFFFFFFu, low, m));
-        t = low == INT32_MAX ? -1 : low;
+          for (int m = 16; m > 0; m >>= 1) low = min(low, __shfl_xor_sync(0xFFFFFFFFu, low, m));
+          t = low == INT32_MAX ? -1 : low;
+        }
+        // which batch members are neighbours of v
+        uint32_t am = 0;
+        for (int64_t q = A.xadj[v] + lane; q < A.xadj[v + 1]; q += 32) {
+          int32_t j = inbatch[A.adj[q]];
+          if (j > 0) am |= 1u << (j - 1);
+        }
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) am |= __shfl_xor_sync(0xFFFFFFFFu, am, m);
+        if (lane == 0) {
+          s_t[w] = t;
+          s_c[w] = c;
+          s_adj[w] = am;
+        }
       }
-      if (t >= 0 && lane == 0) {
-        A.part[v] = t;
-        A.bw[B] -= c;
-        A.bw[t] += c;
-        atomicAdd(A.moved, 1ull);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        uint32_t moved_mask = 0;
+        int32_t j = 0;
+        s_stop = 0;
+        for (; j < nb; ++j) {
+          if (A.bw[B] <= A.cap[B]) {
+            s_stop = 1;
+            break;
+          }
+          int32_t t = s_t[j];
+          int64_t c = s_c[j];
+          if (j > 0 && ((s_adj[j] & moved_mask) || (t >= 0 && A.bw[t] + c > A.cap[t]))) break;
+          if (t >= 0) {
+            A.part[s_v[j]] = t;
+            A.bw[B] -= c;
+            A.bw[t] += c;
+            atomicAdd(A.moved, 1ull);
+            moved_mask |= 1u << j;
+          }
+        }
+        s_next = j;
       }
-      __syncwarp();
+      __syncthreads();
+      if (w < nb && lane == 0) inbatch[s_v[w]] = 0;
+      __syncthreads();
+      i += s_next;
+      if (s_stop) break;
     }
   }
 }
@@ -248,8 +304,8 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   Context &C = ctx();
   cudaStream_t s = C.stream;
   int32_t n = g.n;
-  DBuf<int64_t> bw(k), cut(1);
-  cut_and_weights(g, part, k, bw, cut);
+  DBuf<int64_t> bw(k);
+  block_weights(g, part, k, bw);
   std::vector<int64_t> hbw(k);
   to_host(hbw.data(), bw.p, k);
   std::vector<uint8_t> hover(k, 0);
@@ -322,12 +378,11 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   KMP_LAUNCHED("bal_segments");
   k_bal_sort<<<k, BAL_T, 0, s>>>(A);
   KMP_LAUNCHED("bal_sort");
-  DBuf<int32_t> gtab1;
-  if (gcap > BAL_STAB) {
-    gtab1.alloc(2ll * gcap);
-    A.gtab = gtab1;
-  }
-  k_bal_moves<<<1, 32, 0, s>>>(A);
+  // one global table per warp of the move kernel, and the batch membership marks
+  DBuf<int32_t> gtab1(2ll * gcap * BM_W), inbatch(n);
+  inbatch.zero();
+  A.gtab = gtab1;
+  k_bal_moves<<<1, BM_T, 0, s>>>(A, inbatch);
   KMP_LAUNCHED("bal_moves");
   return (int64_t)read1(moved.p);
 }

@@ -168,22 +168,39 @@ __global__ void k_large_sizes(int32_t nc, const unsigned long long *cub, int64_t
   }
 }
 
-// one warp per member position; members of small rows are skipped
-__global__ void __launch_bounds__(256) k_large_insert(int32_t n, const int64_t *xadj, const int32_t *adj,
+// work units: chunks of LARGE_CHUNK entries of the rows of members of large
+// coarse nodes (so one very high-degree member is spread over many warps)
+constexpr int64_t LARGE_CHUNK = 512;
+
+__global__ void k_large_chunks(int32_t n, const int64_t *xadj, const int32_t *map,
+                               const unsigned long long *cub, int64_t *nch) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    nch[v] = cub[map[v]] > (unsigned long long)CW_UB ? ceil_div(xadj[v + 1] - xadj[v], LARGE_CHUNK) : 0;
+}
+
+__global__ void __launch_bounds__(256) k_large_insert(int32_t n, int64_t total, const int64_t *choff,
+                                                      const int64_t *xadj, const int32_t *adj,
                                                       const int32_t *ew, const int32_t *map,
-                                                      const int32_t *members,
-                                                      const unsigned long long *cub, const int64_t *ltoff,
-                                                      const int64_t *tsz, int32_t *lk, int32_t *lv) {
+                                                      const int64_t *ltoff, const int64_t *tsz, int32_t *lk,
+                                                      int32_t *lv) {
   int lane = threadIdx.x & 31;
   int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = gw; i < n; i += nw) {
-    int32_t v = members[i];
-    int32_t x = map[v];
-    if (cub[x] <= (unsigned long long)CW_UB) continue;
+  for (int64_t c = gw; c < total; c += nw) {
+    // node owning chunk c: last v with choff[v] <= c (ties resolve to the node with chunks)
+    int32_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+      int32_t mid = (lo + hi + 1) >> 1;
+      if (choff[mid] <= c) lo = mid;
+      else hi = mid - 1;
+    }
+    int32_t v = lo, x = map[v];
     int32_t *K = lk + ltoff[x], *V = lv + ltoff[x];
     uint32_t mask = (uint32_t)(tsz[x] - 1);
-    for (int64_t q = xadj[v] + lane; q < xadj[v + 1]; q += 32) {
+    int64_t b = xadj[v] + (c - choff[v]) * LARGE_CHUNK;
+    int64_t e = b + LARGE_CHUNK < xadj[v + 1] ? b + LARGE_CHUNK : xadj[v + 1];
+    for (int64_t q = b + lane; q < e; q += 32) {
       int32_t y = map[adj[q]];
       if (y != x) ht_add(K, V, mask, y, ew ? ew[q] : 1);
     }
@@ -383,8 +400,13 @@ Graph contract_graph(const Graph &g, const int32_t *label, int32_t *map) {
     lk.fill_bytes(0xFF);
     lv.zero();
     lcnt.zero();
-    k_large_insert<<<grid_for((int64_t)n * 32, 256, 8), 256, 0, s>>>(
-        n, g.xadj, g.adj, g.ew, map, members, cub, ltoff, tsz, lk, lv);
+    DBuf<int64_t> nch(n), choff(n), chtot(1);
+    k_large_chunks<<<grid, 256, 0, s>>>(n, g.xadj, map, cub, nch);
+    KMP_LAUNCHED("large_chunks");
+    scan_excl_i64(nch, choff, n, chtot);
+    int64_t CT = read1(chtot.p);
+    k_large_insert<<<grid_for(CT * 32, 256, 8), 256, 0, s>>>(n, CT, choff, g.xadj, g.adj, g.ew, map,
+                                                             ltoff, tsz, lk, lv);
     KMP_LAUNCHED("large_insert");
     int64_t cap_entries = LT / 2 + 1;
     DBuf<uint64_t> ek(cap_entries), ektmp(cap_entries);
@@ -470,6 +492,35 @@ __global__ void __launch_bounds__(256) k_cut_bw(int32_t n, int32_t k, const int6
 }
 
 __global__ void k_half(int64_t *c) { *c /= 2; }
+
+// block weights only (no edge traffic)
+__global__ void __launch_bounds__(256) k_bw_only(int32_t n, int32_t k, const int32_t *vw,
+                                                 const int32_t *part, unsigned long long *bw) {
+  __shared__ unsigned long long sbw[CUT_SBW];
+  bool local = k <= CUT_SBW;
+  if (local)
+    for (int i = threadIdx.x; i < k; i += blockDim.x) sbw[i] = 0;
+  __syncthreads();
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long w = (unsigned long long)(vw ? vw[v] : 1);
+    if (local) atomicAdd(&sbw[part[v]], w);
+    else atomicAdd(&bw[part[v]], w);
+  }
+  __syncthreads();
+  if (local)
+    for (int i = threadIdx.x; i < k; i += blockDim.x)
+      if (sbw[i]) atomicAdd(&bw[i], sbw[i]);
+}
+
+void block_weights(const Graph &g, const int32_t *part, int32_t k, int64_t *bw_dev) {
+  cudaStream_t s = ctx().stream;
+  KMP_CUDA(cudaMemsetAsync(bw_dev, 0, (size_t)k * sizeof(int64_t), s));
+  if (g.n == 0) return;
+  k_bw_only<<<grid_for(g.n, 256, 4), 256, 0, s>>>(g.n, k, g.vw, part,
+                                                  reinterpret_cast<unsigned long long *>(bw_dev));
+  KMP_LAUNCHED("bw_only");
+}
 
 void cut_and_weights(const Graph &g, const int32_t *part, int32_t k, int64_t *bw_dev,
                      int64_t *cut_dev) {

@@ -20,6 +20,7 @@ struct Error {
 };
 
 [[noreturn]] void fail(int code, const std::string &msg);
+void set_last_error(const std::string &s);  // message kmp_last_error returns
 void check_cuda(cudaError_t e, const char *what);
 #define KMP_CUDA(call) ::kmp::check_cuda((call), #call)
 // after a kernel launch: launch errors only (no sync)
@@ -37,6 +38,8 @@ struct Context {
   int device = 0;
   int64_t launches = 0;
   int *d_status = nullptr;  // device status word: 0 ok, else KMP_ERR_* set by kernels
+  // schedule parameters (never change results); see kmp_autotune
+  kmp_tuning tune{6, 2048, 2048, 4};
   // live profiling of the LP rating launches (CUDA events on `stream`)
   bool profile = false;
   double prof_rate_ms = 0, prof_rate_bytes = 0;
@@ -259,9 +262,11 @@ void project(int32_t n_fine, const int32_t *map, const int32_t *part_c, int32_t 
 // cut and block weights (device out arrays: bw int64[k], cut int64[1])
 void cut_and_weights(const Graph &g, const int32_t *part, int32_t k, int64_t *bw_dev,
                      int64_t *cut_dev);
-// refinement wrapper: caps host int32[k]
+// block weights only (device out int64[k])
+void block_weights(const Graph &g, const int32_t *part, int32_t k, int64_t *bw_dev);
+// refinement wrapper: caps host int32[k]; returns the cut when want_cut, else 0
 int64_t refine(const Graph &g, int32_t k, const int32_t *caps_host, int32_t rounds,
-               uint64_t seed, int32_t *part, LPStats *st);
+               uint64_t seed, int32_t *part, LPStats *st, bool want_cut = true);
 int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *part);
 // Algorithm 2, one split round; f in/out (host), returns new block count
 int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::vector<int32_t> &f,

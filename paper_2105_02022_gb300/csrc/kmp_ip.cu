@@ -184,6 +184,25 @@ __device__ void warp_bitonic_hv(uint64_t *h, int32_t *v, int32_t P) {
     }
 }
 
+// warp bitonic of P (power of two) 64-bit keys ascending
+__device__ void warp_bitonic_u64(uint64_t *a, int32_t P) {
+  int lane = threadIdx.x & 31;
+  for (int32_t k = 2; k <= P; k <<= 1)
+    for (int32_t j = k >> 1; j > 0; j >>= 1) {
+      for (int32_t i = lane; i < P; i += 32) {
+        int32_t l = i ^ j;
+        if (l > i) {
+          uint64_t x = a[i], y = a[l];
+          if ((x > y) == ((i & k) == 0)) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncwarp();
+    }
+}
+
 __device__ __forceinline__ int32_t pow2_at_least(int32_t x) {
   int32_t p = 1;
   while (p < x) p <<= 1;
@@ -193,13 +212,16 @@ __device__ __forceinline__ int32_t pow2_at_least(int32_t x) {
 // ------------------------------------------------------ item clustering
 // rating of node u by one warp; returns (via lane 0) proposal target or -1
 __device__ void item_rate(const LG &g, int32_t u, const int32_t *label, const int32_t *wt, int32_t U,
-                          uint32_t rk_hi, int32_t *keys, int32_t *vals, int32_t *out_t,
-                          int32_t *out_g) {
+                          uint32_t rk_hi, int32_t *skeys, int32_t *svals, int32_t *gkeys,
+                          int32_t *gvals, int32_t *out_t, int32_t *out_g) {
   int lane = threadIdx.x & 31;
   int32_t b = g.xadj[u], e = g.xadj[u + 1], deg = e - b;
   uint32_t cap = 32;
   while ((int64_t)cap < 2ll * deg) cap <<= 1;
   uint32_t mask = cap - 1;
+  // shared-memory table unless this node's table does not fit there
+  int32_t *keys = cap <= (uint32_t)IP_WTAB ? skeys : gkeys;
+  int32_t *vals = cap <= (uint32_t)IP_WTAB ? svals : gvals;
   for (uint32_t i = lane; i < cap; i += 32) {
     keys[i] = HT_EMPTY;
     vals[i] = 0;
@@ -288,9 +310,10 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
   }
   __syncthreads();
   int32_t *mk = wkeys + w * IP_WTAB, *mv = wvals + w * IP_WTAB;
+  int32_t *gk = nullptr, *gv = nullptr;
   if (gtab) {
-    mk = gtab + (int64_t)w * 2 * gcap;
-    mv = mk + gcap;
+    gk = gtab + (int64_t)w * 2 * gcap;
+    gv = gk + gcap;
   }
   for (int32_t r = 0; r < A.ip_lp_rounds; ++r) {
     uint64_t rk = key_step(basekey, (uint64_t)r);
@@ -303,7 +326,7 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
       for (int32_t u = w; u < n; u += IPW) {
         bool rate = act[u] && g.xadj[u + 1] > g.xadj[u] &&
                     (int32_t)(key_step(rk, (uint64_t)(uint32_t)u) & (uint64_t)(A.S - 1)) == s;
-        if (rate) item_rate(g, u, label, wt, U, rk_hi, mk, mv, &pt[u], &pg[u]);
+        if (rate) item_rate(g, u, label, wt, U, rk_hi, mk, mv, gk, gv, &pt[u], &pg[u]);
         else if (lane == 0) pt[u] = -1;
       }
       if (threadIdx.x == 0) s_cnt = 0;
@@ -359,18 +382,22 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
           __syncthreads();
         }
         // apply
+        // one warp per accepted move: lane 0 moves the node, the lanes mark its
+        // neighbours active for the next round
         int32_t mv_local = 0;
-        for (int32_t i = threadIdx.x; i < np; i += IPT) {
+        for (int32_t i = w; i < np; i += IPW) {
           uint64_t k = pl[i];
           if (!(k >> 63)) continue;
           int32_t T = (int32_t)((k >> 47) & 0xFFFF);
           int32_t u = (int32_t)(k & 0xFFFF);
-          int32_t own = label[u], c = g.vw[u];
-          label[u] = T;
-          atomicAdd(&wt[T], c);
-          atomicSub(&wt[own], c);
-          ++mv_local;
-          for (int32_t q = g.xadj[u]; q < g.xadj[u + 1]; ++q) act2[g.adj[q]] = 1;
+          if (lane == 0) {
+            int32_t own = label[u], c = g.vw[u];
+            label[u] = T;
+            atomicAdd(&wt[T], c);
+            atomicSub(&wt[own], c);
+            ++mv_local;
+          }
+          for (int32_t q = g.xadj[u] + lane; q < g.xadj[u + 1]; q += 32) act2[g.adj[q]] = 1;
         }
         if (mv_local) atomicAdd(&s_moved, mv_local);
       }
@@ -419,8 +446,8 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
 }
 
 // contraction of one item level; fills *out (arrays allocated from B)
-__device__ void item_contract(const LG &g, const int32_t *label, int32_t *map, LG *out, Bump &B) {
-  __shared__ int32_t s_cnt;
+__device__ void item_contract(const LG &g, const int32_t *label, int32_t *map, LG *out, Bump &B,
+                              int32_t *wkeys, int32_t *wvals) {
   int32_t n = g.n;
   int32_t *cid = B.take(n + 1);
   if (B.oom) return;
@@ -431,10 +458,9 @@ __device__ void item_contract(const LG &g, const int32_t *label, int32_t *map, L
   int32_t nc = block_scan_excl<int32_t>(cid, cid, n);
   for (int32_t v = threadIdx.x; v < n; v += IPT) map[v] = cid[label[v]];
   __syncthreads();
-  // coarse arrays (kept)
+  // coarse arrays (kept); rows hold at most the cross entries of the level
   int32_t *cvw = B.take(nc);
   int32_t *cx = B.take(nc + 1);
-  // pair count
   int64_t cnt = 0;
   for (int32_t v = threadIdx.x; v < n; v += IPT)
     for (int32_t q = g.xadj[v]; q < g.xadj[v + 1]; ++q) cnt += (map[v] != map[g.adj[q]]);
@@ -442,54 +468,96 @@ __device__ void item_contract(const LG &g, const int32_t *label, int32_t *map, L
   int32_t *cadj = B.take(np);
   int32_t *cew = B.take(np);
   int64_t mark = B.top;
-  int32_t P = pow2_at_least(np > 1 ? np : 2);
-  uint64_t *key = reinterpret_cast<uint64_t *>(B.take(2ll * P));
-  int32_t *val = B.take(P);
-  int32_t *head = B.take(P + 1);
+  // members grouped by coarse node; members' total degree per coarse node
+  int32_t *moff = B.take(nc + 1), *mcur = B.take(nc), *members = B.take(n);
+  int32_t *ub = B.take(nc + 1), *toff = B.take(nc + 1), *rowlen = B.take(nc + 1);
+  int32_t *tadj = B.take(g.m > 0 ? g.m : 1), *tw = B.take(g.m > 0 ? g.m : 1);
   if (B.oom) return;
-  for (int32_t x = threadIdx.x; x < nc; x += IPT) {
-    cvw[x] = 0;
-    cx[x] = 0;
-  }
-  if (threadIdx.x == 0) {
-    s_cnt = 0;
-    cx[nc] = 0;
+  for (int32_t x = threadIdx.x; x <= nc; x += IPT) {
+    if (x < nc) {
+      cvw[x] = 0;
+      mcur[x] = 0;
+    }
+    moff[x] = 0;
+    ub[x] = 0;
   }
   __syncthreads();
   for (int32_t v = threadIdx.x; v < n; v += IPT) {
-    atomicAdd(&cvw[map[v]], g.vw[v]);
-    int32_t a = map[v];
-    for (int32_t q = g.xadj[v]; q < g.xadj[v + 1]; ++q) {
-      int32_t b = map[g.adj[q]];
-      if (a == b) continue;
-      int32_t p = atomicAdd(&s_cnt, 1);
-      key[p] = ((uint64_t)(uint32_t)a << 32) | (uint32_t)b;
-      val[p] = g.ew[q];
+    int32_t x = map[v];
+    atomicAdd(&cvw[x], g.vw[v]);
+    atomicAdd(&moff[x], 1);
+    atomicAdd(&ub[x], g.xadj[v + 1] - g.xadj[v]);
+  }
+  __syncthreads();
+  block_scan_excl<int32_t>(moff, moff, nc + 1);
+  int32_t maxub = 0;
+  for (int32_t x = threadIdx.x; x < nc; x += IPT) maxub = max(maxub, ub[x]);
+  maxub = block_max32(maxub);
+  block_scan_excl<int32_t>(ub, toff, nc + 1);
+  for (int32_t v = threadIdx.x; v < n; v += IPT) {
+    int32_t x = map[v];
+    members[moff[x] + atomicAdd(&mcur[x], 1)] = v;
+  }
+  // per-warp global table and sort list for rows that do not fit shared memory
+  int32_t dmax = maxub < nc ? maxub : nc;
+  int32_t gcap = 32;
+  while (gcap < 2 * dmax) gcap <<= 1;
+  int32_t lcap = pow2_at_least(dmax > 1 ? dmax : 2);
+  int32_t *gtab = gcap > IP_WTAB ? B.take(2ll * gcap * IPW) : nullptr;
+  uint64_t *lbuf = reinterpret_cast<uint64_t *>(B.take(2ll * lcap * IPW));
+  __syncthreads();
+  if (B.oom) return;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint64_t *L = lbuf + (int64_t)w * lcap;
+  // one warp per coarse node: aggregate, compact, sort by neighbour, write the row
+  for (int32_t x = w; x < nc; x += IPW) {
+    int32_t d = ub[x] < nc ? ub[x] : nc;
+    uint32_t cap = 32;
+    while ((int32_t)cap < 2 * d) cap <<= 1;
+    int32_t *K = cap <= (uint32_t)IP_WTAB ? wkeys + w * IP_WTAB : gtab + (int64_t)w * 2 * gcap;
+    int32_t *V = cap <= (uint32_t)IP_WTAB ? wvals + w * IP_WTAB : K + gcap;
+    for (uint32_t i = lane; i < cap; i += 32) {
+      K[i] = HT_EMPTY;
+      V[i] = 0;
     }
-  }
-  for (int32_t i = np + threadIdx.x; i < P; i += IPT) {
-    key[i] = ~0ull;
-    val[i] = 0;
+    __syncwarp();
+    for (int32_t mi = moff[x]; mi < moff[x + 1]; ++mi) {
+      int32_t v = members[mi];
+      for (int32_t q = g.xadj[v] + lane; q < g.xadj[v + 1]; q += 32) {
+        int32_t y = map[g.adj[q]];
+        if (y != x) ht_add(K, V, cap - 1, y, g.ew[q]);
+      }
+    }
+    __syncwarp();
+    int32_t c = 0;
+    for (uint32_t i0 = 0; i0 < cap; i0 += 32) {
+      uint32_t i = i0 + lane;
+      bool has = K[i] != HT_EMPTY;
+      unsigned bal = __ballot_sync(0xFFFFFFFFu, has);
+      if (has) L[c + __popc(bal & ((1u << lane) - 1u))] = ((uint64_t)(uint32_t)K[i] << 32) | (uint32_t)V[i];
+      c += __popc(bal);
+    }
+    int32_t P = pow2_at_least(c > 1 ? c : 2);
+    for (int32_t i = c + lane; i < P; i += 32) L[i] = ~0ull;
+    __syncwarp();
+    warp_bitonic_u64(L, P);
+    for (int32_t i = lane; i < c; i += 32) {
+      tadj[toff[x] + i] = (int32_t)(L[i] >> 32);
+      tw[toff[x] + i] = (int32_t)(uint32_t)L[i];
+    }
+    if (lane == 0) rowlen[x] = c;
+    __syncwarp();
   }
   __syncthreads();
-  block_bitonic(key, val, P);
-  for (int32_t i = threadIdx.x; i < np; i += IPT) head[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
+  if (threadIdx.x == 0) rowlen[nc] = 0;
   __syncthreads();
-  int32_t m2 = block_scan_excl<int32_t>(head, head, np);  // head[i] -> exclusive rank
-  // run sums: each run head sums its run
-  for (int32_t i = threadIdx.x; i < np; i += IPT) {
-    bool h = (i == 0 || key[i] != key[i - 1]);
-    if (!h) continue;
-    int64_t s = 0;
-    int32_t j = i;
-    while (j < np && key[j] == key[i]) s += val[j++];
-    int32_t r = head[i];
-    cadj[r] = (int32_t)(uint32_t)key[i];
-    cew[r] = (int32_t)s;
-    atomicAdd(&cx[(int32_t)(key[i] >> 32)], 1);
-  }
+  int32_t m2 = block_scan_excl<int32_t>(rowlen, cx, nc + 1);
+  for (int32_t x = w; x < nc; x += IPW)
+    for (int32_t i = lane; i < cx[x + 1] - cx[x]; i += 32) {
+      cadj[cx[x] + i] = tadj[toff[x] + i];
+      cew[cx[x] + i] = tw[toff[x] + i];
+    }
   __syncthreads();
-  block_scan_excl<int32_t>(cx, cx, nc + 1);
   B.top = mark;
   out->n = nc;
   out->m = m2;
@@ -763,7 +831,7 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
     if (nc == g.n) break;
     int32_t *map = B.take(g.n);
     LG c;
-    item_contract(g, label, map, &c, B);
+    item_contract(g, label, map, &c, B, wkeys, wvals);
     if (B.oom) break;
     int32_t cmd = 0, cmc = 0;
     for (int32_t x = threadIdx.x; x < c.n; x += IPT) {
@@ -1131,7 +1199,7 @@ int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::
       A.fm_stop = cfg.fm_stop;
       A.conv_num = cfg.conv_num;
       A.conv_den = cfg.conv_den;
-      int gridip = (int)std::min<int64_t>((int64_t)items.size(), (int64_t)C.sms * 4);
+      int gridip = (int)std::min<int64_t>((int64_t)items.size(), (int64_t)C.sms * C.tune.ip_blocks_per_sm);
       k_ip_items<<<gridip, IPT, 0, s>>>(A);
       KMP_LAUNCHED("ip_items");
       int32_t oom = 0;

@@ -29,15 +29,15 @@ constexpr int BIN_TILE = 2048;  // nodes per binning tile
 constexpr int RATE_T = 256;
 constexpr int WARP_TAB = 512;   // per-warp hash table (bin 4: degree <= 256)
 constexpr int CTA_TAB = 4096;   // per-CTA shared table (bin 5: degree <= 2048)
-constexpr int64_t HUGE_DEG = 2048;
+constexpr int64_t HUGE_DEG_MAX = CTA_TAB / 2;  // largest degree a shared CTA table serves
 
-__host__ __device__ __forceinline__ int deg_bin(int64_t d) {
+__host__ __device__ __forceinline__ int deg_bin(int64_t d, int64_t huge) {
   if (d <= 4) return 0;
   if (d <= 8) return 1;
   if (d <= 16) return 2;
   if (d <= 32) return 3;
   if (d <= 256) return 4;
-  if (d <= HUGE_DEG) return 5;
+  if (d <= huge) return 5;
   return 6;
 }
 
@@ -70,7 +70,7 @@ struct LPArgs {
   int32_t *ctr;                // [0] slots, [1] bucket top, [2] big movers
   int32_t *bigmove;            // high-degree nodes that moved in this sub-round
   unsigned long long *ctr64;   // [0] scanned entries, [1] moved nodes
-  // bin 6 (degree > HUGE_DEG) with many labels: per-hub global tables filled
+  // bin 6 (degree > huge_deg) with many labels: per-hub global tables filled
   // by many CTAs in parallel
   const int32_t *hubs;         // hub node ids, ascending
   int32_t nhubs;
@@ -80,12 +80,13 @@ struct LPArgs {
   unsigned long long *hkc;     // best admissible key per hub
   unsigned long long *hku;     // best key per hub
   int32_t *hrown;              // rating of the hub's own cluster
-  int32_t *hstamp;             // per hub: stamp of the sub-round it is rated in
-  const int64_t *hechunk;      // per hub: first edge chunk (exclusive prefix)
-  const int64_t *htchunk;      // per hub: first table chunk
-  int64_t hchunks_total, htchunks_total;
-  int32_t stamp;               // stamp of the current sub-round (round * S + s + 1)
+  int32_t *plan_h;             // per sub-round hub plan: hub index of each bin-6 entry,
+  int64_t *plan_e;             // exclusive prefix of its edge chunks,
+  int64_t *plan_t;             // exclusive prefix of its table chunks,
+  int64_t *plan_tot;           // [0] edge chunks, [1] table chunks
   int32_t small_labels;        // all labels fit a CTA table: bin 6 handled like bin 5
+  int64_t huge_deg;            // degree above which a node is a hub (<= HUGE_DEG_MAX)
+  int64_t hub_chunk;           // edges per hub insert work unit
   int32_t nlab;
   int32_t S;
   uint64_t rk;
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(256) k_bin_count(LPArgs A, int32_t *cnt, int64
     int64_t d = A.xadj[v + 1] - A.xadj[v];
     if (d == 0) continue;
     int s = (int)(key_step(A.rk, (uint64_t)(uint32_t)v) & (uint64_t)(A.S - 1));
-    atomicAdd(&c[s * NB + deg_bin(d)], 1);
+    atomicAdd(&c[s * NB + deg_bin(d, A.huge_deg)], 1);
     atomicAdd(&sdeg[s], (unsigned long long)d);
     my += (unsigned long long)d;
   }
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(LPArgs A, const int32_t *of
       int64_t d = A.xadj[v + 1] - A.xadj[v];
       if (d > 0) {
         int s = (int)(key_step(A.rk, (uint64_t)(uint32_t)v) & (uint64_t)(A.S - 1));
-        k = s * NB + deg_bin(d);
+        k = s * NB + deg_bin(d, A.huge_deg);
       }
     }
     if (v < A.n) A.act[v] = 0;
@@ -245,14 +246,14 @@ __device__ __forceinline__ void rate_group(const LPArgs &A, int32_t u, int32_t p
     l = A.label[A.adj[beg + gl]];
     w = edge_w(A, beg + gl);
   }
-  int32_t r = 0, rown = 0;
-#pragma unroll
-  for (int j = 0; j < G; ++j) {
-    int32_t lj = __shfl_sync(0xFFFFFFFFu, l, j, G);
-    int32_t wj = __shfl_sync(0xFFFFFFFFu, w, j, G);
-    r += (lj == l) ? wj : 0;
-    rown += (lj == own) ? wj : 0;
-  }
+  // lanes of one group holding the same label form a peer set; its weight sum
+  // is the rating r(label)
+  uint64_t mkey = ((uint64_t)(uint32_t)(lane / G) << 32) | (uint32_t)l;
+  unsigned peers = __match_any_sync(0xFFFFFFFFu, mkey);
+  int32_t r = __reduce_add_sync(peers, w);
+  unsigned bown = __ballot_sync(0xFFFFFFFFu, l >= 0 && l == own) & gmask;
+  int32_t rown = __shfl_sync(0xFFFFFFFFu, r, bown ? __ffs(bown) - 1 : lane);
+  if (!bown) rown = 0;
   bool valid = l >= 0 && l != own;
   uint64_t ku = valid ? rate_key(A, l, r) : 0ull;
   bool adm = valid && ((int64_t)A.wt[l] + cu <= cap_of(A, l));
@@ -268,22 +269,22 @@ __device__ __forceinline__ void rate_group(const LPArgs &A, int32_t u, int32_t p
 // one node per warp, neighbours aggregated in a shared-memory table of WARP_TAB
 __device__ __forceinline__ void rate_warp(const LPArgs &A, int32_t u, int32_t pos, int lane,
                                           int32_t *keys, int32_t *vals) {
-#pragma unroll
-  for (int i = lane; i < WARP_TAB; i += 32) {
+  int64_t beg = A.xadj[u];
+  int32_t deg = (int32_t)(A.xadj[u + 1] - beg);
+  uint32_t tcap = table_cap(deg, A.nlab);  // <= WARP_TAB for degree <= 256
+  for (uint32_t i = lane; i < tcap; i += 32) {
     keys[i] = HT_EMPTY;
     vals[i] = 0;
   }
   __syncwarp();
-  int64_t beg = A.xadj[u];
-  int32_t deg = (int32_t)(A.xadj[u + 1] - beg);
   int32_t own = A.label[u], cu = node_w(A, u);
   for (int32_t e = lane; e < deg; e += 32)
-    ht_add(keys, vals, WARP_TAB - 1, A.label[A.adj[beg + e]], edge_w(A, beg + e));
+    ht_add(keys, vals, tcap - 1, A.label[A.adj[beg + e]], edge_w(A, beg + e));
   __syncwarp();
-  int32_t rown = ht_get(keys, vals, WARP_TAB - 1, own);
+  int32_t rown = ht_get(keys, vals, tcap - 1, own);
   uint64_t kc = 0, ku = 0;
   int32_t lc = -1, lu = -1;
-  for (int i = lane; i < WARP_TAB; i += 32) {
+  for (uint32_t i = lane; i < tcap; i += 32) {
     int32_t K = keys[i];
     if (K == HT_EMPTY || K == own) continue;
     uint64_t k = rate_key(A, K, vals[i]);
@@ -356,12 +357,6 @@ __global__ void __launch_bounds__(RATE_T) k_rate(LPArgs A, int s) {
   int64_t gw = (int64_t)blockIdx.x * (RATE_T / 32) + w;
   int64_t nw = (int64_t)gridDim.x * (RATE_T / 32);
   const int32_t *bo = A.boff + s * NB;
-  if (!A.small_labels && A.nhubs > 0) {
-    // stamp the hubs rated in this sub-round for the hub kernels
-    for (int64_t p = bo[6] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < bo[7];
-         p += (int64_t)gridDim.x * blockDim.x)
-      A.hstamp[hub_index(A, A.vlist[p])] = A.stamp;
-  }
 #define KMP_GROUP_BIN(BIN, G)                                                  \
   {                                                                            \
     int32_t lo = bo[BIN], hi = bo[BIN + 1];                                    \
@@ -395,7 +390,6 @@ __global__ void __launch_bounds__(RATE_T) k_rate(LPArgs A, int s) {
 }
 
 // ---- hubs (bin 6) with many labels: insert / reduce / emit
-constexpr int64_t HUB_CHUNK = 2048;   // edges per insert work unit
 constexpr int64_t HUB_RCHUNK = 4096;  // table entries per reduce work unit
 
 __device__ __forceinline__ int32_t hub_index(const LPArgs &A, int32_t u) {
@@ -408,7 +402,6 @@ __device__ __forceinline__ int32_t hub_index(const LPArgs &A, int32_t u) {
   return lo;
 }
 
-// the hubs of the current sub-round carry its stamp (set by k_rate)
 __device__ __forceinline__ int32_t find_seg(const int64_t *off, int32_t cnt, int64_t x) {
   int32_t lo = 0, hi = cnt - 1;  // last index with off[idx] <= x
   while (lo < hi) {
@@ -419,51 +412,123 @@ __device__ __forceinline__ int32_t find_seg(const int64_t *off, int32_t cnt, int
   return lo;
 }
 
-// work units: edge chunks of all hubs (global index space, fixed per run)
-__global__ void __launch_bounds__(256) k_hub_insert(LPArgs A, int32_t stamp) {
-  for (int64_t c = blockIdx.x; c < A.hchunks_total; c += gridDim.x) {
-    int32_t h = find_seg(A.hechunk, A.nhubs, c);
-    if (A.hstamp[h] != stamp) continue;
+// work plan of one sub-round: the hubs it rates, with exclusive prefixes of
+// their edge chunks and table chunks (one block, any number of hubs)
+__global__ void __launch_bounds__(1024) k_hub_plan(LPArgs A, int s) {
+  __shared__ int64_t we[32], wt2[32];
+  __shared__ int64_t carry_e, carry_t;
+  const int32_t *bo = A.boff + s * NB;
+  int32_t lo = bo[6], cnt = bo[7] - bo[6];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) { carry_e = 0; carry_t = 0; }
+  __syncthreads();
+  for (int32_t base = 0; base < cnt; base += blockDim.x) {
+    int32_t i = base + threadIdx.x;
+    int64_t ne = 0, nt = 0;
+    int32_t h = 0;
+    if (i < cnt) {
+      int32_t u = A.vlist[lo + i];
+      h = hub_index(A, u);
+      int64_t deg = A.xadj[u + 1] - A.xadj[u];
+      ne = ceil_div(deg, A.hub_chunk);
+      nt = ceil_div((int64_t)next_pow2_dev(2 * deg), HUB_RCHUNK);
+    }
+    int64_t xe = ne, xt = nt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      int64_t ye = (int64_t)__shfl_up_sync(0xFFFFFFFFu, (unsigned long long)xe, d);
+      int64_t yt = (int64_t)__shfl_up_sync(0xFFFFFFFFu, (unsigned long long)xt, d);
+      if (lane >= d) { xe += ye; xt += yt; }
+    }
+    if (lane == 31) { we[w] = xe; wt2[w] = xt; }
+    __syncthreads();
+    int64_t pe = carry_e, pt = carry_t, te = 0, tt = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      if (k < w) { pe += we[k]; pt += wt2[k]; }
+      te += we[k];
+      tt += wt2[k];
+    }
+    if (i < cnt) {
+      A.plan_h[i] = h;
+      A.plan_e[i] = pe + xe - ne;
+      A.plan_t[i] = pt + xt - nt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { carry_e += te; carry_t += tt; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    A.plan_tot[0] = carry_e;
+    A.plan_tot[1] = carry_t;
+  }
+}
+
+// work units: edge chunks of the sub-round's hubs
+__global__ void __launch_bounds__(256) k_hub_insert(LPArgs A, int s) {
+  const int32_t *bo = A.boff + s * NB;
+  int32_t cnt = bo[7] - bo[6];
+  int64_t total = A.plan_tot[0];
+  for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
+    int32_t i = find_seg(A.plan_e, cnt, c);
+    int32_t h = A.plan_h[i];
     int32_t u = A.hubs[h];
     int64_t b = A.xadj[u], deg = A.xadj[u + 1] - b;
     uint32_t mask = next_pow2_dev(2 * deg) - 1;
     int32_t *keys = A.hkeys + A.hoff[h], *vals = A.hvals + A.hoff[h];
-    int64_t cc = c - A.hechunk[h];
-    int64_t e0 = b + cc * HUB_CHUNK, e1 = e0 + HUB_CHUNK < b + deg ? e0 + HUB_CHUNK : b + deg;
+    int64_t cc = c - A.plan_e[i];
+    int64_t e0 = b + cc * A.hub_chunk, e1 = e0 + A.hub_chunk < b + deg ? e0 + A.hub_chunk : b + deg;
     for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x)
       ht_add(keys, vals, mask, A.label[A.adj[e]], edge_w(A, e));
   }
 }
 
-// work units: table chunks of all hubs
-__global__ void __launch_bounds__(256) k_hub_reduce(LPArgs A, int32_t stamp) {
+// work units: table chunks of the sub-round's hubs
+__global__ void __launch_bounds__(256) k_hub_reduce(LPArgs A, int s) {
   __shared__ unsigned long long red_c[8], red_u[8];
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int64_t c = blockIdx.x; c < A.htchunks_total; c += gridDim.x) {
-    int32_t h = find_seg(A.htchunk, A.nhubs, c);
-    if (A.hstamp[h] != stamp) continue;
+  const int32_t *bo = A.boff + s * NB;
+  int32_t cnt = bo[7] - bo[6];
+  int64_t total = A.plan_tot[1];
+  for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
+    int32_t i = find_seg(A.plan_t, cnt, c);
+    int32_t h = A.plan_h[i];
     int32_t u = A.hubs[h];
     int64_t deg = A.xadj[u + 1] - A.xadj[u];
     int64_t cap = next_pow2_dev(2 * deg);
     int32_t own = A.label[u], cu = node_w(A, u);
     int32_t *keys = A.hkeys + A.hoff[h], *vals = A.hvals + A.hoff[h];
-    int64_t cc = c - A.htchunk[h];
+    int64_t cc = c - A.plan_t[i];
     {
       uint64_t kc = 0, ku = 0;
-      int64_t e1 = (cc + 1) * HUB_RCHUNK < cap ? (cc + 1) * HUB_RCHUNK : cap;
-      for (int64_t i = cc * HUB_RCHUNK + threadIdx.x; i < e1; i += blockDim.x) {
-        int32_t K = keys[i];
+      int64_t e0 = cc * HUB_RCHUNK;
+      int64_t e1 = e0 + HUB_RCHUNK < cap ? e0 + HUB_RCHUNK : cap;
+      // all loads of this thread's entries first (independent, overlapped),
+      // then the cluster weights of the non-empty ones, then the clears
+      constexpr int PER = HUB_RCHUNK / 256;
+      int32_t Kv[PER], Rv[PER], Wv[PER];
+#pragma unroll
+      for (int j = 0; j < PER; ++j) {
+        int64_t i = e0 + threadIdx.x + (int64_t)j * blockDim.x;
+        Kv[j] = i < e1 ? keys[i] : HT_EMPTY;
+        Rv[j] = i < e1 ? vals[i] : 0;
+      }
+#pragma unroll
+      for (int j = 0; j < PER; ++j)
+        Wv[j] = (Kv[j] != HT_EMPTY && Kv[j] != own) ? A.wt[Kv[j]] : 0;
+#pragma unroll
+      for (int j = 0; j < PER; ++j) {
+        int64_t i = e0 + threadIdx.x + (int64_t)j * blockDim.x;
+        int32_t K = Kv[j];
         if (K == HT_EMPTY) continue;
-        int32_t r = vals[i];
         keys[i] = HT_EMPTY;  // leave the table empty for its next use
         vals[i] = 0;
         if (K == own) {
-          A.hrown[h] = r;
+          A.hrown[h] = Rv[j];
           continue;
         }
-        uint64_t k = rate_key(A, K, r);
+        uint64_t k = rate_key(A, K, Rv[j]);
         ku = k > ku ? k : ku;
-        if ((int64_t)A.wt[K] + cu <= cap_of(A, K) && k > kc) kc = k;
+        if ((int64_t)Wv[j] + cu <= cap_of(A, K) && k > kc) kc = k;
       }
       kc = group_max64<32>(kc);
       ku = group_max64<32>(ku);
@@ -482,16 +547,6 @@ __global__ void __launch_bounds__(256) k_hub_reduce(LPArgs A, int32_t stamp) {
   }
 }
 
-// hub ids, table offsets and chunk offsets of one run
-__global__ void k_hub_chunks(int32_t nh, const int32_t *hubs, const int64_t *xadj, int64_t *ech,
-                             int64_t *tch) {
-  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < nh;
-       h += (int64_t)gridDim.x * blockDim.x) {
-    int64_t deg = xadj[hubs[h] + 1] - xadj[hubs[h]];
-    ech[h] = ceil_div(deg, HUB_CHUNK);
-    tch[h] = ceil_div((int64_t)next_pow2_dev(2 * deg), HUB_RCHUNK);
-  }
-}
 
 __global__ void __launch_bounds__(256) k_hub_emit(LPArgs A, int s) {
   const int32_t *bo = A.boff + s * NB;
@@ -510,10 +565,10 @@ __global__ void __launch_bounds__(256) k_hub_emit(LPArgs A, int s) {
   }
 }
 
-__global__ void k_hub_flags(int32_t n, const int64_t *xadj, uint8_t *flag) {
+__global__ void k_hub_flags(int32_t n, const int64_t *xadj, int64_t huge, uint8_t *flag) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x)
-    flag[v] = (xadj[v + 1] - xadj[v]) > HUGE_DEG ? 1 : 0;
+    flag[v] = (xadj[v + 1] - xadj[v]) > huge ? 1 : 0;
 }
 
 __global__ void k_hub_list(int32_t n, const int64_t *xadj, const uint8_t *flag, const int32_t *pos,
@@ -764,16 +819,16 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   // hubs: with few labels (refinement) a shared-memory table always fits;
   // otherwise every hub gets its own global table region for the whole run
   bool small_labels = 2 * (int64_t)nlab <= CTA_TAB;
-  bool hub_path = !small_labels && g.maxdeg > HUGE_DEG;
+  const int64_t huge = C.tune.hub_degree;
+  bool hub_path = !small_labels && g.maxdeg > huge;
   int32_t nhubs = 0;
-  DBuf<int32_t> hubs, hkeys, hvals, hrown, hstamp;
-  DBuf<int64_t> hoff, hechunk, htchunk;
-  int64_t hchunks_total = 0, htchunks_total = 0;
+  DBuf<int32_t> hubs, hkeys, hvals, hrown, plan_h;
+  DBuf<int64_t> hoff, plan_e, plan_t, plan_tot;
   DBuf<unsigned long long> hkc, hku;
   if (hub_path) {
     DBuf<uint8_t> flag(n);
     DBuf<int32_t> pos(n), cnt(1);
-    k_hub_flags<<<grid_for(n, 256), 256, 0, stream>>>(n, g.xadj, flag);
+    k_hub_flags<<<grid_for(n, 256), 256, 0, stream>>>(n, g.xadj, huge, flag);
     KMP_LAUNCHED("hub_flags");
     scan_excl_u8_to_i32(flag, pos, n, cnt);
     nhubs = read1(cnt.p);
@@ -791,22 +846,13 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
     hkc.alloc(nhubs);
     hku.alloc(nhubs);
     hrown.alloc(nhubs);
-    hstamp.alloc(nhubs);
     hkc.zero();
     hku.zero();
     hrown.zero();
-    hstamp.zero();
-    DBuf<int64_t> ech(nhubs), tch(nhubs), tots(2);
-    hechunk.alloc(nhubs);
-    htchunk.alloc(nhubs);
-    k_hub_chunks<<<grid_for(nhubs, 256), 256, 0, stream>>>(nhubs, hubs, g.xadj, ech, tch);
-    KMP_LAUNCHED("hub_chunks");
-    scan_excl_i64(ech, hechunk, nhubs, tots.p);
-    scan_excl_i64(tch, htchunk, nhubs, tots.p + 1);
-    int64_t ht[2];
-    to_host(ht, tots.p, 2);
-    hchunks_total = ht[0];
-    htchunks_total = ht[1];
+    plan_h.alloc(nhubs);
+    plan_e.alloc(nhubs + 1);
+    plan_t.alloc(nhubs + 1);
+    plan_tot.alloc(2);
   }
 
   LPArgs A;
@@ -846,17 +892,17 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   A.hkc = hkc.p;
   A.hku = hku.p;
   A.hrown = hrown.p;
-  A.hstamp = hstamp.p;
-  A.hechunk = hechunk.p;
-  A.htchunk = htchunk.p;
-  A.hchunks_total = hchunks_total;
-  A.htchunks_total = htchunks_total;
-  A.stamp = 0;
+  A.plan_h = plan_h.p;
+  A.plan_e = plan_e.p;
+  A.plan_t = plan_t.p;
+  A.plan_tot = plan_tot.p;
   A.small_labels = small_labels ? 1 : 0;
+  A.huge_deg = huge;
+  A.hub_chunk = C.tune.hub_chunk;
   A.nlab = nlab;
   A.S = S;
 
-  int grid_rate = 6 * C.sms;
+  int grid_rate = C.tune.rate_blocks_per_sm * C.sms;
   int grid_hub = 4 * C.sms;
   int grid_commit = grid_for(ceil_div(n, S), 256, 8);
   unsigned long long h64[10];
@@ -884,13 +930,14 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
         ev.push_back(b);
         KMP_CUDA(cudaEventRecord(a, stream));
       }
-      A.stamp = r * S + s + 1;
       k_rate<<<grid_rate, RATE_T, 0, stream>>>(A, s);
       KMP_LAUNCHED("rate");
       if (hub_path) {
-        k_hub_insert<<<grid_hub, 256, 0, stream>>>(A, A.stamp);
+        k_hub_plan<<<1, 1024, 0, stream>>>(A, s);
+        KMP_LAUNCHED("hub_plan");
+        k_hub_insert<<<grid_hub, 256, 0, stream>>>(A, s);
         KMP_LAUNCHED("hub_insert");
-        k_hub_reduce<<<grid_hub, 256, 0, stream>>>(A, A.stamp);
+        k_hub_reduce<<<grid_hub, 256, 0, stream>>>(A, s);
         KMP_LAUNCHED("hub_reduce");
         k_hub_emit<<<grid_for(nhubs, 256), 256, 0, stream>>>(A, s);
         KMP_LAUNCHED("hub_emit");

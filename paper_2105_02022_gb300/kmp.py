@@ -58,6 +58,11 @@ class Stats(ctypes.Structure):
         return d
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in (
+        "rate_blocks_per_sm", "hub_degree", "hub_chunk", "ip_blocks_per_sm")]
+
+
 def load():
     """Load libkmp.so (built by __graft_entry__.build()); raise if it is missing."""
     global _LIB
@@ -90,6 +95,9 @@ def load():
         "kmp_partition_graph": (ctypes.c_int, [P, i32, dbl, u64, P, P]),
         "kmp_last_stats": (ctypes.c_int, [P]),
         "kmp_set_profiling": (ctypes.c_int, [ctypes.c_int]),
+        "kmp_set_tuning": (ctypes.c_int, [P]),
+        "kmp_get_tuning": (ctypes.c_int, [P]),
+        "kmp_autotune": (ctypes.c_int, [P, i32, dbl, u64, P]),
         "kmp_profile_read": (ctypes.c_int, [P, P, P, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
@@ -290,6 +298,23 @@ def last_stats() -> Stats:
     st = Stats()
     load().kmp_last_stats(ctypes.byref(st))
     return st
+
+
+def set_tuning(t: Tuning):
+    _check(load().kmp_set_tuning(ctypes.byref(t)))
+
+
+def get_tuning() -> Tuning:
+    t = Tuning()
+    _check(load().kmp_get_tuning(ctypes.byref(t)))
+    return t
+
+
+def autotune(dg: DeviceGraph, k: int, eps: float, seed: int) -> Tuning:
+    _stream()
+    t = Tuning()
+    _check(load().kmp_autotune(dg.h, int(k), float(eps), ctypes.c_uint64(seed), ctypes.byref(t)))
+    return t
 
 
 def set_profiling(on: bool):

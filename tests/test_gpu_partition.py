@@ -127,6 +127,36 @@ def test_partition_parity(kmp, name, make, ks):
             assert list(st.level_n[: st.levels]) == list(rst.level_n[: rst.levels])
 
 
+@pytest.mark.parametrize("tune", [(4, 1024, 1024, 2), (8, 2048, 4096, 8), (2, 256, 256, 1)])
+def test_tuning_invariance(kmp, tune):
+    """Schedule parameters (grids, hub threshold, chunking) never change results."""
+    g = gg.hubs(30000, [700, 3000, 12000], 60000, 8)
+    dg = kmp.DeviceGraph.from_host(g)
+    old = kmp.get_tuning()
+    try:
+        kmp.set_tuning(kmp.Tuning(*tune))
+        for k in (16, 5):
+            part, rc, st = kmp.partition_graph(dg, k, 0.03, 3)
+            rp, rrc, _ = O.partition(g, k, 0.03, 3)
+            assert np.array_equal(part.cpu().numpy(), rp)
+    finally:
+        kmp.set_tuning(old)
+
+
+def test_autotune_then_parity(kmp):
+    g = gg.rmat(14, 16, 5)
+    dg = kmp.DeviceGraph.from_host(g)
+    old = kmp.get_tuning()
+    try:
+        best = kmp.autotune(dg, 32, 0.03, 1)
+        assert best.rate_blocks_per_sm in (4, 6, 8) and best.hub_degree in (1024, 2048)
+        part, rc, st = kmp.partition_graph(dg, 32, 0.03, 1)
+        rp, rrc, _ = O.partition(g, 32, 0.03, 1)
+        assert np.array_equal(part.cpu().numpy(), rp)
+    finally:
+        kmp.set_tuning(old)
+
+
 def test_host_partition_entry(kmp):
     g = gg.rgg(6000, 8, 11)
     part, rc = kmp.partition(g, 12, 0.05, 4)
