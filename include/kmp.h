@@ -240,6 +240,30 @@ int kmp_get_tuning(kmp_tuning *t);
  */
 int kmp_autotune(const kmp_graph *g, int32_t k, double eps, uint64_t seed, kmp_tuning *best);
 
+/*
+ * Cut and block weights without any device allocation.  The paper has no
+ * counterpart: this is a library-side variant of kmp_cut (the cut of
+ * Section 2) for callers that cannot let the library allocate at call time:
+ * code whose device memory belongs to another allocator or a fixed arena that
+ * must account for every byte, processes that reserve all device memory up
+ * front, and loops that cannot take the implicit synchronisation or the
+ * possible failure of an allocation.  Its scratch is one fixed device array
+ * of KMP_NOALLOC_MAX_K + 2 64-bit words (about 512 KB) inside the library,
+ * kept until the process exits.
+ *
+ * g: graph handle; part: DEVICE int32[n] with values in [0, k); k in
+ * [1, KMP_NOALLOC_MAX_K] (else KMP_ERR_ARG, nothing launched); cut_out (host,
+ * nullable): the cut; block_weights_out (host int64[k], nullable): c(V_b).
+ * A part value outside [0, k) gives KMP_ERR_ARG (outputs unspecified).
+ * Runs on the stream of kmp_set_stream and returns after it drained.  The
+ * first call on a device looks the array's device address up once.
+ * Overlapping calls (from several host threads or streams) share the one
+ * array and race: serialise them.
+ */
+#define KMP_NOALLOC_MAX_K 65536
+int kmp_cut_noalloc(const kmp_graph *g, const kmp_vid *part, int32_t k, int64_t *cut_out,
+                    int64_t *block_weights_out);
+
 #ifdef __cplusplus
 }
 #endif

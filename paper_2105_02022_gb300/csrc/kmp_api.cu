@@ -10,10 +10,6 @@
 
 #include "kmp_internal.cuh"
 
-struct kmp_graph {
-  kmp::Graph g;
-};
-
 namespace kmp {
 
 void set_last_error(const std::string &s);

@@ -278,3 +278,8 @@ void split_caps(double eps, int64_t cV, int32_t k, int64_t cB, int32_t fB, int32
 int32_t block_cap(double eps, int64_t cV, int32_t k, int32_t fb, int32_t maxc);
 
 }  // namespace kmp
+
+// the opaque handle of include/kmp.h: a device graph
+struct kmp_graph {
+  kmp::Graph g;
+};

@@ -90,6 +90,7 @@ def load():
         "kmp_balance": (ctypes.c_int, [P, i32, P, P, P]),
         "kmp_project": (ctypes.c_int, [i32, P, P, P]),
         "kmp_cut": (ctypes.c_int, [P, P, i32, P, P]),
+        "kmp_cut_noalloc": (ctypes.c_int, [P, P, i32, P, P]),
         "kmp_bipartition_blocks": (ctypes.c_int, [P, i32, P, dbl, i64, i32, u64, P, P, P]),
         "kmp_partition": (ctypes.c_int, [i32, P, P, P, P, i32, dbl, u64, P]),
         "kmp_partition_graph": (ctypes.c_int, [P, i32, dbl, u64, P, P]),
@@ -256,6 +257,19 @@ def cut(dg: DeviceGraph, part: torch.Tensor, k: int):
     bw = np.zeros(k, np.int64)
     c = ctypes.c_int64()
     _check(load().kmp_cut(dg.h, _ptr(part), int(k), ctypes.byref(c), _ptr(bw)))
+    return c.value, bw
+
+
+KMP_NOALLOC_MAX_K = 65536
+
+
+def cut_noalloc(dg: DeviceGraph, part: torch.Tensor, k: int):
+    """Same result as cut(), computed without any device allocation (fixed
+    library-side scratch; calls must not overlap)."""
+    _stream()
+    bw = np.zeros(max(int(k), 0), np.int64)
+    c = ctypes.c_int64()
+    _check(load().kmp_cut_noalloc(dg.h, _ptr(part), int(k), ctypes.byref(c), _ptr(bw) if k > 0 else None))
     return c.value, bw
 
 
