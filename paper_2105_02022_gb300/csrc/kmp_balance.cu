@@ -12,8 +12,10 @@
 // GPU mapping: candidates of all overloaded blocks in one full-GPU pass (one
 // warp per node, connectivity in a per-warp hash table); grouping by block
 // with a radix sort of (block, node) keys; one CTA per overloaded block sorts
-// its candidates by the exact rational order; one warp performs the moves in
-// order (each move depends on the weights left by the previous ones).
+// its candidates by the exact rational order; one CTA performs the moves in
+// order (each move depends on the weights left by the previous ones), in
+// batches whose members it evaluates at once and commits while they provably
+// do not interact.
 #include <algorithm>
 
 #include "kmp_internal.cuh"
@@ -62,7 +64,27 @@ __device__ int64_t conn_table(const BalArgs &A, int32_t v, int32_t *K, int32_t *
     V[i] = 0;
   }
   __syncwarp();
-  for (int64_t q = b + lane; q < e; q += 32) ht_add(K, V, mask, A.part[A.adj[q]], A.ew ? A.ew[q] : 1);
+  // 128 entries per pass (four gathers in flight per lane); lanes that hit the
+  // same block add their weights first, so a hub's many entries into one block
+  // cost one atomic per pass instead of one per entry
+  for (int64_t base = b; base < e; base += 128) {
+    int32_t u[4], wt[4], blk[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int64_t q = base + r * 32 + lane;
+      bool ok = q < e;
+      u[r] = ok ? A.adj[q] : -1;
+      wt[r] = ok ? (A.ew ? A.ew[q] : 1) : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) blk[r] = u[r] >= 0 ? A.part[u[r]] : HT_EMPTY;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      unsigned peers = __match_any_sync(0xFFFFFFFFu, blk[r]);
+      int32_t s = __reduce_add_sync(peers, wt[r]);
+      if (blk[r] != HT_EMPTY && lane == __ffs(peers) - 1) ht_add(K, V, mask, blk[r], s);
+    }
+  }
   __syncwarp();
   return ht_get(K, V, mask, A.part[v]);
 }
@@ -196,48 +218,103 @@ __global__ void __launch_bounds__(BAL_T) k_bal_sort(BalArgs A) {
     A.keys[lo + i] = ((uint64_t)(uint32_t)B << A.bitsN) | (uint64_t)(uint32_t)vv[i];
 }
 
-// Moves in candidate order, evaluated 32 at a time.  Warp j computes the
-// target of candidate i+j from the state at the start of the batch; thread 0
-// then commits them in order.  While a block is emptied, every other block
-// only gains weight, so a target that is still admissible is still the best
-// (or still the lowest-id admissible one), and "no admissible target" stays
-// true; only a move of a neighbour changes connectivity.  A candidate passes
-// iff its target still fits and no earlier move of the batch was its
-// neighbour; at the first one that does not, the next batch starts there (its
-// first candidate always passes).  The result equals one move at a time.
+// Moves in candidate order, evaluated in batches of up to 32.  A batch holds
+// the shortest prefix of the remaining candidates whose weights cover the
+// overload (it may need more moves, never fewer).  The whole CTA walks the
+// batch's adjacency rows at once, building one connectivity table per member
+// and marking which members are neighbours of each other; warp j then picks
+// member j's target from the state at the start of the batch, and thread 0
+// commits in order.  While a block is emptied, every other block only gains
+// weight, so a target that is still admissible is still the best (or still
+// the lowest-id admissible one), and "no admissible target" stays true; only
+// a move of a neighbour changes connectivity.  A member passes iff its target
+// still fits and no earlier move of the batch was its neighbour; at the first
+// one that does not, the next batch starts there (its first member always
+// passes).  The result equals one move at a time.
 constexpr int BM_T = 1024;
 constexpr int BM_W = BM_T / 32;
 
 __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch) {
   __shared__ int32_t s_v[BM_W], s_t[BM_W];
-  __shared__ int64_t s_c[BM_W];
+  __shared__ int64_t s_c[BM_W], s_eoff[BM_W + 1];
   __shared__ uint32_t s_adj[BM_W];
-  __shared__ int32_t s_next, s_stop;
+  __shared__ int32_t s_nb, s_next, s_stop;
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int32_t *K = A.gtab + (int64_t)w * 2 * A.gcap, *V = K + A.gcap;
-  uint64_t mask = (1ull << A.bitsN) - 1ull;
+  uint64_t vmask = (1ull << A.bitsN) - 1ull;
+  uint32_t gcap = A.gcap, hmask = gcap - 1;
   for (int32_t B = 0; B < A.k; ++B) {
     if (!A.over[B]) continue;
     int32_t lo = A.seg_lo[B], hi = A.seg_hi[B];
     int32_t i = lo;
     while (i < hi) {
       if (A.bw[B] <= A.cap[B]) break;
-      int32_t nb = hi - i < BM_W ? hi - i : BM_W;
-      if (w < nb) {
-        int32_t v = (int32_t)(A.keys[i + w] & mask);
+      if (w == 0) {
+        int32_t avail = hi - i < BM_W ? hi - i : BM_W;
+        int32_t v = lane < avail ? (int32_t)(A.keys[i + lane] & vmask) : 0;
+        int64_t c = lane < avail ? bw_node(A, v) : 0;
+        int64_t deg = lane < avail ? A.xadj[v + 1] - A.xadj[v] : 0;
+        // inclusive prefix sums of weights and degrees
+#pragma unroll
+        for (int m = 1; m < 32; m <<= 1) {
+          int64_t oc = (int64_t)__shfl_up_sync(0xFFFFFFFFu, (unsigned long long)c, m);
+          int64_t od = (int64_t)__shfl_up_sync(0xFFFFFFFFu, (unsigned long long)deg, m);
+          if (lane >= m) {
+            c += oc;
+            deg += od;
+          }
+        }
+        unsigned enough = __ballot_sync(0xFFFFFFFFu, lane < avail && c >= A.bw[B] - A.cap[B]);
+        int32_t nb = enough ? __ffs(enough) : avail;
+        if (lane < nb) {
+          s_v[lane] = v;
+          s_eoff[lane + 1] = deg;
+          s_adj[lane] = 0;
+          inbatch[v] = lane + 1;
+        }
         if (lane == 0) {
-          s_v[w] = v;
-          inbatch[v] = w + 1;
+          s_eoff[0] = 0;
+          s_nb = nb;
+        }
+      }
+      __syncthreads();
+      int32_t nb = s_nb;
+      for (int64_t x = threadIdx.x; x < (int64_t)nb * gcap; x += BM_T) {
+        int32_t *K = A.gtab + (x / gcap) * 2ll * gcap;
+        K[x % gcap] = HT_EMPTY;
+        K[gcap + x % gcap] = 0;
+      }
+      __syncthreads();
+      int64_t E = s_eoff[nb];
+      for (int64_t base = 0; base < E; base += BM_T) {
+        int64_t t = base + threadIdx.x;
+        bool ok = t < E;
+        int32_t j = 0;
+        if (ok)
+          while (s_eoff[j + 1] <= t) ++j;
+        int32_t blk = HT_EMPTY, wt = 0;
+        if (ok) {
+          int64_t q = A.xadj[s_v[j]] + (t - s_eoff[j]);
+          int32_t u = A.adj[q];
+          blk = A.part[u];
+          wt = A.ew ? A.ew[q] : 1;
+          int32_t jj = inbatch[u];
+          if (jj > 0) atomicOr(&s_adj[j], 1u << (jj - 1));
+        }
+        uint64_t key = ok ? ((uint64_t)(uint32_t)j << 32) | (uint32_t)blk : ~0ull;
+        unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+        int32_t s = __reduce_add_sync(peers, wt);
+        if (ok && lane == __ffs(peers) - 1) {
+          int32_t *K = A.gtab + (int64_t)j * 2 * gcap;
+          ht_add(K, K + gcap, hmask, blk, s);
         }
       }
       __syncthreads();
       if (w < nb) {
         int32_t v = s_v[w];
         int64_t c = bw_node(A, v);
-        uint32_t tm;
-        conn_table(A, v, K, V, tm);
+        const int32_t *K = A.gtab + (int64_t)w * 2 * gcap, *V = K + gcap;
         uint64_t bestk = 0;  // (conn, ~block): largest connectivity, then lowest id
-        for (uint32_t x = lane; x <= tm; x += 32) {
+        for (uint32_t x = lane; x < gcap; x += 32) {
           int32_t b = K[x];
           if (b == HT_EMPTY || b == B) continue;
           if (A.bw[b] + c > A.cap[b]) continue;
@@ -254,18 +331,9 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
           for (int m = 16; m > 0; m >>= 1) low = min(low, __shfl_xor_sync(0xFFFFFFFFu, low, m));
           t = low == INT32_MAX ? -1 : low;
         }
-        // which batch members are neighbours of v
-        uint32_t am = 0;
-        for (int64_t q = A.xadj[v] + lane; q < A.xadj[v + 1]; q += 32) {
-          int32_t j = inbatch[A.adj[q]];
-          if (j > 0) am |= 1u << (j - 1);
-        }
-#pragma unroll
-        for (int m = 16; m > 0; m >>= 1) am |= __shfl_xor_sync(0xFFFFFFFFu, am, m);
         if (lane == 0) {
           s_t[w] = t;
           s_c[w] = c;
-          s_adj[w] = am;
         }
       }
       __syncthreads();
@@ -292,7 +360,7 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
         s_next = j;
       }
       __syncthreads();
-      if (w < nb && lane == 0) inbatch[s_v[w]] = 0;
+      if (threadIdx.x < nb) inbatch[s_v[threadIdx.x]] = 0;
       __syncthreads();
       i += s_next;
       if (s_stop) break;
