@@ -69,6 +69,12 @@ typedef struct {
   int32_t rep_ggg;       /* greedy graph growing (8) */
   int32_t fm_passes;     /* 2-way FM passes per level (8) */
   int32_t fm_stop;       /* fruitless FM moves that end a pass (64) */
+  int32_t learned;       /* learned mode (0): the proposer set by kmp_set_proposer seeds one
+                            bipartition first, then a reduced portfolio runs; the rest of the
+                            plain portfolio runs only if the best so far is infeasible */
+  int32_t lrep_random;   /* learned-mode repetitions (each at most its rep_*): random (0) */
+  int32_t lrep_bfs;      /* BFS (0) */
+  int32_t lrep_ggg;      /* greedy graph growing (1) */
 } kmp_config;
 
 /* Per-call measurements of kmp_partition / kmp_partition_graph (CUDA events). */
@@ -190,6 +196,18 @@ int kmp_bipartition_blocks(const kmp_graph *g, int32_t nblocks, const int32_t *f
                            int32_t *nblocks_out, int32_t *f_out);
 
 /*
+ * The bipartitioner of Section 4.2 on every block of part (device int32[n],
+ * values in [0, nblocks)) with explicit caps: caps is host int32[4*nblocks],
+ * (target0, target1, L0, L1) of block b at 4b (targets >= 0, caps >= 1).
+ * Blocks are the items of one batched launch, item key step(roundkey, b) as
+ * in kmp_bipartition_blocks; on return node v of block b is in block
+ * 2b + side.  For bipartitioning many independent subgraphs at once (give
+ * the disjoint union and the subgraph index as part).
+ */
+int kmp_bipartition_each(const kmp_graph *g, int32_t nblocks, const int32_t *caps, uint64_t roundkey,
+                         kmp_vid *part);
+
+/*
  * Full deep multilevel partition (Algorithm 1) of a host CSR into k blocks
  * with imbalance eps.  part_out: host int32[n].  Returns KMP_ERR_INFEASIBLE
  * (result still written) when a block exceeds L_k = floor((1+eps) ceil(c(V)/k)).
@@ -239,6 +257,77 @@ int kmp_get_tuning(kmp_tuning *t);
  * {1024, 4096}.
  */
 int kmp_autotune(const kmp_graph *g, int32_t k, double eps, uint64_t seed, kmp_tuning *best);
+
+/*
+ * Learned seed proposer for the bipartitioner (learned mode of kmp_config).
+ * The paper bipartitions a coarsest graph by repeating random, BFS and
+ * greedy-graph-growing starts and keeping the best (Section 4.2); in learned
+ * mode a message-passing network scores the coarsest graph's nodes first and
+ * its score order (first fit to block 0's target, like the random start)
+ * becomes one more start, FM-refined and compared exactly like the others,
+ * ahead of a reduced portfolio; the rest of the portfolio runs only if the
+ * best so far is infeasible.  So every result is still FM-refined and
+ * balance-checked by the method itself.
+ *
+ * Network: 8 node features (1; c(v)/mean c; deg/max deg; weighted degree /
+ * mean; BFS hops from two anchors over (max hops + 1); two +-1 key bits),
+ * two layers h' = relu(W_self h + W_nbr mean_w(h_nbr) + b) of width 64, and a
+ * linear read-out.  Parameters: KMP_MPNN_PARAMS floats in the order W1_self
+ * [64][8], W1_nbr [64][8], b1 [64], W2_self [64][64], W2_nbr [64][64], b2 [64],
+ * w_out [64], b_out.  The model keeps fp32 master weights and Adam moments;
+ * every kernel computes with the BF16-rounded weights and fp32 arithmetic
+ * (fixed-order fused multiply-adds, so scores are reproducible exactly).
+ *
+ * Batches (forward, gradients, train): ng graphs as one disjoint union in
+ * HOST arrays: noff[ng+1] node offsets (noff[0] = 0), xadj[N+1] (int64), adj
+ * (union node ids; symmetric, no self-loops), vw[N] and ew[E] (NULL: ones),
+ * keys[ng] (the key of each graph's features), side[N] (0/1 labels, e.g. the
+ * best-of-portfolio sides from the sample sink).  Loss: per graph the mean
+ * binary cross-entropy of sigmoid(score) against side (block 0 = 1) under
+ * the better of the two block orientations, averaged over graphs.
+ */
+#define KMP_MPNN_PARAMS 9409
+typedef struct kmp_mpnn kmp_mpnn;
+int kmp_mpnn_num_params(void);
+/* new model with He-uniform weights from seed; free with kmp_mpnn_free */
+int kmp_mpnn_create(uint64_t seed, kmp_mpnn **out);
+int kmp_mpnn_free(kmp_mpnn *m);
+/* params: host float[KMP_MPNN_PARAMS]; get returns the BF16 weights as floats */
+int kmp_mpnn_get_params(const kmp_mpnn *m, float *params);
+int kmp_mpnn_set_params(kmp_mpnn *m, const float *params);
+/* scores[N] (host); features[N*8] (host, nullable) */
+int kmp_mpnn_forward(kmp_mpnn *m, int32_t ng, const int32_t *noff, const int64_t *xadj,
+                     const int32_t *adj, const int32_t *vw, const int32_t *ew, const uint64_t *keys,
+                     float *scores, float *features);
+/* loss and its gradient with respect to the (BF16) weights; grad_out host
+ * float[KMP_MPNN_PARAMS] or NULL; the model is not changed */
+int kmp_mpnn_gradients(kmp_mpnn *m, int32_t ng, const int32_t *noff, const int64_t *xadj,
+                       const int32_t *adj, const int32_t *vw, const int32_t *ew,
+                       const uint64_t *keys, const int32_t *side, float *loss_out, float *grad_out);
+/* `epochs` full-batch Adam steps (beta 0.9/0.999) at learning rate lr;
+ * loss_per_epoch host float[epochs] or NULL (loss before each step) */
+int kmp_mpnn_train(kmp_mpnn *m, int32_t ng, const int32_t *noff, const int64_t *xadj,
+                   const int32_t *adj, const int32_t *vw, const int32_t *ew, const uint64_t *keys,
+                   const int32_t *side, int32_t epochs, float lr, float *loss_per_epoch);
+/* proposer used by learned mode from now on (NULL: none, learned mode then
+ * runs the plain portfolio); the model must outlive its use */
+int kmp_set_proposer(const kmp_mpnn *m);
+
+/*
+ * Sample sink: while open, every item of the batched bipartitioner (the
+ * blocks split by kmp_bipartition_blocks, kmp_partition and friends) appends
+ * its coarsest graph and the winning bipartition of the portfolio there --
+ * the training data of the proposer, generated by the method itself.  Items
+ * beyond the capacity are dropped and counted.  read: the kept samples as
+ * one union (format of the batches above) ordered by item key; the host
+ * arrays must hold count's totals (noff graphs+1, xadj nodes+1, adj/ew
+ * entries, vw/side nodes, keys graphs).  open replaces an open sink.
+ */
+int kmp_sample_sink_open(int32_t max_graphs, int64_t max_nodes, int64_t max_entries);
+int kmp_sample_sink_count(int32_t *graphs, int64_t *nodes, int64_t *entries, int64_t *dropped);
+int kmp_sample_sink_read(int32_t *noff, int64_t *xadj, int32_t *adj, int32_t *vw, int32_t *ew,
+                         uint64_t *keys, int32_t *side);
+int kmp_sample_sink_close(void);
 
 /*
  * Cut and block weights without any device allocation.  The paper has no

@@ -33,7 +33,8 @@ def build() -> str:
 class Config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "C", "lp_rounds", "refine_rounds", "subrounds", "two_hop", "conv_num", "conv_den",
-        "ip_C", "ip_lp_rounds", "rep_random", "rep_bfs", "rep_ggg", "fm_passes", "fm_stop")]
+        "ip_C", "ip_lp_rounds", "rep_random", "rep_bfs", "rep_ggg", "fm_passes", "fm_stop",
+        "learned", "lrep_random", "lrep_bfs", "lrep_ggg")]
 
 
 class OGraph(ctypes.Structure):
@@ -91,6 +92,10 @@ def lib():
             "kmpo_mpnn_loss": (dbl, [i32, P, P, P]),
             "kmpo_mpnn_backward": (None, [i32, P, P, P, P, P, P, P]),
             "kmpo_mpnn_propose": (None, [i32, P, P, i32, P]),
+            "kmpo_mpnn_scores_f32": (None, [i32, P, P, P, P, u64, P, P]),
+            "kmpo_mpnn_score_key": (ctypes.c_uint32, [ctypes.c_float]),
+            "kmpo_set_proposer": (None, [P]),
+            "kmpo_learned_initial": (None, [i32, P, P, P, P, i32, u64, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -308,6 +313,37 @@ def mpnn_propose(g, S, target0):
     side = np.zeros(n, np.int32)
     lib().kmpo_mpnn_propose(n, _p(vw), _p(S), int(target0), _p(side))
     return side
+
+
+def mpnn_scores_f32(g, key_, W):
+    """Scores in the kernel's precision; W: parameters as float32 values."""
+    n, xadj, adj, vw, ew = _g(g)
+    W = np.ascontiguousarray(W, np.float32)
+    S = np.zeros(max(n, 1), np.float32)
+    lib().kmpo_mpnn_scores_f32(n, _p(xadj), _p(adj), _p(vw), _p(ew), key_, _p(W), _p(S))
+    return S[:n]
+
+
+def mpnn_score_key(s) -> int:
+    return int(lib().kmpo_mpnn_score_key(ctypes.c_float(float(s))))
+
+
+def set_proposer(W):
+    """Proposer of learned mode (None clears); W: float32 parameters."""
+    if W is None:
+        lib().kmpo_set_proposer(None)
+        return
+    W = np.ascontiguousarray(W, np.float32)
+    assert W.size == mpnn_num_params()
+    lib().kmpo_set_proposer(_p(W))
+
+
+def learned_initial(g, target0, key_, W):
+    n, xadj, adj, vw, ew = _g(g)
+    W = np.ascontiguousarray(W, np.float32)
+    side = np.zeros(max(n, 1), np.int32)
+    lib().kmpo_learned_initial(n, _p(xadj), _p(adj), _p(vw), _p(ew), int(target0), key_, _p(W), _p(side))
+    return side[:n]
 
 
 def async_cluster(g, U, rounds):

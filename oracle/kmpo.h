@@ -39,6 +39,10 @@ typedef struct {
   int32_t rep_ggg;
   int32_t fm_passes;     /* 2-way FM passes per level */
   int32_t fm_stop;       /* a pass ends after this many moves without a new best */
+  int32_t learned;       /* learned mode: proposal first, reduced portfolio (B6) */
+  int32_t lrep_random;   /* portfolio repetitions in learned mode */
+  int32_t lrep_bfs;
+  int32_t lrep_ggg;
 } kmpo_config;
 
 /* graph owned by the oracle (returned by kmpo_contract) */
@@ -164,6 +168,18 @@ void kmpo_mpnn_backward(int32_t n, const int64_t *xadj, const int32_t *adj, cons
                         const double *X, const double *P, const double *gS, double *gP);
 void kmpo_mpnn_propose(int32_t n, const int32_t *vw, const double *S, int32_t target0,
                        int32_t *side);
+/* inference in the kernel's precision (fp32, fused multiply-adds in a fixed
+ * order); W: parameters as fp32 values */
+void kmpo_mpnn_scores_f32(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
+                          const int32_t *ew, uint64_t key, const float *W, float *S);
+uint32_t kmpo_mpnn_score_key(float s);
+/* proposer used by learned mode (copied; NULL clears) */
+void kmpo_set_proposer(const float *W);
+const float *kmpo_proposer(void);
+/* learned start: first fit to target0 in (score key, id) order */
+void kmpo_learned_initial(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
+                          const int32_t *ew, int32_t target0, uint64_t key, const float *W,
+                          int32_t *side);
 
 #ifdef __cplusplus
 }

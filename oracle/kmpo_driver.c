@@ -66,6 +66,10 @@ void kmpo_config_default(kmpo_config *c) {
   c->rep_ggg = 8;
   c->fm_passes = 8;
   c->fm_stop = 64;
+  c->learned = 0;
+  c->lrep_random = 0;
+  c->lrep_bfs = 0;
+  c->lrep_ggg = 1;
 }
 
 static int32_t ceil_log2(int32_t f) {

@@ -30,13 +30,25 @@
  *     pass is rolled back to its best prefix, ordered by (infeasible?,
  *     overload if infeasible, cut).  Passes repeat (<= fm_passes) while they
  *     improve.
+ *  B6 Learned mode (cfg->learned with a proposer set, kmpo_mpnn.c): the
+ *     candidates are the learned start (nodes by network score, first fit to
+ *     target0; key step(itemkey, DOM_LEARNED)) followed by the first
+ *     lrep_random random, lrep_bfs BFS and lrep_ggg greedy graph growing
+ *     repetitions of B2 (same keys).  Only if the best of these is infeasible
+ *     do the remaining repetitions of B2 run, in B2's order.  Every candidate
+ *     is FM-refined and compared exactly as in B2 (first best wins).
  */
 #include <stdlib.h>
 #include <string.h>
 
 #include "kmpo.h"
 
-enum { DOM_IP_LP = 4, DOM_RANDOM = 5, DOM_BFS = 6, DOM_GGG = 7 };
+enum { DOM_IP_LP = 4, DOM_RANDOM = 5, DOM_BFS = 6, DOM_GGG = 7, DOM_LEARNED = 9 };
+
+const float *kmpo_proposer(void);
+void kmpo_learned_initial(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
+                          const int32_t *ew, int32_t target0, uint64_t key, const float *W,
+                          int32_t *side);
 
 uint64_t kmpo_step(uint64_t x, uint64_t w);
 int32_t kmpo_cluster_key(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
@@ -309,23 +321,43 @@ int64_t kmpo_bipartition(int32_t n, const int64_t *xadj, const int32_t *adj, con
   fmkey_t bestk = {0, 0, 0};
   int32_t reps[3] = {cfg->rep_random, cfg->rep_bfs, cfg->rep_ggg};
   uint64_t doms[3] = {DOM_RANDOM, DOM_BFS, DOM_GGG};
-  for (int32_t a = 0; a < 3; ++a)
-    for (int32_t r = 0; r < reps[a]; ++r) {
-      uint64_t key = kmpo_step(kmpo_step(itemkey, doms[a]), (uint64_t)r);
-      kmpo_initial(a, h->n, h->xadj, h->adj, h->vw, h->ew, target0, key, side);
-      int64_t cut = kmpo_fm(h->n, h->xadj, h->adj, h->vw, h->ew, hL0, hL1, cfg, side);
-      int64_t W0 = 0, W1 = 0;
-      for (int32_t v = 0; v < h->n; ++v) {
-        if (side[v] == 0) W0 += vwt(h->vw, v);
-        else W1 += vwt(h->vw, v);
-      }
-      fmkey_t k = make_key(W0, W1, hL0, hL1, cut);
-      if (!have || key_less(k, bestk)) {
-        have = 1;
-        bestk = k;
-        memcpy(best, side, sizeof(int32_t) * (size_t)h->n);
+  const float *W = cfg->learned ? kmpo_proposer() : NULL;
+  /* B6: in learned mode the first pass takes the proposal and a prefix of
+   * each algorithm's repetitions, the second the rest if still infeasible */
+  int32_t first[3] = {reps[0], reps[1], reps[2]};
+  if (W) {
+    first[0] = cfg->lrep_random < reps[0] ? cfg->lrep_random : reps[0];
+    first[1] = cfg->lrep_bfs < reps[1] ? cfg->lrep_bfs : reps[1];
+    first[2] = cfg->lrep_ggg < reps[2] ? cfg->lrep_ggg : reps[2];
+  }
+  for (int32_t pass = 0; pass < 2; ++pass) {
+    if (pass == 1 && (!W || (have && !bestk.inf))) break;
+    for (int32_t a = (pass == 0 && W) ? -1 : 0; a < 3; ++a) {
+      int32_t r0 = a < 0 ? 0 : (pass == 0 ? 0 : first[a]);
+      int32_t r1 = a < 0 ? 1 : (pass == 0 ? first[a] : reps[a]);
+      for (int32_t r = r0; r < r1; ++r) {
+        if (a < 0) {
+          kmpo_learned_initial(h->n, h->xadj, h->adj, h->vw, h->ew, target0,
+                               kmpo_step(itemkey, DOM_LEARNED), W, side);
+        } else {
+          uint64_t key = kmpo_step(kmpo_step(itemkey, doms[a]), (uint64_t)r);
+          kmpo_initial(a, h->n, h->xadj, h->adj, h->vw, h->ew, target0, key, side);
+        }
+        int64_t cut = kmpo_fm(h->n, h->xadj, h->adj, h->vw, h->ew, hL0, hL1, cfg, side);
+        int64_t W0 = 0, W1 = 0;
+        for (int32_t v = 0; v < h->n; ++v) {
+          if (side[v] == 0) W0 += vwt(h->vw, v);
+          else W1 += vwt(h->vw, v);
+        }
+        fmkey_t k = make_key(W0, W1, hL0, hL1, cut);
+        if (!have || key_less(k, bestk)) {
+          have = 1;
+          bestk = k;
+          memcpy(best, side, sizeof(int32_t) * (size_t)h->n);
+        }
       }
     }
+  }
   /* uncoarsen with FM on every level */
   int64_t cut = 0;
   int32_t *cur = best;

@@ -10,7 +10,7 @@
  *   m_v = sum_u w(v,u) h_u / sum_u w(v,u)      (0 for isolated nodes)
  *   h'_v = relu(W_self h_v + W_nbr m_v + b)    (8 -> 64 -> 64)
  * and a linear read-out s_v = w_o . h2_v + b_o.
- * Features: 1; c(v)/mean c; log(1+deg)/log(1+max deg); weighted degree /
+ * Features: 1; c(v)/mean c; deg/max deg; weighted degree /
  * mean; BFS hops from anchor a (smallest key) and from anchor b (farthest from
  * a, smallest id), each divided by (max hops + 1), unreachable = 1; two
  * +-1 key bits (symmetry breaking).
@@ -18,6 +18,8 @@
  * cross-entropy of sigmoid(s) against the best-of-portfolio sides.
  * Proposal: nodes by (score desc, id asc) join block 0 while it stays within
  * its target (first fit), like the random start with a learned order.
+ * Every feature is an integer sum or a correctly rounded quotient of integer
+ * sums (no transcendental function), so a GPU computes the same values.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -96,7 +98,7 @@ void kmpo_mpnn_features(int32_t n, const int64_t *xadj, const int32_t *adj, cons
     uint64_t h = kmpo_step(key, (uint64_t)(uint32_t)v);
     x[0] = 1.0;
     x[1] = (vw ? vw[v] : 1) / meanc;
-    x[2] = maxdeg > 0 ? log1p((double)deg) / log1p((double)maxdeg) : 0.0;
+    x[2] = maxdeg > 0 ? (double)deg / (double)maxdeg : 0.0;
     x[3] = meanw > 0 ? wd / meanw : 0.0;
     x[4] = d1[v] >= 0 ? (double)d1[v] / (double)(D1 + 1) : 1.0;
     x[5] = d2[v] >= 0 ? (double)d2[v] / (double)(D2 + 1) : 1.0;
@@ -282,5 +284,126 @@ void kmpo_mpnn_propose(int32_t n, const int32_t *vw, const double *S, int32_t ta
       W0 += c;
     }
   }
+  free(o);
+}
+
+/* ----------------------------------------------------------------------
+ * Inference in the kernel's precision.  The score order decides an integer
+ * result (the proposal), so both sides take that decision in the same
+ * arithmetic: features in fp64 from integer sums (exact) and correctly
+ * rounded divisions, rounded once to fp32; layers in fp32 with every
+ * product-accumulate a fused multiply-add in this fixed order:
+ *   neighbour mean:  s = fma(w(v,u), h_u, s) over v's row in CSR order,
+ *                    then s / sum w (0 for isolated nodes)
+ *   pre-activation:  a = b_o; for i: a = fma(Ws[o][i], h[i], a);
+ *                                    a = fma(Wn[o][i], m[i], a)
+ *   read-out:        s = b_o; for o: s = fma(w_o[o], h2[o], s)
+ * W holds the network's parameters as fp32 values (BF16-representable).
+ */
+static void nbr_mean_f32(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *ew,
+                         const float *Hin, int32_t d, float *M) {
+  for (int32_t v = 0; v < n; ++v)
+    for (int32_t j = 0; j < d; ++j) {
+      float s = 0.f, ws = 0.f;
+      for (int64_t e = xadj[v]; e < xadj[v + 1]; ++e) {
+        float w = ew ? (float)ew[e] : 1.f;
+        ws += w;
+        s = fmaf(w, Hin[(size_t)adj[e] * d + j], s);
+      }
+      M[(size_t)v * d + j] = ws > 0.f ? s / ws : 0.f;
+    }
+}
+
+static void layer_f32(int32_t n, const float *W, int32_t ws, int32_t wn, int32_t b, int32_t din,
+                      const float *Hin, const float *M, float *H) {
+  for (int32_t v = 0; v < n; ++v)
+    for (int32_t o = 0; o < HID; ++o) {
+      float a = W[b + o];
+      for (int32_t i = 0; i < din; ++i) {
+        a = fmaf(W[ws + o * din + i], Hin[(size_t)v * din + i], a);
+        a = fmaf(W[wn + o * din + i], M[(size_t)v * din + i], a);
+      }
+      H[(size_t)v * HID + o] = a > 0.f ? a : 0.f;
+    }
+}
+
+void kmpo_mpnn_scores_f32(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
+                          const int32_t *ew, uint64_t key, const float *W, float *S) {
+  if (n <= 0) return;
+  double *Xd = (double *)malloc(sizeof(double) * (size_t)n * F_IN);
+  float *X = (float *)malloc(sizeof(float) * (size_t)n * F_IN);
+  float *M0 = (float *)malloc(sizeof(float) * (size_t)n * F_IN);
+  float *H1 = (float *)malloc(sizeof(float) * (size_t)n * HID);
+  float *M1 = (float *)malloc(sizeof(float) * (size_t)n * HID);
+  float *H2 = (float *)malloc(sizeof(float) * (size_t)n * HID);
+  kmpo_mpnn_features(n, xadj, adj, vw, ew, key, Xd);
+  for (size_t i = 0; i < (size_t)n * F_IN; ++i) X[i] = (float)Xd[i];
+  nbr_mean_f32(n, xadj, adj, ew, X, F_IN, M0);
+  layer_f32(n, W, P_W1S, P_W1N, P_B1, F_IN, X, M0, H1);
+  nbr_mean_f32(n, xadj, adj, ew, H1, HID, M1);
+  layer_f32(n, W, P_W2S, P_W2N, P_B2, HID, H1, M1, H2);
+  for (int32_t v = 0; v < n; ++v) {
+    float s = W[P_BO];
+    for (int32_t o = 0; o < HID; ++o) s = fmaf(W[P_WO + o], H2[(size_t)v * HID + o], s);
+    S[v] = s;
+  }
+  free(Xd); free(X); free(M0); free(H1); free(M1); free(H2);
+}
+
+/* order key of a score for the proposal: ascending key = descending score;
+ * -0 and +0 are the same score */
+uint32_t kmpo_mpnn_score_key(float s) {
+  uint32_t u = 0;
+  if (s != 0.f) memcpy(&u, &s, sizeof u);
+  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u); /* ascending in s */
+  return ~u;
+}
+
+/* the proposer the bipartitioner uses in learned mode (copied; NULL clears) */
+static float g_prop[P_TOTAL];
+static int g_have_prop;
+
+void kmpo_set_proposer(const float *W) {
+  g_have_prop = W != NULL;
+  if (W) memcpy(g_prop, W, sizeof g_prop);
+}
+
+const float *kmpo_proposer(void) { return g_have_prop ? g_prop : NULL; }
+
+/* learned start: nodes by (score key asc, id asc) join block 0 while it stays
+ * within target0 (first fit) */
+typedef struct {
+  uint32_t k;
+  int32_t v;
+} kv_t;
+
+static int cmp_kv(const void *a, const void *b) {
+  const kv_t *x = (const kv_t *)a, *y = (const kv_t *)b;
+  if (x->k != y->k) return x->k < y->k ? -1 : 1;
+  return x->v < y->v ? -1 : (x->v > y->v);
+}
+
+void kmpo_learned_initial(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
+                          const int32_t *ew, int32_t target0, uint64_t key, const float *W,
+                          int32_t *side) {
+  float *S = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+  kv_t *o = (kv_t *)malloc(sizeof(kv_t) * (size_t)(n > 0 ? n : 1));
+  kmpo_mpnn_scores_f32(n, xadj, adj, vw, ew, key, W, S);
+  for (int32_t v = 0; v < n; ++v) {
+    o[v].k = kmpo_mpnn_score_key(S[v]);
+    o[v].v = v;
+  }
+  qsort(o, (size_t)n, sizeof(kv_t), cmp_kv);
+  int64_t W0 = 0;
+  for (int32_t v = 0; v < n; ++v) side[v] = 1;
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t v = o[i].v;
+    int64_t c = vw ? vw[v] : 1;
+    if (W0 + c <= target0) {
+      side[v] = 0;
+      W0 += c;
+    }
+  }
+  free(S);
   free(o);
 }

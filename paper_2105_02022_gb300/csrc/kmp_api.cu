@@ -365,6 +365,10 @@ void kmp_config_default(kmp_config *c) {
   c->rep_ggg = 8;
   c->fm_passes = 8;
   c->fm_stop = 64;
+  c->learned = 0;
+  c->lrep_random = 0;
+  c->lrep_bfs = 0;
+  c->lrep_ggg = 1;
 }
 
 int kmp_set_config(const kmp_config *c) {
@@ -375,7 +379,8 @@ int kmp_set_config(const kmp_config *c) {
         c->refine_rounds > 64 || !pow2 || c->conv_den <= 0 || c->conv_num < 0 || c->ip_C < 1 ||
         c->ip_lp_rounds < 0 || c->ip_lp_rounds > 64 || c->rep_random < 0 || c->rep_bfs < 0 ||
         c->rep_ggg < 0 || c->rep_random + c->rep_bfs + c->rep_ggg < 1 ||
-        c->rep_random + c->rep_bfs + c->rep_ggg > 64 || c->fm_passes < 0 || c->fm_stop < 1)
+        c->rep_random + c->rep_bfs + c->rep_ggg > 64 || c->fm_passes < 0 || c->fm_stop < 1 ||
+        c->learned < 0 || c->learned > 1 || c->lrep_random < 0 || c->lrep_bfs < 0 || c->lrep_ggg < 0)
       fail(KMP_ERR_ARG, "invalid configuration");
     ctx().cfg = *c;
   });
@@ -544,6 +549,23 @@ int kmp_bipartition_blocks(const kmp_graph *g, int32_t nblocks, const int32_t *f
     sync_and_check("bipartition_blocks");
     *nblocks_out = nb;
     for (int32_t i = 0; i < nb; ++i) f_out[i] = fv[i];
+  });
+}
+
+int kmp_bipartition_each(const kmp_graph *g, int32_t nblocks, const int32_t *caps, uint64_t roundkey,
+                         kmp_vid *part) {
+  return guarded([&] {
+    if (!g || !caps || !part) fail(KMP_ERR_ARG, "NULL argument");
+    if (nblocks < 1) fail(KMP_ERR_ARG, "nblocks < 1");
+    for (int32_t b = 0; b < nblocks; ++b) {
+      const int32_t *c = caps + 4 * b;
+      if (c[0] < 0 || c[1] < 0 || c[2] < 1 || c[3] < 1) fail(KMP_ERR_ARG, "invalid caps");
+    }
+    check_range(g->g.n, part, 0, nblocks, "part");
+    std::vector<int32_t> fv(nblocks, 2);
+    int32_t items = 0;
+    bipartition_blocks(g->g, part, nblocks, fv, 0.0, 1, 1, roundkey, &items, caps);
+    sync_and_check("bipartition_each");
   });
 }
 

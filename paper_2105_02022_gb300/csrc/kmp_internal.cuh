@@ -158,7 +158,8 @@ enum : uint64_t {
   DOM_RANDOM = 5,
   DOM_BFS = 6,
   DOM_GGG = 7,
-  DOM_REFINE_LEVEL = 8
+  DOM_REFINE_LEVEL = 8,
+  DOM_LEARNED = 9
 };
 
 // ----------------------------------------------------------- warp helpers
@@ -271,7 +272,7 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
 // Algorithm 2, one split round; f in/out (host), returns new block count
 int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::vector<int32_t> &f,
                            double eps, int64_t cV, int32_t k, uint64_t roundkey,
-                           int32_t *items_out);
+                           int32_t *items_out, const int32_t *caps4 = nullptr);
 // caps (host)
 void split_caps(double eps, int64_t cV, int32_t k, int64_t cB, int32_t fB, int32_t *t0,
                 int32_t *t1, int32_t *L0, int32_t *L1);

@@ -8,7 +8,11 @@
 //      packs isolated nodes, and contracts (sort of (cu, cv) pairs, run sums),
 //      level after level until nothing contracts or the shrink stalls;
 //   2. runs the portfolio -- random, BFS and greedy graph growing starts, each
-//      refined by 2-way FM -- with one warp per repetition;
+//      refined by 2-way FM -- with one warp per repetition; in learned mode
+//      the CTA first scores the coarsest graph with the message-passing
+//      network (kmp_mpnn.cuh) and its score order is one more start, ahead of
+//      a reduced portfolio; the rest of the portfolio runs only if the best so
+//      far is infeasible;
 //   3. projects the best bipartition up the item's hierarchy and runs 2-way FM
 //      (one warp) on every level.
 // Scratch comes from a per-item region through a bump allocator; if a region
@@ -19,6 +23,7 @@
 #include <numeric>
 
 #include "kmp_internal.cuh"
+#include "kmp_mpnn.cuh"
 
 namespace kmp {
 
@@ -54,6 +59,10 @@ struct IPArgs {
   // configuration
   int32_t S, ip_C, ip_lp_rounds, rep_random, rep_bfs, rep_ggg, fm_passes, fm_stop;
   int32_t conv_num, conv_den;
+  // learned mode: proposer weights (null: plain portfolio) and reduced repetitions
+  const __nv_bfloat16 *W;
+  int32_t lrep_random, lrep_bfs, lrep_ggg;
+  SampleSink sink;  // counters null: no recording
 };
 
 struct LG {
@@ -684,14 +693,17 @@ __device__ int64_t warp_fm(const IPArgs &A, const LG &g, int32_t *side, int64_t 
 }
 
 // portfolio initial bipartition by one warp: algo 0 random, 1 BFS, 2 GGG
+// algo 0 random, 1 BFS, 2 greedy graph growing, 3 learned (first fit in the
+// order of `score`, like random with a learned order)
 __device__ void warp_initial(int algo, const LG &g, int32_t t0, uint64_t key, int32_t *side,
-                             uint64_t *oh, int32_t *ov, int32_t *gain, int32_t *vis, int32_t *queue) {
+                             uint64_t *oh, int32_t *ov, int32_t *gain, int32_t *vis, int32_t *queue,
+                             const float *score) {
   int lane = threadIdx.x & 31;
   int32_t n = g.n;
   int32_t P = pow2_at_least(n > 1 ? n : 2);
   for (int32_t i = lane; i < P; i += 32) {
     if (i < n) {
-      oh[i] = key_step(key, (uint64_t)(uint32_t)i);
+      oh[i] = algo == 3 ? (uint64_t)mp_score_key(score[i]) : key_step(key, (uint64_t)(uint32_t)i);
       ov[i] = i;
     } else {
       oh[i] = ~0ull;
@@ -701,7 +713,7 @@ __device__ void warp_initial(int algo, const LG &g, int32_t t0, uint64_t key, in
   for (int32_t v = lane; v < n; v += 32) side[v] = 1;
   __syncwarp();
   warp_bitonic_hv(oh, ov, P);
-  if (algo == 0) {
+  if (algo == 0 || algo == 3) {
     if (lane == 0) {
       int64_t W0 = 0;
       for (int32_t i = 0; i < n; ++i) {
@@ -773,10 +785,49 @@ __device__ __forceinline__ int32_t level_cap(int32_t L, int32_t t, int32_t maxc)
   return b > L ? (int32_t)b : L;
 }
 
+// append the coarsest graph of an item and its winning sides to the sink
+// (skipped and counted as dropped when the sink is full)
+__device__ void record_sample(const SampleSink &K, const LG &h, const int32_t *side, uint64_t key) {
+  __shared__ unsigned long long s_nb, s_eb;
+  __shared__ int32_t s_ok;
+  if (threadIdx.x == 0) {
+    unsigned long long gi = atomicAdd(&K.counters[0], 1ull);
+    unsigned long long nb = atomicAdd(&K.counters[1], (unsigned long long)h.n);
+    unsigned long long eb = atomicAdd(&K.counters[2], (unsigned long long)h.m);
+    bool ok = gi < (unsigned long long)K.max_graphs && nb + h.n <= (unsigned long long)K.max_nodes &&
+              eb + h.m <= (unsigned long long)K.max_entries;
+    if (ok) {
+      int64_t *r = K.rec + 5 * gi;
+      r[0] = (int64_t)nb;
+      r[1] = h.n;
+      r[2] = (int64_t)eb;
+      r[3] = h.m;
+      r[4] = (int64_t)key;
+    } else {
+      atomicAdd(&K.counters[3], 1ull);
+    }
+    s_ok = ok;
+    s_nb = nb;
+    s_eb = eb;
+  }
+  __syncthreads();
+  if (s_ok) {
+    for (int32_t v = threadIdx.x; v < h.n; v += IPT) {
+      K.deg[s_nb + v] = h.xadj[v + 1] - h.xadj[v];
+      K.vw[s_nb + v] = h.vw[v];
+      K.side[s_nb + v] = side[v];
+    }
+    for (int32_t e = threadIdx.x; e < h.m; e += IPT) {
+      K.adj[s_eb + e] = h.adj[e];
+      K.ew[s_eb + e] = h.ew[e];
+    }
+  }
+  __syncthreads();
+}
+
 __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *wvals) {
   __shared__ LG lv[IP_MAXL + 1];
   __shared__ int32_t *maps[IP_MAXL + 1];
-  __shared__ int32_t s_nl;
   __shared__ int64_t s_wk[IPW][3];
   __shared__ int32_t s_wrep[IPW];
   const ItemDesc D = A.items[it];
@@ -812,7 +863,6 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
     g0.maxdeg = md;
     g0.maxc = mc;
     lv[0] = g0;
-    s_nl = 1;
   }
   __syncthreads();
   // 1. coarsen
@@ -866,6 +916,23 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
     if (threadIdx.x == 0) atomicExch(A.oom, 1);
     return;
   }
+  // learned mode: scores of the coarsest graph's nodes (whole CTA)
+  const float *score = nullptr;
+  if (A.W) {
+    float *X = reinterpret_cast<float *>(B.take((int64_t)nH * MF));
+    int32_t *d1 = B.take(nH), *d2 = B.take(nH);
+    float *scr = reinterpret_cast<float *>(B.take((int64_t)nH * (MF + 3 * MH)));
+    float *sc = reinterpret_cast<float *>(B.take(nH));
+    if (B.oom) {
+      if (threadIdx.x == 0) atomicExch(A.oom, 1);
+      return;
+    }
+    GView<int32_t> G{nH, h.xadj, h.adj, 0, h.vw, h.ew};
+    mp_features(G, key_step(D.key, DOM_LEARNED), X, d1, d2);
+    mp_forward_cta(G, A.W, X, scr, sc);
+    score = sc;
+  }
+  __shared__ int32_t s_bw;
   {
     int32_t *base = wbuf + per_warp * w;
     int32_t *side = base;
@@ -878,64 +945,89 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
     uint64_t *oh = reinterpret_cast<uint64_t *>(ov + PH);  // offset 6 nH + PH: even
     int32_t reps[3] = {A.rep_random, A.rep_bfs, A.rep_ggg};
     uint64_t doms[3] = {DOM_RANDOM, DOM_BFS, DOM_GGG};
-    int32_t R = reps[0] + reps[1] + reps[2];
+    // candidates in order: [learned], the first `first[a]` repetitions of each
+    // algorithm, then (learned mode, best still infeasible) the rest
+    int32_t nlrn = score ? 1 : 0;
+    int32_t first[3] = {reps[0], reps[1], reps[2]};
+    if (score) {
+      first[0] = min(A.lrep_random, reps[0]);
+      first[1] = min(A.lrep_bfs, reps[1]);
+      first[2] = min(A.lrep_ggg, reps[2]);
+    }
+    int32_t rest[3] = {reps[0] - first[0], reps[1] - first[1], reps[2] - first[2]};
+    int32_t R0 = nlrn + first[0] + first[1] + first[2];
+    int32_t R1 = rest[0] + rest[1] + rest[2];
     bool have = false;
     int32_t binf = 0, brep = -1;
     int64_t bov = 0, bcut = 0;
-    for (int32_t q = w; q < R; q += IPW) {
-      int a = q < reps[0] ? 0 : (q < reps[0] + reps[1] ? 1 : 2);
-      int32_t r = a == 0 ? q : (a == 1 ? q - reps[0] : q - reps[0] - reps[1]);
-      uint64_t key = key_step(key_step(D.key, doms[a]), (uint64_t)r);
-      warp_initial(a, h, D.t0, key, side, oh, ov, gain, locked, queue);
-      FMBuf fb{gain, locked, moves};
-      int64_t cut = warp_fm(A, h, side, hL0, hL1, fb);
-      int64_t W0 = 0, W1 = 0;
-      for (int32_t v = lane; v < nH; v += 32) {
-        if (side[v] == 0) W0 += h.vw[v];
-        else W1 += h.vw[v];
+    for (int phase = 0; phase < 2; ++phase) {
+      if (phase == 1 && (R1 == 0 || s_wk[s_bw][0] == 0)) break;
+      int32_t Rp = phase == 0 ? R0 : R1;
+      const int32_t *cnt = phase == 0 ? first : rest;
+      for (int32_t q = w; q < Rp; q += IPW) {
+        int a, r;
+        if (phase == 0 && q < nlrn) {
+          a = 3;
+          r = 0;
+        } else {
+          int32_t x = phase == 0 ? q - nlrn : q;
+          a = x < cnt[0] ? 0 : (x < cnt[0] + cnt[1] ? 1 : 2);
+          r = a == 0 ? x : (a == 1 ? x - cnt[0] : x - cnt[0] - cnt[1]);
+          if (phase == 1) r += first[a];
+        }
+        uint64_t key = a == 3 ? 0 : key_step(key_step(D.key, doms[a]), (uint64_t)r);
+        warp_initial(a, h, D.t0, key, side, oh, ov, gain, locked, queue, score);
+        FMBuf fb{gain, locked, moves};
+        int64_t cut = warp_fm(A, h, side, hL0, hL1, fb);
+        int64_t W0 = 0, W1 = 0;
+        for (int32_t v = lane; v < nH; v += 32) {
+          if (side[v] == 0) W0 += h.vw[v];
+          else W1 += h.vw[v];
+        }
+        W0 = warp_sum64(W0);
+        W1 = warp_sum64(W1);
+        int64_t o0 = W0 - hL0, o1 = W1 - hL1;
+        int64_t o = o0 > o1 ? o0 : o1;
+        int32_t inf = o > 0;
+        int64_t ovv = inf ? o : 0;
+        if (!have || fm_less(inf, ovv, cut, binf, bov, bcut)) {
+          have = true;
+          binf = inf;
+          bov = ovv;
+          bcut = cut;
+          brep = phase == 0 ? q : R0 + q;
+          for (int32_t v = lane; v < nH; v += 32) best[v] = side[v];
+        }
+        __syncwarp();
       }
-      W0 = warp_sum64(W0);
-      W1 = warp_sum64(W1);
-      int64_t o0 = W0 - hL0, o1 = W1 - hL1;
-      int64_t o = o0 > o1 ? o0 : o1;
-      int32_t inf = o > 0;
-      int64_t ovv = inf ? o : 0;
-      if (!have || fm_less(inf, ovv, cut, binf, bov, bcut)) {
-        have = true;
-        binf = inf;
-        bov = ovv;
-        bcut = cut;
-        brep = q;
-        for (int32_t v = lane; v < nH; v += 32) best[v] = side[v];
+      if (lane == 0) {
+        s_wk[w][0] = have ? binf : 2;
+        s_wk[w][1] = bov;
+        s_wk[w][2] = bcut;
+        s_wrep[w] = have ? brep : INT32_MAX;
       }
-      __syncwarp();
-    }
-    if (lane == 0) {
-      s_wk[w][0] = have ? binf : 2;
-      s_wk[w][1] = bov;
-      s_wk[w][2] = bcut;
-      s_wrep[w] = have ? brep : INT32_MAX;
+      __syncthreads();
+      // the first candidate with the best (infeasible?, overload, cut) wins
+      if (threadIdx.x == 0) {
+        int32_t bw_ = 0;
+        for (int32_t x = 1; x < IPW; ++x) {
+          bool better = fm_less((int32_t)s_wk[x][0], s_wk[x][1], s_wk[x][2], (int32_t)s_wk[bw_][0],
+                                s_wk[bw_][1], s_wk[bw_][2]);
+          bool tie = !better && !fm_less((int32_t)s_wk[bw_][0], s_wk[bw_][1], s_wk[bw_][2],
+                                         (int32_t)s_wk[x][0], s_wk[x][1], s_wk[x][2]);
+          if (better || (tie && s_wrep[x] < s_wrep[bw_])) bw_ = x;
+        }
+        s_bw = bw_;
+      }
+      __syncthreads();
     }
   }
-  __syncthreads();
-  __shared__ int32_t s_bw;
-  if (threadIdx.x == 0) {
-    int32_t bw_ = 0;
-    for (int32_t x = 1; x < IPW; ++x) {
-      bool better = fm_less((int32_t)s_wk[x][0], s_wk[x][1], s_wk[x][2], (int32_t)s_wk[bw_][0],
-                            s_wk[bw_][1], s_wk[bw_][2]);
-      bool tie = !better && !fm_less((int32_t)s_wk[bw_][0], s_wk[bw_][1], s_wk[bw_][2],
-                                     (int32_t)s_wk[x][0], s_wk[x][1], s_wk[x][2]);
-      if (better || (tie && s_wrep[x] < s_wrep[bw_])) bw_ = x;
-    }
-    s_bw = bw_;
-  }
-  __syncthreads();
   {
     int32_t *bsrc = wbuf + per_warp * s_bw + nH;
     for (int32_t v = threadIdx.x; v < nH; v += IPT) fin[v] = bsrc[v];
   }
   __syncthreads();
+  if (A.sink.counters) record_sample(A.sink, h, fin, D.key);
   // 3. uncoarsen with FM on every level (warp 0)
   int32_t *cur = fin;
   int32_t *fmbuf = B.take(3ll * n0);
@@ -1071,8 +1163,11 @@ __global__ void k_write_parts(int32_t n, const int32_t *members, const int32_t *
   }
 }
 
+// caps4 (host, nullable): explicit (t0, t1, L0, L1) per block instead of the
+// caps Algorithm 2 derives from (eps, cV, k, f)
 int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::vector<int32_t> &f,
-                           double eps, int64_t cV, int32_t k, uint64_t roundkey, int32_t *items_out) {
+                           double eps, int64_t cV, int32_t k, uint64_t roundkey, int32_t *items_out,
+                           const int32_t *caps4) {
   Context &C = ctx();
   const kmp_config &cfg = C.cfg;
   cudaStream_t s = C.stream;
@@ -1147,7 +1242,14 @@ int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::
     d.ebase = eb;
     d.n = hcount[b];
     d.m = (int32_t)he[b];
-    split_caps(eps, cV, k, (int64_t)hw[b], f[b], &d.t0, &d.t1, &d.L0, &d.L1);
+    if (caps4) {
+      d.t0 = caps4[4 * b];
+      d.t1 = caps4[4 * b + 1];
+      d.L0 = caps4[4 * b + 2];
+      d.L1 = caps4[4 * b + 3];
+    } else {
+      split_caps(eps, cV, k, (int64_t)hw[b], f[b], &d.t0, &d.t1, &d.L0, &d.L1);
+    }
     d.key = key_step(roundkey, (uint64_t)b);
     items.push_back(d);
   }
@@ -1163,6 +1265,7 @@ int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::
     });
     DBuf<int32_t> dorder(items.size()), q(2);
     to_dev(dorder.p, order.data(), order.size());
+    bool learned = cfg.learned && proposer().W;
     int64_t mult = 1;
     for (int attempt = 0; attempt < 6; ++attempt, mult *= 4) {
       int64_t total = 0;
@@ -1170,7 +1273,8 @@ int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::
         int64_t nP = next_pow2((uint64_t)std::max(d.n, 2));
         int64_t mP = next_pow2((uint64_t)std::max(d.m, 2));
         d.sbase = total;
-        d.ssize = mult * (96ll * d.n + 64ll * nP + 16ll * d.m + 8ll * mP + 2048);
+        d.ssize = mult * (96ll * d.n + 64ll * nP + 16ll * d.m + 8ll * mP + 2048 +
+                          (learned ? (int64_t)(2 * MF + 3 * MH + 4) * d.n + 64 : 0));
         total += d.ssize;
       }
       DBuf<ItemDesc> ditems(items.size());
@@ -1199,6 +1303,11 @@ int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::
       A.fm_stop = cfg.fm_stop;
       A.conv_num = cfg.conv_num;
       A.conv_den = cfg.conv_den;
+      A.W = cfg.learned ? proposer().W : nullptr;
+      A.lrep_random = cfg.lrep_random;
+      A.lrep_bfs = cfg.lrep_bfs;
+      A.lrep_ggg = cfg.lrep_ggg;
+      A.sink = sample_sink();
       int gridip = (int)std::min<int64_t>((int64_t)items.size(), (int64_t)C.sms * C.tune.ip_blocks_per_sm);
       k_ip_items<<<gridip, IPT, 0, s>>>(A);
       KMP_LAUNCHED("ip_items");

@@ -33,7 +33,8 @@ class KmpError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "C", "lp_rounds", "refine_rounds", "subrounds", "two_hop", "conv_num", "conv_den",
-        "ip_C", "ip_lp_rounds", "rep_random", "rep_bfs", "rep_ggg", "fm_passes", "fm_stop")]
+        "ip_C", "ip_lp_rounds", "rep_random", "rep_bfs", "rep_ggg", "fm_passes", "fm_stop",
+        "learned", "lrep_random", "lrep_bfs", "lrep_ggg")]
 
 
 class Stats(ctypes.Structure):
@@ -92,10 +93,24 @@ def load():
         "kmp_cut": (ctypes.c_int, [P, P, i32, P, P]),
         "kmp_cut_noalloc": (ctypes.c_int, [P, P, i32, P, P]),
         "kmp_bipartition_blocks": (ctypes.c_int, [P, i32, P, dbl, i64, i32, u64, P, P, P]),
+        "kmp_bipartition_each": (ctypes.c_int, [P, i32, P, u64, P]),
         "kmp_partition": (ctypes.c_int, [i32, P, P, P, P, i32, dbl, u64, P]),
         "kmp_partition_graph": (ctypes.c_int, [P, i32, dbl, u64, P, P]),
         "kmp_last_stats": (ctypes.c_int, [P]),
         "kmp_set_profiling": (ctypes.c_int, [ctypes.c_int]),
+        "kmp_mpnn_num_params": (ctypes.c_int, []),
+        "kmp_mpnn_create": (ctypes.c_int, [u64, PP]),
+        "kmp_mpnn_free": (ctypes.c_int, [P]),
+        "kmp_mpnn_get_params": (ctypes.c_int, [P, P]),
+        "kmp_mpnn_set_params": (ctypes.c_int, [P, P]),
+        "kmp_mpnn_forward": (ctypes.c_int, [P, i32, P, P, P, P, P, P, P, P]),
+        "kmp_mpnn_gradients": (ctypes.c_int, [P, i32, P, P, P, P, P, P, P, P, P]),
+        "kmp_mpnn_train": (ctypes.c_int, [P, i32, P, P, P, P, P, P, P, i32, ctypes.c_float, P]),
+        "kmp_set_proposer": (ctypes.c_int, [P]),
+        "kmp_sample_sink_open": (ctypes.c_int, [i32, i64, i64]),
+        "kmp_sample_sink_count": (ctypes.c_int, [P, P, P, P]),
+        "kmp_sample_sink_read": (ctypes.c_int, [P, P, P, P, P, P, P]),
+        "kmp_sample_sink_close": (ctypes.c_int, []),
         "kmp_set_tuning": (ctypes.c_int, [P]),
         "kmp_get_tuning": (ctypes.c_int, [P]),
         "kmp_autotune": (ctypes.c_int, [P, i32, dbl, u64, P]),
@@ -273,6 +288,15 @@ def cut_noalloc(dg: DeviceGraph, part: torch.Tensor, k: int):
     return c.value, bw
 
 
+def bipartition_each(dg: DeviceGraph, nblocks: int, caps, roundkey: int, part: torch.Tensor):
+    """Bipartition every block with explicit (t0, t1, L0, L1) caps; part becomes 2b + side."""
+    _stream()
+    caps = np.ascontiguousarray(caps, np.int32).reshape(-1)
+    assert caps.size == 4 * nblocks
+    _check(load().kmp_bipartition_each(dg.h, int(nblocks), _ptr(caps), ctypes.c_uint64(roundkey), _ptr(part)))
+    return part
+
+
 def bipartition_blocks(dg: DeviceGraph, nblocks: int, f, eps: float, cV: int, k: int, roundkey: int,
                        part: torch.Tensor):
     _stream()
@@ -340,3 +364,124 @@ def profile_read(reset: bool = False):
     ms, by, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
     _check(load().kmp_profile_read(ctypes.byref(ms), ctypes.byref(by), ctypes.byref(n), 1 if reset else 0))
     return ms.value, by.value, n.value
+
+
+# ------------------------------------------------------------ learned proposer
+MPNN_PARAMS = 9409
+
+
+class Batch:
+    """Disjoint union of graphs in host arrays (the proposer's batch format)."""
+
+    def __init__(self, noff, xadj, adj, vw, ew, keys, side=None):
+        self.noff = np.ascontiguousarray(noff, np.int32)
+        self.xadj = np.ascontiguousarray(xadj, np.int64)
+        self.adj = np.ascontiguousarray(adj, np.int32)
+        self.vw = None if vw is None else np.ascontiguousarray(vw, np.int32)
+        self.ew = None if ew is None else np.ascontiguousarray(ew, np.int32)
+        self.keys = np.ascontiguousarray(keys, np.uint64)
+        self.side = None if side is None else np.ascontiguousarray(side, np.int32)
+
+    @property
+    def ng(self):
+        return len(self.noff) - 1
+
+    @property
+    def n(self):
+        return int(self.noff[-1])
+
+    def _args(self):
+        return (int(self.ng), _ptr(self.noff), _ptr(self.xadj), _ptr(self.adj), _ptr(self.vw), _ptr(self.ew),
+                _ptr(self.keys))
+
+    @staticmethod
+    def from_graphs(graphs, keys, sides=None):
+        noff, xs, adjs, vws, ews = [0], [np.zeros(1, np.int64)], [], [], []
+        nb = eb = 0
+        for g in graphs:
+            xs.append(np.asarray(g.xadj[1:], np.int64) + eb)
+            adjs.append(np.asarray(g.adjncy, np.int32) + nb)
+            vws.append(np.ones(g.n, np.int32) if g.vwgt is None else np.asarray(g.vwgt, np.int32))
+            ews.append(np.ones(len(g.adjncy), np.int32) if g.adjwgt is None else np.asarray(g.adjwgt, np.int32))
+            nb += g.n
+            eb += len(g.adjncy)
+            noff.append(nb)
+        side = None if sides is None else np.concatenate([np.asarray(x, np.int32) for x in sides])
+        return Batch(noff, np.concatenate(xs), np.concatenate(adjs) if adjs else np.zeros(0, np.int32),
+                     np.concatenate(vws), np.concatenate(ews) if ews else np.zeros(0, np.int32), keys, side)
+
+
+class Mpnn:
+    """A proposer model (device-resident weights, Adam state)."""
+
+    def __init__(self, seed: int = 1):
+        _stream()
+        h = ctypes.c_void_p()
+        _check(load().kmp_mpnn_create(ctypes.c_uint64(seed), ctypes.byref(h)))
+        self.h = h
+
+    def free(self):
+        if self.h:
+            _check(load().kmp_mpnn_free(self.h))
+            self.h = None
+
+    def get_params(self):
+        p = np.zeros(MPNN_PARAMS, np.float32)
+        _check(load().kmp_mpnn_get_params(self.h, _ptr(p)))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        assert p.size == MPNN_PARAMS
+        _check(load().kmp_mpnn_set_params(self.h, _ptr(p)))
+
+    def forward(self, b: Batch, features=False):
+        _stream()
+        S = np.zeros(max(b.n, 1), np.float32)
+        X = np.zeros((max(b.n, 1), 8), np.float32) if features else None
+        _check(load().kmp_mpnn_forward(self.h, *b._args(), _ptr(S), _ptr(X)))
+        return (S[: b.n], X[: b.n]) if features else S[: b.n]
+
+    def gradients(self, b: Batch):
+        _stream()
+        loss = ctypes.c_float()
+        g = np.zeros(MPNN_PARAMS, np.float32)
+        _check(load().kmp_mpnn_gradients(self.h, *b._args(), _ptr(b.side), ctypes.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def train(self, b: Batch, epochs: int, lr: float):
+        _stream()
+        losses = np.zeros(max(epochs, 1), np.float32)
+        _check(load().kmp_mpnn_train(self.h, *b._args(), _ptr(b.side), int(epochs), ctypes.c_float(lr),
+                                     _ptr(losses)))
+        return losses[:epochs]
+
+
+def set_proposer(m: "Mpnn | None"):
+    _check(load().kmp_set_proposer(m.h if m is not None else None))
+
+
+def sample_sink_open(max_graphs: int, max_nodes: int, max_entries: int):
+    _stream()
+    _check(load().kmp_sample_sink_open(int(max_graphs), int(max_nodes), int(max_entries)))
+
+
+def sample_sink_read():
+    """(Batch of the kept samples with their sides, dropped count)."""
+    ng, nn, ne, dr = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().kmp_sample_sink_count(ctypes.byref(ng), ctypes.byref(nn), ctypes.byref(ne), ctypes.byref(dr)))
+    noff = np.zeros(ng.value + 1, np.int32)
+    xadj = np.zeros(nn.value + 1, np.int64)
+    adj = np.zeros(max(ne.value, 1), np.int32)
+    vw = np.zeros(max(nn.value, 1), np.int32)
+    ew = np.zeros(max(ne.value, 1), np.int32)
+    keys = np.zeros(max(ng.value, 1), np.uint64)
+    side = np.zeros(max(nn.value, 1), np.int32)
+    _check(load().kmp_sample_sink_read(_ptr(noff), _ptr(xadj), _ptr(adj), _ptr(vw), _ptr(ew), _ptr(keys), _ptr(side)))
+    b = Batch(noff, xadj, adj[: ne.value], vw[: nn.value], ew[: ne.value], keys[: ng.value], side[: nn.value])
+    return b, dr.value
+
+
+def sample_sink_close():
+    _check(load().kmp_sample_sink_close())
+

@@ -67,7 +67,7 @@ def test_features_on_a_path():
     assert np.allclose(X[:, 0], 1.0)
     assert np.allclose(X[:, 1], 1.0)                      # unit weights: c(v)/mean = 1
     deg = np.diff(g.xadj)
-    assert np.allclose(X[:, 2], np.log1p(deg) / np.log1p(2))
+    assert np.allclose(X[:, 2], deg / 2)
     assert np.allclose(X[:, 3], deg / deg.mean())
     assert set(np.unique(X[:, 6:])) <= {-1.0, 1.0}
 
@@ -78,3 +78,85 @@ def test_propose_first_fit_by_score():
     # order: 1 (0.9), 2 (0.9, id 2), 4 (0.5), 0, 3; target 4: 1 (w1) + 2 (w2) -> 3, 4 (w1) -> 4
     side = O.mpnn_propose(g, S, 4)
     assert side.tolist() == [1, 0, 0, 1, 0]
+
+
+def _bf16(x):
+    """Round float32 values to the nearest BF16 value (ties to even)."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def test_bf16_rounding_helper():
+    # 1 + 2^-8 is halfway between BF16 neighbours 1 and 1 + 2^-7: ties to even -> 1
+    x = np.array([1.0, 1 + 2.0**-8, 1 + 3 * 2.0**-8, -2.5], np.float32)
+    assert _bf16(x).tolist() == [1.0, 1.0, 1 + 2.0**-6, -2.5]
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_fp32_scores_follow_the_fp64_network(seed):
+    # the kernel-precision path is the same network: it agrees with the fp64
+    # forward to fp32 rounding (a wrong index or a dropped term would not)
+    g = gg.with_weights(gg.random_graph(60, 150, seed), 9, 13, seed)
+    P = _bf16(_params(seed, 0.25).astype(np.float32))
+    key = O.key(seed, [3])
+    S32 = O.mpnn_scores_f32(g, key, P)
+    S64 = O.mpnn_forward(g, O.mpnn_features(g, key), P.astype(np.float64))
+    assert np.max(np.abs(S32 - S64)) <= 1e-4 * (1 + np.max(np.abs(S64)))
+
+
+def test_score_key_orders_descending_and_merges_zeros():
+    vals = [3.5, 1.0, 1e-30, 0.0, -1e-30, -2.0, -np.inf]
+    keys = [O.mpnn_score_key(v) for v in vals]
+    assert keys == sorted(keys) and len(set(keys)) == len(keys)
+    assert O.mpnn_score_key(-0.0) == O.mpnn_score_key(0.0)
+    assert O.mpnn_score_key(np.inf) < keys[0]
+
+
+def _distance_net():
+    """score = -d1 / (D1 + 1): only the hop distance from anchor a counts"""
+    P = np.zeros(O.mpnn_num_params(), np.float32)
+    P[0 * 8 + 4] = 1.0            # W1_self[0][4]: h1_0 = relu(x4)
+    P[1088 + 0 * 64 + 0] = 1.0    # W2_self[0][0]: h2_0 = h1_0
+    P[9344 + 0] = -1.0            # w_o[0]
+    return P
+
+
+def test_learned_start_grows_from_the_anchor():
+    # with the distance network, the learned start is the first fit in
+    # (hop distance from anchor a, id) order: on a path, a contiguous segment
+    n, t0 = 9, 4
+    g = gg.path(n)
+    key = O.key(7, [2])
+    hs = [O.step(key, v) for v in range(n)]
+    a = int(np.argmin(hs))
+    order = sorted(range(n), key=lambda v: (abs(v - a), v))
+    want = np.ones(n, np.int32)
+    want[order[:t0]] = 0
+    side = O.learned_initial(g, t0, key, _distance_net())
+    assert side.tolist() == want.tolist()
+
+
+def test_learned_mode_bipartition_is_optimal_on_a_path():
+    # learned start alone (no portfolio repetitions), then FM: one cut edge,
+    # the brute-force optimum of a balanced path bisection
+    g = gg.path(18)
+    cfg = O.config()
+    cfg.learned, cfg.lrep_random, cfg.lrep_bfs, cfg.lrep_ggg = 1, 0, 0, 0
+    O.set_proposer(_distance_net())
+    try:
+        side, cut = O.bipartition(g, 9, 9, 9, 9, O.key(1, [5]), cfg)
+    finally:
+        O.set_proposer(None)
+    assert cut == O.brute_bisection(g, 9, 9)[0] == 1
+    # the bipartitioner's caps allow target + max c(v) (reading B5)
+    assert abs(int(np.sum(side == 0)) - 9) <= 1
+
+
+def test_learned_mode_without_a_proposer_is_the_plain_method():
+    g = gg.with_weights(gg.rgg(3000, 8, 3), 4, 6, 3)
+    cfg = O.config()
+    p0, _, _ = O.partition(g, 8, 0.03, 2, cfg)
+    cfg.learned = 1
+    p1, _, _ = O.partition(g, 8, 0.03, 2, cfg)
+    assert np.array_equal(p0, p1)
