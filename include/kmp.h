@@ -245,6 +245,9 @@ typedef struct {
                                  multi-CTA hub kernels (256..2048) */
   int32_t hub_chunk;          /* edges per hub work unit (256..65536, power of two) */
   int32_t ip_blocks_per_sm;   /* bipartitioner CTAs per SM (1..8) */
+  int32_t dense_hub_degree;   /* with few labels (refinement: labels are block ids), degree
+                                 above which a node's rating is split over many CTAs into a
+                                 dense per-label row instead of one CTA (512..2^30) */
 } kmp_tuning;
 
 int kmp_set_tuning(const kmp_tuning *t);

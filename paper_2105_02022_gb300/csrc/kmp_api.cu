@@ -628,7 +628,8 @@ int kmp_set_tuning(const kmp_tuning *t) {
     bool pow2 = t->hub_chunk > 0 && (t->hub_chunk & (t->hub_chunk - 1)) == 0;
     if (t->rate_blocks_per_sm < 2 || t->rate_blocks_per_sm > 16 || t->hub_degree < 256 ||
         t->hub_degree > 2048 || !pow2 || t->hub_chunk < 256 || t->hub_chunk > 65536 ||
-        t->ip_blocks_per_sm < 1 || t->ip_blocks_per_sm > 8)
+        t->ip_blocks_per_sm < 1 || t->ip_blocks_per_sm > 8 || t->dense_hub_degree < 512 ||
+        t->dense_hub_degree > (1 << 30))
       fail(KMP_ERR_ARG, "invalid tuning");
     ctx().tune = *t;
   });
@@ -662,7 +663,7 @@ int kmp_autotune(const kmp_graph *g, int32_t k, double eps, uint64_t seed, kmp_t
     for (int gi : grids)
       for (int hd : hubs)
         for (int hc : chunks) {
-          C.tune = kmp_tuning{gi, hd, hc, keep.ip_blocks_per_sm};
+          C.tune = kmp_tuning{gi, hd, hc, keep.ip_blocks_per_sm, keep.dense_hub_degree};
           LPStats st;
           cluster_level(G, (int32_t)U, C.cfg.lp_rounds, key_of(seed, {DOM_COARSEN, 0}), false, label,
                         nullptr, &st, nullptr);

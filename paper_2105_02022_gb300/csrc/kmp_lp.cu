@@ -30,6 +30,7 @@ constexpr int RATE_T = 256;
 constexpr int WARP_TAB = 512;   // per-warp hash table (bin 4: degree <= 256)
 constexpr int CTA_TAB = 4096;   // per-CTA shared table (bin 5: degree <= 2048)
 constexpr int64_t HUGE_DEG_MAX = CTA_TAB / 2;  // largest degree a shared CTA table serves
+static_assert(HUGE_DEG_MAX == 2048, "upper bound of kmp_tuning.hub_degree");
 
 __host__ __device__ __forceinline__ int deg_bin(int64_t d, int64_t huge) {
   if (d <= 4) return 0;
@@ -80,12 +81,16 @@ struct LPArgs {
   unsigned long long *hkc;     // best admissible key per hub
   unsigned long long *hku;     // best key per hub
   int32_t *hrown;              // rating of the hub's own cluster
+  int32_t *hlist;              // occupied table slots of each hub (same offsets as the table)
+  int32_t *hcount;             // number of occupied slots per hub
   int32_t *plan_h;             // per sub-round hub plan: hub index of each bin-6 entry,
   int64_t *plan_e;             // exclusive prefix of its edge chunks,
   int64_t *plan_t;             // exclusive prefix of its table chunks,
   int64_t *plan_tot;           // [0] edge chunks, [1] table chunks
   int32_t small_labels;        // all labels fit a CTA table: bin 6 handled like bin 5
-  int64_t huge_deg;            // degree above which a node is a hub (<= HUGE_DEG_MAX)
+  int32_t *hdense;             // few labels: bin-6 entry i of a sub-round owns row i of
+                               // a [hubs][nlab] rating array filled by many CTAs
+  int64_t huge_deg;            // degree above which a node is a hub (many labels: <= HUGE_DEG_MAX)
   int64_t hub_chunk;           // edges per hub insert work unit
   int32_t nlab;
   int32_t S;
@@ -379,8 +384,9 @@ __global__ void __launch_bounds__(RATE_T) k_rate(LPArgs A, int s) {
   }
   __syncthreads();
   {
-    // bin 5, and bin 6 as well when every label set fits a shared table
-    int32_t lo = bo[5], hi = A.small_labels ? bo[7] : bo[6];
+    // bin 5, and bin 6 as well when every label set fits a shared table and
+    // no dense hub array is in use
+    int32_t lo = bo[5], hi = (A.small_labels && !A.hdense) ? bo[7] : bo[6];
     for (int64_t idx = lo + blockIdx.x; idx < hi; idx += gridDim.x) {
       int32_t u = A.vlist[idx];
       uint32_t cap = table_cap(A.xadj[u + 1] - A.xadj[u], A.nlab);
@@ -390,7 +396,7 @@ __global__ void __launch_bounds__(RATE_T) k_rate(LPArgs A, int s) {
 }
 
 // ---- hubs (bin 6) with many labels: insert / reduce / emit
-constexpr int64_t HUB_RCHUNK = 4096;  // table entries per reduce work unit
+constexpr int64_t HUB_RCHUNK = 4096;  // occupied-slot list entries per reduce work unit
 
 __device__ __forceinline__ int32_t hub_index(const LPArgs &A, int32_t u) {
   int32_t lo = 0, hi = A.nhubs - 1;
@@ -428,7 +434,7 @@ __global__ void __launch_bounds__(1024) k_hub_plan(LPArgs A, int s) {
     int32_t h = 0;
     if (i < cnt) {
       int32_t u = A.vlist[lo + i];
-      h = hub_index(A, u);
+      h = A.hubs ? hub_index(A, u) : i;
       int64_t deg = A.xadj[u + 1] - A.xadj[u];
       ne = ceil_div(deg, A.hub_chunk);
       nt = ceil_div((int64_t)next_pow2_dev(2 * deg), HUB_RCHUNK);
@@ -475,11 +481,71 @@ __global__ void __launch_bounds__(256) k_hub_insert(LPArgs A, int s) {
     int64_t b = A.xadj[u], deg = A.xadj[u + 1] - b;
     uint32_t mask = next_pow2_dev(2 * deg) - 1;
     int32_t *keys = A.hkeys + A.hoff[h], *vals = A.hvals + A.hoff[h];
+    int32_t *list = A.hlist + A.hoff[h];
     int64_t cc = c - A.plan_e[i];
     int64_t e0 = b + cc * A.hub_chunk, e1 = e0 + A.hub_chunk < b + deg ? e0 + A.hub_chunk : b + deg;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x)
-      ht_add(keys, vals, mask, A.label[A.adj[e]], edge_w(A, e));
+    int lane = threadIdx.x & 31;
+    for (int64_t base = e0 + (threadIdx.x & ~31); base < e1; base += blockDim.x) {
+      int64_t e = base + lane;
+      int32_t fresh = -1;  // slot this lane occupied first
+      if (e < e1) {
+        int32_t K = A.label[A.adj[e]], x = edge_w(A, e);
+        uint32_t t = fmix32((uint32_t)K) & mask;
+        // the table holds >= 2 deg slots, so a free one is always found
+        for (uint32_t probe = 0; probe <= mask; ++probe) {
+          int32_t old = atomicCAS(&keys[t], HT_EMPTY, K);
+          if (old == HT_EMPTY || old == K) {
+            atomicAdd(&vals[t], x);
+            if (old == HT_EMPTY) fresh = (int32_t)t;
+            break;
+          }
+          t = (t + 1) & mask;
+        }
+      }
+      // one list reservation per warp
+      unsigned m = __ballot_sync(0xFFFFFFFFu, fresh >= 0);
+      if (m) {
+        int32_t at = 0;
+        if (lane == __ffs(m) - 1) at = atomicAdd(&A.hcount[h], __popc(m));
+        at = __shfl_sync(0xFFFFFFFFu, at, __ffs(m) - 1);
+        if (fresh >= 0) list[at + __popc(m & ((1u << lane) - 1))] = fresh;
+      }
+    }
   }
+}
+
+// reduce work units: chunks of each hub's occupied-slot list (known only
+// after the inserts)
+__global__ void __launch_bounds__(1024) k_hub_plan_list(LPArgs A, int s) {
+  __shared__ int64_t wt2[32];
+  __shared__ int64_t carry;
+  const int32_t *bo = A.boff + s * NB;
+  int32_t cnt = bo[7] - bo[6];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int32_t base = 0; base < cnt; base += blockDim.x) {
+    int32_t i = base + threadIdx.x;
+    int64_t nt = i < cnt ? ceil_div(A.hcount[A.plan_h[i]], HUB_RCHUNK) : 0;
+    int64_t xt = nt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      int64_t yt = (int64_t)__shfl_up_sync(0xFFFFFFFFu, (unsigned long long)xt, d);
+      if (lane >= d) xt += yt;
+    }
+    if (lane == 31) wt2[w] = xt;
+    __syncthreads();
+    int64_t pt = carry, tt = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      if (k < w) pt += wt2[k];
+      tt += wt2[k];
+    }
+    if (i < cnt) A.plan_t[i] = pt + xt - nt;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tt;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) A.plan_tot[1] = carry;
 }
 
 // work units: table chunks of the sub-round's hubs
@@ -493,35 +559,38 @@ __global__ void __launch_bounds__(256) k_hub_reduce(LPArgs A, int s) {
     int32_t i = find_seg(A.plan_t, cnt, c);
     int32_t h = A.plan_h[i];
     int32_t u = A.hubs[h];
-    int64_t deg = A.xadj[u + 1] - A.xadj[u];
-    int64_t cap = next_pow2_dev(2 * deg);
     int32_t own = A.label[u], cu = node_w(A, u);
     int32_t *keys = A.hkeys + A.hoff[h], *vals = A.hvals + A.hoff[h];
+    const int32_t *list = A.hlist + A.hoff[h];
     int64_t cc = c - A.plan_t[i];
     {
       uint64_t kc = 0, ku = 0;
       int64_t e0 = cc * HUB_RCHUNK;
-      int64_t e1 = e0 + HUB_RCHUNK < cap ? e0 + HUB_RCHUNK : cap;
+      int64_t occ = A.hcount[h];
+      int64_t e1 = e0 + HUB_RCHUNK < occ ? e0 + HUB_RCHUNK : occ;
       // all loads of this thread's entries first (independent, overlapped),
-      // then the cluster weights of the non-empty ones, then the clears
+      // then the cluster weights, then the clears
       constexpr int PER = HUB_RCHUNK / 256;
-      int32_t Kv[PER], Rv[PER], Wv[PER];
+      int32_t Tv[PER], Kv[PER], Rv[PER], Wv[PER];
 #pragma unroll
       for (int j = 0; j < PER; ++j) {
-        int64_t i = e0 + threadIdx.x + (int64_t)j * blockDim.x;
-        Kv[j] = i < e1 ? keys[i] : HT_EMPTY;
-        Rv[j] = i < e1 ? vals[i] : 0;
+        int64_t x = e0 + threadIdx.x + (int64_t)j * blockDim.x;
+        Tv[j] = x < e1 ? list[x] : -1;
+      }
+#pragma unroll
+      for (int j = 0; j < PER; ++j) {
+        Kv[j] = Tv[j] >= 0 ? keys[Tv[j]] : HT_EMPTY;
+        Rv[j] = Tv[j] >= 0 ? vals[Tv[j]] : 0;
       }
 #pragma unroll
       for (int j = 0; j < PER; ++j)
         Wv[j] = (Kv[j] != HT_EMPTY && Kv[j] != own) ? A.wt[Kv[j]] : 0;
 #pragma unroll
       for (int j = 0; j < PER; ++j) {
-        int64_t i = e0 + threadIdx.x + (int64_t)j * blockDim.x;
         int32_t K = Kv[j];
         if (K == HT_EMPTY) continue;
-        keys[i] = HT_EMPTY;  // leave the table empty for its next use
-        vals[i] = 0;
+        keys[Tv[j]] = HT_EMPTY;  // leave the table empty for its next use
+        vals[Tv[j]] = 0;
         if (K == own) {
           A.hrown[h] = Rv[j];
           continue;
@@ -562,6 +631,88 @@ __global__ void __launch_bounds__(256) k_hub_emit(LPArgs A, int s) {
     A.hkc[h] = 0;
     A.hku[h] = 0;
     A.hrown[h] = 0;
+    A.hcount[h] = 0;
+  }
+}
+
+// ---- hubs with few labels (refinement): dense rating rows
+// work units: edge chunks of the sub-round's hubs; a CTA sums its chunk per
+// label in shared memory (lanes of a warp that hit the same label add first)
+// and adds the non-zero sums to the hub's row
+__global__ void __launch_bounds__(256) k_hubd_insert(LPArgs A, int s) {
+  extern __shared__ int32_t cnt_s[];
+  const int32_t *bo = A.boff + s * NB;
+  int32_t lo = bo[6], cnt = bo[7] - bo[6];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t total = A.plan_tot[0];
+  for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
+    int32_t i = find_seg(A.plan_e, cnt, c);
+    int32_t u = A.vlist[lo + i];
+    int64_t b = A.xadj[u], deg = A.xadj[u + 1] - b;
+    int64_t e0 = b + (c - A.plan_e[i]) * A.hub_chunk;
+    int64_t e1 = e0 + A.hub_chunk < b + deg ? e0 + A.hub_chunk : b + deg;
+    for (int32_t l = threadIdx.x; l < A.nlab; l += blockDim.x) cnt_s[l] = 0;
+    __syncthreads();
+    for (int64_t base = e0 + 32 * w; base < e1; base += blockDim.x) {
+      int64_t e = base + lane;
+      bool ok = e < e1;
+      int32_t L = ok ? A.label[A.adj[e]] : -1;
+      int32_t x = ok ? edge_w(A, e) : 0;
+      unsigned peers = __match_any_sync(0xFFFFFFFFu, L);
+      int32_t sum = __reduce_add_sync(peers, x);
+      if (ok && lane == __ffs(peers) - 1) atomicAdd(&cnt_s[L], sum);
+    }
+    __syncthreads();
+    int32_t *row = A.hdense + (int64_t)i * A.nlab;
+    for (int32_t l = threadIdx.x; l < A.nlab; l += blockDim.x)
+      if (cnt_s[l]) atomicAdd(&row[l], cnt_s[l]);
+    __syncthreads();
+  }
+}
+
+// one CTA per hub of the sub-round: best labels from its row (cleared for
+// the next use), then the same decision as every other bin
+__global__ void __launch_bounds__(256) k_hubd_reduce(LPArgs A, int s) {
+  __shared__ unsigned long long red_c[8], red_u[8];
+  __shared__ int32_t s_rown;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int32_t *bo = A.boff + s * NB;
+  int32_t lo = bo[6], cnt = bo[7] - bo[6];
+  for (int32_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+    int32_t u = A.vlist[lo + i];
+    int32_t own = A.label[u], cu = node_w(A, u);
+    int32_t *row = A.hdense + (int64_t)i * A.nlab;
+    if (threadIdx.x == 0) s_rown = 0;
+    __syncthreads();
+    uint64_t kc = 0, ku = 0;
+    for (int32_t K = threadIdx.x; K < A.nlab; K += blockDim.x) {
+      int32_t r = row[K];
+      if (r == 0) continue;
+      row[K] = 0;
+      if (K == own) {
+        s_rown = r;
+        continue;
+      }
+      uint64_t k = rate_key(A, K, r);
+      ku = k > ku ? k : ku;
+      if ((int64_t)A.wt[K] + cu <= cap_of(A, K) && k > kc) kc = k;
+    }
+    kc = group_max64<32>(kc);
+    ku = group_max64<32>(ku);
+    if (lane == 0) {
+      red_c[w] = kc;
+      red_u[w] = ku;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int x = 1; x < (int)(blockDim.x >> 5); ++x) {
+        kc = red_c[x] > kc ? red_c[x] : kc;
+        ku = red_u[x] > ku ? red_u[x] : ku;
+      }
+      emit(A, u, lo + i, s_rown, kc, kc ? label_of_key(A.rk_hi, kc) : -1, ku,
+           ku ? label_of_key(A.rk_hi, ku) : -1);
+    }
+    __syncthreads();
   }
 }
 
@@ -819,10 +970,11 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   // hubs: with few labels (refinement) a shared-memory table always fits;
   // otherwise every hub gets its own global table region for the whole run
   bool small_labels = 2 * (int64_t)nlab <= CTA_TAB;
-  const int64_t huge = C.tune.hub_degree;
+  const int64_t huge = small_labels ? C.tune.dense_hub_degree : C.tune.hub_degree;
   bool hub_path = !small_labels && g.maxdeg > huge;
+  bool dense_hubs = small_labels && g.maxdeg > huge;
   int32_t nhubs = 0;
-  DBuf<int32_t> hubs, hkeys, hvals, hrown, plan_h;
+  DBuf<int32_t> hubs, hkeys, hvals, hrown, plan_h, hdense, hlist, hcount;
   DBuf<int64_t> hoff, plan_e, plan_t, plan_tot;
   DBuf<unsigned long long> hkc, hku;
   if (hub_path) {
@@ -841,14 +993,30 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
     int64_t T = read1(tot.p);
     hkeys.alloc(T);
     hvals.alloc(T);
+    hlist.alloc(T);
+    hcount.alloc(nhubs);
     hkeys.fill_bytes(0xFF);
     hvals.zero();
+    hcount.zero();
     hkc.alloc(nhubs);
     hku.alloc(nhubs);
     hrown.alloc(nhubs);
     hkc.zero();
     hku.zero();
     hrown.zero();
+    plan_h.alloc(nhubs);
+    plan_e.alloc(nhubs + 1);
+    plan_t.alloc(nhubs + 1);
+    plan_tot.alloc(2);
+  } else if (dense_hubs) {
+    DBuf<uint8_t> flag(n);
+    DBuf<int32_t> pos(n), cnt(1);
+    k_hub_flags<<<grid_for(n, 256), 256, 0, stream>>>(n, g.xadj, huge, flag);
+    KMP_LAUNCHED("hub_flags");
+    scan_excl_u8_to_i32(flag, pos, n, cnt);
+    nhubs = read1(cnt.p);
+    hdense.alloc((int64_t)nhubs * nlab);
+    hdense.zero();
     plan_h.alloc(nhubs);
     plan_e.alloc(nhubs + 1);
     plan_t.alloc(nhubs + 1);
@@ -892,11 +1060,14 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   A.hkc = hkc.p;
   A.hku = hku.p;
   A.hrown = hrown.p;
+  A.hlist = hlist.p;
+  A.hcount = hcount.p;
   A.plan_h = plan_h.p;
   A.plan_e = plan_e.p;
   A.plan_t = plan_t.p;
   A.plan_tot = plan_tot.p;
   A.small_labels = small_labels ? 1 : 0;
+  A.hdense = dense_hubs ? hdense.p : nullptr;
   A.huge_deg = huge;
   A.hub_chunk = C.tune.hub_chunk;
   A.nlab = nlab;
@@ -937,10 +1108,19 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
         KMP_LAUNCHED("hub_plan");
         k_hub_insert<<<grid_hub, 256, 0, stream>>>(A, s);
         KMP_LAUNCHED("hub_insert");
+        k_hub_plan_list<<<1, 1024, 0, stream>>>(A, s);
+        KMP_LAUNCHED("hub_plan_list");
         k_hub_reduce<<<grid_hub, 256, 0, stream>>>(A, s);
         KMP_LAUNCHED("hub_reduce");
         k_hub_emit<<<grid_for(nhubs, 256), 256, 0, stream>>>(A, s);
         KMP_LAUNCHED("hub_emit");
+      } else if (dense_hubs) {
+        k_hub_plan<<<1, 1024, 0, stream>>>(A, s);
+        KMP_LAUNCHED("hub_plan");
+        k_hubd_insert<<<grid_hub, 256, nlab * sizeof(int32_t), stream>>>(A, s);
+        KMP_LAUNCHED("hubd_insert");
+        k_hubd_reduce<<<std::min(nhubs, grid_hub), 256, 0, stream>>>(A, s);
+        KMP_LAUNCHED("hubd_reduce");
       }
       if (C.profile) KMP_CUDA(cudaEventRecord(ev.back(), stream));
       k_classify<<<grid_commit, 256, 0, stream>>>(A, s);

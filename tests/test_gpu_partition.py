@@ -127,7 +127,7 @@ def test_partition_parity(kmp, name, make, ks):
             assert list(st.level_n[: st.levels]) == list(rst.level_n[: rst.levels])
 
 
-@pytest.mark.parametrize("tune", [(4, 1024, 1024, 2), (8, 2048, 4096, 8), (2, 256, 256, 1)])
+@pytest.mark.parametrize("tune", [(4, 1024, 1024, 2, 600), (8, 2048, 4096, 8, 1 << 30), (2, 256, 256, 1, 4096)])
 def test_tuning_invariance(kmp, tune):
     """Schedule parameters (grids, hub threshold, chunking) never change results."""
     g = gg.hubs(30000, [700, 3000, 12000], 60000, 8)
