@@ -63,6 +63,7 @@ struct IPArgs {
   const __nv_bfloat16 *W;
   int32_t lrep_random, lrep_bfs, lrep_ggg;
   SampleSink sink;  // counters null: no recording
+  int32_t dyn_words;  // dynamic shared memory per CTA (int32 words) for FM and portfolio state
 };
 
 struct LG {
@@ -292,7 +293,7 @@ __device__ int64_t block_seg_scan(int64_t x, bool head) {
 // LP clustering of one item level + isolated packing; returns #clusters
 __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_t basekey,
                                 int32_t *label, Bump &B, int32_t *wkeys, int32_t *wvals) {
-  __shared__ int32_t s_cnt;
+  __shared__ int32_t s_cnt, s_fast;
   __shared__ int32_t s_moved;
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int32_t n = g.n;
@@ -302,6 +303,9 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
   int32_t *act2 = B.take(n);
   int32_t *pt = B.take(n);
   int32_t *pg = B.take(n);
+  int32_t *sl = B.take(n);    // the round's nodes by sub-round
+  int32_t *fl = B.take(n);    // accepted proposals of uncontested targets
+  int32_t *tsum = B.take(n);  // proposed weight per target (kept zero between uses)
   int32_t P = pow2_at_least(n > 1 ? n : 2);
   uint64_t *pl = reinterpret_cast<uint64_t *>(B.take(2ll * P));
   int32_t *gtab = nullptr;
@@ -316,6 +320,7 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
     label[v] = v;
     wt[v] = g.vw[v];
     act[v] = 1;
+    tsum[v] = 0;
   }
   __syncthreads();
   int32_t *mk = wkeys + w * IP_WTAB, *mv = wvals + w * IP_WTAB;
@@ -327,29 +332,68 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
   for (int32_t r = 0; r < A.ip_lp_rounds; ++r) {
     uint64_t rk = key_step(basekey, (uint64_t)r);
     uint32_t rk_hi = (uint32_t)(rk >> 32);
-    for (int32_t v = threadIdx.x; v < n; v += IPT) act2[v] = 0;
+    // the round's active nodes (with edges) bucketed by sub-round
+    __shared__ int32_t s_soff[9], s_fill[8];
+    if (threadIdx.x < 8) s_fill[threadIdx.x] = 0;
     if (threadIdx.x == 0) s_moved = 0;
     __syncthreads();
+    for (int32_t v = threadIdx.x; v < n; v += IPT) {
+      act2[v] = 0;
+      if (act[v] && g.xadj[v + 1] > g.xadj[v])
+        atomicAdd(&s_fill[(int32_t)(key_step(rk, (uint64_t)(uint32_t)v) & (uint64_t)(A.S - 1))], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_soff[0] = 0;
+      for (int32_t x = 0; x < A.S; ++x) {
+        s_soff[x + 1] = s_soff[x] + s_fill[x];
+        s_fill[x] = 0;
+      }
+    }
+    __syncthreads();
+    for (int32_t v = threadIdx.x; v < n; v += IPT)
+      if (act[v] && g.xadj[v + 1] > g.xadj[v]) {
+        int32_t x = (int32_t)(key_step(rk, (uint64_t)(uint32_t)v) & (uint64_t)(A.S - 1));
+        sl[s_soff[x] + atomicAdd(&s_fill[x], 1)] = v;
+      }
+    __syncthreads();
     for (int32_t s = 0; s < A.S; ++s) {
+      const int32_t lo = s_soff[s], hi = s_soff[s + 1];
       // rating
-      for (int32_t u = w; u < n; u += IPW) {
-        bool rate = act[u] && g.xadj[u + 1] > g.xadj[u] &&
-                    (int32_t)(key_step(rk, (uint64_t)(uint32_t)u) & (uint64_t)(A.S - 1)) == s;
-        if (rate) item_rate(g, u, label, wt, U, rk_hi, mk, mv, gk, gv, &pt[u], &pg[u]);
-        else if (lane == 0) pt[u] = -1;
+      for (int32_t i = lo + w; i < hi; i += IPW) {
+        int32_t u = sl[i];
+        item_rate(g, u, label, wt, U, rk_hi, mk, mv, gk, gv, &pt[u], &pg[u]);
       }
-      if (threadIdx.x == 0) s_cnt = 0;
+      if (threadIdx.x == 0) {
+        s_cnt = 0;
+        s_fast = 0;
+      }
       __syncthreads();
-      // collect (target, gain desc, node) keys
-      for (int32_t u = threadIdx.x; u < n; u += IPT) {
-        int32_t T = pt[u];
+      // proposed weight per target
+      for (int32_t i = lo + threadIdx.x; i < hi; i += IPT) {
+        int32_t u = sl[i], T = pt[u];
+        if (T >= 0) atomicAdd(&tsum[T], g.vw[u]);
+      }
+      __syncthreads();
+      // a target whose proposals all fit takes them all; only the proposals
+      // of contested targets need the (target, gain desc, node) order
+      for (int32_t i = lo + threadIdx.x; i < hi; i += IPT) {
+        int32_t u = sl[i], T = pt[u];
         if (T < 0) continue;
-        int32_t p = atomicAdd(&s_cnt, 1);
-        pl[p] = ((uint64_t)(uint32_t)T << 47) | ((uint64_t)(uint32_t)(0x7FFFFFFF - pg[u]) << 16) |
-                (uint64_t)(uint32_t)u;
+        if ((int64_t)wt[T] + tsum[T] <= U) {
+          fl[atomicAdd(&s_fast, 1)] = u;
+        } else {
+          int32_t p = atomicAdd(&s_cnt, 1);
+          pl[p] = ((uint64_t)(uint32_t)T << 47) | ((uint64_t)(uint32_t)(0x7FFFFFFF - pg[u]) << 16) |
+                  (uint64_t)(uint32_t)u;
+        }
       }
       __syncthreads();
-      int32_t np = s_cnt;
+      for (int32_t i = lo + threadIdx.x; i < hi; i += IPT) {
+        int32_t T = pt[sl[i]];
+        if (T >= 0) tsum[T] = 0;  // every reader is past the barrier above
+      }
+      int32_t np = s_cnt, nf = s_fast;
       if (np > 0) {
         int32_t Pp = pow2_at_least(np);
         for (int32_t i = np + threadIdx.x; i < Pp; i += IPT) pl[i] = ~0ull;
@@ -390,26 +434,31 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
           }
           __syncthreads();
         }
-        // apply
-        // one warp per accepted move: lane 0 moves the node, the lanes mark its
-        // neighbours active for the next round
-        int32_t mv_local = 0;
-        for (int32_t i = w; i < np; i += IPW) {
-          uint64_t k = pl[i];
-          if (!(k >> 63)) continue;
-          int32_t T = (int32_t)((k >> 47) & 0xFFFF);
-          int32_t u = (int32_t)(k & 0xFFFF);
-          if (lane == 0) {
-            int32_t own = label[u], c = g.vw[u];
-            label[u] = T;
-            atomicAdd(&wt[T], c);
-            atomicSub(&wt[own], c);
-            ++mv_local;
-          }
-          for (int32_t q = g.xadj[u] + lane; q < g.xadj[u + 1]; q += 32) act2[g.adj[q]] = 1;
-        }
-        if (mv_local) atomicAdd(&s_moved, mv_local);
       }
+      // apply: one warp per accepted move; lane 0 moves the node, the lanes
+      // mark its neighbours active for the next round
+      int32_t mv_local = 0;
+      for (int32_t i = w; i < nf + np; i += IPW) {
+        int32_t u, T;
+        if (i < nf) {
+          u = fl[i];
+          T = pt[u];
+        } else {
+          uint64_t k = pl[i - nf];
+          if (!(k >> 63)) continue;
+          T = (int32_t)((k >> 47) & 0xFFFF);
+          u = (int32_t)(k & 0xFFFF);
+        }
+        if (lane == 0) {
+          int32_t own = label[u], c = g.vw[u];
+          label[u] = T;
+          atomicAdd(&wt[T], c);
+          atomicSub(&wt[own], c);
+          ++mv_local;
+        }
+        for (int32_t q = g.xadj[u] + lane; q < g.xadj[u + 1]; q += 32) act2[g.adj[q]] = 1;
+      }
+      if (mv_local) atomicAdd(&s_moved, mv_local);
       __syncthreads();
     }
     int32_t moved = s_moved;
@@ -590,6 +639,92 @@ __device__ __forceinline__ bool fm_less(int32_t ia, int64_t oa, int64_t ca, int3
 }
 
 // 2-way FM by one warp (same decisions as the oracle); returns the final cut
+// the moves of one FM pass by one warp, from gains and locks already set:
+// repeatedly the better feasible top of the two sides (gain desc, id asc),
+// until no unlocked node is left or fm_stop moves bring no new best; then
+// the pass is rolled back to its best prefix.  Returns the kept moves (0: the
+// pass found nothing better) and updates cut.
+__device__ int32_t fm_pass_moves(const IPArgs &A, const LG &g, int32_t *side, int64_t L0, int64_t L1,
+                                 FMBuf fb, int64_t W0, int64_t W1, int64_t &cut) {
+  int lane = threadIdx.x & 31;
+  int32_t n = g.n;
+  auto mk = [&](int32_t &inf, int64_t &ov) {
+    int64_t o0 = W0 - L0, o1 = W1 - L1;
+    int64_t o = o0 > o1 ? o0 : o1;
+    inf = o > 0;
+    ov = inf ? o : 0;
+  };
+  int32_t binf;
+  int64_t bov;
+  mk(binf, bov);
+  int64_t bcut = cut;
+  int32_t best_step = 0, nsteps = 0;
+  for (;;) {
+    uint64_t t0 = 0, t1 = 0;  // (gain biased, ~id): larger is better; 0 = none
+    for (int32_t v = lane; v < n; v += 32) {
+      if (fb.locked[v]) continue;
+      uint64_t k = ((uint64_t)((uint32_t)fb.gain[v] ^ 0x80000000u) << 32) | (0xFFFFFFFFu - (uint32_t)v);
+      if (side[v] == 0) t0 = k > t0 ? k : t0;
+      else t1 = k > t1 ? k : t1;
+    }
+    t0 = group_max64<32>(t0);
+    t1 = group_max64<32>(t1);
+    if (t0 == 0 && t1 == 0) break;
+    int32_t v0 = t0 ? (int32_t)(0xFFFFFFFFu - (uint32_t)t0) : -1;
+    int32_t v1 = t1 ? (int32_t)(0xFFFFFFFFu - (uint32_t)t1) : -1;
+    bool f0 = v0 >= 0 && W1 + g.vw[v0] <= L1;
+    bool f1 = v1 >= 0 && W0 + g.vw[v1] <= L0;
+    int32_t v;
+    if (f0 && f1) v = (t0 > t1) ? v0 : v1;
+    else if (f0) v = v0;
+    else if (f1) v = v1;
+    else {
+      if (lane == 0) {
+        if (v0 >= 0) fb.locked[v0] = 1;
+        if (v1 >= 0) fb.locked[v1] = 1;
+      }
+      __syncwarp();
+      continue;
+    }
+    int32_t from = side[v], to = 1 - from;
+    int32_t gv = fb.gain[v];
+    __syncwarp();
+    if (lane == 0) {
+      side[v] = to;
+      fb.locked[v] = 1;
+    }
+    int32_t c = g.vw[v];
+    if (from == 0) { W0 -= c; W1 += c; } else { W1 -= c; W0 += c; }
+    cut -= gv;
+    for (int32_t q = g.xadj[v] + lane; q < g.xadj[v + 1]; q += 32) {
+      int32_t x = g.adj[q];
+      if (side[x] == to) fb.gain[x] -= 2 * g.ew[q];
+      else fb.gain[x] += 2 * g.ew[q];
+    }
+    __syncwarp();
+    if (lane == 0) {
+      fb.gain[v] = -gv;
+      fb.moves[nsteps] = v;
+    }
+    ++nsteps;
+    __syncwarp();
+    int32_t inf;
+    int64_t ov;
+    mk(inf, ov);
+    if (fm_less(inf, ov, cut, binf, bov, bcut)) {
+      binf = inf;
+      bov = ov;
+      bcut = cut;
+      best_step = nsteps;
+    }
+    if (nsteps - best_step >= A.fm_stop) break;
+  }
+  for (int32_t i = best_step + lane; i < nsteps; i += 32) side[fb.moves[i]] ^= 1;
+  __syncwarp();
+  cut = bcut;
+  return best_step;
+}
+
 __device__ int64_t warp_fm(const IPArgs &A, const LG &g, int32_t *side, int64_t L0, int64_t L1,
                            FMBuf fb) {
   int lane = threadIdx.x & 31;
@@ -613,81 +748,55 @@ __device__ int64_t warp_fm(const IPArgs &A, const LG &g, int32_t *side, int64_t 
     W0 = warp_sum64(W0);
     W1 = warp_sum64(W1);
     __syncwarp();
-    auto mk = [&](int32_t &inf, int64_t &ov) {
-      int64_t o0 = W0 - L0, o1 = W1 - L1;
-      int64_t o = o0 > o1 ? o0 : o1;
-      inf = o > 0;
-      ov = inf ? o : 0;
-    };
-    int32_t binf;
-    int64_t bov;
-    mk(binf, bov);
-    int64_t bcut = cut;
-    int32_t best_step = 0, nsteps = 0;
-    for (;;) {
-      uint64_t t0 = 0, t1 = 0;  // (gain biased, ~id): larger is better; 0 = none
-      for (int32_t v = lane; v < n; v += 32) {
-        if (fb.locked[v]) continue;
-        uint64_t k = ((uint64_t)((uint32_t)fb.gain[v] ^ 0x80000000u) << 32) | (0xFFFFFFFFu - (uint32_t)v);
-        if (side[v] == 0) t0 = k > t0 ? k : t0;
-        else t1 = k > t1 ? k : t1;
-      }
-      t0 = group_max64<32>(t0);
-      t1 = group_max64<32>(t1);
-      if (t0 == 0 && t1 == 0) break;
-      int32_t v0 = t0 ? (int32_t)(0xFFFFFFFFu - (uint32_t)t0) : -1;
-      int32_t v1 = t1 ? (int32_t)(0xFFFFFFFFu - (uint32_t)t1) : -1;
-      bool f0 = v0 >= 0 && W1 + g.vw[v0] <= L1;
-      bool f1 = v1 >= 0 && W0 + g.vw[v1] <= L0;
-      int32_t v;
-      if (f0 && f1) v = (t0 > t1) ? v0 : v1;
-      else if (f0) v = v0;
-      else if (f1) v = v1;
-      else {
-        if (lane == 0) {
-          if (v0 >= 0) fb.locked[v0] = 1;
-          if (v1 >= 0) fb.locked[v1] = 1;
-        }
-        __syncwarp();
-        continue;
-      }
-      int32_t from = side[v], to = 1 - from;
-      int32_t gv = fb.gain[v];
-      __syncwarp();
-      if (lane == 0) {
-        side[v] = to;
-        fb.locked[v] = 1;
-      }
-      int32_t c = g.vw[v];
-      if (from == 0) { W0 -= c; W1 += c; } else { W1 -= c; W0 += c; }
-      cut -= gv;
-      for (int32_t q = g.xadj[v] + lane; q < g.xadj[v + 1]; q += 32) {
-        int32_t x = g.adj[q];
-        if (side[x] == to) fb.gain[x] -= 2 * g.ew[q];
-        else fb.gain[x] += 2 * g.ew[q];
-      }
-      __syncwarp();
-      if (lane == 0) {
-        fb.gain[v] = -gv;
-        fb.moves[nsteps] = v;
-      }
-      ++nsteps;
-      __syncwarp();
-      int32_t inf;
-      int64_t ov;
-      mk(inf, ov);
-      if (fm_less(inf, ov, cut, binf, bov, bcut)) {
-        binf = inf;
-        bov = ov;
-        bcut = cut;
-        best_step = nsteps;
-      }
-      if (nsteps - best_step >= A.fm_stop) break;
+    if (fm_pass_moves(A, g, side, L0, L1, fb, W0, W1, cut) == 0) break;
+  }
+  return cut;
+}
+
+// the same FM with the whole CTA: cut, gains and weights of every pass by all
+// warps (a warp per node, lanes over its row), the moves by warp 0
+__device__ int64_t cta_fm(const IPArgs &A, const LG &g, int32_t *side, int64_t L0, int64_t L1, FMBuf fb) {
+  __shared__ int64_t s_cut;
+  __shared__ int32_t s_kept;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t n = g.n;
+  int64_t c = 0;
+  for (int32_t v = w; v < n; v += IPW) {
+    int32_t sv = side[v];
+    for (int32_t q = g.xadj[v] + lane; q < g.xadj[v + 1]; q += 32)
+      if (side[g.adj[q]] != sv) c += g.ew[q];
+  }
+  int64_t cut = block_sum64(c) / 2;
+  for (int32_t pass = 0; pass < A.fm_passes; ++pass) {
+    int64_t W0 = 0, W1 = 0;
+    for (int32_t v = threadIdx.x; v < n; v += IPT) {
+      if (side[v] == 0) W0 += g.vw[v];
+      else W1 += g.vw[v];
     }
-    for (int32_t i = best_step + lane; i < nsteps; i += 32) side[fb.moves[i]] ^= 1;
-    __syncwarp();
-    cut = bcut;
-    if (best_step == 0) break;
+    for (int32_t v = w; v < n; v += IPW) {
+      int32_t sv = side[v], gs = 0;
+      for (int32_t q = g.xadj[v] + lane; q < g.xadj[v + 1]; q += 32)
+        gs += (side[g.adj[q]] != sv) ? g.ew[q] : -g.ew[q];
+      gs = warp_sum32(gs);
+      if (lane == 0) {
+        fb.gain[v] = gs;
+        fb.locked[v] = 0;
+      }
+    }
+    W0 = block_sum64(W0);  // its barriers also publish the gains
+    W1 = block_sum64(W1);
+    if (w == 0) {
+      int32_t kept = fm_pass_moves(A, g, side, L0, L1, fb, W0, W1, cut);
+      if (lane == 0) {
+        s_kept = kept;
+        s_cut = cut;
+      }
+    }
+    __syncthreads();
+    cut = s_cut;
+    int32_t kept = s_kept;
+    __syncthreads();
+    if (kept == 0) break;
   }
   return cut;
 }
@@ -825,7 +934,7 @@ __device__ void record_sample(const SampleSink &K, const LG &h, const int32_t *s
   __syncthreads();
 }
 
-__device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *wvals) {
+__device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *wvals, int32_t *dyn) {
   __shared__ LG lv[IP_MAXL + 1];
   __shared__ int32_t *maps[IP_MAXL + 1];
   __shared__ int64_t s_wk[IPW][3];
@@ -910,7 +1019,8 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
   int32_t PH = pow2_at_least(nH > 1 ? nH : 2);
   int32_t hL0 = level_cap(D.L0, D.t0, h.maxc), hL1 = level_cap(D.L1, D.t1, h.maxc);
   int64_t per_warp = 8ll * nH + 3ll * PH + 16;  // even: keeps every warp's 64-bit area aligned
-  int32_t *wbuf = B.take(per_warp * IPW);
+  // the portfolio's working state lives in shared memory when it fits
+  int32_t *wbuf = per_warp * IPW <= A.dyn_words ? dyn : B.take(per_warp * IPW);
   int32_t *fin = B.take(nH);
   if (B.oom) {
     if (threadIdx.x == 0) atomicExch(A.oom, 1);
@@ -1044,10 +1154,21 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
       return;
     }
     const int32_t *map = maps[l];
-    for (int32_t v = threadIdx.x; v < g.n; v += IPT) fine[v] = cur[map[v]];
+    // FM's state (sides, gains, locks, moves) in shared memory when it fits:
+    // every FM step scans all nodes
+    bool in_smem = 4ll * g.n <= A.dyn_words;
+    int32_t *fs = in_smem ? dyn : fine;
+    for (int32_t v = threadIdx.x; v < g.n; v += IPT) fs[v] = cur[map[v]];
     __syncthreads();
-    if (w == 0) warp_fm(A, g, fine, level_cap(D.L0, D.t0, g.maxc), level_cap(D.L1, D.t1, g.maxc), fb);
+    {
+      FMBuf sb{dyn + g.n, dyn + 2ll * g.n, dyn + 3ll * g.n};
+      cta_fm(A, g, fs, level_cap(D.L0, D.t0, g.maxc), level_cap(D.L1, D.t1, g.maxc), in_smem ? sb : fb);
+    }
     __syncthreads();
+    if (in_smem) {
+      for (int32_t v = threadIdx.x; v < g.n; v += IPT) fine[v] = fs[v];
+      __syncthreads();
+    }
     cur = fine;
   }
   for (int32_t v = threadIdx.x; v < n0; v += IPT) A.side_out[D.vbase + v] = cur[v];
@@ -1058,13 +1179,14 @@ __global__ void __launch_bounds__(IPT) k_ip_items(IPArgs A) {
   __shared__ int32_t wkeys[IPW * IP_WTAB];
   __shared__ int32_t wvals[IPW * IP_WTAB];
   __shared__ int32_t s_it;
+  extern __shared__ __align__(16) int32_t ipdyn[];
   for (;;) {
     if (threadIdx.x == 0) s_it = atomicAdd(A.queue, 1);
     __syncthreads();
     int32_t q = s_it;
     __syncthreads();
     if (q >= A.nitems) break;
-    run_item(A, A.order[q], wkeys, wvals);
+    run_item(A, A.order[q], wkeys, wvals, ipdyn);
   }
 }
 
@@ -1273,7 +1395,7 @@ int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::
         int64_t nP = next_pow2((uint64_t)std::max(d.n, 2));
         int64_t mP = next_pow2((uint64_t)std::max(d.m, 2));
         d.sbase = total;
-        d.ssize = mult * (96ll * d.n + 64ll * nP + 16ll * d.m + 8ll * mP + 2048 +
+        d.ssize = mult * (104ll * d.n + 64ll * nP + 16ll * d.m + 8ll * mP + 2048 +
                           (learned ? (int64_t)(2 * MF + 3 * MH + 4) * d.n + 64 : 0));
         total += d.ssize;
       }
@@ -1308,8 +1430,19 @@ int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::
       A.lrep_bfs = cfg.lrep_bfs;
       A.lrep_ggg = cfg.lrep_ggg;
       A.sink = sample_sink();
+      // dynamic shared memory: FM state of the largest item (4 words a node),
+      // at least 16 KB (the portfolio of small coarsest graphs), at most 64 KB
+      int64_t maxn = 0;
+      for (auto &d : items) maxn = std::max<int64_t>(maxn, d.n);
+      A.dyn_words = (int32_t)std::min<int64_t>(std::max<int64_t>(4 * maxn, 4096), 16384);
+      size_t dyn_bytes = (size_t)A.dyn_words * sizeof(int32_t);
+      static bool attr_set = false;
+      if (!attr_set) {
+        KMP_CUDA(cudaFuncSetAttribute(k_ip_items, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 4));
+        attr_set = true;
+      }
       int gridip = (int)std::min<int64_t>((int64_t)items.size(), (int64_t)C.sms * C.tune.ip_blocks_per_sm);
-      k_ip_items<<<gridip, IPT, 0, s>>>(A);
+      k_ip_items<<<gridip, IPT, dyn_bytes, s>>>(A);
       KMP_LAUNCHED("ip_items");
       int32_t oom = 0;
       to_host(&oom, q.p + 1, 1);
