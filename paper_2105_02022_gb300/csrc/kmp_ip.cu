@@ -627,9 +627,17 @@ __device__ void item_contract(const LG &g, const int32_t *label, int32_t *map, L
 }
 
 // ------------------------------------------------------------ warp FM
+// FM state: gains, locks, the move log, and per side the selection key of
+// every node of that side that may still move (0 otherwise), so that finding
+// the top of a side is a branch-free max over one array
 struct FMBuf {
   int32_t *gain, *locked, *moves;
+  uint64_t *key0, *key1;
 };
+
+__device__ __forceinline__ uint64_t fm_key(int32_t gain, int32_t v) {
+  return ((uint64_t)((uint32_t)gain ^ 0x80000000u) << 32) | (0xFFFFFFFFu - (uint32_t)v);
+}
 
 __device__ __forceinline__ bool fm_less(int32_t ia, int64_t oa, int64_t ca, int32_t ib, int64_t ob,
                                         int64_t cb) {
@@ -661,11 +669,11 @@ __device__ int32_t fm_pass_moves(const IPArgs &A, const LG &g, int32_t *side, in
   int32_t best_step = 0, nsteps = 0;
   for (;;) {
     uint64_t t0 = 0, t1 = 0;  // (gain biased, ~id): larger is better; 0 = none
+#pragma unroll 4
     for (int32_t v = lane; v < n; v += 32) {
-      if (fb.locked[v]) continue;
-      uint64_t k = ((uint64_t)((uint32_t)fb.gain[v] ^ 0x80000000u) << 32) | (0xFFFFFFFFu - (uint32_t)v);
-      if (side[v] == 0) t0 = k > t0 ? k : t0;
-      else t1 = k > t1 ? k : t1;
+      uint64_t a = fb.key0[v], b = fb.key1[v];
+      t0 = a > t0 ? a : t0;
+      t1 = b > t1 ? b : t1;
     }
     t0 = group_max64<32>(t0);
     t1 = group_max64<32>(t1);
@@ -680,8 +688,14 @@ __device__ int32_t fm_pass_moves(const IPArgs &A, const LG &g, int32_t *side, in
     else if (f1) v = v1;
     else {
       if (lane == 0) {
-        if (v0 >= 0) fb.locked[v0] = 1;
-        if (v1 >= 0) fb.locked[v1] = 1;
+        if (v0 >= 0) {
+          fb.locked[v0] = 1;
+          fb.key0[v0] = 0;
+        }
+        if (v1 >= 0) {
+          fb.locked[v1] = 1;
+          fb.key1[v1] = 0;
+        }
       }
       __syncwarp();
       continue;
@@ -692,14 +706,21 @@ __device__ int32_t fm_pass_moves(const IPArgs &A, const LG &g, int32_t *side, in
     if (lane == 0) {
       side[v] = to;
       fb.locked[v] = 1;
+      fb.key0[v] = 0;
+      fb.key1[v] = 0;
     }
     int32_t c = g.vw[v];
     if (from == 0) { W0 -= c; W1 += c; } else { W1 -= c; W0 += c; }
     cut -= gv;
     for (int32_t q = g.xadj[v] + lane; q < g.xadj[v + 1]; q += 32) {
       int32_t x = g.adj[q];
-      if (side[x] == to) fb.gain[x] -= 2 * g.ew[q];
-      else fb.gain[x] += 2 * g.ew[q];
+      int32_t sx = side[x];
+      int32_t gx = fb.gain[x] + (sx == to ? -2 * g.ew[q] : 2 * g.ew[q]);
+      fb.gain[x] = gx;
+      if (!fb.locked[x]) {
+        if (sx == 0) fb.key0[x] = fm_key(gx, x);
+        else fb.key1[x] = fm_key(gx, x);
+      }
     }
     __syncwarp();
     if (lane == 0) {
@@ -744,6 +765,8 @@ __device__ int64_t warp_fm(const IPArgs &A, const LG &g, int32_t *side, int64_t 
         gsum += (side[g.adj[q]] != side[v]) ? g.ew[q] : -g.ew[q];
       fb.gain[v] = gsum;
       fb.locked[v] = 0;
+      fb.key0[v] = side[v] == 0 ? fm_key(gsum, v) : 0;
+      fb.key1[v] = side[v] == 0 ? 0 : fm_key(gsum, v);
     }
     W0 = warp_sum64(W0);
     W1 = warp_sum64(W1);
@@ -781,6 +804,8 @@ __device__ int64_t cta_fm(const IPArgs &A, const LG &g, int32_t *side, int64_t L
       if (lane == 0) {
         fb.gain[v] = gs;
         fb.locked[v] = 0;
+        fb.key0[v] = sv == 0 ? fm_key(gs, v) : 0;
+        fb.key1[v] = sv == 0 ? 0 : fm_key(gs, v);
       }
     }
     W0 = block_sum64(W0);  // its barriers also publish the gains
@@ -1018,7 +1043,7 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
   int32_t nH = h.n;
   int32_t PH = pow2_at_least(nH > 1 ? nH : 2);
   int32_t hL0 = level_cap(D.L0, D.t0, h.maxc), hL1 = level_cap(D.L1, D.t1, h.maxc);
-  int64_t per_warp = 8ll * nH + 3ll * PH + 16;  // even: keeps every warp's 64-bit area aligned
+  int64_t per_warp = 12ll * nH + 3ll * PH + 16;  // even: keeps every warp's 64-bit areas aligned
   // the portfolio's working state lives in shared memory when it fits
   int32_t *wbuf = per_warp * IPW <= A.dyn_words ? dyn : B.take(per_warp * IPW);
   int32_t *fin = B.take(nH);
@@ -1087,7 +1112,7 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
         }
         uint64_t key = a == 3 ? 0 : key_step(key_step(D.key, doms[a]), (uint64_t)r);
         warp_initial(a, h, D.t0, key, side, oh, ov, gain, locked, queue, score);
-        FMBuf fb{gain, locked, moves};
+        FMBuf fb{gain, locked, moves, oh + PH, oh + PH + nH};
         int64_t cut = warp_fm(A, h, side, hL0, hL1, fb);
         int64_t W0 = 0, W1 = 0;
         for (int32_t v = lane; v < nH; v += 32) {
@@ -1140,12 +1165,13 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
   if (A.sink.counters) record_sample(A.sink, h, fin, D.key);
   // 3. uncoarsen with FM on every level (warp 0)
   int32_t *cur = fin;
-  int32_t *fmbuf = B.take(3ll * n0);
+  int32_t *fmbuf = B.take(7ll * n0 + 2);
   if (B.oom) {
     if (threadIdx.x == 0) atomicExch(A.oom, 1);
     return;
   }
-  FMBuf fb{fmbuf, fmbuf + n0, fmbuf + 2ll * n0};
+  FMBuf fb{fmbuf, fmbuf + n0, fmbuf + 2ll * n0, reinterpret_cast<uint64_t *>(fmbuf + 3ll * n0 + (n0 & 1)),
+           reinterpret_cast<uint64_t *>(fmbuf + 3ll * n0 + (n0 & 1)) + n0};
   for (int32_t l = nl - 2; l >= 0; --l) {
     LG g = lv[l];
     int32_t *fine = B.take(g.n);
@@ -1156,12 +1182,13 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
     const int32_t *map = maps[l];
     // FM's state (sides, gains, locks, moves) in shared memory when it fits:
     // every FM step scans all nodes
-    bool in_smem = 4ll * g.n <= A.dyn_words;
+    bool in_smem = 8ll * g.n + 2 <= A.dyn_words;
     int32_t *fs = in_smem ? dyn : fine;
     for (int32_t v = threadIdx.x; v < g.n; v += IPT) fs[v] = cur[map[v]];
     __syncthreads();
     {
-      FMBuf sb{dyn + g.n, dyn + 2ll * g.n, dyn + 3ll * g.n};
+      uint64_t *k0 = reinterpret_cast<uint64_t *>(dyn + 4ll * g.n + 2 - ((4ll * g.n) & 1));
+      FMBuf sb{dyn + g.n, dyn + 2ll * g.n, dyn + 3ll * g.n, k0, k0 + g.n};
       cta_fm(A, g, fs, level_cap(D.L0, D.t0, g.maxc), level_cap(D.L1, D.t1, g.maxc), in_smem ? sb : fb);
     }
     __syncthreads();
@@ -1434,7 +1461,7 @@ int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::
       // at least 16 KB (the portfolio of small coarsest graphs), at most 64 KB
       int64_t maxn = 0;
       for (auto &d : items) maxn = std::max<int64_t>(maxn, d.n);
-      A.dyn_words = (int32_t)std::min<int64_t>(std::max<int64_t>(4 * maxn, 4096), 16384);
+      A.dyn_words = (int32_t)std::min<int64_t>(std::max<int64_t>(8 * maxn + 2, 4096), 16384);
       size_t dyn_bytes = (size_t)A.dyn_words * sizeof(int32_t);
       static bool attr_set = false;
       if (!attr_set) {
