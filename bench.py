@@ -11,9 +11,12 @@ value    = LP edges/s per round: directed CSR entries rated by all LP rounds
 e2e      = the same quantity through kmp_partition with host buffers: entries
            rated / wall time of the call (CSR upload and partition download
            included).
-roofline = the LP rating kernel: algorithmic bytes / summed launch time (CUDA
-           events on the library stream, live in the timed region) against the
-           measured HBM copy bandwidth.
+roofline = k_rate, the LP rating kernel (every launch of the timed steps):
+           algorithmic bytes (per rated entry adjncy + neighbour label, per
+           rated node 24 B; hubs rated by the hub kernels excluded) / summed
+           launch time (CUDA events on the library stream, live in the timed
+           region) against the measured HBM copy bandwidth; traffic = DRAM
+           bytes per launch from the committed ncu capture of one step.
 cpu_baseline = the CPU oracle (single thread) on a bounded sample: level-0
            coarsening LP of the same graph.
 
@@ -23,6 +26,7 @@ project) on the same workload, one bounded sample per step.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -278,12 +282,17 @@ def main():
 
     peak, peak_kind = _peaks()
     achieved = (rate_bytes / (rate_ms / 1e3)) / 1e9 if rate_ms > 0 else 0.0
+    # DRAM bytes per k_rate launch from the committed ncu capture of this step,
+    # valid only while the LP source it was taken from is unchanged
     traffic = None
     prof = os.path.join(ROOT, "profiles", "lp_rate_traffic.json")
     if os.path.exists(prof):
         try:
-            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
-        except Exception:
+            rec = json.load(open(prof))
+            src = os.path.join(ROOT, "paper_2105_02022_gb300", "csrc", "kmp_lp.cu")
+            if rec.get("kmp_lp_cu_sha256") == hashlib.sha256(open(src, "rb").read()).hexdigest():
+                traffic = rec.get("dram_bytes_per_launch")
+        except (OSError, ValueError):
             traffic = None
 
     if rank != 0:
@@ -305,9 +314,10 @@ def main():
                      "refine": stats.ms_refine, "project": stats.ms_project, "total": stats.ms_total},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": "LP rating (k_rate)", "bound": "hbm", "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": "k_rate (LP rating)", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak if peak else None,
                      "traffic": traffic, "launches": int(rate_launches),
+                     "algorithmic_bytes_per_launch": rate_bytes / rate_launches if rate_launches else None,
                      "algorithmic_bytes": rate_bytes, "ms": rate_ms},
         "clocks": clk,
     }

@@ -70,7 +70,8 @@ struct LPArgs {
   int32_t *bucket;
   int32_t *ctr;                // [0] slots, [1] bucket top, [2] big movers
   int32_t *bigmove;            // high-degree nodes that moved in this sub-round
-  unsigned long long *ctr64;   // [0] scanned entries, [1] moved nodes
+  unsigned long long *ctr64;   // [0] scanned entries, [1] moved nodes, [2+s] degree sum of
+                               // sub-round s, [10+s] the same over bin 6 (hubs)
   // bin 6 (degree > huge_deg) with many labels: per-hub global tables filled
   // by many CTAs in parallel
   const int32_t *hubs;         // hub node ids, ascending
@@ -152,8 +153,11 @@ __global__ void __launch_bounds__(256) k_bin_count(LPArgs A, int32_t *cnt, int64
   __syncthreads();
   int64_t base = (int64_t)blockIdx.x * BIN_TILE;
   unsigned long long my = 0;
-  __shared__ unsigned long long sdeg[8];
-  if (threadIdx.x < 8) sdeg[threadIdx.x] = 0;
+  __shared__ unsigned long long sdeg[8], sdeg6[8];
+  if (threadIdx.x < 8) {
+    sdeg[threadIdx.x] = 0;
+    sdeg6[threadIdx.x] = 0;
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < BIN_TILE; i += blockDim.x) {
     int64_t v = base + i;
@@ -161,8 +165,10 @@ __global__ void __launch_bounds__(256) k_bin_count(LPArgs A, int32_t *cnt, int64
     int64_t d = A.xadj[v + 1] - A.xadj[v];
     if (d == 0) continue;
     int s = (int)(key_step(A.rk, (uint64_t)(uint32_t)v) & (uint64_t)(A.S - 1));
-    atomicAdd(&c[s * NB + deg_bin(d, A.huge_deg)], 1);
+    int bin = deg_bin(d, A.huge_deg);
+    atomicAdd(&c[s * NB + bin], 1);
     atomicAdd(&sdeg[s], (unsigned long long)d);
+    if (bin == 6) atomicAdd(&sdeg6[s], (unsigned long long)d);
     my += (unsigned long long)d;
   }
   atomicAdd(&scanned, my);
@@ -170,6 +176,7 @@ __global__ void __launch_bounds__(256) k_bin_count(LPArgs A, int32_t *cnt, int64
   for (int i = threadIdx.x; i < A.S * NB; i += blockDim.x) cnt[(int64_t)i * ntiles + blockIdx.x] = c[i];
   if (threadIdx.x == 0) atomicAdd(&A.ctr64[0], scanned);
   if (threadIdx.x < A.S && sdeg[threadIdx.x]) atomicAdd(&A.ctr64[2 + threadIdx.x], sdeg[threadIdx.x]);
+  if (threadIdx.x < A.S && sdeg6[threadIdx.x]) atomicAdd(&A.ctr64[10 + threadIdx.x], sdeg6[threadIdx.x]);
 }
 
 __global__ void k_bin_boff(LPArgs A, const int32_t *off, const int32_t *total, int64_t ntiles) {
@@ -958,7 +965,7 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   DBuf<int32_t> vlist(n), boff(S * NB + 1), prop_t(n), prop_g(n), pos_in_t(n);
   DBuf<int32_t> tsum(nlab), tcnt(nlab), tcur(nlab), tslot(nlab);
   DBuf<int32_t> slot_t(n), slot_base(n), bucket(n), ctr(8), bigmove(n);
-  DBuf<unsigned long long> ctr64(2 + 8);  // scanned, moved, per-sub-round degree sums
+  DBuf<unsigned long long> ctr64(2 + 16);  // scanned, moved, per-sub-round degree sums (all, hubs)
   DBuf<int32_t> bcnt(S * NB * ntiles), boffs(S * NB * ntiles), btotal(1);
   act.fill_bytes(1);
   act_next.zero();
@@ -1076,7 +1083,7 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   int grid_rate = C.tune.rate_blocks_per_sm * C.sms;
   int grid_hub = 4 * C.sms;
   int grid_commit = grid_for(ceil_div(n, S), 256, 8);
-  unsigned long long h64[10];
+  unsigned long long h64[18];
   int32_t hboff[8 * NB + 1];
   std::vector<cudaEvent_t> ev;  // profiling: event pairs around every rating launch
   std::vector<double> ev_bytes;
@@ -1103,6 +1110,7 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
       }
       k_rate<<<grid_rate, RATE_T, 0, stream>>>(A, s);
       KMP_LAUNCHED("rate");
+      if (C.profile) KMP_CUDA(cudaEventRecord(ev.back(), stream));
       if (hub_path) {
         k_hub_plan<<<1, 1024, 0, stream>>>(A, s);
         KMP_LAUNCHED("hub_plan");
@@ -1122,7 +1130,6 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
         k_hubd_reduce<<<std::min(nhubs, grid_hub), 256, 0, stream>>>(A, s);
         KMP_LAUNCHED("hubd_reduce");
       }
-      if (C.profile) KMP_CUDA(cudaEventRecord(ev.back(), stream));
       k_classify<<<grid_commit, 256, 0, stream>>>(A, s);
       KMP_LAUNCHED("classify");
       k_bucket<<<grid_commit, 256, 0, stream>>>(A, s);
@@ -1136,15 +1143,21 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
         KMP_LAUNCHED("scatter_big");
       }
     }
-    to_host(h64, ctr64.p, 2 + S);
+    to_host(h64, ctr64.p, 18);
     if (C.profile) {
-      // algorithmic bytes of each rating launch: per edge visit adjncy + neighbour
-      // label (+ edge weight); per rated node xadj, list entry, own label,
-      // proposal (target, gain) (+ node weight)
+      // algorithmic bytes of each k_rate launch: per edge visit adjncy +
+      // neighbour label (+ edge weight); per rated node xadj, list entry, own
+      // label, proposal (target, gain) (+ node weight).  Hubs rated by the hub
+      // kernels (bin 6 when those run) are not k_rate's work.
       to_host(hboff, boff.p, S * NB + 1);
+      bool hubs_outside = hub_path || dense_hubs;
       for (int s = 0; s < S; ++s) {
         double V = (double)(hboff[(s + 1) * NB] - hboff[s * NB]);
         double D = (double)h64[2 + s];
+        if (hubs_outside) {
+          V -= (double)(hboff[s * NB + 7] - hboff[s * NB + 6]);
+          D -= (double)h64[10 + s];
+        }
         ev_bytes.push_back(D * (8.0 + (g.ew ? 4.0 : 0.0)) + V * (24.0 + (g.vw ? 4.0 : 0.0)));
       }
       (void)ev0;
