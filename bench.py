@@ -14,9 +14,13 @@ e2e      = the same quantity through kmp_partition with host buffers: entries
 roofline = k_rate, the LP rating kernel (every launch of the timed steps):
            algorithmic bytes (per rated entry adjncy + neighbour label, per
            rated node 24 B; hubs rated by the hub kernels excluded) / summed
-           launch time (CUDA events on the library stream, live in the timed
-           region) against the measured HBM copy bandwidth; traffic = DRAM
-           bytes per launch from the committed ncu capture of one step.
+           launch time, live in the timed region, against the measured HBM
+           copy bandwidth.  A launch's time is the span from its first CTA's
+           start to its last CTA's end on the device's global timer, stamped
+           inside the kernel: the LP rounds run as a replayed CUDA graph, and
+           event-record nodes in it would add about 7 us each to the step.
+           traffic = DRAM bytes per launch from the committed ncu capture of
+           one step.
 cpu_baseline = the CPU oracle (single thread) on a bounded sample: level-0
            coarsening LP of the same graph.
 

@@ -248,6 +248,8 @@ typedef struct {
   int32_t dense_hub_degree;   /* with few labels (refinement: labels are block ids), degree
                                  above which a node's rating is split over many CTAs into a
                                  dense per-label row instead of one CTA (512..2^30) */
+  int32_t lp_graphs;          /* 1: each LP run captures one round as a CUDA graph and replays
+                                 it for every round; 0: direct launches (default 1) */
 } kmp_tuning;
 
 int kmp_set_tuning(const kmp_tuning *t);

@@ -629,7 +629,7 @@ int kmp_set_tuning(const kmp_tuning *t) {
     if (t->rate_blocks_per_sm < 2 || t->rate_blocks_per_sm > 16 || t->hub_degree < 256 ||
         t->hub_degree > 2048 || !pow2 || t->hub_chunk < 256 || t->hub_chunk > 65536 ||
         t->ip_blocks_per_sm < 1 || t->ip_blocks_per_sm > 8 || t->dense_hub_degree < 512 ||
-        t->dense_hub_degree > (1 << 30))
+        t->dense_hub_degree > (1 << 30) || t->lp_graphs < 0 || t->lp_graphs > 1)
       fail(KMP_ERR_ARG, "invalid tuning");
     ctx().tune = *t;
   });
@@ -663,7 +663,7 @@ int kmp_autotune(const kmp_graph *g, int32_t k, double eps, uint64_t seed, kmp_t
     for (int gi : grids)
       for (int hd : hubs)
         for (int hc : chunks) {
-          C.tune = kmp_tuning{gi, hd, hc, keep.ip_blocks_per_sm, keep.dense_hub_degree};
+          C.tune = kmp_tuning{gi, hd, hc, keep.ip_blocks_per_sm, keep.dense_hub_degree, keep.lp_graphs};
           LPStats st;
           cluster_level(G, (int32_t)U, C.cfg.lp_rounds, key_of(seed, {DOM_COARSEN, 0}), false, label,
                         nullptr, &st, nullptr);

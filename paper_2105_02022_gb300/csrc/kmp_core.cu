@@ -193,6 +193,21 @@ static void scan_impl(const Tin *in, Tout *out, int64_t n, Tacc *total_dev) {
   }
 }
 
+int64_t scan_tmp_count(int64_t n) { return ceil_div(n > 0 ? n : 1, SCAN_TILE); }
+
+void scan_excl_i32_on(const int32_t *in, int32_t *out, int64_t n, int32_t *total_dev, int32_t *bsum,
+                      cudaStream_t s) {
+  int64_t nb = scan_tmp_count(n);
+  k_scan_reduce<int32_t, int32_t><<<(unsigned)nb, SCAN_T, 0, s>>>(in, n, bsum);
+  KMP_LAUNCHED("scan_reduce");
+  k_scan_bsums<int32_t><<<1, SCAN_T, 0, s>>>(bsum, nb, total_dev);
+  KMP_LAUNCHED("scan_bsums");
+  if (n > 0) {
+    k_scan_down<int32_t, int32_t, int32_t><<<(unsigned)nb, SCAN_T, 0, s>>>(in, out, n, bsum);
+    KMP_LAUNCHED("scan_down");
+  }
+}
+
 void scan_excl_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *total_dev) {
   scan_impl<int32_t, int64_t, int64_t>(in, out, n, total_dev);
 }

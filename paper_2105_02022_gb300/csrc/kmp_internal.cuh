@@ -39,9 +39,10 @@ struct Context {
   int64_t launches = 0;
   int *d_status = nullptr;  // device status word: 0 ok, else KMP_ERR_* set by kernels
   // schedule parameters (never change results); see kmp_autotune
-  kmp_tuning tune{8, 2048, 2048, 4, 8192};
+  kmp_tuning tune{8, 2048, 2048, 4, 8192, 1};
   // live profiling of the LP rating launches (CUDA events on `stream`)
   bool profile = false;
+  cudaStream_t capture_stream = nullptr;  // created on first use: CUDA graph capture of LP rounds
   double prof_rate_ms = 0, prof_rate_bytes = 0;
   int64_t prof_rate_launches = 0;
 };
@@ -231,6 +232,11 @@ __device__ __forceinline__ uint32_t next_pow2_dev(int64_t x) {
 // exclusive scan of n values; out[i] = sum in[0..i), *total_dev (device, nullable) = sum
 void scan_excl_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *total_dev);
 void scan_excl_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *total_dev);
+// the same on stream s with caller-provided block sums (scan_tmp_count(n) entries):
+// no allocation, so it can be captured into a CUDA graph
+int64_t scan_tmp_count(int64_t n);
+void scan_excl_i32_on(const int32_t *in, int32_t *out, int64_t n, int32_t *total_dev, int32_t *bsum,
+                      cudaStream_t s);
 void scan_excl_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev);
 void scan_excl_u8_to_i32(const uint8_t *in, int32_t *out, int64_t n, int32_t *total_dev);
 // stable LSD radix sort of 64-bit keys over the low `bits` bits (in place via tmp)

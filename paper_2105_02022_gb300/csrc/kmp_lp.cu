@@ -42,6 +42,16 @@ __host__ __device__ __forceinline__ int deg_bin(int64_t d, int64_t huge) {
   return 6;
 }
 
+// per-round values, read by the kernels from device memory so that one
+// captured round can be replayed for every round of a run
+struct LPRound {
+  uint64_t rk;     // round key
+  uint32_t rk_hi;  // its high word (tie-break permutation)
+  int32_t r;       // round index; its parity selects the active-flag buffers
+  int32_t next;    // index of the next round
+  int32_t pad;
+};
+
 struct LPArgs {
   int32_t n;
   const int64_t *xadj;
@@ -53,8 +63,7 @@ struct LPArgs {
   const int32_t *cap;
   int32_t U;
   int32_t *fav;
-  uint8_t *act;
-  uint8_t *act_next;
+  uint8_t *act0, *act1;       // active flags: round r reads act_{r&1}, marks act_{1-(r&1)}
   int32_t *vlist;
   int32_t *boff;  // [S*NB+1]
   int32_t *prop_t;
@@ -70,8 +79,8 @@ struct LPArgs {
   int32_t *bucket;
   int32_t *ctr;                // [0] slots, [1] bucket top, [2] big movers
   int32_t *bigmove;            // high-degree nodes that moved in this sub-round
-  unsigned long long *ctr64;   // [0] scanned entries, [1] moved nodes, [2+s] degree sum of
-                               // sub-round s, [10+s] the same over bin 6 (hubs)
+  unsigned long long *ctr64;   // 18 per round: [0] scanned entries, [1] moved nodes, [2+s]
+                               // degree sum of sub-round s, [10+s] the same over bin 6 (hubs)
   // bin 6 (degree > huge_deg) with many labels: per-hub global tables filled
   // by many CTAs in parallel
   const int32_t *hubs;         // hub node ids, ascending
@@ -95,9 +104,42 @@ struct LPArgs {
   int64_t hub_chunk;           // edges per hub insert work unit
   int32_t nlab;
   int32_t S;
-  uint64_t rk;
-  uint32_t rk_hi;
+  LPRound *R;                  // current round (written by k_round_begin)
+  unsigned long long *tmin;    // profiling (nullable): per k_rate launch (round * S + sub-round)
+  unsigned long long *tmax;    // the earliest CTA start and the latest CTA end, global-timer ns
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t rkh(const LPArgs &A) { return __ldg(&A.R->rk_hi); }
+__device__ __forceinline__ uint64_t rkey(const LPArgs &A) { return __ldg(&A.R->rk); }
+__device__ __forceinline__ uint8_t *act_cur(const LPArgs &A) { return (__ldg(&A.R->r) & 1) ? A.act1 : A.act0; }
+__device__ __forceinline__ uint8_t *act_nxt(const LPArgs &A) { return (__ldg(&A.R->r) & 1) ? A.act0 : A.act1; }
+__device__ __forceinline__ unsigned long long *ctr_cur(const LPArgs &A) {
+  return A.ctr64 + 18 * __ldg(&A.R->r);
+}
+
+// profiling: this round's bin offsets into its slot of boff_all
+__global__ void k_save_boff(LPArgs A, int32_t *boff_all) {
+  int32_t m = A.S * NB + 1;
+  int32_t *dst = boff_all + (int64_t)m * __ldg(&A.R->r);
+  for (int32_t i = threadIdx.x; i < m; i += blockDim.x) dst[i] = A.boff[i];
+}
+
+// the next round's key and index (one thread, first launch of every round)
+__global__ void k_round_begin(LPArgs A, uint64_t basekey) {
+  LPRound *R = A.R;
+  int32_t r = R->next;
+  uint64_t rk = key_step(basekey, (uint64_t)r);
+  R->r = r;
+  R->rk = rk;
+  R->rk_hi = (uint32_t)(rk >> 32);
+  R->next = r + 1;
+}
 
 // inverse of perm32: the label whose tie-break rank is p
 __device__ __forceinline__ int32_t perm32_inv(uint32_t rk_hi, uint32_t p) {
@@ -125,7 +167,7 @@ __device__ __forceinline__ int64_t cap_of(const LPArgs &A, int32_t K) {
   return A.cap ? (int64_t)A.cap[K] : (int64_t)A.U;
 }
 __device__ __forceinline__ uint64_t rate_key(const LPArgs &A, int32_t K, int32_t r) {
-  return ((uint64_t)(uint32_t)r << 32) | (uint64_t)(0xFFFFFFFFu - perm32(A.rk_hi, K));
+  return ((uint64_t)(uint32_t)r << 32) | (uint64_t)(0xFFFFFFFFu - perm32(rkh(A), K));
 }
 
 // final decision for node u given the best constrained / unconstrained keys
@@ -159,12 +201,14 @@ __global__ void __launch_bounds__(256) k_bin_count(LPArgs A, int32_t *cnt, int64
     sdeg6[threadIdx.x] = 0;
   }
   __syncthreads();
+  const uint8_t *act = act_cur(A);
+  const uint64_t rk = rkey(A);
   for (int i = threadIdx.x; i < BIN_TILE; i += blockDim.x) {
     int64_t v = base + i;
-    if (v >= A.n || !A.act[v]) continue;
+    if (v >= A.n || !act[v]) continue;
     int64_t d = A.xadj[v + 1] - A.xadj[v];
     if (d == 0) continue;
-    int s = (int)(key_step(A.rk, (uint64_t)(uint32_t)v) & (uint64_t)(A.S - 1));
+    int s = (int)(key_step(rk, (uint64_t)(uint32_t)v) & (uint64_t)(A.S - 1));
     int bin = deg_bin(d, A.huge_deg);
     atomicAdd(&c[s * NB + bin], 1);
     atomicAdd(&sdeg[s], (unsigned long long)d);
@@ -174,9 +218,10 @@ __global__ void __launch_bounds__(256) k_bin_count(LPArgs A, int32_t *cnt, int64
   atomicAdd(&scanned, my);
   __syncthreads();
   for (int i = threadIdx.x; i < A.S * NB; i += blockDim.x) cnt[(int64_t)i * ntiles + blockIdx.x] = c[i];
-  if (threadIdx.x == 0) atomicAdd(&A.ctr64[0], scanned);
-  if (threadIdx.x < A.S && sdeg[threadIdx.x]) atomicAdd(&A.ctr64[2 + threadIdx.x], sdeg[threadIdx.x]);
-  if (threadIdx.x < A.S && sdeg6[threadIdx.x]) atomicAdd(&A.ctr64[10 + threadIdx.x], sdeg6[threadIdx.x]);
+  unsigned long long *ctr = ctr_cur(A);
+  if (threadIdx.x == 0) atomicAdd(&ctr[0], scanned);
+  if (threadIdx.x < A.S && sdeg[threadIdx.x]) atomicAdd(&ctr[2 + threadIdx.x], sdeg[threadIdx.x]);
+  if (threadIdx.x < A.S && sdeg6[threadIdx.x]) atomicAdd(&ctr[10 + threadIdx.x], sdeg6[threadIdx.x]);
 }
 
 __global__ void k_bin_boff(LPArgs A, const int32_t *off, const int32_t *total, int64_t ntiles) {
@@ -195,19 +240,21 @@ __global__ void __launch_bounds__(256) k_bin_scatter(LPArgs A, const int32_t *of
   for (int i = threadIdx.x; i < W * 8 * NB; i += blockDim.x) (&wcnt[0][0])[i] = 0;
   __syncthreads();
   int64_t base = (int64_t)blockIdx.x * BIN_TILE;
+  uint8_t *act = act_cur(A);
+  const uint64_t rk = rkey(A);
   // pass 1: keys and per-warp counts; warp w owns nodes [w*256, w*256+256) of the tile
   for (int it = 0; it < BIN_TILE / (W * 32); ++it) {
     int li = w * (BIN_TILE / W) + it * 32 + lane;
     int64_t v = base + li;
     int k = 255;
-    if (v < A.n && A.act[v]) {
+    if (v < A.n && act[v]) {
       int64_t d = A.xadj[v + 1] - A.xadj[v];
       if (d > 0) {
-        int s = (int)(key_step(A.rk, (uint64_t)(uint32_t)v) & (uint64_t)(A.S - 1));
+        int s = (int)(key_step(rk, (uint64_t)(uint32_t)v) & (uint64_t)(A.S - 1));
         k = s * NB + deg_bin(d, A.huge_deg);
       }
     }
-    if (v < A.n) A.act[v] = 0;
+    if (v < A.n) act[v] = 0;
     key[li] = (uint8_t)k;
     unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
     if (k != 255 && (peers & ((1u << lane) - 1u)) == 0) wcnt[w][k] += __popc(peers);
@@ -365,6 +412,8 @@ __global__ void __launch_bounds__(RATE_T) k_rate(LPArgs A, int s) {
     A.ctr[1] = 0;
     A.ctr[2] = 0;
   }
+  const int64_t tslot = A.tmin ? (int64_t)__ldg(&A.R->r) * A.S + s : 0;
+  if (A.tmin && threadIdx.x == 0) atomicMin(&A.tmin[tslot], global_ns());
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int64_t gw = (int64_t)blockIdx.x * (RATE_T / 32) + w;
   int64_t nw = (int64_t)gridDim.x * (RATE_T / 32);
@@ -399,6 +448,10 @@ __global__ void __launch_bounds__(RATE_T) k_rate(LPArgs A, int s) {
       uint32_t cap = table_cap(A.xadj[u + 1] - A.xadj[u], A.nlab);
       rate_cta(A, u, (int32_t)idx, tkeys, tvals, cap - 1);
     }
+  }
+  if (A.tmin) {
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(&A.tmax[tslot], global_ns());
   }
 }
 
@@ -633,8 +686,8 @@ __global__ void __launch_bounds__(256) k_hub_emit(LPArgs A, int s) {
     int32_t h = hub_index(A, u);
     uint64_t kc = A.hkc[h], ku = A.hku[h];
     int32_t rown = A.hrown[h];
-    emit(A, u, (int32_t)p, rown, kc, kc ? label_of_key(A.rk_hi, kc) : -1, ku,
-         ku ? label_of_key(A.rk_hi, ku) : -1);
+    emit(A, u, (int32_t)p, rown, kc, kc ? label_of_key(rkh(A), kc) : -1, ku,
+         ku ? label_of_key(rkh(A), ku) : -1);
     A.hkc[h] = 0;
     A.hku[h] = 0;
     A.hrown[h] = 0;
@@ -716,8 +769,8 @@ __global__ void __launch_bounds__(256) k_hubd_reduce(LPArgs A, int s) {
         kc = red_c[x] > kc ? red_c[x] : kc;
         ku = red_u[x] > ku ? red_u[x] : ku;
       }
-      emit(A, u, lo + i, s_rown, kc, kc ? label_of_key(A.rk_hi, kc) : -1, ku,
-           ku ? label_of_key(A.rk_hi, ku) : -1);
+      emit(A, u, lo + i, s_rown, kc, kc ? label_of_key(rkh(A), kc) : -1, ku,
+           ku ? label_of_key(rkh(A), ku) : -1);
     }
     __syncthreads();
   }
@@ -899,6 +952,7 @@ __global__ void __launch_bounds__(256) k_resolve(LPArgs A) {
 
 __global__ void __launch_bounds__(256) k_apply(LPArgs A, int s) {
   int32_t lo = A.boff[s * NB], hi = A.boff[(s + 1) * NB];
+  uint8_t *nxt = act_nxt(A);
   unsigned long long moved = 0;
   for (int64_t pos = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pos < hi;
        pos += (int64_t)gridDim.x * blockDim.x) {
@@ -915,7 +969,7 @@ __global__ void __launch_bounds__(256) k_apply(LPArgs A, int s) {
       if (e1 - b > 64) {
         A.bigmove[atomicAdd(&A.ctr[2], 1)] = u;  // neighbours marked by k_scatter_big
       } else {
-        for (int64_t e = b; e < e1; ++e) A.act_next[A.adj[e]] = 1;
+        for (int64_t e = b; e < e1; ++e) nxt[A.adj[e]] = 1;
       }
     } else if (A.fav) {
       A.fav[u] = T;
@@ -926,15 +980,16 @@ __global__ void __launch_bounds__(256) k_apply(LPArgs A, int s) {
   }
 #pragma unroll
   for (int m = 16; m > 0; m >>= 1) moved += __shfl_xor_sync(0xFFFFFFFFu, moved, m);
-  if ((threadIdx.x & 31) == 0 && moved) atomicAdd(&A.ctr64[1], moved);
+  if ((threadIdx.x & 31) == 0 && moved) atomicAdd(&ctr_cur(A)[1], moved);
 }
 
 // neighbours of high-degree nodes that moved become active: one block per node
 __global__ void __launch_bounds__(256) k_scatter_big(LPArgs A) {
   int32_t nb = A.ctr[2];
+  uint8_t *nxt = act_nxt(A);
   for (int32_t i = blockIdx.x; i < nb; i += gridDim.x) {
     int32_t u = A.bigmove[i];
-    for (int64_t e = A.xadj[u] + threadIdx.x; e < A.xadj[u + 1]; e += blockDim.x) A.act_next[A.adj[e]] = 1;
+    for (int64_t e = A.xadj[u] + threadIdx.x; e < A.xadj[u + 1]; e += blockDim.x) nxt[A.adj[e]] = 1;
   }
 }
 
@@ -965,7 +1020,6 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   DBuf<int32_t> vlist(n), boff(S * NB + 1), prop_t(n), prop_g(n), pos_in_t(n);
   DBuf<int32_t> tsum(nlab), tcnt(nlab), tcur(nlab), tslot(nlab);
   DBuf<int32_t> slot_t(n), slot_base(n), bucket(n), ctr(8), bigmove(n);
-  DBuf<unsigned long long> ctr64(2 + 16);  // scanned, moved, per-sub-round degree sums (all, hubs)
   DBuf<int32_t> bcnt(S * NB * ntiles), boffs(S * NB * ntiles), btotal(1);
   act.fill_bytes(1);
   act_next.zero();
@@ -1030,7 +1084,7 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
     plan_tot.alloc(2);
   }
 
-  LPArgs A;
+  LPArgs A{};
   A.n = n;
   A.xadj = g.xadj;
   A.adj = g.adj;
@@ -1041,8 +1095,8 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   A.cap = cap;
   A.U = U;
   A.fav = fav;
-  A.act = act;
-  A.act_next = act_next;
+  A.act0 = act;
+  A.act1 = act_next;
   A.vlist = vlist;
   A.boff = boff;
   A.prop_t = prop_t;
@@ -1058,7 +1112,6 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   A.bucket = bucket;
   A.ctr = ctr;
   A.bigmove = bigmove;
-  A.ctr64 = ctr64;
   A.hubs = hubs.p;
   A.nhubs = nhubs;
   A.hoff = hoff.p;
@@ -1083,92 +1136,159 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   int grid_rate = C.tune.rate_blocks_per_sm * C.sms;
   int grid_hub = 4 * C.sms;
   int grid_commit = grid_for(ceil_div(n, S), 256, 8);
-  unsigned long long h64[18];
-  int32_t hboff[8 * NB + 1];
-  std::vector<cudaEvent_t> ev;  // profiling: event pairs around every rating launch
-  std::vector<double> ev_bytes;
-  for (int r = 0; r < rounds; ++r) {
-    A.rk = key_step(basekey, (uint64_t)r);
-    A.rk_hi = (uint32_t)(A.rk >> 32);
-    ctr64.zero();
-    k_bin_count<<<(unsigned)ntiles, 256, 0, stream>>>(A, bcnt, ntiles);
+  // per-round state and counters in device memory (18 counters a round)
+  DBuf<LPRound> rstate(1);
+  DBuf<unsigned long long> ctr_all((size_t)18 * rounds);
+  DBuf<int32_t> sbsum(scan_tmp_count((int64_t)S * NB * ntiles));
+  rstate.zero();
+  ctr_all.zero();
+  A.R = rstate;
+  A.ctr64 = ctr_all;
+  // profiling: the span of every k_rate launch on the device's global timer
+  // (first CTA start to last CTA end; stamps taken inside the kernel, so the
+  // replayed graph needs no extra nodes) and each round's bin offsets, all
+  // read after the run
+  DBuf<int32_t> boff_all;
+  DBuf<unsigned long long> tmin, tmax;
+  if (C.profile) {
+    boff_all.alloc((size_t)(S * NB + 1) * rounds);
+    tmin.alloc((size_t)S * rounds);
+    tmax.alloc((size_t)S * rounds);
+    tmin.fill_bytes(0xFF);
+    tmax.zero();
+    A.tmin = tmin;
+    A.tmax = tmax;
+  }
+  // one LP round: binning, then per sub-round rating, hub rating and commit
+  auto launch_round = [&](cudaStream_t st) {
+    k_round_begin<<<1, 1, 0, st>>>(A, basekey);
+    KMP_LAUNCHED("round_begin");
+    k_bin_count<<<(unsigned)ntiles, 256, 0, st>>>(A, bcnt, ntiles);
     KMP_LAUNCHED("bin_count");
-    scan_excl_i32(bcnt, boffs, (int64_t)S * NB * ntiles, btotal);
-    k_bin_boff<<<1, 64, 0, stream>>>(A, boffs, btotal, ntiles);
+    scan_excl_i32_on(bcnt, boffs, (int64_t)S * NB * ntiles, btotal, sbsum, st);
+    k_bin_boff<<<1, 64, 0, st>>>(A, boffs, btotal, ntiles);
     KMP_LAUNCHED("bin_boff");
-    k_bin_scatter<<<(unsigned)ntiles, 256, 0, stream>>>(A, boffs, ntiles);
+    k_bin_scatter<<<(unsigned)ntiles, 256, 0, st>>>(A, boffs, ntiles);
     KMP_LAUNCHED("bin_scatter");
-    size_t ev0 = ev.size();
+    if (C.profile) {
+      k_save_boff<<<1, 128, 0, st>>>(A, boff_all);
+      KMP_LAUNCHED("save_boff");
+    }
     for (int s = 0; s < S; ++s) {
-      if (C.profile) {
-        cudaEvent_t a, b;
-        KMP_CUDA(cudaEventCreate(&a));
-        KMP_CUDA(cudaEventCreate(&b));
-        ev.push_back(a);
-        ev.push_back(b);
-        KMP_CUDA(cudaEventRecord(a, stream));
-      }
-      k_rate<<<grid_rate, RATE_T, 0, stream>>>(A, s);
+      k_rate<<<grid_rate, RATE_T, 0, st>>>(A, s);
       KMP_LAUNCHED("rate");
-      if (C.profile) KMP_CUDA(cudaEventRecord(ev.back(), stream));
       if (hub_path) {
-        k_hub_plan<<<1, 1024, 0, stream>>>(A, s);
+        k_hub_plan<<<1, 1024, 0, st>>>(A, s);
         KMP_LAUNCHED("hub_plan");
-        k_hub_insert<<<grid_hub, 256, 0, stream>>>(A, s);
+        k_hub_insert<<<grid_hub, 256, 0, st>>>(A, s);
         KMP_LAUNCHED("hub_insert");
-        k_hub_plan_list<<<1, 1024, 0, stream>>>(A, s);
+        k_hub_plan_list<<<1, 1024, 0, st>>>(A, s);
         KMP_LAUNCHED("hub_plan_list");
-        k_hub_reduce<<<grid_hub, 256, 0, stream>>>(A, s);
+        k_hub_reduce<<<grid_hub, 256, 0, st>>>(A, s);
         KMP_LAUNCHED("hub_reduce");
-        k_hub_emit<<<grid_for(nhubs, 256), 256, 0, stream>>>(A, s);
+        k_hub_emit<<<grid_for(nhubs, 256), 256, 0, st>>>(A, s);
         KMP_LAUNCHED("hub_emit");
       } else if (dense_hubs) {
-        k_hub_plan<<<1, 1024, 0, stream>>>(A, s);
+        k_hub_plan<<<1, 1024, 0, st>>>(A, s);
         KMP_LAUNCHED("hub_plan");
-        k_hubd_insert<<<grid_hub, 256, nlab * sizeof(int32_t), stream>>>(A, s);
+        k_hubd_insert<<<grid_hub, 256, nlab * sizeof(int32_t), st>>>(A, s);
         KMP_LAUNCHED("hubd_insert");
-        k_hubd_reduce<<<std::min(nhubs, grid_hub), 256, 0, stream>>>(A, s);
+        k_hubd_reduce<<<std::min(nhubs, grid_hub), 256, 0, st>>>(A, s);
         KMP_LAUNCHED("hubd_reduce");
       }
-      k_classify<<<grid_commit, 256, 0, stream>>>(A, s);
+      k_classify<<<grid_commit, 256, 0, st>>>(A, s);
       KMP_LAUNCHED("classify");
-      k_bucket<<<grid_commit, 256, 0, stream>>>(A, s);
+      k_bucket<<<grid_commit, 256, 0, st>>>(A, s);
       KMP_LAUNCHED("bucket");
-      k_resolve<<<grid_commit, 256, 0, stream>>>(A);
+      k_resolve<<<grid_commit, 256, 0, st>>>(A);
       KMP_LAUNCHED("resolve");
-      k_apply<<<grid_commit, 256, 0, stream>>>(A, s);
+      k_apply<<<grid_commit, 256, 0, st>>>(A, s);
       KMP_LAUNCHED("apply");
       if (g.maxdeg > 64) {
-        k_scatter_big<<<2 * C.sms, 256, 0, stream>>>(A);
+        k_scatter_big<<<2 * C.sms, 256, 0, st>>>(A);
         KMP_LAUNCHED("scatter_big");
       }
     }
-    to_host(h64, ctr64.p, 18);
-    if (C.profile) {
-      // algorithmic bytes of each k_rate launch: per edge visit adjncy +
-      // neighbour label (+ edge weight); per rated node xadj, list entry, own
-      // label, proposal (target, gain) (+ node weight).  Hubs rated by the hub
-      // kernels (bin 6 when those run) are not k_rate's work.
-      to_host(hboff, boff.p, S * NB + 1);
-      bool hubs_outside = hub_path || dense_hubs;
+  };
+  // profiling: k_rate times and algorithmic bytes of rounds [0, nr) (per edge
+  // visit adjncy + neighbour label (+ edge weight); per rated node xadj, list
+  // entry, own label, proposal (target, gain) (+ node weight); hubs rated by
+  // the hub kernels are not k_rate's work)
+  auto profile_rounds = [&](int nr) {
+    std::vector<unsigned long long> h((size_t)18 * nr), t0((size_t)S * nr), t1((size_t)S * nr);
+    std::vector<int32_t> hb((size_t)(S * NB + 1) * nr);
+    to_host(h.data(), ctr_all.p, h.size());
+    to_host(hb.data(), boff_all.p, hb.size());
+    to_host(t0.data(), tmin.p, t0.size());
+    to_host(t1.data(), tmax.p, t1.size());
+    bool hubs_outside = hub_path || dense_hubs;
+    for (int r = 0; r < nr; ++r) {
+      const int32_t *hboff = hb.data() + (size_t)(S * NB + 1) * r;
       for (int s = 0; s < S; ++s) {
         double V = (double)(hboff[(s + 1) * NB] - hboff[s * NB]);
-        double D = (double)h64[2 + s];
+        double D = (double)h[18 * r + 2 + s];
         if (hubs_outside) {
           V -= (double)(hboff[s * NB + 7] - hboff[s * NB + 6]);
-          D -= (double)h64[10 + s];
+          D -= (double)h[18 * r + 10 + s];
         }
-        ev_bytes.push_back(D * (8.0 + (g.ew ? 4.0 : 0.0)) + V * (24.0 + (g.vw ? 4.0 : 0.0)));
+        size_t i = (size_t)S * r + s;
+        C.prof_rate_ms += t1[i] > t0[i] ? (double)(t1[i] - t0[i]) * 1e-6 : 0.0;
+        C.prof_rate_launches += 1;
+        C.prof_rate_bytes += D * (8.0 + (g.ew ? 4.0 : 0.0)) + V * (24.0 + (g.vw ? 4.0 : 0.0));
       }
-      (void)ev0;
     }
+  };
+  if (C.tune.lp_graphs) {
+    // one captured round, replayed for every round: its kernels read the
+    // round's key, buffers and counters from device memory.  A round after
+    // one that moved nothing has no active node and changes nothing, so all
+    // rounds can be queued without reading the move counts in between.
+    if (!C.capture_stream) KMP_CUDA(cudaStreamCreateWithFlags(&C.capture_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t before = C.launches;
+    KMP_CUDA(cudaStreamBeginCapture(C.capture_stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      launch_round(C.capture_stream);
+    } catch (...) {
+      cudaStreamEndCapture(C.capture_stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    KMP_CUDA(cudaStreamEndCapture(C.capture_stream, &graph));
+    int64_t per_round = C.launches - before;
+    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    KMP_CUDA(ie);
+    cudaError_t le = cudaSuccess;
+    for (int r = 0; r < rounds && le == cudaSuccess; ++r) {
+      le = cudaGraphLaunch(exec, stream);
+      if (r > 0) C.launches += per_round;
+    }
+    // an executable graph still in flight is released when it completes
+    cudaGraphExecDestroy(exec);
+    KMP_CUDA(le);
+    if (C.profile) profile_rounds(rounds);
+  } else {
+    int r = 0;
+    for (; r < rounds; ++r) {
+      launch_round(stream);
+      unsigned long long mv = read1(ctr_all.p + 18 * r + 1);
+      if (mv == 0) {
+        ++r;
+        break;
+      }
+    }
+    if (C.profile) profile_rounds(r);
+  }
+  // statistics: rounds up to and including the first that moved nothing
+  std::vector<unsigned long long> hall((size_t)18 * rounds);
+  to_host(hall.data(), ctr_all.p, hall.size());
+  for (int r = 0; r < rounds; ++r) {
     st->rounds = r + 1;
-    st->scanned += (int64_t)h64[0];
-    st->moved_total += (int64_t)h64[1];
-    uint8_t *t = A.act;
-    A.act = A.act_next;
-    A.act_next = t;
-    if (h64[1] == 0) break;
+    st->scanned += (int64_t)hall[18 * r];
+    st->moved_total += (int64_t)hall[18 * r + 1];
+    if (hall[18 * r + 1] == 0) break;
   }
   KMP_CUDA(cudaEventRecord(e1, stream));
   KMP_CUDA(cudaEventSynchronize(e1));
@@ -1177,15 +1297,6 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   st->ms = ms;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  for (size_t i = 0; i + 1 < ev.size(); i += 2) {
-    float t = 0;
-    KMP_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
-    C.prof_rate_ms += t;
-    C.prof_rate_launches += 1;
-    C.prof_rate_bytes += ev_bytes[i / 2];
-    cudaEventDestroy(ev[i]);
-    cudaEventDestroy(ev[i + 1]);
-  }
 }
 
 // ------------------------------------------------ clustering of one level

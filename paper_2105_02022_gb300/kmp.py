@@ -61,7 +61,7 @@ class Stats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
-        "rate_blocks_per_sm", "hub_degree", "hub_chunk", "ip_blocks_per_sm", "dense_hub_degree")]
+        "rate_blocks_per_sm", "hub_degree", "hub_chunk", "ip_blocks_per_sm", "dense_hub_degree", "lp_graphs")]
 
 
 def load():

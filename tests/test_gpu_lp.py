@@ -150,3 +150,35 @@ def test_full_size_rmat20_level0(kmp):
     label = kmp.coarsen_level(dg, U, 5, 1, 0)
     ref = O.cluster(g, U, 5, 1, 0)
     assert np.array_equal(label.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_rating_profile_is_consistent(kmp, graphs):
+    """The k_rate spans recorded on the device timer (profiling) are positive,
+    one per rating launch, and fit inside the wall time of the whole LP call
+    measured with CUDA events on the same stream; profiling changes no result."""
+    g = gg.rmat(16, 16, 3)
+    dg = kmp.DeviceGraph.from_host(g)
+    U = int(np.floor(0.03 * g.n / 64))
+    old = kmp.get_tuning()
+    t = kmp.Tuning(old.rate_blocks_per_sm, old.hub_degree, old.hub_chunk, old.ip_blocks_per_sm,
+                   old.dense_hub_degree, graphs)
+    kmp.set_tuning(t)
+    try:
+        plain = kmp.coarsen_level(dg, U, 5, 7, 0)
+        kmp.set_profiling(True)
+        kmp.profile_read(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        prof = kmp.coarsen_level(dg, U, 5, 7, 0)
+        e1.record()
+        e1.synchronize()
+        ms, by, nl = kmp.profile_read(reset=True)
+    finally:
+        kmp.set_profiling(False)
+        kmp.set_tuning(old)
+    assert torch.equal(plain, prof)
+    S = kmp.get_config().subrounds
+    assert nl > 0 and nl % S == 0 and nl <= 5 * S
+    assert by > 0
+    assert 0 < ms <= e0.elapsed_time(e1)

@@ -127,7 +127,8 @@ def test_partition_parity(kmp, name, make, ks):
             assert list(st.level_n[: st.levels]) == list(rst.level_n[: rst.levels])
 
 
-@pytest.mark.parametrize("tune", [(4, 1024, 1024, 2, 600), (8, 2048, 4096, 8, 1 << 30), (2, 256, 256, 1, 4096)])
+@pytest.mark.parametrize("tune", [(4, 1024, 1024, 2, 600, 0), (8, 2048, 4096, 8, 1 << 30, 1),
+                                  (2, 256, 256, 1, 4096, 0)])
 def test_tuning_invariance(kmp, tune):
     """Schedule parameters (grids, hub threshold, chunking) never change results."""
     g = gg.hubs(30000, [700, 3000, 12000], 60000, 8)
