@@ -36,6 +36,8 @@ struct BalArgs {
   int64_t *bw;
   const int32_t *cap;
   const uint8_t *over;
+  const int32_t *olist;  // the overloaded blocks, ascending
+  int32_t nover;
   int32_t *slack;        // sorted cap - weight of all blocks (Pk entries)
   int64_t *cand_d;       // [n] d of candidate nodes
   uint64_t *keys;        // (block << bitsN | node) of candidates
@@ -183,8 +185,7 @@ __device__ __forceinline__ bool rg_before(int64_t d1, int64_t c1, int32_t v1, in
 
 // one CTA per overloaded block: bitonic sort of its candidates
 __global__ void __launch_bounds__(BAL_T) k_bal_sort(BalArgs A) {
-  int32_t B = blockIdx.x;
-  if (!A.over[B]) return;
+  int32_t B = A.olist[blockIdx.x];
   int32_t lo = A.seg_lo[B], hi = A.seg_hi[B];
   int32_t len = hi - lo;
   if (len <= 1) return;
@@ -242,8 +243,8 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint64_t vmask = (1ull << A.bitsN) - 1ull;
   uint32_t gcap = A.gcap, hmask = gcap - 1;
-  for (int32_t B = 0; B < A.k; ++B) {
-    if (!A.over[B]) continue;
+  for (int32_t ob = 0; ob < A.nover; ++ob) {
+    int32_t B = A.olist[ob];
     int32_t lo = A.seg_lo[B], hi = A.seg_hi[B];
     int32_t i = lo;
     while (i < hi) {
@@ -377,13 +378,13 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   std::vector<int64_t> hbw(k);
   to_host(hbw.data(), bw.p, k);
   std::vector<uint8_t> hover(k, 0);
-  bool any = false;
+  std::vector<int32_t> holist;
   for (int32_t b = 0; b < k; ++b)
     if (hbw[b] > caps_host[b]) {
       hover[b] = 1;
-      any = true;
+      holist.push_back(b);
     }
-  if (!any || n == 0) return 0;
+  if (holist.empty() || n == 0) return 0;
   int32_t Pk = (int32_t)next_pow2((uint64_t)std::max(k, 2));
   int bitsN = 1;
   while ((1ll << bitsN) < (int64_t)n) ++bitsN;
@@ -396,6 +397,8 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   DBuf<unsigned long long> moved(1);
   to_dev(cap.p, caps_host, k);
   to_dev(over.p, hover.data(), k);
+  DBuf<int32_t> olist(holist.size());
+  to_dev(olist.p, holist.data(), holist.size());
   ncand.zero();
   moved.zero();
   seg_lo.zero();
@@ -416,6 +419,8 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   A.bw = bw;
   A.cap = cap;
   A.over = over;
+  A.olist = olist;
+  A.nover = (int32_t)holist.size();
   A.slack = slack;
   A.cand_d = cand_d;
   A.keys = keys;
@@ -444,7 +449,7 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   radix_sort_u64(keys, tmp, N, bitsN + bitsK);
   k_bal_segments<<<grid_for(N, 256), 256, 0, s>>>(A, N);
   KMP_LAUNCHED("bal_segments");
-  k_bal_sort<<<k, BAL_T, 0, s>>>(A);
+  k_bal_sort<<<A.nover, BAL_T, 0, s>>>(A);
   KMP_LAUNCHED("bal_sort");
   // one global table per warp of the move kernel, and the batch membership marks
   DBuf<int32_t> gtab1(2ll * gcap * BM_W), inbatch(n);

@@ -292,22 +292,45 @@ __device__ int64_t block_seg_scan(int64_t x, bool head) {
 
 // LP clustering of one item level + isolated packing; returns #clusters
 __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_t basekey,
-                                int32_t *label, Bump &B, int32_t *wkeys, int32_t *wvals) {
+                                int32_t *label, Bump &B, int32_t *wkeys, int32_t *wvals, int32_t *dyn,
+                                int32_t dyn_words) {
   __shared__ int32_t s_cnt, s_fast;
   __shared__ int32_t s_moved;
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int32_t n = g.n;
   int64_t mark = B.top;
-  int32_t *wt = B.take(n);
-  int32_t *act = B.take(n);
-  int32_t *act2 = B.take(n);
-  int32_t *pt = B.take(n);
-  int32_t *pg = B.take(n);
-  int32_t *sl = B.take(n);    // the round's nodes by sub-round
-  int32_t *fl = B.take(n);    // accepted proposals of uncontested targets
-  int32_t *tsum = B.take(n);  // proposed weight per target (kept zero between uses)
   int32_t P = pow2_at_least(n > 1 ? n : 2);
-  uint64_t *pl = reinterpret_cast<uint64_t *>(B.take(2ll * P));
+  // working arrays: in shared memory when the level fits (every phase of a
+  // sub-round reads them), else in the item's scratch; labels are written
+  // to `label` at the end either way
+  int32_t *lab, *wt, *act, *act2, *pt, *pg, *sl, *fl, *tsum;
+  uint64_t *pl;
+  const bool fast = 9ll * n + 2ll * P + 2 <= dyn_words;
+  if (fast) {
+    int32_t *q = dyn;
+    lab = q; q += n;
+    wt = q; q += n;
+    act = q; q += n;
+    act2 = q; q += n;
+    pt = q; q += n;
+    pg = q; q += n;
+    sl = q; q += n;
+    fl = q; q += n;
+    tsum = q; q += n;
+    q += (q - dyn) & 1;  // 8-byte alignment
+    pl = reinterpret_cast<uint64_t *>(q);
+  } else {
+    lab = label;
+    wt = B.take(n);
+    act = B.take(n);
+    act2 = B.take(n);
+    pt = B.take(n);
+    pg = B.take(n);
+    sl = B.take(n);    // the round's nodes by sub-round
+    fl = B.take(n);    // accepted proposals of uncontested targets
+    tsum = B.take(n);  // proposed weight per target (kept zero between uses)
+    pl = reinterpret_cast<uint64_t *>(B.take(2ll * P));
+  }
   int32_t *gtab = nullptr;
   uint32_t gcap = 0;
   if (g.maxdeg > IP_WTAB / 2) {
@@ -317,7 +340,7 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
   }
   if (B.oom) return -1;
   for (int32_t v = threadIdx.x; v < n; v += IPT) {
-    label[v] = v;
+    lab[v] = v;
     wt[v] = g.vw[v];
     act[v] = 1;
     tsum[v] = 0;
@@ -362,7 +385,7 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
       // rating
       for (int32_t i = lo + w; i < hi; i += IPW) {
         int32_t u = sl[i];
-        item_rate(g, u, label, wt, U, rk_hi, mk, mv, gk, gv, &pt[u], &pg[u]);
+        item_rate(g, u, lab, wt, U, rk_hi, mk, mv, gk, gv, &pt[u], &pg[u]);
       }
       if (threadIdx.x == 0) {
         s_cnt = 0;
@@ -450,8 +473,8 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
           u = (int32_t)(k & 0xFFFF);
         }
         if (lane == 0) {
-          int32_t own = label[u], c = g.vw[u];
-          label[u] = T;
+          int32_t own = lab[u], c = g.vw[u];
+          lab[u] = T;
           atomicAdd(&wt[T], c);
           atomicSub(&wt[own], c);
           ++mv_local;
@@ -480,25 +503,29 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
     if (g.xadj[v + 1] != g.xadj[v]) continue;
     int64_t P0 = iw[v], c = g.vw[v];
     int64_t q = P0 / U, qe = (P0 + c - 1) / U;
-    if (q == qe) atomicMin(&first[q], label[v]);
+    if (q == qe) atomicMin(&first[q], lab[v]);
   }
   __syncthreads();
   for (int32_t v = threadIdx.x; v < n; v += IPT) {
     if (g.xadj[v + 1] != g.xadj[v]) continue;
     int64_t P0 = iw[v], c = g.vw[v];
     int64_t q = P0 / U, qe = (P0 + c - 1) / U;
-    if (q == qe) label[v] = first[q];
+    if (q == qe) lab[v] = first[q];
   }
   __syncthreads();
   // count clusters
   int32_t *used = pt;
   for (int32_t v = threadIdx.x; v < n; v += IPT) used[v] = 0;
   __syncthreads();
-  for (int32_t v = threadIdx.x; v < n; v += IPT) used[label[v]] = 1;
+  for (int32_t v = threadIdx.x; v < n; v += IPT) used[lab[v]] = 1;
   __syncthreads();
   int64_t c = 0;
   for (int32_t v = threadIdx.x; v < n; v += IPT) c += used[v];
   int32_t nc = (int32_t)block_sum64(c);
+  if (fast) {
+    for (int32_t v = threadIdx.x; v < n; v += IPT) label[v] = lab[v];
+    __syncthreads();
+  }
   B.top = mark;
   return nc;
 }
@@ -1010,7 +1037,8 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
     if (UB < 1) UB = 1;
     int32_t *label = B.take(g.n);
     if (B.oom) break;
-    int32_t nc = item_cluster(A, g, (int32_t)UB, key_step(lpkey, (uint64_t)(nl - 1)), label, B, wkeys, wvals);
+    int32_t nc = item_cluster(A, g, (int32_t)UB, key_step(lpkey, (uint64_t)(nl - 1)), label, B, wkeys, wvals,
+                              dyn, A.dyn_words);
     if (B.oom) break;
     if (nc == g.n) break;
     int32_t *map = B.take(g.n);
@@ -1457,11 +1485,12 @@ int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::
       A.lrep_bfs = cfg.lrep_bfs;
       A.lrep_ggg = cfg.lrep_ggg;
       A.sink = sample_sink();
-      // dynamic shared memory: FM state of the largest item (4 words a node),
-      // at least 16 KB (the portfolio of small coarsest graphs), at most 64 KB
+      // dynamic shared memory: the LP working arrays (13 words a node) and
+      // then the FM state (8 words a node) of the largest item, at least 16 KB
+      // (the portfolio of small coarsest graphs), at most 64 KB
       int64_t maxn = 0;
       for (auto &d : items) maxn = std::max<int64_t>(maxn, d.n);
-      A.dyn_words = (int32_t)std::min<int64_t>(std::max<int64_t>(8 * maxn + 2, 4096), 16384);
+      A.dyn_words = (int32_t)std::min<int64_t>(std::max<int64_t>(13 * maxn + 2, 4096), 16384);
       size_t dyn_bytes = (size_t)A.dyn_words * sizeof(int32_t);
       static bool attr_set = false;
       if (!attr_set) {
