@@ -32,6 +32,11 @@ constexpr int IPW = IPT / 32;
 constexpr int IP_WTAB = 512;       // per-warp shared table: degree <= 256
 constexpr int IP_MAXL = 63;
 constexpr int32_t IP_MAX_N = 65535;
+// dynamic shared memory per bipartitioner CTA, at most (words): 184 KB, which
+// with the kernel's 40 KB of static shared memory stays within the 227 KB a
+// CTA may use
+constexpr int32_t IP_DYN_MAX_WORDS = 46000;
+constexpr int32_t IP_DYN_SHARED_WORDS = 18000;  // 72 KB: two CTAs per SM
 
 struct ItemDesc {
   int64_t vbase;  // first member position
@@ -1486,15 +1491,21 @@ int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::
       A.lrep_ggg = cfg.lrep_ggg;
       A.sink = sample_sink();
       // dynamic shared memory: the LP working arrays (13 words a node) and
-      // then the FM state (8 words a node) of the largest item, at least 16 KB
-      // (the portfolio of small coarsest graphs), at most 64 KB
+      // then the FM state (8 words a node) of the largest item of the round,
+      // at least 16 KB (the portfolio of small coarsest graphs), at most what
+      // the SM offers next to the kernel's static shared memory when the round
+      // has no more items than SMs (its items are then on the critical path,
+      // one CTA per SM), else at most 72 KB (two CTAs per SM); an item that
+      // does not fit works in its global scratch
       int64_t maxn = 0;
       for (auto &d : items) maxn = std::max<int64_t>(maxn, d.n);
-      A.dyn_words = (int32_t)std::min<int64_t>(std::max<int64_t>(13 * maxn + 2, 4096), 16384);
+      int32_t cap_words = (int64_t)items.size() <= C.sms ? IP_DYN_MAX_WORDS : IP_DYN_SHARED_WORDS;
+      A.dyn_words = (int32_t)std::min<int64_t>(std::max<int64_t>(13 * maxn + 2, 4096), cap_words);
       size_t dyn_bytes = (size_t)A.dyn_words * sizeof(int32_t);
       static bool attr_set = false;
       if (!attr_set) {
-        KMP_CUDA(cudaFuncSetAttribute(k_ip_items, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 4));
+        KMP_CUDA(cudaFuncSetAttribute(k_ip_items, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      IP_DYN_MAX_WORDS * (int)sizeof(int32_t)));
         attr_set = true;
       }
       int gridip = (int)std::min<int64_t>((int64_t)items.size(), (int64_t)C.sms * C.tune.ip_blocks_per_sm);
