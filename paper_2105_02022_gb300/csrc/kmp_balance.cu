@@ -12,10 +12,12 @@
 // GPU mapping: candidates of all overloaded blocks in one full-GPU pass (one
 // warp per node, connectivity in a per-warp hash table); grouping by block
 // with a radix sort of (block, node) keys; one CTA per overloaded block sorts
-// its candidates by the exact rational order; one CTA performs the moves in
-// order (each move depends on the weights left by the previous ones), in
-// batches whose members it evaluates at once and commits while they provably
-// do not interact.
+// its candidates by the exact rational order; then every overloaded block
+// speculates its moves at once (one warp each, as if it were emptied first),
+// and one CTA commits in block order: a speculated move stands while its
+// target still fits, everything else is decided again exactly, in batches
+// whose members are evaluated at once and committed while they provably do
+// not interact.
 #include <algorithm>
 
 #include "kmp_internal.cuh"
@@ -49,7 +51,14 @@ struct BalArgs {
   int32_t *gtab;         // per-warp global tables when labels do not fit shared memory
   uint32_t gcap;
   unsigned long long *moved;
+  // speculation: per overloaded block (index in olist) up to SPEC_MAX moves
+  int32_t *spec_v, *spec_t;  // [nover][SPEC_MAX]
+  int32_t *spec_n;           // moves recorded
+  int32_t *spec_end;         // candidate position where the speculation stopped
+  int32_t *spec_sat;         // 1: the block fits after its recorded moves
 };
+
+constexpr int SPEC_MAX = 16;
 
 __device__ __forceinline__ int32_t bw_node(const BalArgs &A, int32_t v) { return A.vw ? A.vw[v] : 1; }
 
@@ -235,6 +244,89 @@ __global__ void __launch_bounds__(BAL_T) k_bal_sort(BalArgs A) {
 constexpr int BM_T = 1024;
 constexpr int BM_W = BM_T / 32;
 
+// Speculation, one warp per overloaded block B, all blocks at once: B's moves
+// in candidate order as if B were the first block emptied (every other block
+// at its starting weight, plus B's own recorded moves).  A decision is only
+// recorded when nothing an earlier block does can change it: blocks other
+// than the overloaded ones only gain weight, so a better block that does not
+// fit keeps not fitting, and the chosen block is checked again at commit; an
+// earlier overloaded block, however, loses weight (it may start to fit) and
+// its moved nodes change their neighbours' connectivity, so a node adjacent
+// to an earlier overloaded block stops the speculation, as does a node that
+// would need the lowest-id fallback.
+__global__ void __launch_bounds__(BAL_T) k_bal_spec(BalArgs A) {
+  __shared__ int32_t sk[BAL_W][BAL_STAB], sv[BAL_W][BAL_STAB];
+  __shared__ int32_t mv_v[BAL_W][SPEC_MAX], mv_t[BAL_W][SPEC_MAX], mv_c[BAL_W][SPEC_MAX];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t gw = (int64_t)blockIdx.x * BAL_W + w, nw = (int64_t)gridDim.x * BAL_W;
+  int32_t *K = sk[w], *V = sv[w];
+  if (A.gtab) {
+    K = A.gtab + gw * 2ll * A.gcap;
+    V = K + A.gcap;
+  }
+  uint64_t vmask = (1ull << A.bitsN) - 1ull;
+  for (int64_t ob = gw; ob < A.nover; ob += nw) {
+    int32_t B = A.olist[ob];
+    int32_t lo = A.seg_lo[B], hi = A.seg_hi[B];
+    int64_t wB = A.bw[B];
+    int32_t nm = 0, i = lo, sat = 0;
+    for (; i < hi; ++i) {
+      if (wB <= A.cap[B]) {
+        sat = 1;
+        break;
+      }
+      if (nm == SPEC_MAX) break;
+      int32_t v = (int32_t)(A.keys[i] & vmask);
+      int64_t c = bw_node(A, v);
+      uint32_t mask;
+      conn_table(A, v, K, V, mask);
+      // B's own recorded moves of neighbours; neighbours in earlier overloaded blocks
+      bool fragile = false;
+      for (int64_t q = A.xadj[v] + lane; q < A.xadj[v + 1]; q += 32) {
+        int32_t u = A.adj[q], bu = A.part[u];
+        if (bu != B && bu < B && A.over[bu]) fragile = true;
+        if (bu == B)
+          for (int j = 0; j < nm; ++j)
+            if (mv_v[w][j] == u) ht_add(K, V, mask, mv_t[w][j], A.ew ? A.ew[q] : 1);
+      }
+      __syncwarp();
+      fragile = __any_sync(0xFFFFFFFFu, fragile);
+      uint64_t bestk = 0;  // (conn, ~block): largest connectivity, then lowest id
+      if (!fragile)
+        for (uint32_t x = lane; x <= mask; x += 32) {
+          int32_t b = K[x];
+          if (b == HT_EMPTY || b == B) continue;
+          int64_t wb = A.bw[b];
+          for (int j = 0; j < nm; ++j)
+            if (mv_t[w][j] == b) wb += mv_c[w][j];
+          if (wb + c > A.cap[b]) continue;
+          uint64_t key = ((uint64_t)(uint32_t)V[x] << 32) | (0xFFFFFFFFu - (uint32_t)b);
+          bestk = key > bestk ? key : bestk;
+        }
+      bestk = group_max64<32>(bestk);
+      if (fragile || bestk == 0) break;  // left to the exact commit
+      int32_t t = (int32_t)(0xFFFFFFFFu - (uint32_t)bestk);
+      if (lane == 0) {
+        mv_v[w][nm] = v;
+        mv_t[w][nm] = t;
+        mv_c[w][nm] = (int32_t)c;
+        A.spec_v[ob * SPEC_MAX + nm] = v;
+        A.spec_t[ob * SPEC_MAX + nm] = t;
+      }
+      __syncwarp();
+      ++nm;
+      wB -= c;
+    }
+    if (i >= hi && wB <= A.cap[B]) sat = 1;
+    if (lane == 0) {
+      A.spec_n[ob] = nm;
+      A.spec_end[ob] = i;
+      A.spec_sat[ob] = sat;
+    }
+    __syncwarp();
+  }
+}
+
 __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch) {
   __shared__ int32_t s_v[BM_W], s_t[BM_W];
   __shared__ int64_t s_c[BM_W], s_eoff[BM_W + 1];
@@ -243,10 +335,28 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint64_t vmask = (1ull << A.bitsN) - 1ull;
   uint32_t gcap = A.gcap, hmask = gcap - 1;
+  __shared__ int32_t s_resume;
   for (int32_t ob = 0; ob < A.nover; ++ob) {
     int32_t B = A.olist[ob];
     int32_t lo = A.seg_lo[B], hi = A.seg_hi[B];
-    int32_t i = lo;
+    // the speculated moves, in order, while their targets still fit under the
+    // weights left by the blocks before; then the exact batches from there
+    if (threadIdx.x == 0) {
+      int32_t nm = A.spec_n[ob], j = 0;
+      for (; j < nm; ++j) {
+        int32_t v = A.spec_v[ob * SPEC_MAX + j], t = A.spec_t[ob * SPEC_MAX + j];
+        int64_t c = bw_node(A, v);
+        if (A.bw[t] + c > A.cap[t]) break;
+        A.part[v] = t;
+        A.bw[B] -= c;
+        A.bw[t] += c;
+        atomicAdd(A.moved, 1ull);
+      }
+      s_resume = (j == nm && A.spec_sat[ob]) ? hi : lo + j;
+      if (j == nm && !A.spec_sat[ob]) s_resume = A.spec_end[ob];
+    }
+    __syncthreads();
+    int32_t i = s_resume;
     while (i < hi) {
       if (A.bw[B] <= A.cap[B]) break;
       if (w == 0) {
@@ -451,6 +561,29 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   KMP_LAUNCHED("bal_segments");
   k_bal_sort<<<A.nover, BAL_T, 0, s>>>(A);
   KMP_LAUNCHED("bal_sort");
+  // speculation over all overloaded blocks (tables as for the candidates)
+  int32_t nover = (int32_t)holist.size();
+  DBuf<int32_t> spec_v((size_t)nover * SPEC_MAX), spec_t((size_t)nover * SPEC_MAX), spec_n(nover),
+      spec_end(nover), spec_sat(nover);
+  A.spec_v = spec_v;
+  A.spec_t = spec_t;
+  A.spec_n = spec_n;
+  A.spec_end = spec_end;
+  A.spec_sat = spec_sat;
+  {
+    int sgrid = (int)ceil_div(nover, BAL_W);
+    DBuf<int32_t> stab;
+    if (gcap > BAL_STAB) {
+      int64_t per_block = 2ll * gcap * BAL_W * (int64_t)sizeof(int32_t);
+      sgrid = (int)std::min<int64_t>(sgrid, std::max<int64_t>(1, (256ll << 20) / per_block));
+      stab.alloc(2ll * gcap * (int64_t)sgrid * BAL_W);
+      A.gtab = stab;
+    } else {
+      A.gtab = nullptr;
+    }
+    k_bal_spec<<<sgrid, BAL_T, 0, s>>>(A);
+    KMP_LAUNCHED("bal_spec");
+  }
   // one global table per warp of the move kernel, and the batch membership marks
   DBuf<int32_t> gtab1(2ll * gcap * BM_W), inbatch(n);
   inbatch.zero();
