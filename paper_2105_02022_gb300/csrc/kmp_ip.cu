@@ -307,34 +307,40 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
   int32_t P = pow2_at_least(n > 1 ? n : 2);
   // working arrays: in shared memory when the level fits (every phase of a
   // sub-round reads them), else in the item's scratch; labels are written
-  // to `label` at the end either way
-  int32_t *lab, *wt, *act, *act2, *pt, *pg, *sl, *fl, *tsum;
-  uint64_t *pl;
-  const bool fast = 9ll * n + 2ll * P + 2 <= dyn_words;
+  // to `label` at the end either way.  The sort space of contested proposals
+  // sits in shared memory behind them when a sub-round's proposals fit
+  // there, else in the scratch (pl_g, always reserved).
+  int32_t *lab, *wt, *pt, *pg, *sl, *fl, *tsum;
+  uint8_t *act, *act2;  // active flags
+  uint64_t *pl_s = nullptr;
+  int32_t pl_cap = 0;   // entries of pl_s
+  uint64_t *pl_g = reinterpret_cast<uint64_t *>(B.take(2ll * P));
+  const int64_t flag_words = (n + 3) / 4;
+  const bool fast = 7ll * n + 2 * flag_words + 2 + 128 <= dyn_words;
   if (fast) {
     int32_t *q = dyn;
     lab = q; q += n;
     wt = q; q += n;
-    act = q; q += n;
-    act2 = q; q += n;
     pt = q; q += n;
     pg = q; q += n;
     sl = q; q += n;
     fl = q; q += n;
     tsum = q; q += n;
+    act = reinterpret_cast<uint8_t *>(q); q += flag_words;
+    act2 = reinterpret_cast<uint8_t *>(q); q += flag_words;
     q += (q - dyn) & 1;  // 8-byte alignment
-    pl = reinterpret_cast<uint64_t *>(q);
+    pl_s = reinterpret_cast<uint64_t *>(q);
+    pl_cap = (int32_t)((dyn_words - (q - dyn)) / 2);
   } else {
     lab = label;
     wt = B.take(n);
-    act = B.take(n);
-    act2 = B.take(n);
+    act = reinterpret_cast<uint8_t *>(B.take(flag_words));
+    act2 = reinterpret_cast<uint8_t *>(B.take(flag_words));
     pt = B.take(n);
     pg = B.take(n);
     sl = B.take(n);    // the round's nodes by sub-round
     fl = B.take(n);    // accepted proposals of uncontested targets
     tsum = B.take(n);  // proposed weight per target (kept zero between uses)
-    pl = reinterpret_cast<uint64_t *>(B.take(2ll * P));
   }
   int32_t *gtab = nullptr;
   uint32_t gcap = 0;
@@ -387,6 +393,8 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
     __syncthreads();
     for (int32_t s = 0; s < A.S; ++s) {
       const int32_t lo = s_soff[s], hi = s_soff[s + 1];
+      // contested proposals are at most the sub-round's nodes
+      uint64_t *pl = pow2_at_least(hi - lo > 1 ? hi - lo : 2) <= pl_cap ? pl_s : pl_g;
       // rating
       for (int32_t i = lo + w; i < hi; i += IPW) {
         int32_t u = sl[i];
@@ -438,7 +446,8 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
           uint64_t k = ok ? pl[i] : 0;
           int32_t T = ok ? (int32_t)(k >> 47) : -1;
           int32_t u = ok ? (int32_t)(k & 0xFFFF) : 0;
-          int32_t Tprev = (i == 0) ? -1 : (int32_t)((pl[i - 1] >> 47) & 0xFFFF);
+          // only threads holding a proposal look at their predecessor (i - 1 < np)
+          int32_t Tprev = (!ok || i == 0) ? -1 : (int32_t)((pl[i - 1] >> 47) & 0xFFFF);
           bool head = !ok || i == 0 || T != Tprev;
           int64_t c = ok ? g.vw[u] : 0;
           int64_t pre = block_seg_scan(c, head || threadIdx.x == 0);
@@ -490,18 +499,18 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
       __syncthreads();
     }
     int32_t moved = s_moved;
-    int32_t *t = act;
+    uint8_t *t = act;
     act = act2;
     act2 = t;
     __syncthreads();
     if (moved == 0) break;
   }
   // isolated packing in id order
-  int32_t *iw = act2;  // reuse: weights of isolated nodes, then prefix
+  int32_t *iw = pg;  // reuse: weights of isolated nodes, then prefix
   for (int32_t v = threadIdx.x; v < n; v += IPT) iw[v] = (g.xadj[v + 1] == g.xadj[v]) ? g.vw[v] : 0;
   __syncthreads();
   block_scan_excl<int32_t>(iw, iw, n);
-  int32_t *first = act;
+  int32_t *first = sl;
   for (int32_t v = threadIdx.x; v < n; v += IPT) first[v] = INT32_MAX;
   __syncthreads();
   for (int32_t v = threadIdx.x; v < n; v += IPT) {
@@ -1490,8 +1499,8 @@ int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::
       A.lrep_bfs = cfg.lrep_bfs;
       A.lrep_ggg = cfg.lrep_ggg;
       A.sink = sample_sink();
-      // dynamic shared memory: the LP working arrays (13 words a node) and
-      // then the FM state (8 words a node) of the largest item of the round,
+      // dynamic shared memory: the LP working arrays (7.5 words a node plus
+      // sort space) and then the FM state (8 words a node) of the largest item of the round,
       // at least 16 KB (the portfolio of small coarsest graphs), at most what
       // the SM offers next to the kernel's static shared memory when the round
       // has no more items than SMs (its items are then on the critical path,
@@ -1500,7 +1509,7 @@ int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::
       int64_t maxn = 0;
       for (auto &d : items) maxn = std::max<int64_t>(maxn, d.n);
       int32_t cap_words = (int64_t)items.size() <= C.sms ? IP_DYN_MAX_WORDS : IP_DYN_SHARED_WORDS;
-      A.dyn_words = (int32_t)std::min<int64_t>(std::max<int64_t>(13 * maxn + 2, 4096), cap_words);
+      A.dyn_words = (int32_t)std::min<int64_t>(std::max<int64_t>(8 * maxn + 2 + 2 * maxn / 4, 4096), cap_words);
       size_t dyn_bytes = (size_t)A.dyn_words * sizeof(int32_t);
       static bool attr_set = false;
       if (!attr_set) {
