@@ -197,3 +197,29 @@ def test_full_size_rmat20_k256(kmp):
     rp, rrc, rst = O.partition(g, 256, 0.03, 1)
     assert np.array_equal(part.cpu().numpy(), rp)
     assert rc == rrc == 0 and st.cut == rst.cut and st.feasible == 1
+
+
+def test_full_size_rgg24_k16384(kmp):
+    """The large-k case: 2D RGG with 2^24 nodes (average degree ~16), k = 2^14.
+    The oracle's whole partition is too slow at this size, so it checks the
+    input level's coarsening bit-exactly (the driver's cluster cap) and the
+    partition by properties that hold at any size: every block within
+    L_k = floor(1.03 ceil(n/k)), the reported cut equal to a recount, and the
+    same result on a second run."""
+    g = gg.rgg(1 << 24, 16, 1)
+    k = 1 << 14
+    dg = kmp.DeviceGraph.from_host(g)
+    kp = min(k, g.n // kmp.get_config().C)
+    U = int(np.floor(0.03 * g.n / kp))
+    label = kmp.coarsen_level(dg, U, 5, 1, 0)
+    assert np.array_equal(label.cpu().numpy(), O.cluster(g, U, 5, 1, 0))
+    part, rc, st = kmp.partition_graph(dg, k, 0.03, 1)
+    part2, rc2, st2 = kmp.partition_graph(dg, k, 0.03, 1)
+    assert rc == rc2 == 0 and st.feasible == 1
+    assert torch.equal(part, part2) and st.cut == st2.cut
+    p = part.cpu().numpy()
+    assert p.min() >= 0 and p.max() < k
+    Lk = int(np.floor(1.03 * ((g.n + k - 1) // k)))
+    assert np.bincount(p, minlength=k).max() <= Lk
+    cut, bw = kmp.cut(dg, part, k)
+    assert cut == st.cut and int(bw.sum()) == g.n
