@@ -6,10 +6,12 @@
 // GPU layout: coarse ids = exclusive scan of "label used" flags (ascending
 // label); members grouped by a counting sort.  A coarse node whose members'
 // total degree is <= 512 is aggregated by one warp in a shared-memory hash
-// table and sorted by a warp bitonic network; larger rows are aggregated by
-// all their members' warps in parallel into global tables, and the distinct
-// entries of all large rows are ordered by one GPU-wide key-value radix sort
-// of (row, neighbour).  Rows go to temporary space at upper-bound offsets; a
+// table and sorted by a warp bitonic network; one whose total degree is <= 8192
+// by one CTA in a shared-memory table sized for it (three bins: 2048, 4096,
+// 8192) and a block bitonic network; larger rows are aggregated by all their
+// members' warps in parallel into global tables, and the distinct entries of
+// all large rows are ordered by one GPU-wide key-value radix sort of
+// (row, neighbour).  Rows go to temporary space at upper-bound offsets; a
 // prefix sum of the row lengths then places them into the final CSR.
 // Also: projection (Algorithm 1), cut and block weights (Section 2), and the
 // per-graph facts the other kernels need (max degree, isolated nodes, weights).
@@ -20,6 +22,17 @@ namespace kmp {
 constexpr int CW_UB = 512;            // warp path: members' total degree <= CW_UB
 constexpr int CW_TAB = 2 * CW_UB;     // per-warp table entries
 constexpr int CW_WARPS = 4;           // warps per block in the warp path
+constexpr int CB_UB = 8192;           // block path: members' total degree <= CB_UB
+constexpr int NCLASS = 5;             // warp path, three block bins, global path
+
+// row class by members' total degree ub
+__host__ __device__ __forceinline__ int row_class(unsigned long long ub) {
+  return ub <= (unsigned long long)CW_UB ? 0
+         : ub <= 2048ull                 ? 1
+         : ub <= 4096ull                 ? 2
+         : ub <= (unsigned long long)CB_UB ? 3
+                                         : 4;
+}
 
 __global__ void k_map_used(int32_t n, const int32_t *label, uint8_t *used) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
@@ -54,19 +67,12 @@ __global__ void k_members(int32_t n, const int32_t *map, const int32_t *moff, in
   }
 }
 
-// split coarse nodes into the warp path and the block path
-__global__ void k_split_ub(int32_t nc, const unsigned long long *cub, int32_t *small_list,
-                           int32_t *nsmall, int32_t *large_list, int32_t *nlarge,
-                           unsigned long long *maxub) {
+// split coarse nodes by row class: list c holds its rows at lists + c * nc
+__global__ void k_split_ub(int32_t nc, const unsigned long long *cub, int32_t *lists, int32_t *counts) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nc;
        x += (int64_t)gridDim.x * blockDim.x) {
-    unsigned long long ub = cub[x];
-    if (ub <= (unsigned long long)CW_UB) {
-      small_list[atomicAdd(nsmall, 1)] = (int32_t)x;
-    } else {
-      large_list[atomicAdd(nlarge, 1)] = (int32_t)x;
-      atomicMax(maxub, ub);
-    }
+    int c = row_class(cub[x]);
+    lists[(int64_t)c * nc + atomicAdd(&counts[c], 1)] = (int32_t)x;
   }
 }
 
@@ -152,12 +158,193 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_aggregate_warp(
   }
 }
 
+// block path: one coarse node per CTA for rows whose members' total degree ub
+// is at most TAB / 2.  The row's table is the power of two >= 2 ub (load
+// factor <= 1/2); its distinct entries (at most ub) are sorted by neighbour id.
+// The members' edges are spread evenly over all NT threads (up to NT members
+// at a time: a prefix sum of their degrees, each thread finds the member of
+// its edge by binary search), so one high-degree member does not serialise
+// the row on one warp.  Ordering: when the row's neighbour ids span at most
+// 32 TAB values (and not far more than the entries), each entry's position is
+// the number of smaller ids, read from a bitmap of the span and a prefix sum
+// of its word popcounts (the freed table is the space); else the entries are
+// sorted by a block bitonic network.
+// exclusive prefix sum of v over the NT threads of the block (all threads call it)
+template <int NT>
+__device__ __forceinline__ int32_t block_scan_excl(int32_t v, int32_t *s_wsum /* NT / 32 */) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t inc = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int32_t t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) s_wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int32_t t = lane < NW ? s_wsum[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t u = __shfl_up_sync(0xFFFFFFFFu, t, o);
+      if (lane >= o) t += u;
+    }
+    if (lane < NW) s_wsum[lane] = t;
+  }
+  __syncthreads();
+  int32_t r = inc - v + (w > 0 ? s_wsum[w - 1] : 0);
+  __syncthreads();  // s_wsum may be reused
+  return r;
+}
+
+template <int TAB, int NT>
+constexpr size_t cta_smem_bytes() {
+  return (size_t)TAB / 2 * sizeof(uint64_t) + (size_t)TAB * 2 * sizeof(int32_t);
+}
+
+template <int TAB, int NT>
+__global__ void __launch_bounds__(NT) k_aggregate_cta(
+    const int32_t *list, int32_t nrows, const unsigned long long *cub, const int64_t *xadj,
+    const int32_t *adj, const int32_t *ew, const int32_t *map, const int32_t *members,
+    const int32_t *moff, const int64_t *toff, int32_t *tadj, int32_t *tw, int32_t *cdeg) {
+  extern __shared__ __align__(16) unsigned char cta_smem[];
+  uint64_t *L = reinterpret_cast<uint64_t *>(cta_smem);      // TAB / 2 sort entries
+  int32_t *K = reinterpret_cast<int32_t *>(L + TAB / 2);     // TAB keys
+  int32_t *V = K + TAB;                                       // TAB weights
+  __shared__ int32_t s_cnt, s_ymin, s_ymax;
+  __shared__ int32_t s_pre[NT + 1];
+  __shared__ int64_t s_b[NT];
+  __shared__ int32_t s_wsum[NT / 32];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int32_t i = blockIdx.x; i < nrows; i += gridDim.x) {
+    int32_t x = list[i];
+    uint32_t ub = (uint32_t)cub[x];
+    uint32_t tsz = 64;
+    while (tsz < 2 * ub) tsz <<= 1;
+    for (uint32_t j = tid; j < tsz; j += NT) {
+      K[j] = HT_EMPTY;
+      V[j] = 0;
+    }
+    if (tid == 0) {
+      s_cnt = 0;
+      s_ymin = INT32_MAX;
+      s_ymax = -1;
+    }
+    __syncthreads();
+    const int32_t m1 = moff[x + 1];
+    for (int32_t c0 = moff[x]; c0 < m1; c0 += NT) {
+      const int32_t cn = m1 - c0 < NT ? m1 - c0 : NT;
+      int32_t d = 0;
+      int64_t b = 0;
+      if (tid < cn) {
+        int32_t v = members[c0 + tid];
+        b = xadj[v];
+        d = (int32_t)(xadj[v + 1] - b);
+      }
+      s_pre[tid + 1] = block_scan_excl<NT>(d, s_wsum) + d;
+      s_b[tid] = b;
+      if (tid == 0) s_pre[0] = 0;
+      __syncthreads();
+      const int32_t tot = s_pre[cn];
+      for (int32_t e = tid; e < tot; e += NT) {
+        int32_t lo = 0, hi = cn - 1;  // the last member whose prefix is <= e owns edge e
+        while (lo < hi) {
+          int32_t mid = (lo + hi + 1) >> 1;
+          if (s_pre[mid] <= e) lo = mid;
+          else hi = mid - 1;
+        }
+        int64_t q = s_b[lo] + (e - s_pre[lo]);
+        int32_t y = map[adj[q]];
+        if (y != x) ht_add(K, V, tsz - 1, y, ew ? ew[q] : 1);
+      }
+      __syncthreads();  // the next chunk rewrites the prefix
+    }
+    // compact into L (order arbitrary; tsz is a multiple of 32)
+    for (uint32_t j0 = (uint32_t)w * 32; j0 < tsz; j0 += NT) {
+      uint32_t j = j0 + lane;
+      bool has = K[j] != HT_EMPTY;
+      unsigned bal = __ballot_sync(0xFFFFFFFFu, has);
+      int32_t p0 = 0;
+      if (lane == 0 && bal) p0 = atomicAdd(&s_cnt, __popc(bal));
+      p0 = __shfl_sync(0xFFFFFFFFu, p0, 0);
+      if (has) L[p0 + __popc(bal & ((1u << lane) - 1u))] = ((uint64_t)(uint32_t)K[j] << 32) | (uint32_t)V[j];
+      int32_t mn = __reduce_min_sync(0xFFFFFFFFu, has ? K[j] : INT32_MAX);
+      int32_t mx = __reduce_max_sync(0xFFFFFFFFu, has ? K[j] : -1);
+      if (lane == 0 && bal) {
+        atomicMin(&s_ymin, mn);
+        atomicMax(&s_ymax, mx);
+      }
+    }
+    __syncthreads();
+    const int32_t cnt = s_cnt, ymin = s_ymin;
+    uint32_t P = 1;
+    while (P < (uint32_t)cnt) P <<= 1;
+    const int32_t W = cnt > 0 ? ((s_ymax - ymin) >> 5) + 1 : 0;
+    int64_t o = toff[x];
+    if (W <= TAB && (uint32_t)W <= 16 * P) {
+      uint32_t *Bm = reinterpret_cast<uint32_t *>(K);  // bitmap of ids ymin.. (W words)
+      int32_t *Pf = V;                                 // popcount prefix per word
+      for (int32_t j = tid; j < W; j += NT) Bm[j] = 0;
+      __syncthreads();
+      for (int32_t j = tid; j < cnt; j += NT) {
+        int32_t d = (int32_t)(L[j] >> 32) - ymin;
+        atomicOr(&Bm[d >> 5], 1u << (d & 31));
+      }
+      __syncthreads();
+      const int32_t seg = (W + NT - 1) / NT, a = tid * seg < W ? tid * seg : W, b = a + seg < W ? a + seg : W;
+      int32_t loc = 0;
+      for (int32_t j = a; j < b; ++j) loc += __popc(Bm[j]);
+      int32_t base = block_scan_excl<NT>(loc, s_wsum);
+      for (int32_t j = a; j < b; ++j) {
+        Pf[j] = base;
+        base += __popc(Bm[j]);
+      }
+      __syncthreads();
+      for (int32_t j = tid; j < cnt; j += NT) {
+        uint64_t ent = L[j];
+        int32_t y = (int32_t)(ent >> 32), d = y - ymin;
+        int32_t r = Pf[d >> 5] + __popc(Bm[d >> 5] & ((1u << (d & 31)) - 1u));
+        tadj[o + r] = y;
+        tw[o + r] = (int32_t)(uint32_t)ent;
+      }
+    } else {
+      for (uint32_t j = cnt + tid; j < P; j += NT) L[j] = ~0ull;
+      __syncthreads();
+      bitonic<true>(L, P, tid, NT);
+      for (int32_t j = tid; j < cnt; j += NT) {
+        tadj[o + j] = (int32_t)(L[j] >> 32);
+        tw[o + j] = (int32_t)(uint32_t)L[j];
+      }
+    }
+    if (tid == 0) cdeg[x] = cnt;
+    __syncthreads();  // the next row reuses the tables and the counter
+  }
+}
+
+template <int TAB, int NT>
+void launch_aggregate_cta(const int32_t *list, int32_t nrows, const unsigned long long *cub, const Graph &g,
+                          const int32_t *map, const int32_t *members, const int32_t *moff,
+                          const int64_t *toff, int32_t *tadj, int32_t *tw, int32_t *cdeg) {
+  static_assert(TAB / 2 >= NT && TAB % NT == 0, "bin shape");
+  constexpr size_t bytes = cta_smem_bytes<TAB, NT>();
+  static bool attr = false;
+  if (!attr) {
+    KMP_CUDA(cudaFuncSetAttribute(k_aggregate_cta<TAB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)bytes));
+    attr = true;
+  }
+  int per_sm = (int)((227u << 10) / (bytes + 1024));
+  if (per_sm < 1) per_sm = 1;
+  int blocks = std::min<int64_t>(nrows, (int64_t)ctx().sms * per_sm);
+  k_aggregate_cta<TAB, NT><<<blocks, NT, bytes, ctx().stream>>>(list, nrows, cub, g.xadj, g.adj, g.ew, map,
+                                                                members, moff, toff, tadj, tw, cdeg);
+  KMP_LAUNCHED("aggregate_cta");
+}
+
 // ---- large rows (members' total degree > CW_UB)
 __global__ void k_large_sizes(int32_t nc, const unsigned long long *cub, int64_t *tsz) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nc;
        x += (int64_t)gridDim.x * blockDim.x) {
     unsigned long long ub = cub[x];
-    if (ub <= (unsigned long long)CW_UB) {
+    if (ub <= (unsigned long long)CB_UB) {
       tsz[x] = 0;
     } else {
       int64_t d = (int64_t)ub < nc ? (int64_t)ub : nc;  // distinct neighbours < nc
@@ -176,10 +363,17 @@ __global__ void k_large_chunks(int32_t n, const int64_t *xadj, const int32_t *ma
                                const unsigned long long *cub, int64_t *nch) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x)
-    nch[v] = cub[map[v]] > (unsigned long long)CW_UB ? ceil_div(xadj[v + 1] - xadj[v], LARGE_CHUNK) : 0;
+    nch[v] = cub[map[v]] > (unsigned long long)CB_UB ? ceil_div(xadj[v + 1] - xadj[v], LARGE_CHUNK) : 0;
 }
 
-__global__ void __launch_bounds__(256) k_large_insert(int32_t n, int64_t total, const int64_t *choff,
+// the node owning every chunk
+__global__ void k_large_owner(int32_t n, const int64_t *nch, const int64_t *choff, int32_t *owner) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t c = 0; c < nch[v]; ++c) owner[choff[v] + c] = (int32_t)v;
+}
+
+__global__ void __launch_bounds__(256) k_large_insert(int64_t total, const int32_t *owner, const int64_t *choff,
                                                       const int64_t *xadj, const int32_t *adj,
                                                       const int32_t *ew, const int32_t *map,
                                                       const int64_t *ltoff, const int64_t *tsz, int32_t *lk,
@@ -188,14 +382,7 @@ __global__ void __launch_bounds__(256) k_large_insert(int32_t n, int64_t total, 
   int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t c = gw; c < total; c += nw) {
-    // node owning chunk c: last v with choff[v] <= c (ties resolve to the node with chunks)
-    int32_t lo = 0, hi = n - 1;
-    while (lo < hi) {
-      int32_t mid = (lo + hi + 1) >> 1;
-      if (choff[mid] <= c) lo = mid;
-      else hi = mid - 1;
-    }
-    int32_t v = lo, x = map[v];
+    int32_t v = owner[c], x = map[v];
     int32_t *K = lk + ltoff[x], *V = lv + ltoff[x];
     uint32_t mask = (uint32_t)(tsz[x] - 1);
     int64_t b = xadj[v] + (c - choff[v]) * LARGE_CHUNK;
@@ -207,11 +394,22 @@ __global__ void __launch_bounds__(256) k_large_insert(int32_t n, int64_t total, 
   }
 }
 
-// distinct entries of all large rows into one (row << bits | neighbour, weight) list
 // Tables are powers of two >= 32 laid out back to back, so every aligned tile
-// of 32 entries belongs to one row: a warp per tile finds its row by binary
-// search (the last row whose offset is <= the tile start owns it).
-__global__ void __launch_bounds__(256) k_large_compact(int32_t nc, int64_t LT, const int64_t *ltoff,
+// of 32 entries belongs to one row: the row of every tile (a warp per large
+// row writes its tiles)
+__global__ void k_large_tiles(const int32_t *large_list, const int32_t *nlarge, const int64_t *ltoff,
+                              const int64_t *tsz, int32_t *tile_row) {
+  int lane = threadIdx.x & 31;
+  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = gw; i < *nlarge; i += nw) {
+    int32_t x = large_list[i];
+    for (int64_t t = ltoff[x] / 32 + lane; t < (ltoff[x] + tsz[x]) / 32; t += 32) tile_row[t] = x;
+  }
+}
+
+// distinct entries of all large rows into one (row << bits | neighbour, weight) list
+__global__ void __launch_bounds__(256) k_large_compact(int64_t LT, const int32_t *tile_row,
                                                        const int32_t *lk, const int32_t *lv, int bits,
                                                        uint64_t *ek, int32_t *ev, int32_t *cnt,
                                                        int32_t *cdeg) {
@@ -220,13 +418,7 @@ __global__ void __launch_bounds__(256) k_large_compact(int32_t nc, int64_t LT, c
   int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t t = gw; t * 32 < LT; t += nw) {
     int64_t e = t * 32;
-    int32_t lo = 0, hi = nc - 1;
-    while (lo < hi) {
-      int32_t mid = (lo + hi + 1) >> 1;
-      if (ltoff[mid] <= e) lo = mid;
-      else hi = mid - 1;
-    }
-    int32_t x = lo;
+    int32_t x = tile_row[t];
     int32_t y = lk[e + lane];
     bool has = y != HT_EMPTY;
     unsigned bal = __ballot_sync(0xFFFFFFFFu, has);
@@ -265,16 +457,30 @@ __global__ void k_large_place(int32_t N, const uint64_t *ek, const int32_t *ev, 
   }
 }
 
-__global__ void k_copy_rows(int32_t nc, const int64_t *toff, const int64_t *cx, const int32_t *tadj,
-                            const int32_t *tw, int32_t *adj, int32_t *ew) {
+// rows from their upper-bound offsets into the final CSR; four loads per lane
+// are issued before their stores
+__global__ void k_copy_rows(int32_t nc, const int64_t *__restrict__ toff, const int64_t *__restrict__ cx,
+                            const int32_t *__restrict__ tadj, const int32_t *__restrict__ tw,
+                            int32_t *__restrict__ adj, int32_t *__restrict__ ew) {
   int lane = threadIdx.x & 31;
   int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t x = gw; x < nc; x += nw) {
-    int64_t o = toff[x], d = cx[x + 1] - cx[x], p = cx[x];
-    for (int64_t j = lane; j < d; j += 32) {
-      adj[p + j] = tadj[o + j];
-      ew[p + j] = tw[o + j];
+    int64_t o = toff[x], p = cx[x], d = cx[x + 1] - p;
+    for (int64_t j = lane; j < d; j += 128) {
+      int32_t a[4], c[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j + 32 * u < d) {
+          a[u] = tadj[o + j + 32 * u];
+          c[u] = tw[o + j + 32 * u];
+        }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j + 32 * u < d) {
+          adj[p + j + 32 * u] = a[u];
+          ew[p + j + 32 * u] = c[u];
+        }
     }
   }
 }
@@ -372,20 +578,28 @@ Graph contract_graph(const Graph &g, const int32_t *label, int32_t *map) {
   int64_t tot = read1(ttot.p);
   DBuf<int32_t> tadj(tot), tw(tot), cdeg(nc + 1);
   cdeg.zero();
-  DBuf<int32_t> small_list(nc), large_list(nc), counts(2);
-  DBuf<unsigned long long> maxub(1);
+  DBuf<int32_t> lists((int64_t)NCLASS * nc), counts(NCLASS);
   counts.zero();
-  maxub.zero();
-  k_split_ub<<<gridc, 256, 0, s>>>(nc, cub, small_list, counts.p, large_list, counts.p + 1, maxub);
+  k_split_ub<<<gridc, 256, 0, s>>>(nc, cub, lists, counts);
   KMP_LAUNCHED("split_ub");
-  int32_t hc[2];
-  to_host(hc, counts.p, 2);
+  int32_t hc[NCLASS];
+  to_host(hc, counts.p, NCLASS);
+  const int32_t *small_list = lists.p, *large_list = lists.p + (int64_t)4 * nc;
+  if (hc[1] > 0)
+    launch_aggregate_cta<4096, 256>(lists.p + (int64_t)1 * nc, hc[1], cub, g, map, members, moff, toff, tadj,
+                                    tw, cdeg);
+  if (hc[2] > 0)
+    launch_aggregate_cta<8192, 512>(lists.p + (int64_t)2 * nc, hc[2], cub, g, map, members, moff, toff, tadj,
+                                    tw, cdeg);
+  if (hc[3] > 0)
+    launch_aggregate_cta<16384, 1024>(lists.p + (int64_t)3 * nc, hc[3], cub, g, map, members, moff, toff, tadj,
+                                      tw, cdeg);
   if (hc[0] > 0) {
     k_aggregate_warp<<<grid_for(hc[0], CW_WARPS, 16), CW_WARPS * 32, 0, s>>>(
         small_list, counts.p, g.xadj, g.adj, g.ew, map, members, moff, toff, tadj, tw, cdeg);
     KMP_LAUNCHED("aggregate_warp");
   }
-  if (hc[1] > 0) {
+  if (hc[4] > 0) {
     // large rows: every member inserts in parallel into its coarse node's global
     // table; the distinct entries of all large rows are then ordered by one
     // key-value radix sort of (row, neighbour) and placed into their rows
@@ -405,13 +619,20 @@ Graph contract_graph(const Graph &g, const int32_t *label, int32_t *map) {
     KMP_LAUNCHED("large_chunks");
     scan_excl_i64(nch, choff, n, chtot);
     int64_t CT = read1(chtot.p);
-    k_large_insert<<<grid_for(CT * 32, 256, 8), 256, 0, s>>>(n, CT, choff, g.xadj, g.adj, g.ew, map,
+    DBuf<int32_t> owner(CT + 1);
+    k_large_owner<<<grid, 256, 0, s>>>(n, nch, choff, owner);
+    KMP_LAUNCHED("large_owner");
+    k_large_insert<<<grid_for(CT * 32, 256, 8), 256, 0, s>>>(CT, owner, choff, g.xadj, g.adj, g.ew, map,
                                                              ltoff, tsz, lk, lv);
     KMP_LAUNCHED("large_insert");
     int64_t cap_entries = LT / 2 + 1;
     DBuf<uint64_t> ek(cap_entries), ektmp(cap_entries);
     DBuf<int32_t> ev(cap_entries), evtmp(cap_entries), seglo(nc);
-    k_large_compact<<<grid_for(LT, 256, 8), 256, 0, s>>>(nc, LT, ltoff, lk, lv, bits, ek, ev, lcnt, cdeg);
+    DBuf<int32_t> tile_row(LT / 32 + 1);
+    k_large_tiles<<<grid_for((int64_t)hc[4] * 32, 256), 256, 0, s>>>(large_list, counts.p + 4, ltoff, tsz,
+                                                                     tile_row);
+    KMP_LAUNCHED("large_tiles");
+    k_large_compact<<<grid_for(LT, 256, 8), 256, 0, s>>>(LT, tile_row, lk, lv, bits, ek, ev, lcnt, cdeg);
     KMP_LAUNCHED("large_compact");
     int32_t NE = read1(lcnt.p);
     radix_sort_kv(ek, ev, ektmp, evtmp, NE, 2 * bits);

@@ -79,6 +79,48 @@ def test_contract_parity(kmp, name):
     assert np.array_equal(h.vwgt, rg.vwgt)
 
 
+def _contract_check(kmp, g, lab):
+    dg = kmp.DeviceGraph.from_host(g)
+    cg, mp = kmp.contract(dg, torch.from_numpy(lab).cuda())
+    rg, rmp = O.contract(g, lab)
+    h = cg.to_host()
+    assert np.array_equal(mp.cpu().numpy(), rmp)
+    assert np.array_equal(h.xadj, rg.xadj)
+    assert np.array_equal(h.adjncy, rg.adjncy)
+    assert np.array_equal(h.adjwgt, rg.adjwgt)
+    assert np.array_equal(h.vwgt, rg.vwgt)
+
+
+@pytest.mark.parametrize("n,m", [(24000, 240000), (240000, 1200000)])
+def test_contract_row_classes(kmp, n, m):
+    """Weighted clusters whose members' total degree falls in every
+    aggregation class (<= 512, <= 2048, <= 4096, <= 8192 and above), filled
+    greedily up to each class bound; the other nodes stay singletons, so on
+    the larger graph a row's neighbour ids span more than 2^17 coarse ids"""
+    g = gg.with_weights(gg.random_graph(n, m, 11), 5, 9, 4)
+    deg = np.diff(g.xadj)
+    order = np.random.default_rng(3).permutation(g.n)
+    lab = np.empty(g.n, np.int32)
+    targets = [300, 512, 2048, 4096, 8192, 30000]
+    pos, c = 0, 0
+    ubs = []
+    for t in targets * 3:
+        s, start = 0, pos
+        while pos < g.n and s + deg[order[pos]] <= t:
+            s += deg[order[pos]]
+            pos += 1
+        if pos == start and pos < g.n:
+            s += deg[order[pos]]
+            pos += 1
+        lab[order[start:pos]] = order[start]
+        ubs.append(s)
+    lab[order[pos:]] = order[pos:]           # the rest are singletons
+    ubs = np.array(ubs)
+    for lo, hi in [(0, 512), (513, 2048), (2049, 4096), (4097, 8192), (8193, 1 << 40)]:
+        assert ((ubs >= lo) & (ubs <= hi)).any(), (lo, hi)
+    _contract_check(kmp, g, lab)
+
+
 def test_two_levels_chain(kmp):
     """coarsen -> contract -> coarsen on the GPU's own coarse graph equals the oracle chain"""
     g = CASES["rmat14"]
@@ -150,6 +192,7 @@ def test_full_size_rmat20_level0(kmp):
     label = kmp.coarsen_level(dg, U, 5, 1, 0)
     ref = O.cluster(g, U, 5, 1, 0)
     assert np.array_equal(label.cpu().numpy(), ref)
+    _contract_check(kmp, g, ref)
 
 
 @pytest.mark.parametrize("graphs", [0, 1])
