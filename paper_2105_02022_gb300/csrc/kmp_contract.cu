@@ -6,9 +6,10 @@
 // GPU layout: coarse ids = exclusive scan of "label used" flags (ascending
 // label); members grouped by a counting sort.  A coarse node whose members'
 // total degree is <= 512 is aggregated by one warp in a shared-memory hash
-// table and sorted by a warp bitonic network; one whose total degree is <= 8192
-// by one CTA in a shared-memory table sized for it (three bins: 2048, 4096,
-// 8192) and a block bitonic network; larger rows are aggregated by all their
+// table (four bins by size: 64, 128, 256, 512) and sorted by a warp bitonic
+// network; one whose total degree is <= 8192 by one CTA in a shared-memory
+// table sized for it (three bins: 2048, 4096, 8192), ordered by a bitmap rank
+// or a block bitonic network; larger rows are aggregated by all their
 // members' warps in parallel into global tables, and the distinct entries of
 // all large rows are ordered by one GPU-wide key-value radix sort of
 // (row, neighbour).  Rows go to temporary space at upper-bound offsets; a
@@ -20,18 +21,21 @@
 namespace kmp {
 
 constexpr int CW_UB = 512;            // warp path: members' total degree <= CW_UB
-constexpr int CW_TAB = 2 * CW_UB;     // per-warp table entries
-constexpr int CW_WARPS = 4;           // warps per block in the warp path
 constexpr int CB_UB = 8192;           // block path: members' total degree <= CB_UB
-constexpr int NCLASS = 5;             // warp path, three block bins, global path
+constexpr int NCLASS = 8;             // four warp bins, three block bins, global path
+constexpr int CLS_GLOBAL = NCLASS - 1;
 
-// row class by members' total degree ub
+// row class by members' total degree ub: warp bins 64 / 128 / 256 / 512, block
+// bins 2048 / 4096 / 8192, then the global path
 __host__ __device__ __forceinline__ int row_class(unsigned long long ub) {
-  return ub <= (unsigned long long)CW_UB ? 0
-         : ub <= 2048ull                 ? 1
-         : ub <= 4096ull                 ? 2
-         : ub <= (unsigned long long)CB_UB ? 3
-                                         : 4;
+  return ub <= 64ull    ? 0
+         : ub <= 128ull  ? 1
+         : ub <= 256ull  ? 2
+         : ub <= (unsigned long long)CW_UB ? 3
+         : ub <= 2048ull ? 4
+         : ub <= 4096ull ? 5
+         : ub <= 8192ull ? 6
+                         : CLS_GLOBAL;
 }
 
 __global__ void k_map_used(int32_t n, const int32_t *label, uint8_t *used) {
@@ -105,57 +109,110 @@ __device__ __forceinline__ void bitonic(uint64_t *a, uint32_t P, uint32_t t, uin
   }
 }
 
-// warp path: one coarse node per warp
-__global__ void __launch_bounds__(CW_WARPS * 32) k_aggregate_warp(
-    const int32_t *small_list, const int32_t *nsmall_p, const int64_t *xadj, const int32_t *adj,
-    const int32_t *ew, const int32_t *map, const int32_t *members, const int32_t *moff,
-    const int64_t *toff, int32_t *tadj, int32_t *tw, int32_t *cdeg) {
-  __shared__ int32_t keys[CW_WARPS][CW_TAB];
-  __shared__ int32_t vals[CW_WARPS][CW_TAB];
-  __shared__ uint64_t lst[CW_WARPS][CW_UB];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int32_t nsmall = *nsmall_p;
-  int64_t gw = (int64_t)blockIdx.x * CW_WARPS + w, nw = (int64_t)gridDim.x * CW_WARPS;
-  int32_t *K = keys[w], *V = vals[w];
-  uint64_t *L = lst[w];
-  for (int64_t i = gw; i < nsmall; i += nw) {
-    int32_t x = small_list[i];
-    for (int j = lane; j < CW_TAB; j += 32) {
-      K[j] = HT_EMPTY;
-      V[j] = 0;
-    }
+// warp path: one coarse node per warp for rows whose members' total degree
+// ub is at most TABW / 2.  The table packs (neighbour << 32 | weight) per slot
+// (key and weight updated as the two 32-bit halves), is sized to the power of
+// two >= 2 ub, and is compacted in place into the sort list, since every entry
+// moves to a slot at or below its own.  Up to 32 members at a time spread
+// their edges over the lanes (a warp prefix sum of their degrees; each lane
+// finds the member of its edge by a five-step search over the prefixes).
+template <int TABW, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_aggregate_warp(
+    const int32_t *list, int32_t nrows, const unsigned long long *cub, const int64_t *xadj,
+    const int32_t *adj, const int32_t *ew, const int32_t *map, const int32_t *members,
+    const int32_t *moff, const int64_t *toff, int32_t *tadj, int32_t *tw, int32_t *cdeg) {
+  __shared__ uint64_t tab[WARPS][TABW];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint64_t *T = tab[w];
+  int32_t *H = reinterpret_cast<int32_t *>(T);  // H[2 j] weight, H[2 j + 1] key of slot j
+  const int64_t gw = (int64_t)blockIdx.x * WARPS + w, nw = (int64_t)gridDim.x * WARPS;
+  for (int64_t i = gw; i < nrows; i += nw) {
+    const int32_t x = list[i];
+    const uint32_t ub = (uint32_t)cub[x];
+    uint32_t tsz = 64;
+    while (tsz < 2 * ub) tsz <<= 1;
+    const uint32_t mask = tsz - 1;
+    for (uint32_t j = lane; j < tsz; j += 32) T[j] = (uint64_t)(uint32_t)HT_EMPTY << 32;
     __syncwarp();
-    for (int32_t mi = moff[x]; mi < moff[x + 1]; ++mi) {
-      int32_t v = members[mi];
-      int64_t b = xadj[v], e = xadj[v + 1];
-      for (int64_t q = b + lane; q < e; q += 32) {
-        int32_t y = map[adj[q]];
-        if (y != x) ht_add(K, V, CW_TAB - 1, y, ew ? ew[q] : 1);
+    const int32_t m1 = moff[x + 1];
+    for (int32_t c0 = moff[x]; c0 < m1; c0 += 32) {
+      int32_t d = 0;
+      int64_t b = 0;
+      if (c0 + lane < m1) {
+        int32_t v = members[c0 + lane];
+        b = xadj[v];
+        d = (int32_t)(xadj[v + 1] - b);
+      }
+      int32_t inc = d;
+      for (int o = 1; o < 32; o <<= 1) {
+        int32_t t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      const int32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+      for (int32_t e0 = 0; e0 < tot; e0 += 32) {
+        const int32_t e = e0 + lane;
+        int32_t j = 0;  // members before the owner of edge e: their inclusive prefix is <= e
+        for (int st = 16; st > 0; st >>= 1) {
+          int32_t t = __shfl_sync(0xFFFFFFFFu, inc, j + st - 1);
+          if (t <= e) j += st;
+        }
+        int64_t bj = __shfl_sync(0xFFFFFFFFu, b, j & 31);
+        int32_t ej = __shfl_sync(0xFFFFFFFFu, inc - d, j & 31);
+        if (e < tot) {
+          int64_t q = bj + (e - ej);
+          int32_t y = map[adj[q]];
+          if (y != x) {
+            int32_t wq = ew ? ew[q] : 1;
+            uint32_t h = fmix32((uint32_t)y) & mask;
+            for (uint32_t probe = 0; probe <= mask; ++probe) {
+              int32_t old = atomicCAS(&H[2 * h + 1], HT_EMPTY, y);
+              if (old == HT_EMPTY || old == y) {
+                atomicAdd(&H[2 * h], wq);
+                break;
+              }
+              h = (h + 1) & mask;
+            }
+          }
+        }
       }
     }
     __syncwarp();
-    // compact the table into L (order arbitrary), then sort by neighbour id
+    // in-place compaction: entry j goes to slot cnt + rank <= j
     int32_t cnt = 0;
-    for (int j0 = 0; j0 < CW_TAB; j0 += 32) {
-      int j = j0 + lane;
-      bool has = K[j] != HT_EMPTY;
-      unsigned b = __ballot_sync(0xFFFFFFFFu, has);
-      if (has) L[cnt + __popc(b & ((1u << lane) - 1u))] = ((uint64_t)(uint32_t)K[j] << 32) | (uint32_t)V[j];
-      cnt += __popc(b);
+    for (uint32_t j0 = 0; j0 < tsz; j0 += 32) {
+      uint64_t ent = T[j0 + lane];
+      bool has = (int32_t)(ent >> 32) != HT_EMPTY;
+      unsigned bal = __ballot_sync(0xFFFFFFFFu, has);
+      __syncwarp();
+      if (has) T[cnt + __popc(bal & ((1u << lane) - 1u))] = ent;
+      cnt += __popc(bal);
+      __syncwarp();
     }
     uint32_t P = 1;
     while (P < (uint32_t)cnt) P <<= 1;
-    for (uint32_t j = cnt + lane; j < P; j += 32) L[j] = ~0ull;
+    for (uint32_t j = cnt + lane; j < P; j += 32) T[j] = ~0ull;
     __syncwarp();
-    bitonic<false>(L, P, lane, 32);
-    int64_t o = toff[x];
+    bitonic<false>(T, P, lane, 32);
+    const int64_t o = toff[x];
     for (int32_t j = lane; j < cnt; j += 32) {
-      tadj[o + j] = (int32_t)(L[j] >> 32);
-      tw[o + j] = (int32_t)(uint32_t)L[j];
+      tadj[o + j] = (int32_t)(T[j] >> 32);
+      tw[o + j] = (int32_t)(uint32_t)T[j];
     }
     if (lane == 0) cdeg[x] = cnt;
     __syncwarp();
   }
+}
+
+template <int TABW, int WARPS>
+void launch_aggregate_warp(const int32_t *list, int32_t nrows, const unsigned long long *cub, const Graph &g,
+                           const int32_t *map, const int32_t *members, const int32_t *moff,
+                           const int64_t *toff, int32_t *tadj, int32_t *tw, int32_t *cdeg) {
+  static_assert(TABW >= 64 && TABW * WARPS * sizeof(uint64_t) <= 48 * 1024, "bin shape");
+  constexpr int per_sm_smem = (int)((227u << 10) / (TABW * WARPS * sizeof(uint64_t) + 1024));
+  constexpr int per_sm = per_sm_smem < 64 / WARPS ? per_sm_smem : 64 / WARPS;
+  k_aggregate_warp<TABW, WARPS><<<grid_for(nrows, WARPS, per_sm), WARPS * 32, 0, ctx().stream>>>(
+      list, nrows, cub, g.xadj, g.adj, g.ew, map, members, moff, toff, tadj, tw, cdeg);
+  KMP_LAUNCHED("aggregate_warp");
 }
 
 // block path: one coarse node per CTA for rows whose members' total degree ub
@@ -584,22 +641,17 @@ Graph contract_graph(const Graph &g, const int32_t *label, int32_t *map) {
   KMP_LAUNCHED("split_ub");
   int32_t hc[NCLASS];
   to_host(hc, counts.p, NCLASS);
-  const int32_t *small_list = lists.p, *large_list = lists.p + (int64_t)4 * nc;
-  if (hc[1] > 0)
-    launch_aggregate_cta<4096, 256>(lists.p + (int64_t)1 * nc, hc[1], cub, g, map, members, moff, toff, tadj,
-                                    tw, cdeg);
-  if (hc[2] > 0)
-    launch_aggregate_cta<8192, 512>(lists.p + (int64_t)2 * nc, hc[2], cub, g, map, members, moff, toff, tadj,
-                                    tw, cdeg);
-  if (hc[3] > 0)
-    launch_aggregate_cta<16384, 1024>(lists.p + (int64_t)3 * nc, hc[3], cub, g, map, members, moff, toff, tadj,
-                                      tw, cdeg);
-  if (hc[0] > 0) {
-    k_aggregate_warp<<<grid_for(hc[0], CW_WARPS, 16), CW_WARPS * 32, 0, s>>>(
-        small_list, counts.p, g.xadj, g.adj, g.ew, map, members, moff, toff, tadj, tw, cdeg);
-    KMP_LAUNCHED("aggregate_warp");
-  }
-  if (hc[4] > 0) {
+  const int32_t *large_list = lists.p + (int64_t)CLS_GLOBAL * nc;
+  auto L = [&](int c) { return lists.p + (int64_t)c * nc; };
+  if (hc[4] > 0) launch_aggregate_cta<4096, 256>(L(4), hc[4], cub, g, map, members, moff, toff, tadj, tw, cdeg);
+  if (hc[5] > 0) launch_aggregate_cta<8192, 512>(L(5), hc[5], cub, g, map, members, moff, toff, tadj, tw, cdeg);
+  if (hc[6] > 0)
+    launch_aggregate_cta<16384, 1024>(L(6), hc[6], cub, g, map, members, moff, toff, tadj, tw, cdeg);
+  if (hc[0] > 0) launch_aggregate_warp<128, 8>(L(0), hc[0], cub, g, map, members, moff, toff, tadj, tw, cdeg);
+  if (hc[1] > 0) launch_aggregate_warp<256, 8>(L(1), hc[1], cub, g, map, members, moff, toff, tadj, tw, cdeg);
+  if (hc[2] > 0) launch_aggregate_warp<512, 8>(L(2), hc[2], cub, g, map, members, moff, toff, tadj, tw, cdeg);
+  if (hc[3] > 0) launch_aggregate_warp<1024, 4>(L(3), hc[3], cub, g, map, members, moff, toff, tadj, tw, cdeg);
+  if (hc[CLS_GLOBAL] > 0) {
     // large rows: every member inserts in parallel into its coarse node's global
     // table; the distinct entries of all large rows are then ordered by one
     // key-value radix sort of (row, neighbour) and placed into their rows
@@ -629,7 +681,7 @@ Graph contract_graph(const Graph &g, const int32_t *label, int32_t *map) {
     DBuf<uint64_t> ek(cap_entries), ektmp(cap_entries);
     DBuf<int32_t> ev(cap_entries), evtmp(cap_entries), seglo(nc);
     DBuf<int32_t> tile_row(LT / 32 + 1);
-    k_large_tiles<<<grid_for((int64_t)hc[4] * 32, 256), 256, 0, s>>>(large_list, counts.p + 4, ltoff, tsz,
+    k_large_tiles<<<grid_for((int64_t)hc[CLS_GLOBAL] * 32, 256), 256, 0, s>>>(large_list, counts.p + CLS_GLOBAL, ltoff, tsz,
                                                                      tile_row);
     KMP_LAUNCHED("large_tiles");
     k_large_compact<<<grid_for(LT, 256, 8), 256, 0, s>>>(LT, tile_row, lk, lv, bits, ek, ev, lcnt, cdeg);

@@ -94,14 +94,14 @@ def _contract_check(kmp, g, lab):
 @pytest.mark.parametrize("n,m", [(24000, 240000), (240000, 1200000)])
 def test_contract_row_classes(kmp, n, m):
     """Weighted clusters whose members' total degree falls in every
-    aggregation class (<= 512, <= 2048, <= 4096, <= 8192 and above), filled
+    aggregation class (<= 64, 128, 256, 512, 2048, 4096, 8192 and above), filled
     greedily up to each class bound; the other nodes stay singletons, so on
     the larger graph a row's neighbour ids span more than 2^17 coarse ids"""
     g = gg.with_weights(gg.random_graph(n, m, 11), 5, 9, 4)
     deg = np.diff(g.xadj)
     order = np.random.default_rng(3).permutation(g.n)
     lab = np.empty(g.n, np.int32)
-    targets = [300, 512, 2048, 4096, 8192, 30000]
+    targets = [40, 64, 100, 128, 200, 256, 300, 512, 2048, 4096, 8192, 30000]
     pos, c = 0, 0
     ubs = []
     for t in targets * 3:
@@ -116,8 +116,21 @@ def test_contract_row_classes(kmp, n, m):
         ubs.append(s)
     lab[order[pos:]] = order[pos:]           # the rest are singletons
     ubs = np.array(ubs)
-    for lo, hi in [(0, 512), (513, 2048), (2049, 4096), (4097, 8192), (8193, 1 << 40)]:
+    bounds = [0, 64, 128, 256, 512, 2048, 4096, 8192, 1 << 40]
+    for lo, hi in zip(bounds[:-1], bounds[1:]):
+        lo += 1
         assert ((ubs >= lo) & (ubs <= hi)).any(), (lo, hi)
+    _contract_check(kmp, g, lab)
+
+
+@pytest.mark.parametrize("group", [40, 100, 700])
+def test_contract_many_members(kmp, group):
+    """Clusters of `group` consecutive nodes of a sparse graph with many
+    isolated nodes: rows with more members than a warp or a CTA chunk holds,
+    most of them of degree 0"""
+    g = CASES["rand_iso"]
+    lab = ((np.arange(g.n) // group) * group).astype(np.int32)
+    assert (np.diff(g.xadj) == 0).sum() > g.n // 4
     _contract_check(kmp, g, lab)
 
 
