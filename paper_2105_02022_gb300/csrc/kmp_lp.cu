@@ -325,31 +325,61 @@ __device__ __forceinline__ void rate_group(const LPArgs &A, int32_t u, int32_t p
   if (gl == 0 && u >= 0) emit(A, u, pos, rown, mc, lc, mu, lu);
 }
 
+// slot of a table insert, when this insert occupied it (else -1)
+__device__ __forceinline__ int32_t ht_add_fresh(int32_t *keys, int32_t *vals, uint32_t mask, int32_t k,
+                                                int32_t w) {
+  uint32_t h = fmix32((uint32_t)k) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    int32_t old = atomicCAS(&keys[h], HT_EMPTY, k);
+    if (old == HT_EMPTY || old == k) {
+      atomicAdd(&vals[h], w);
+      return old == HT_EMPTY ? (int32_t)h : -1;
+    }
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
+// The shared tables of the warp and CTA bins start empty (cleared once per
+// launch) and every node leaves them empty: its inserts record the slots they
+// occupy in a list (at most cap / 2 distinct labels), and the selection pass
+// walks only that list, clearing each slot after reading it.  Table size and
+// hashing are unchanged, so per-node work scales with the distinct labels,
+// not with the table capacity.
+
 // one node per warp, neighbours aggregated in a shared-memory table of WARP_TAB
 __device__ __forceinline__ void rate_warp(const LPArgs &A, int32_t u, int32_t pos, int lane,
-                                          int32_t *keys, int32_t *vals) {
+                                          int32_t *keys, int32_t *vals, uint16_t *list) {
   int64_t beg = A.xadj[u];
   int32_t deg = (int32_t)(A.xadj[u + 1] - beg);
   uint32_t tcap = table_cap(deg, A.nlab);  // <= WARP_TAB for degree <= 256
-  for (uint32_t i = lane; i < tcap; i += 32) {
-    keys[i] = HT_EMPTY;
-    vals[i] = 0;
+  int32_t own = A.label[u], cu = node_w(A, u);
+  int32_t cnt = 0;
+  for (int32_t e0 = 0; e0 < deg; e0 += 32) {
+    int32_t e = e0 + lane;
+    int32_t sl = e < deg ? ht_add_fresh(keys, vals, tcap - 1, A.label[A.adj[beg + e]], edge_w(A, beg + e)) : -1;
+    unsigned m = __ballot_sync(0xFFFFFFFFu, sl >= 0);
+    if (sl >= 0) list[cnt + __popc(m & ((1u << lane) - 1u))] = (uint16_t)sl;
+    cnt += __popc(m);
   }
   __syncwarp();
-  int32_t own = A.label[u], cu = node_w(A, u);
-  for (int32_t e = lane; e < deg; e += 32)
-    ht_add(keys, vals, tcap - 1, A.label[A.adj[beg + e]], edge_w(A, beg + e));
-  __syncwarp();
-  int32_t rown = ht_get(keys, vals, tcap - 1, own);
+  int32_t rown = 0;
   uint64_t kc = 0, ku = 0;
   int32_t lc = -1, lu = -1;
-  for (uint32_t i = lane; i < tcap; i += 32) {
-    int32_t K = keys[i];
-    if (K == HT_EMPTY || K == own) continue;
-    uint64_t k = rate_key(A, K, vals[i]);
+  for (int32_t i = lane; i < cnt; i += 32) {
+    int32_t sl = list[i];
+    int32_t K = keys[sl], r = vals[sl];
+    keys[sl] = HT_EMPTY;
+    vals[sl] = 0;
+    if (K == own) {
+      rown = r;
+      continue;
+    }
+    uint64_t k = rate_key(A, K, r);
     if (k > ku) { ku = k; lu = K; }
     if ((int64_t)A.wt[K] + cu <= cap_of(A, K) && k > kc) { kc = k; lc = K; }
   }
+  rown = (int32_t)__reduce_max_sync(0xFFFFFFFFu, (uint32_t)rown);
   uint64_t mc = group_max64<32>(kc), mu = group_max64<32>(ku);
   unsigned bc = __ballot_sync(0xFFFFFFFFu, mc != 0 && kc == mc);
   unsigned bu = __ballot_sync(0xFFFFFFFFu, mu != 0 && ku == mu);
@@ -359,35 +389,51 @@ __device__ __forceinline__ void rate_warp(const LPArgs &A, int32_t u, int32_t po
   __syncwarp();
 }
 
-// one node per CTA with a table of `mask+1` entries (shared or global memory)
+// one node per CTA with a shared table of `mask+1` entries
 __device__ void rate_cta(const LPArgs &A, int32_t u, int32_t pos, int32_t *keys, int32_t *vals,
-                         uint32_t mask) {
+                         uint16_t *list, uint32_t mask) {
   __shared__ uint64_t red_c[RATE_T / 32], red_u[RATE_T / 32];
-  __shared__ int32_t lab_c, lab_u;
-  for (uint32_t i = threadIdx.x; i <= mask; i += blockDim.x) {
-    keys[i] = HT_EMPTY;
-    vals[i] = 0;
+  __shared__ int32_t lab_c, lab_u, s_cnt, s_rown;
+  if (threadIdx.x == 0) {
+    lab_c = -1;
+    lab_u = -1;
+    s_cnt = 0;
+    s_rown = 0;
   }
-  if (threadIdx.x == 0) { lab_c = -1; lab_u = -1; }
   __syncthreads();
   int64_t beg = A.xadj[u];
   int64_t deg = A.xadj[u + 1] - beg;
   int32_t own = A.label[u], cu = node_w(A, u);
-  for (int64_t e = threadIdx.x; e < deg; e += blockDim.x)
-    ht_add(keys, vals, mask, A.label[A.adj[beg + e]], edge_w(A, beg + e));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t e0 = threadIdx.x & ~31; e0 < deg; e0 += blockDim.x) {
+    int64_t e = e0 + lane;
+    int32_t sl = e < deg ? ht_add_fresh(keys, vals, mask, A.label[A.adj[beg + e]], edge_w(A, beg + e)) : -1;
+    unsigned m = __ballot_sync(0xFFFFFFFFu, sl >= 0);
+    if (m) {
+      int32_t at = 0;
+      if (lane == 0) at = atomicAdd(&s_cnt, __popc(m));
+      at = __shfl_sync(0xFFFFFFFFu, at, 0);
+      if (sl >= 0) list[at + __popc(m & ((1u << lane) - 1u))] = (uint16_t)sl;
+    }
+  }
   __syncthreads();
-  int32_t rown = ht_get(keys, vals, mask, own);
+  const int32_t cnt = s_cnt;
   uint64_t kc = 0, ku = 0;
   int32_t lc = -1, lu = -1;
-  for (uint32_t i = threadIdx.x; i <= mask; i += blockDim.x) {
-    int32_t K = keys[i];
-    if (K == HT_EMPTY || K == own) continue;
-    uint64_t k = rate_key(A, K, vals[i]);
+  for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    int32_t sl = list[i];
+    int32_t K = keys[sl], r = vals[sl];
+    keys[sl] = HT_EMPTY;
+    vals[sl] = 0;
+    if (K == own) {
+      s_rown = r;
+      continue;
+    }
+    uint64_t k = rate_key(A, K, r);
     if (k > ku) { ku = k; lu = K; }
     if ((int64_t)A.wt[K] + cu <= cap_of(A, K) && k > kc) { kc = k; lc = K; }
   }
   uint64_t wc = group_max64<32>(kc), wu = group_max64<32>(ku);
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) { red_c[w] = wc; red_u[w] = wu; }
   __syncthreads();
   uint64_t mc = 0, mu = 0;
@@ -398,7 +444,7 @@ __device__ void rate_cta(const LPArgs &A, int32_t u, int32_t pos, int32_t *keys,
   if (mc != 0 && kc == mc) lab_c = lc;  // unique label per key: benign identical writes
   if (mu != 0 && ku == mu) lab_u = lu;
   __syncthreads();
-  if (threadIdx.x == 0) emit(A, u, pos, rown, mc, lab_c, mu, lab_u);
+  if (threadIdx.x == 0) emit(A, u, pos, s_rown, mc, lab_c, mu, lab_u);
   __syncthreads();
 }
 
@@ -407,6 +453,7 @@ __device__ __forceinline__ int32_t hub_index(const LPArgs &A, int32_t u);
 __global__ void __launch_bounds__(RATE_T) k_rate(LPArgs A, int s) {
   __shared__ int32_t tkeys[CTA_TAB];
   __shared__ int32_t tvals[CTA_TAB];
+  __shared__ uint16_t tlist[CTA_TAB / 2];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     A.ctr[0] = 0;
     A.ctr[1] = 0;
@@ -418,6 +465,14 @@ __global__ void __launch_bounds__(RATE_T) k_rate(LPArgs A, int s) {
   int64_t gw = (int64_t)blockIdx.x * (RATE_T / 32) + w;
   int64_t nw = (int64_t)gridDim.x * (RATE_T / 32);
   const int32_t *bo = A.boff + s * NB;
+  if ((int64_t)bo[4] + (int64_t)blockIdx.x * (RATE_T / 32) < bo[5] ||
+      (int64_t)bo[5] + blockIdx.x < ((A.small_labels && !A.hdense) ? bo[7] : bo[6])) {
+    for (int i = threadIdx.x; i < CTA_TAB; i += blockDim.x) {  // only blocks with table work
+      tkeys[i] = HT_EMPTY;
+      tvals[i] = 0;
+    }
+  }
+  __syncthreads();
 #define KMP_GROUP_BIN(BIN, G)                                                  \
   {                                                                            \
     int32_t lo = bo[BIN], hi = bo[BIN + 1];                                    \
@@ -436,7 +491,8 @@ __global__ void __launch_bounds__(RATE_T) k_rate(LPArgs A, int s) {
   {
     int32_t lo = bo[4], hi = bo[5];
     for (int64_t idx = lo + gw; idx < hi; idx += nw)
-      rate_warp(A, A.vlist[idx], (int32_t)idx, lane, tkeys + w * WARP_TAB, tvals + w * WARP_TAB);
+      rate_warp(A, A.vlist[idx], (int32_t)idx, lane, tkeys + w * WARP_TAB, tvals + w * WARP_TAB,
+                tlist + w * (WARP_TAB / 2));
   }
   __syncthreads();
   {
@@ -446,7 +502,7 @@ __global__ void __launch_bounds__(RATE_T) k_rate(LPArgs A, int s) {
     for (int64_t idx = lo + blockIdx.x; idx < hi; idx += gridDim.x) {
       int32_t u = A.vlist[idx];
       uint32_t cap = table_cap(A.xadj[u + 1] - A.xadj[u], A.nlab);
-      rate_cta(A, u, (int32_t)idx, tkeys, tvals, cap - 1);
+      rate_cta(A, u, (int32_t)idx, tkeys, tvals, tlist, cap - 1);
     }
   }
   if (A.tmin) {
