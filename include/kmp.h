@@ -243,7 +243,8 @@ typedef struct {
   int32_t rate_blocks_per_sm; /* LP rating grid = this * SMs (2..16) */
   int32_t hub_degree;         /* degree above which coarsening rates a node with the
                                  multi-CTA hub kernels (256..2048) */
-  int32_t hub_chunk;          /* edges per hub work unit (256..65536, power of two) */
+  int32_t hub_chunk;          /* edges per hub work unit (256..65536, power of two;
+                                 default 512) */
   int32_t ip_blocks_per_sm;   /* bipartitioner CTAs per SM (1..8) */
   int32_t dense_hub_degree;   /* with few labels (refinement: labels are block ids), degree
                                  above which a node's rating is split over many CTAs into a
@@ -259,7 +260,7 @@ int kmp_get_tuning(kmp_tuning *t);
  * (one run per candidate, cap derived from k and eps as the partitioner
  * does), keeps the fastest with kmp_set_tuning and returns it in *best.
  * Candidates: rating grid {4, 6, 8} x SMs, hub degree {1024, 2048}, hub chunk
- * {1024, 4096}.
+ * {512, 2048}.
  */
 int kmp_autotune(const kmp_graph *g, int32_t k, double eps, uint64_t seed, kmp_tuning *best);
 

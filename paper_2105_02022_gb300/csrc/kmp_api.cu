@@ -659,7 +659,7 @@ int kmp_autotune(const kmp_graph *g, int32_t k, double eps, uint64_t seed, kmp_t
     DBuf<int32_t> label(G.n > 0 ? G.n : 1);
     const int grids[3] = {4, 6, 8};
     const int hubs[2] = {1024, 2048};
-    const int chunks[2] = {1024, 4096};
+    const int chunks[2] = {512, 2048};
     for (int gi : grids)
       for (int hd : hubs)
         for (int hc : chunks) {
