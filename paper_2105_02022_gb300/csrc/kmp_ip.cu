@@ -270,6 +270,52 @@ __device__ void item_rate(const LG &g, int32_t u, const int32_t *label, const in
   __syncwarp();
 }
 
+// rating of 32 / G nodes by one warp, G lanes per node (degree <= G, one
+// neighbour per lane; u < 0: no node): lanes of a group holding the same
+// label form a peer set whose weight sum is that label's rating.  Same
+// decision as item_rate.
+template <int G>
+__device__ __forceinline__ void item_rate_group(const LG &g, int32_t u, const int32_t *label, const int32_t *wt,
+                                                int32_t U, uint32_t rk_hi, int32_t *out_t, int32_t *out_g) {
+  const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+  const unsigned gmask = (G == 32) ? 0xFFFFFFFFu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  int32_t b = 0, deg = 0, own = -1, cu = 0;
+  if (u >= 0) {
+    b = g.xadj[u];
+    deg = g.xadj[u + 1] - b;
+    own = label[u];
+    cu = g.vw[u];
+  }
+  int32_t l = -1, x = 0;
+  if (gl < deg) {
+    l = label[g.adj[b + gl]];
+    x = g.ew[b + gl];
+  }
+  unsigned peers = __match_any_sync(0xFFFFFFFFu, ((uint64_t)(uint32_t)(lane / G) << 32) | (uint32_t)l);
+  int32_t r = __reduce_add_sync(peers, x);
+  unsigned bown = __ballot_sync(0xFFFFFFFFu, l >= 0 && l == own) & gmask;
+  int32_t rown = __shfl_sync(0xFFFFFFFFu, r, bown ? __ffs(bown) - 1 : lane);
+  if (!bown) rown = 0;
+  bool adm = l >= 0 && l != own && (int64_t)wt[l] + cu <= U;
+  uint64_t k = adm ? ((uint64_t)(uint32_t)r << 32) | (uint64_t)(0xFFFFFFFFu - perm32(rk_hi, l)) : 0ull;
+  uint64_t mc = group_max64<G>(k);
+  unsigned bc = __ballot_sync(0xFFFFFFFFu, mc != 0 && k == mc) & gmask;
+  int32_t lc = __shfl_sync(0xFFFFFFFFu, l, bc ? __ffs(bc) - 1 : lane);
+  if (gl == 0 && u >= 0) {
+    int32_t rc = (int32_t)(mc >> 32);
+    if (mc != 0 && rc > rown) {
+      *out_t = lc;
+      *out_g = rc - rown;
+    } else {
+      *out_t = -1;
+    }
+  }
+}
+
+// degree class of a node for the item rating schedule: 0 (<= 16, two nodes
+// per warp), 1 (<= 32, one node per warp, no table), 2 (table)
+__device__ __forceinline__ int32_t item_deg_class(int32_t deg) { return deg <= 16 ? 0 : (deg <= 32 ? 1 : 2); }
+
 // segmented inclusive scan in shared memory (one element per thread)
 __device__ int64_t block_seg_scan(int64_t x, bool head) {
   __shared__ int64_t sv[IPT];
@@ -366,37 +412,55 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
   for (int32_t r = 0; r < A.ip_lp_rounds; ++r) {
     uint64_t rk = key_step(basekey, (uint64_t)r);
     uint32_t rk_hi = (uint32_t)(rk >> 32);
-    // the round's active nodes (with edges) bucketed by sub-round
-    __shared__ int32_t s_soff[9], s_fill[8];
-    if (threadIdx.x < 8) s_fill[threadIdx.x] = 0;
+    // the round's active nodes (with edges) bucketed by sub-round and, inside
+    // a sub-round, by degree class (the rating schedule; any order inside a
+    // sub-round gives the same result)
+    __shared__ int32_t s_soff[3 * 8 + 1], s_fill[3 * 8];
+    if (threadIdx.x < 3 * 8) s_fill[threadIdx.x] = 0;
     if (threadIdx.x == 0) s_moved = 0;
     __syncthreads();
     for (int32_t v = threadIdx.x; v < n; v += IPT) {
       act2[v] = 0;
-      if (act[v] && g.xadj[v + 1] > g.xadj[v])
-        atomicAdd(&s_fill[(int32_t)(key_step(rk, (uint64_t)(uint32_t)v) & (uint64_t)(A.S - 1))], 1);
+      int32_t d = g.xadj[v + 1] - g.xadj[v];
+      if (act[v] && d > 0)
+        atomicAdd(&s_fill[3 * (int32_t)(key_step(rk, (uint64_t)(uint32_t)v) & (uint64_t)(A.S - 1)) +
+                          item_deg_class(d)],
+                  1);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       s_soff[0] = 0;
-      for (int32_t x = 0; x < A.S; ++x) {
+      for (int32_t x = 0; x < 3 * A.S; ++x) {
         s_soff[x + 1] = s_soff[x] + s_fill[x];
         s_fill[x] = 0;
       }
     }
     __syncthreads();
-    for (int32_t v = threadIdx.x; v < n; v += IPT)
-      if (act[v] && g.xadj[v + 1] > g.xadj[v]) {
-        int32_t x = (int32_t)(key_step(rk, (uint64_t)(uint32_t)v) & (uint64_t)(A.S - 1));
+    for (int32_t v = threadIdx.x; v < n; v += IPT) {
+      int32_t d = g.xadj[v + 1] - g.xadj[v];
+      if (act[v] && d > 0) {
+        int32_t x = 3 * (int32_t)(key_step(rk, (uint64_t)(uint32_t)v) & (uint64_t)(A.S - 1)) + item_deg_class(d);
         sl[s_soff[x] + atomicAdd(&s_fill[x], 1)] = v;
       }
+    }
     __syncthreads();
     for (int32_t s = 0; s < A.S; ++s) {
-      const int32_t lo = s_soff[s], hi = s_soff[s + 1];
+      const int32_t lo = s_soff[3 * s], hi = s_soff[3 * s + 3];
+      const int32_t m1 = s_soff[3 * s + 1], m2 = s_soff[3 * s + 2];
       // contested proposals are at most the sub-round's nodes
       uint64_t *pl = pow2_at_least(hi - lo > 1 ? hi - lo : 2) <= pl_cap ? pl_s : pl_g;
-      // rating
-      for (int32_t i = lo + w; i < hi; i += IPW) {
+      // rating: two nodes per warp, then one per warp without a table, then
+      // one per warp with a table
+      for (int32_t i0 = lo + 2 * w; i0 < m1; i0 += 2 * IPW) {
+        int32_t i = i0 + (lane >> 4);
+        int32_t u = i < m1 ? sl[i] : -1;
+        item_rate_group<16>(g, u, lab, wt, U, rk_hi, u >= 0 ? &pt[u] : nullptr, u >= 0 ? &pg[u] : nullptr);
+      }
+      for (int32_t i = m1 + w; i < m2; i += IPW) {
+        int32_t u = sl[i];
+        item_rate_group<32>(g, u, lab, wt, U, rk_hi, &pt[u], &pg[u]);
+      }
+      for (int32_t i = m2 + w; i < hi; i += IPW) {
         int32_t u = sl[i];
         item_rate(g, u, lab, wt, U, rk_hi, mk, mv, gk, gv, &pt[u], &pg[u]);
       }
@@ -818,16 +882,17 @@ __device__ int64_t warp_fm(const IPArgs &A, const LG &g, int32_t *side, int64_t 
 }
 
 // the same FM with the whole CTA: cut, gains and weights of every pass by all
-// warps (a warp per node, lanes over its row), the moves by warp 0
+// warps (a half-warp per node, its 16 lanes over the row), the moves by warp 0
 __device__ int64_t cta_fm(const IPArgs &A, const LG &g, int32_t *side, int64_t L0, int64_t L1, FMBuf fb) {
   __shared__ int64_t s_cut;
   __shared__ int32_t s_kept;
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int hl = lane & 15, hf = lane >> 4;
   int32_t n = g.n;
   int64_t c = 0;
-  for (int32_t v = w; v < n; v += IPW) {
+  for (int32_t v = 2 * w + hf; v < n; v += 2 * IPW) {
     int32_t sv = side[v];
-    for (int32_t q = g.xadj[v] + lane; q < g.xadj[v + 1]; q += 32)
+    for (int32_t q = g.xadj[v] + hl; q < g.xadj[v + 1]; q += 16)
       if (side[g.adj[q]] != sv) c += g.ew[q];
   }
   int64_t cut = block_sum64(c) / 2;
@@ -837,12 +902,17 @@ __device__ int64_t cta_fm(const IPArgs &A, const LG &g, int32_t *side, int64_t L
       if (side[v] == 0) W0 += g.vw[v];
       else W1 += g.vw[v];
     }
-    for (int32_t v = w; v < n; v += IPW) {
-      int32_t sv = side[v], gs = 0;
-      for (int32_t q = g.xadj[v] + lane; q < g.xadj[v + 1]; q += 32)
-        gs += (side[g.adj[q]] != sv) ? g.ew[q] : -g.ew[q];
-      gs = warp_sum32(gs);
-      if (lane == 0) {
+    for (int32_t v0 = 2 * w; v0 < n; v0 += 2 * IPW) {
+      const int32_t v = v0 + hf;
+      int32_t sv = 0, gs = 0;
+      if (v < n) {
+        sv = side[v];
+        for (int32_t q = g.xadj[v] + hl; q < g.xadj[v + 1]; q += 16)
+          gs += (side[g.adj[q]] != sv) ? g.ew[q] : -g.ew[q];
+      }
+#pragma unroll
+      for (int m = 8; m > 0; m >>= 1) gs += __shfl_xor_sync(0xFFFFFFFFu, gs, m);  // within the half
+      if (hl == 0 && v < n) {
         fb.gain[v] = gs;
         fb.locked[v] = 0;
         fb.key0[v] = sv == 0 ? fm_key(gs, v) : 0;
