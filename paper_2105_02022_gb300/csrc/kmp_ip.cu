@@ -274,29 +274,42 @@ __device__ void item_rate(const LG &g, int32_t u, const int32_t *label, const in
 // neighbour per lane; u < 0: no node): lanes of a group holding the same
 // label form a peer set whose weight sum is that label's rating.  Same
 // decision as item_rate.
+// loads of one group node: neighbour label and edge weight of this lane,
+// own label and node weight (u < 0: no node)
+struct GroupIn {
+  int32_t l, x, own, cu;
+};
 template <int G>
-__device__ __forceinline__ void item_rate_group(const LG &g, int32_t u, const int32_t *label, const int32_t *wt,
-                                                int32_t U, uint32_t rk_hi, int32_t *out_t, int32_t *out_g) {
+__device__ __forceinline__ GroupIn item_group_load(const LG &g, int32_t u, const int32_t *label) {
+  const int gl = (threadIdx.x & 31) & (G - 1);
+  GroupIn r{-1, 0, -1, 0};
+  if (u >= 0) {
+    int32_t b = g.xadj[u], deg = g.xadj[u + 1] - b;
+    r.own = label[u];
+    r.cu = g.vw[u];
+    if (gl < deg) {
+      r.l = label[g.adj[b + gl]];
+      r.x = g.ew[b + gl];
+    }
+  }
+  return r;
+}
+
+// rating of 32 / G nodes by one warp, G lanes per node (degree <= G, one
+// neighbour per lane): lanes of a group holding the same label form a peer
+// set whose weight sum is that label's rating.  Same decision as item_rate.
+template <int G>
+__device__ __forceinline__ void item_group_rate(const GroupIn &in, int32_t u, const int32_t *wt, int32_t U,
+                                                uint32_t rk_hi, int32_t *pt, int32_t *pg) {
   const int lane = threadIdx.x & 31, gl = lane & (G - 1);
   const unsigned gmask = (G == 32) ? 0xFFFFFFFFu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-  int32_t b = 0, deg = 0, own = -1, cu = 0;
-  if (u >= 0) {
-    b = g.xadj[u];
-    deg = g.xadj[u + 1] - b;
-    own = label[u];
-    cu = g.vw[u];
-  }
-  int32_t l = -1, x = 0;
-  if (gl < deg) {
-    l = label[g.adj[b + gl]];
-    x = g.ew[b + gl];
-  }
+  const int32_t l = in.l;
   unsigned peers = __match_any_sync(0xFFFFFFFFu, ((uint64_t)(uint32_t)(lane / G) << 32) | (uint32_t)l);
-  int32_t r = __reduce_add_sync(peers, x);
-  unsigned bown = __ballot_sync(0xFFFFFFFFu, l >= 0 && l == own) & gmask;
+  int32_t r = __reduce_add_sync(peers, in.x);
+  unsigned bown = __ballot_sync(0xFFFFFFFFu, l >= 0 && l == in.own) & gmask;
   int32_t rown = __shfl_sync(0xFFFFFFFFu, r, bown ? __ffs(bown) - 1 : lane);
   if (!bown) rown = 0;
-  bool adm = l >= 0 && l != own && (int64_t)wt[l] + cu <= U;
+  bool adm = l >= 0 && l != in.own && (int64_t)wt[l] + in.cu <= U;
   uint64_t k = adm ? ((uint64_t)(uint32_t)r << 32) | (uint64_t)(0xFFFFFFFFu - perm32(rk_hi, l)) : 0ull;
   uint64_t mc = group_max64<G>(k);
   unsigned bc = __ballot_sync(0xFFFFFFFFu, mc != 0 && k == mc) & gmask;
@@ -304,11 +317,26 @@ __device__ __forceinline__ void item_rate_group(const LG &g, int32_t u, const in
   if (gl == 0 && u >= 0) {
     int32_t rc = (int32_t)(mc >> 32);
     if (mc != 0 && rc > rown) {
-      *out_t = lc;
-      *out_g = rc - rown;
+      pt[u] = lc;
+      pg[u] = rc - rown;
     } else {
-      *out_t = -1;
+      pt[u] = -1;
     }
+  }
+}
+
+// the nodes sl[lo..hi) rated 32 / G per warp step
+template <int G>
+__device__ __forceinline__ void item_rate_groups(const LG &g, const int32_t *sl, int32_t lo, int32_t hi,
+                                                 const int32_t *label, const int32_t *wt, int32_t U,
+                                                 uint32_t rk_hi, int32_t *pt, int32_t *pg) {
+  constexpr int per = 32 / G;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int32_t i0 = lo + per * w; i0 < hi; i0 += per * IPW) {
+    int32_t i = i0 + lane / G;
+    int32_t u = i < hi ? sl[i] : -1;
+    GroupIn a = item_group_load<G>(g, u, label);
+    item_group_rate<G>(a, u, wt, U, rk_hi, pt, pg);
   }
 }
 
@@ -451,15 +479,8 @@ __device__ int32_t item_cluster(const IPArgs &A, const LG &g, int32_t U, uint64_
       uint64_t *pl = pow2_at_least(hi - lo > 1 ? hi - lo : 2) <= pl_cap ? pl_s : pl_g;
       // rating: two nodes per warp, then one per warp without a table, then
       // one per warp with a table
-      for (int32_t i0 = lo + 2 * w; i0 < m1; i0 += 2 * IPW) {
-        int32_t i = i0 + (lane >> 4);
-        int32_t u = i < m1 ? sl[i] : -1;
-        item_rate_group<16>(g, u, lab, wt, U, rk_hi, u >= 0 ? &pt[u] : nullptr, u >= 0 ? &pg[u] : nullptr);
-      }
-      for (int32_t i = m1 + w; i < m2; i += IPW) {
-        int32_t u = sl[i];
-        item_rate_group<32>(g, u, lab, wt, U, rk_hi, &pt[u], &pg[u]);
-      }
+      item_rate_groups<16>(g, sl, lo, m1, lab, wt, U, rk_hi, pt, pg);
+      item_rate_groups<32>(g, sl, m1, m2, lab, wt, U, rk_hi, pt, pg);
       for (int32_t i = m2 + w; i < hi; i += IPW) {
         int32_t u = sl[i];
         item_rate(g, u, lab, wt, U, rk_hi, mk, mv, gk, gv, &pt[u], &pg[u]);
@@ -684,11 +705,37 @@ __device__ void item_contract(const LG &g, const int32_t *label, int32_t *map, L
       V[i] = 0;
     }
     __syncwarp();
-    for (int32_t mi = moff[x]; mi < moff[x + 1]; ++mi) {
-      int32_t v = members[mi];
-      for (int32_t q = g.xadj[v] + lane; q < g.xadj[v + 1]; q += 32) {
-        int32_t y = map[g.adj[q]];
-        if (y != x) ht_add(K, V, cap - 1, y, g.ew[q]);
+    // up to 32 members at a time spread their edges over the lanes: a warp
+    // prefix of their degrees, and each lane finds the member of its edge
+    for (int32_t c0 = moff[x]; c0 < moff[x + 1]; c0 += 32) {
+      int32_t d = 0, b = 0;
+      if (c0 + lane < moff[x + 1]) {
+        int32_t v = members[c0 + lane];
+        b = g.xadj[v];
+        d = g.xadj[v + 1] - b;
+      }
+      int32_t inc = d;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int32_t t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      const int32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+      for (int32_t e0 = 0; e0 < tot; e0 += 32) {
+        const int32_t e = e0 + lane;
+        int32_t j = 0;  // members before the owner of edge e
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+          int32_t t = __shfl_sync(0xFFFFFFFFu, inc, j + st - 1);
+          if (t <= e) j += st;
+        }
+        int32_t bj = __shfl_sync(0xFFFFFFFFu, b, j & 31);
+        int32_t ej = __shfl_sync(0xFFFFFFFFu, inc - d, j & 31);
+        if (e < tot) {
+          int32_t q = bj + (e - ej);
+          int32_t y = map[g.adj[q]];
+          if (y != x) ht_add(K, V, cap - 1, y, g.ew[q]);
+        }
       }
     }
     __syncwarp();
