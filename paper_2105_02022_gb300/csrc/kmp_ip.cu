@@ -832,8 +832,20 @@ __device__ int32_t fm_pass_moves(const IPArgs &A, const LG &g, int32_t *side, in
     if (t0 == 0 && t1 == 0) break;
     int32_t v0 = t0 ? (int32_t)(0xFFFFFFFFu - (uint32_t)t0) : -1;
     int32_t v1 = t1 ? (int32_t)(0xFFFFFFFFu - (uint32_t)t1) : -1;
-    bool f0 = v0 >= 0 && W1 + g.vw[v0] <= L1;
-    bool f1 = v1 >= 0 && W0 + g.vw[v1] <= L0;
+    // both candidates' weights and row bounds in one round of loads
+    int32_t c0 = 0, c1 = 0, b0 = 0, e0 = 0, b1 = 0, e1 = 0;
+    if (v0 >= 0) {
+      c0 = g.vw[v0];
+      b0 = g.xadj[v0];
+      e0 = g.xadj[v0 + 1];
+    }
+    if (v1 >= 0) {
+      c1 = g.vw[v1];
+      b1 = g.xadj[v1];
+      e1 = g.xadj[v1 + 1];
+    }
+    bool f0 = v0 >= 0 && W1 + c0 <= L1;
+    bool f1 = v1 >= 0 && W0 + c1 <= L0;
     int32_t v;
     if (f0 && f1) v = (t0 > t1) ? v0 : v1;
     else if (f0) v = v0;
@@ -861,10 +873,12 @@ __device__ int32_t fm_pass_moves(const IPArgs &A, const LG &g, int32_t *side, in
       fb.key0[v] = 0;
       fb.key1[v] = 0;
     }
-    int32_t c = g.vw[v];
+    const bool is0 = v == v0;
+    int32_t c = is0 ? c0 : c1;
     if (from == 0) { W0 -= c; W1 += c; } else { W1 -= c; W0 += c; }
     cut -= gv;
-    for (int32_t q = g.xadj[v] + lane; q < g.xadj[v + 1]; q += 32) {
+    const int32_t qe = is0 ? e0 : e1;
+    for (int32_t q = (is0 ? b0 : b1) + lane; q < qe; q += 32) {
       int32_t x = g.adj[q];
       int32_t sx = side[x];
       int32_t gx = fb.gain[x] + (sx == to ? -2 * g.ew[q] : 2 * g.ew[q]);
