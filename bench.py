@@ -149,6 +149,34 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def ksweep(gg, kmp, torch, np):
+    """Large-k sweep (deep multilevel at k up to n / 16): time, cut, balance and
+    feasibility of one partition per k after a warm-up partition at the same k."""
+    kmp.load()
+    kmp.set_config(kmp.config())
+    t0 = time.perf_counter()
+    g = gg.rgg(1 << 24, 16, SEED)
+    gen_s = time.perf_counter() - t0
+    dg = kmp.DeviceGraph.from_host(g)
+    for k in (1 << 11, 1 << 14, 1 << 17, 1 << 20):
+        kmp.partition_graph(dg, k, EPS, SEED)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        part, rc, st = kmp.partition_graph(dg, k, EPS, SEED)
+        e1.record()
+        e1.synchronize()
+        bw = np.bincount(part.cpu().numpy(), minlength=k)
+        lk = int(np.floor((1.0 + EPS) * ((g.n + k - 1) // k)))
+        print(json.dumps({"mode": "ksweep", "workload": "rgg_2^24_deg16", "n": g.n, "m_directed": g.m_directed,
+                          "k": k, "ms": e0.elapsed_time(e1), "cut": int(st.cut), "feasible": bool(st.feasible),
+                          "rc": rc, "max_block_weight": int(bw.max()), "L_k": lk,
+                          "overloaded_blocks": int((bw > lk).sum()), "levels": int(st.levels),
+                          "ip_items": int(st.ip_items), "phase_ms": {"lp": st.ms_lp, "contract": st.ms_contract,
+                          "ip": st.ms_ip, "balance": st.ms_balance, "refine": st.ms_refine},
+                          "generate_s": gen_s}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -156,10 +184,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="partition", choices=["partition", "coarsen1", "launchlist"],
+    ap.add_argument("--mode", default="partition", choices=["partition", "coarsen1", "launchlist", "ksweep"],
                     help="coarsen1: one level-0 coarsening (LP) of the workload graph only; "
                          "launchlist: one warm-up partition and one partition inside the NVTX "
-                         "range kmp_step (for ncu launch lists); both are used for kernel profiles")
+                         "range kmp_step (for ncu launch lists); both are used for kernel profiles; "
+                         "ksweep: the large-k sweep k in {2^11, 2^14, 2^17, 2^20} on the 2D random "
+                         "geometric graph with 2^24 nodes (average degree 16), one JSON line per k")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -176,6 +206,9 @@ def main():
     from paper_2105_02022_gb300 import kmp
 
     torch.cuda.set_device(local)
+    if args.mode == "ksweep":
+        ksweep(gg, kmp, torch, np)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -109,6 +109,9 @@ PARTS = [
     ("rgg_w", lambda: gg.with_weights(gg.rgg(12000, 8, 6), 5, 9, 6), [7, 16]),
     ("rmat14", lambda: gg.rmat(14, 16, 2), [32, 5]),
     ("hubs", lambda: gg.hubs(30000, [3000, 12000], 60000, 8), [16]),
+    # 16 nodes per block: L_k leaves no slack, so the result may be infeasible
+    # (both sides must agree on that too)
+    ("rgg15_k2048", lambda: gg.workload_rgg_small(1), [2048]),
 ]
 
 
