@@ -102,6 +102,25 @@ def test_balance_parity(kmp, case):
     assert np.array_equal(pt.cpu().numpy(), rp)
 
 
+def test_balance_many_adjacent_overloaded_blocks(kmp):
+    """480 blocks of 15 and 10 nodes alternating over an RGG whose ids are
+    spatially local, cap 12: half the blocks are overloaded and most border
+    another one, so candidates' connectivities change as earlier blocks are
+    emptied (the cases the speculative schedule must hand to the exact commit)"""
+    g = gg.rgg(6000, 8, 3)
+    k = 480
+    sizes = np.where(np.arange(k) % 2 == 0, 15, 10)
+    sizes[-1] += g.n - sizes.sum()
+    part = np.repeat(np.arange(k), sizes).astype(np.int32)
+    cap = np.full(k, int(1.03 * g.n / k), np.int64)
+    dg = kmp.DeviceGraph.from_host(g)
+    pt = torch.from_numpy(part).cuda()
+    mv = kmp.balance(dg, k, cap, pt)
+    rp, rmv = O.balance(g, k, cap.astype(np.int32), part)
+    assert mv == rmv and mv > 0
+    assert np.array_equal(pt.cpu().numpy(), rp)
+
+
 PARTS = [
     ("path", lambda: gg.path(700), [2, 5]),
     ("grid", lambda: gg.grid(40, 60), [2, 4, 7]),
