@@ -177,6 +177,28 @@ def ksweep(gg, kmp, torch, np):
                           "generate_s": gen_s}), flush=True)
 
 
+def replicas(gg, kmp, torch, np):
+    """Replication of the coarsest levels (Section 3, "Parallelization"):
+    median of three partitions per R after a warm-up, same seed."""
+    kmp.load()
+    for name, g, k in (("rmat_scale20_ef16", gg.workload_rmat20(SEED), K_BLOCKS),
+                       ("rgg_2^15_deg8", gg.workload_rgg_small(SEED), 8)):
+        dg = kmp.DeviceGraph.from_host(g)
+        for R in (1, 2, 4, 8):
+            kmp.set_config(kmp.config(replicas=R))
+            kmp.partition_graph(dg, k, EPS, SEED)
+            ms, st = [], None
+            for _ in range(3):
+                torch.cuda.synchronize()
+                _, rc, st = kmp.partition_graph(dg, k, EPS, SEED)
+                ms.append(st.ms_total)
+            print(json.dumps({"mode": "replicas", "workload": name, "k": k, "replicas": R,
+                              "ms": statistics.median(ms), "cut": int(st.cut), "feasible": bool(st.feasible),
+                              "levels": int(st.levels), "ip_items": int(st.ip_items)}), flush=True)
+        del dg
+    kmp.set_config(kmp.config())
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -184,12 +206,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="partition", choices=["partition", "coarsen1", "launchlist", "ksweep"],
+    ap.add_argument("--mode", default="partition",
+                    choices=["partition", "coarsen1", "launchlist", "ksweep", "replicas"],
                     help="coarsen1: one level-0 coarsening (LP) of the workload graph only; "
                          "launchlist: one warm-up partition and one partition inside the NVTX "
                          "range kmp_step (for ncu launch lists); both are used for kernel profiles; "
                          "ksweep: the large-k sweep k in {2^11, 2^14, 2^17, 2^20} on the 2D random "
-                         "geometric graph with 2^24 nodes (average degree 16), one JSON line per k")
+                         "geometric graph with 2^24 nodes (average degree 16), one JSON line per k; "
+                         "replicas: cut and time with R = 1, 2, 4, 8 copies of the coarsest levels "
+                         "on the benchmark graph (k = 256) and the small RGG (k = 8)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -208,6 +233,9 @@ def main():
     torch.cuda.set_device(local)
     if args.mode == "ksweep":
         ksweep(gg, kmp, torch, np)
+        return
+    if args.mode == "replicas":
+        replicas(gg, kmp, torch, np)
         return
     dist = None
     if world > 1:

@@ -75,6 +75,11 @@ typedef struct {
   int32_t lrep_random;   /* learned-mode repetitions (each at most its rep_*): random (0) */
   int32_t lrep_bfs;      /* BFS (0) */
   int32_t lrep_ggg;      /* greedy graph growing (1) */
+  int32_t replicas;      /* R, a power of two in 1..64 (1 = off): the coarsest graph is taken by
+                            two copies, each coarsened further and partitioned on its own with
+                            R/2 under its own seed, and the better partition is kept (feasible
+                            first, then the smaller cut); coarsening stops at max(R, 2) C nodes
+                            (Section 3, "Parallelization", with R in the role of the PEs) */
 } kmp_config;
 
 /* Per-call measurements of kmp_partition / kmp_partition_graph (CUDA events). */

@@ -43,6 +43,7 @@ typedef struct {
   int32_t lrep_random;   /* portfolio repetitions in learned mode */
   int32_t lrep_bfs;
   int32_t lrep_ggg;
+  int32_t replicas;      /* R, copies of the coarsest graph (Section 3, "Parallelization"): 1 = off */
 } kmpo_config;
 
 /* graph owned by the oracle (returned by kmpo_contract) */

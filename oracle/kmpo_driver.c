@@ -30,6 +30,18 @@
  *     until the block fits.
  *  D6 Final feasibility uses L_k = floor((1+eps) ceil(c(V)/k)) (Section 2,
  *     footnote; Section 5).
+ *  D7 Replication (Section 3, "Parallelization"), with R = cfg->replicas
+ *     standing for the PEs p: coarsening stops at n_i <= max(R, 2) C instead
+ *     of 2C.  For R >= 2 the coarsest graph G_C is then taken by two copies,
+ *     each solved recursively with R/2 from G_C under its own seed
+ *     key(seed, {10, copy}): it coarsens further (with R/2, the same k'
+ *     schedule and U), partitions and uncoarsens back to G_C, where its
+ *     blocks follow the G_C rule k_i = ceil2(n_C / C).  The better of the two
+ *     partitions of G_C is kept: the feasible one if only one is feasible
+ *     under the D4 caps, else the one with the smaller cut, the first copy on
+ *     a tie.  From G_C on the run continues as before (split rounds if
+ *     applicable, balancing, refinement, then the finer levels).  R = 1 is
+ *     the plain method.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -38,7 +50,7 @@
 
 #include "kmpo.h"
 
-enum { DOM_COARSEN = 1, DOM_IP = 3, DOM_REFINE_LEVEL = 8 };
+enum { DOM_COARSEN = 1, DOM_IP = 3, DOM_REFINE_LEVEL = 8, DOM_REPLICA = 10 };
 
 uint64_t kmpo_step(uint64_t x, uint64_t w);
 
@@ -70,6 +82,7 @@ void kmpo_config_default(kmpo_config *c) {
   c->lrep_random = 0;
   c->lrep_bfs = 0;
   c->lrep_ggg = 1;
+  c->replicas = 1;
 }
 
 static int32_t ceil_log2(int32_t f) {
@@ -306,34 +319,41 @@ int32_t kmpo_bipartition_blocks(int32_t n, const int64_t *xadj, const int32_t *a
   return nb;
 }
 
-int32_t kmpo_partition(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
-                       const int32_t *ew, int32_t k, double eps, uint64_t seed,
-                       const kmpo_config *cfg, int32_t *part_out, kmpo_stats *st) {
-  double t0 = now_s();
-  kmpo_stats dummy;
-  if (!st) st = &dummy;
-  memset(st, 0, sizeof(*st));
-  if (k <= 1) {
-    for (int32_t v = 0; v < n; ++v) part_out[v] = 0;
-    st->feasible = 1;
-    return 0;
-  }
-  int64_t cV = 0;
-  for (int32_t v = 0; v < n; ++v) cV += vwt(vw, v);
+/* D4 feasibility of a partition of one level */
+static int level_feasible(const glvl_t *g, const int32_t *part, int32_t nblocks, const int32_t *f,
+                          double eps, int64_t cV, int32_t k) {
+  int64_t *bw = (int64_t *)calloc((size_t)nblocks, sizeof(int64_t));
+  for (int32_t v = 0; v < g->n; ++v) bw[part[v]] += vwt(g->vw, v);
+  int32_t maxc = max_vw(g->n, g->vw);
+  int ok = 1;
+  for (int32_t b = 0; b < nblocks; ++b)
+    if (bw[b] > kmpo_block_cap(eps, cV, k, f[b], maxc)) ok = 0;
+  free(bw);
+  return ok;
+}
+
+typedef struct {
+  int32_t *part;  /* on the hierarchy's first graph */
+  int32_t nblocks;
+  int32_t *f;     /* final block counts, 2k + 2 entries */
+} deep_out;
+
+/* Algorithm 1 on the hierarchy that starts at G0 (D1, D2, D7); `input`: G0 is
+ * the input graph (k_i = k there); `top`: record the level statistics */
+static void deep(const glvl_t *G0, int32_t R, uint64_t seed, int input, int top, int32_t n_in,
+                 int32_t k, double eps, int64_t cV, const kmpo_config *cfg, kmpo_stats *st,
+                 double *tip, double *tref, deep_out *out) {
   glvl_t lv[64];
   int32_t nl = 1;
-  lv[0].n = n;
-  lv[0].xadj = (int64_t *)xadj;
-  lv[0].adj = (int32_t *)adj;
-  lv[0].vw = (int32_t *)vw;
-  lv[0].ew = (int32_t *)ew;
+  lv[0] = *G0;
   lv[0].map = NULL;
   lv[0].owned = 0;
-  int64_t kp = n / cfg->C;
+  int64_t kp = n_in / cfg->C;
   if (kp > k) kp = k;
   if (kp < 1) kp = 1;
+  const int64_t stop = (int64_t)(R > 2 ? R : 2) * cfg->C;
   /* D1: coarsening */
-  while (nl < 63 && lv[nl - 1].n > 2 * cfg->C) {
+  while (nl < 63 && lv[nl - 1].n > stop) {
     glvl_t *g = &lv[nl - 1];
     while (kp > 1 && 2 * (int64_t)g->n <= kp * cfg->C) kp /= 2;
     int64_t U = (int64_t)floor(eps * (double)cV / (double)kp);
@@ -363,20 +383,41 @@ int32_t kmpo_partition(int32_t n, const int64_t *xadj, const int32_t *adj, const
     ++nl;
     if ((int64_t)cfg->conv_den * cg.n > (int64_t)cfg->conv_num * g->n) break;
   }
-  double t1 = now_s();
-  st->t_coarsen = t1 - t0;
-  st->levels = nl;
-  for (int32_t l = 0; l < nl && l < 64; ++l) {
-    st->level_n[l] = lv[l].n;
-    st->level_m[l] = lv[l].xadj[lv[l].n];
+  if (top) {
+    st->levels = nl;
+    for (int32_t l = 0; l < nl && l < 64; ++l) {
+      st->level_n[l] = lv[l].n;
+      st->level_m[l] = lv[l].xadj[lv[l].n];
+    }
   }
-  /* D2: uncoarsening with recursive bipartitioning, balancing, refinement */
+  /* D7: the coarsest graph's partition from two recursive copies, or {V} */
   int32_t *f = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * k + 2));
   int32_t *cap = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * k + 2));
   int32_t nblocks = 1;
-  f[0] = k;
-  int32_t *part = (int32_t *)calloc((size_t)lv[nl - 1].n, sizeof(int32_t));
-  double tip = 0, tref = 0;
+  int32_t *part;
+  const glvl_t *gc = &lv[nl - 1];
+  if (R >= 2) {
+    deep_out o[2];
+    int fe[2];
+    int64_t ct[2];
+    for (int c = 0; c < 2; ++c) {
+      uint64_t w[2] = {DOM_REPLICA, (uint64_t)c};
+      deep(gc, R / 2, kmpo_key(seed, 2, w), 0, 0, n_in, k, eps, cV, cfg, st, tip, tref, &o[c]);
+      fe[c] = level_feasible(gc, o[c].part, o[c].nblocks, o[c].f, eps, cV, k);
+      ct[c] = kmpo_cut(gc->n, gc->xadj, gc->adj, gc->ew, o[c].part);
+    }
+    int pick = (fe[0] != fe[1]) ? (fe[0] ? 0 : 1) : (ct[1] < ct[0] ? 1 : 0);
+    part = o[pick].part;
+    nblocks = o[pick].nblocks;
+    memcpy(f, o[pick].f, sizeof(int32_t) * (size_t)nblocks);
+    free(o[1 - pick].part);
+    free(o[0].f);
+    free(o[1].f);
+  } else {
+    part = (int32_t *)calloc((size_t)gc->n, sizeof(int32_t));
+    f[0] = k;
+  }
+  /* D2: uncoarsening with recursive bipartitioning, balancing, refinement */
   for (int32_t l = nl - 1; l >= 0; --l) {
     glvl_t *g = &lv[l];
     if (l < nl - 1) {
@@ -386,7 +427,7 @@ int32_t kmpo_partition(int32_t n, const int64_t *xadj, const int32_t *adj, const
       part = fine;
     }
     int64_t ki;
-    if (l == 0) {
+    if (input && l == 0) {
       ki = k;
     } else {
       ki = 1;
@@ -400,7 +441,7 @@ int32_t kmpo_partition(int32_t n, const int64_t *xadj, const int32_t *adj, const
       bipartition_blocks(g, part, &nblocks, f, eps, cV, k, kmpo_key(seed, 3, w), cfg);
     }
     double b = now_s();
-    tip += b - a;
+    *tip += b - a;
     int32_t maxc = max_vw(g->n, g->vw);
     for (int32_t i = 0; i < nblocks; ++i) cap[i] = kmpo_block_cap(eps, cV, k, f[i], maxc);
     kmpo_balance(g->n, g->xadj, g->adj, g->vw, g->ew, nblocks, cap, part);
@@ -409,11 +450,8 @@ int32_t kmpo_partition(int32_t n, const int64_t *xadj, const int32_t *adj, const
     kmpo_refine(g->n, g->xadj, g->adj, g->vw, g->ew, nblocks, cap, cfg->refine_rounds,
                 kmpo_key(seed, 2, w2), cfg, part, &ls);
     for (int32_t r = 0; r < ls.rounds && r < 16; ++r) st->refine_scanned += ls.scanned[r];
-    tref += now_s() - b;
+    *tref += now_s() - b;
   }
-  memcpy(part_out, part, sizeof(int32_t) * (size_t)n);
-  free(part);
-  free(f);
   free(cap);
   for (int32_t l = 0; l < nl; ++l) {
     free(lv[l].map);
@@ -421,6 +459,39 @@ int32_t kmpo_partition(int32_t n, const int64_t *xadj, const int32_t *adj, const
       free(lv[l].xadj); free(lv[l].adj); free(lv[l].vw); free(lv[l].ew);
     }
   }
+  out->part = part;
+  out->nblocks = nblocks;
+  out->f = f;
+}
+
+int32_t kmpo_partition(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
+                       const int32_t *ew, int32_t k, double eps, uint64_t seed,
+                       const kmpo_config *cfg, int32_t *part_out, kmpo_stats *st) {
+  double t0 = now_s();
+  kmpo_stats dummy;
+  if (!st) st = &dummy;
+  memset(st, 0, sizeof(*st));
+  if (k <= 1) {
+    for (int32_t v = 0; v < n; ++v) part_out[v] = 0;
+    st->feasible = 1;
+    return 0;
+  }
+  int64_t cV = 0;
+  for (int32_t v = 0; v < n; ++v) cV += vwt(vw, v);
+  glvl_t g0;
+  g0.n = n;
+  g0.xadj = (int64_t *)xadj;
+  g0.adj = (int32_t *)adj;
+  g0.vw = (int32_t *)vw;
+  g0.ew = (int32_t *)ew;
+  g0.map = NULL;
+  g0.owned = 0;
+  double tip = 0, tref = 0;
+  deep_out o;
+  deep(&g0, cfg->replicas > 1 ? cfg->replicas : 1, seed, 1, 1, n, k, eps, cV, cfg, st, &tip, &tref, &o);
+  memcpy(part_out, o.part, sizeof(int32_t) * (size_t)n);
+  free(o.part);
+  free(o.f);
   /* D6 */
   int64_t Lk = (int64_t)floor((1.0 + eps) * (double)((cV + k - 1) / k));
   int64_t *bw = (int64_t *)calloc((size_t)k, sizeof(int64_t));
@@ -434,5 +505,6 @@ int32_t kmpo_partition(int32_t n, const int64_t *xadj, const int32_t *adj, const
   st->t_ip = tip;
   st->t_refine = tref;
   st->t_total = now_s() - t0;
+  st->t_coarsen = st->t_total - tip - tref;
   return feas ? 0 : -5;
 }

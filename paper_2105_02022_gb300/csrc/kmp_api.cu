@@ -214,37 +214,43 @@ __global__ void k_zero_i32(int64_t n, int32_t *p) {
     p[i] = 0;
 }
 
-static void partition_graph(const Graph &g0, int32_t k, double eps, uint64_t seed, int32_t *part_out,
-                            kmp_stats *st) {
+// D4 feasibility of a partition of one level (block caps by final counts)
+static bool level_feasible(const Graph &g, const int32_t *part, int32_t nblocks, const std::vector<int32_t> &f,
+                           double eps, int64_t cV, int32_t k, int64_t *cut_out) {
+  DBuf<int64_t> bw(nblocks), cut(1);
+  cut_and_weights(g, part, nblocks, bw, cut);
+  std::vector<int64_t> hbw(nblocks);
+  to_host(hbw.data(), bw.p, nblocks);
+  *cut_out = read1(cut.p);
+  for (int32_t b = 0; b < nblocks; ++b)
+    if (hbw[b] > block_cap(eps, cV, k, f[b], g.max_vw)) return false;
+  return true;
+}
+
+struct DeepOut {
+  DBuf<int32_t> part;  // on the hierarchy's first graph
+  int32_t nblocks = 1;
+  std::vector<int32_t> f;
+};
+
+// Algorithm 1 on the hierarchy that starts at g0.  Coarsening stops at
+// n <= max(R, 2) C; with R >= 2 the coarsest graph's partition is the better
+// of two copies solved recursively with R / 2 under their own seeds
+// (Section 3, "Parallelization"); `input`: g0 is the input graph (k blocks
+// there); `top`: record the level statistics.
+static void deep(const Graph &g0, int32_t R, uint64_t seed, bool input, bool top, int32_t n_in, int32_t k,
+                 double eps, int64_t cV, kmp_stats *st, DeepOut &out) {
   Context &C = ctx();
   const kmp_config &cfg = C.cfg;
-  cudaStream_t s = C.stream;
-  memset(st, 0, sizeof(*st));
-  int64_t launches0 = C.launches;
-  Timer total;
-  int32_t n = g0.n;
-  if (k <= 1 || n == 0) {
-    if (n > 0) {
-      k_zero_i32<<<grid_for(n, 256), 256, 0, s>>>(n, part_out);
-      KMP_LAUNCHED("zero");
-    }
-    st->levels = 1;
-    st->level_n[0] = n;
-    st->level_m[0] = g0.m;
-    st->feasible = 1;
-    st->ms_total = total.stop();
-    st->gpu_launches = (int32_t)(C.launches - launches0);
-    return;
-  }
-  int64_t cV = g0.total_vw;
   std::vector<Graph> lv;
   std::vector<DBuf<int32_t>> maps;
   lv.push_back(g0);
   lv[0].owned = false;
-  int64_t kp = n / cfg.C;
+  int64_t kp = n_in / cfg.C;
   if (kp > k) kp = k;
   if (kp < 1) kp = 1;
-  while (lv.size() < 63 && lv.back().n > 2 * cfg.C) {
+  const int64_t stop = (int64_t)(R > 2 ? R : 2) * cfg.C;
+  while (lv.size() < 63 && lv.back().n > stop) {
     const Graph &cur = lv.back();
     while (kp > 1 && 2 * (int64_t)cur.n <= kp * cfg.C) kp /= 2;
     int64_t U = (int64_t)std::floor(eps * (double)cV / (double)kp);
@@ -260,7 +266,7 @@ static void partition_graph(const Graph &g0, int32_t k, double eps, uint64_t see
     st->lp_rounds_run += ls.rounds;
     st->ms_lp += ls.ms;
     st->ms_cluster_other += ms_other;
-    if (level == 0) {
+    if (top && level == 0) {
       st->ms_lp_level0 = ls.ms;
       st->lp_scanned_level0 = ls.scanned;
       st->lp_rounds_level0 = ls.rounds;
@@ -276,15 +282,34 @@ static void partition_graph(const Graph &g0, int32_t k, double eps, uint64_t see
     if ((int64_t)cfg.conv_den * coarse.n > (int64_t)cfg.conv_num * nprev) break;
   }
   int L = (int)lv.size();
-  st->levels = L;
-  for (int l = 0; l < L && l < 64; ++l) {
-    st->level_n[l] = lv[l].n;
-    st->level_m[l] = lv[l].m;
+  if (top) {
+    st->levels = L;
+    for (int l = 0; l < L && l < 64; ++l) {
+      st->level_n[l] = lv[l].n;
+      st->level_m[l] = lv[l].m;
+    }
   }
   std::vector<int32_t> f(1, k);
   int32_t nblocks = 1;
-  DBuf<int32_t> part(lv[L - 1].n);
-  part.zero();
+  DBuf<int32_t> part;
+  if (R >= 2) {
+    // the coarsest graph's partition: the better of two recursive copies
+    const Graph &gc = lv[L - 1];
+    DeepOut o[2];
+    bool fe[2];
+    int64_t ct[2];
+    for (int c = 0; c < 2; ++c) {
+      deep(gc, R / 2, key_of(seed, {DOM_REPLICA, (uint64_t)c}), false, false, n_in, k, eps, cV, st, o[c]);
+      fe[c] = level_feasible(gc, o[c].part, o[c].nblocks, o[c].f, eps, cV, k, &ct[c]);
+    }
+    int pick = (fe[0] != fe[1]) ? (fe[0] ? 0 : 1) : (ct[1] < ct[0] ? 1 : 0);
+    part = std::move(o[pick].part);
+    nblocks = o[pick].nblocks;
+    f = o[pick].f;
+  } else {
+    part.alloc(lv[L - 1].n);
+    part.zero();
+  }
   for (int l = L - 1; l >= 0; --l) {
     Graph &g = lv[l];
     if (l < L - 1) {
@@ -295,7 +320,7 @@ static void partition_graph(const Graph &g0, int32_t k, double eps, uint64_t see
       st->ms_project += tp.stop();
     }
     int64_t ki;
-    if (l == 0) {
+    if (input && l == 0) {
       ki = k;
     } else {
       ki = 1;
@@ -326,7 +351,38 @@ static void partition_graph(const Graph &g0, int32_t k, double eps, uint64_t see
     st->refine_scanned += rs.scanned;
     st->ms_refine += rs.ms;
   }
-  KMP_CUDA(cudaMemcpyAsync(part_out, part.p, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  for (int l = 1; l < L; ++l) free_graph(lv[l]);
+  out.part = std::move(part);
+  out.nblocks = nblocks;
+  out.f = f;
+}
+
+static void partition_graph(const Graph &g0, int32_t k, double eps, uint64_t seed, int32_t *part_out,
+                            kmp_stats *st) {
+  Context &C = ctx();
+  const kmp_config &cfg = C.cfg;
+  cudaStream_t s = C.stream;
+  memset(st, 0, sizeof(*st));
+  int64_t launches0 = C.launches;
+  Timer total;
+  int32_t n = g0.n;
+  if (k <= 1 || n == 0) {
+    if (n > 0) {
+      k_zero_i32<<<grid_for(n, 256), 256, 0, s>>>(n, part_out);
+      KMP_LAUNCHED("zero");
+    }
+    st->levels = 1;
+    st->level_n[0] = n;
+    st->level_m[0] = g0.m;
+    st->feasible = 1;
+    st->ms_total = total.stop();
+    st->gpu_launches = (int32_t)(C.launches - launches0);
+    return;
+  }
+  int64_t cV = g0.total_vw;
+  DeepOut o;
+  deep(g0, cfg.replicas > 1 ? cfg.replicas : 1, seed, true, true, n, k, eps, cV, st, o);
+  KMP_CUDA(cudaMemcpyAsync(part_out, o.part.p, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   DBuf<int64_t> bw(k), cut(1);
   cut_and_weights(g0, part_out, k, bw, cut);
   std::vector<int64_t> hbw(k);
@@ -336,7 +392,6 @@ static void partition_graph(const Graph &g0, int32_t k, double eps, uint64_t see
   st->feasible = 1;
   for (int b = 0; b < k; ++b)
     if (hbw[b] > Lk) st->feasible = 0;
-  for (int l = 1; l < L; ++l) free_graph(lv[l]);
   sync_and_check("partition");
   st->ms_total = total.stop();
   st->gpu_launches = (int32_t)(C.launches - launches0);
@@ -369,6 +424,7 @@ void kmp_config_default(kmp_config *c) {
   c->lrep_random = 0;
   c->lrep_bfs = 0;
   c->lrep_ggg = 1;
+  c->replicas = 1;
 }
 
 int kmp_set_config(const kmp_config *c) {
@@ -380,7 +436,8 @@ int kmp_set_config(const kmp_config *c) {
         c->ip_lp_rounds < 0 || c->ip_lp_rounds > 64 || c->rep_random < 0 || c->rep_bfs < 0 ||
         c->rep_ggg < 0 || c->rep_random + c->rep_bfs + c->rep_ggg < 1 ||
         c->rep_random + c->rep_bfs + c->rep_ggg > 64 || c->fm_passes < 0 || c->fm_stop < 1 ||
-        c->learned < 0 || c->learned > 1 || c->lrep_random < 0 || c->lrep_bfs < 0 || c->lrep_ggg < 0)
+        c->learned < 0 || c->learned > 1 || c->lrep_random < 0 || c->lrep_bfs < 0 || c->lrep_ggg < 0 ||
+        c->replicas < 1 || c->replicas > 64 || (c->replicas & (c->replicas - 1)) != 0)
       fail(KMP_ERR_ARG, "invalid configuration");
     ctx().cfg = *c;
   });

@@ -160,7 +160,8 @@ enum : uint64_t {
   DOM_BFS = 6,
   DOM_GGG = 7,
   DOM_REFINE_LEVEL = 8,
-  DOM_LEARNED = 9
+  DOM_LEARNED = 9,
+  DOM_REPLICA = 10
 };
 
 // ----------------------------------------------------------- warp helpers

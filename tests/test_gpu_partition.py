@@ -134,6 +134,33 @@ PARTS = [
 ]
 
 
+REPL = [
+    ("rgg15", lambda: gg.workload_rgg_small(1), 8, [2, 4, 8]),
+    ("rgg_w", lambda: gg.with_weights(gg.rgg(12000, 8, 6), 5, 9, 6), 7, [2, 4]),
+    ("rmat14", lambda: gg.rmat(14, 16, 2), 32, [2, 8]),
+    ("rgg300", lambda: gg.rgg(300, 8, 6), 2, [2]),
+]
+
+
+@pytest.mark.parametrize("name,make,k,Rs", REPL, ids=[p[0] for p in REPL])
+def test_replication_parity(kmp, name, make, k, Rs):
+    """Replication of the coarsest levels (Section 3, "Parallelization") on
+    the GPU against the oracle, bit for bit"""
+    g = make()
+    dg = kmp.DeviceGraph.from_host(g)
+    try:
+        for R in Rs:
+            kmp.set_config(kmp.config(replicas=R))
+            part, rc, st = kmp.partition_graph(dg, k, 0.03, 1)
+            rp, rrc, rst = O.partition(g, k, 0.03, 1, O.config(replicas=R))
+            assert np.array_equal(part.cpu().numpy(), rp), (name, R)
+            assert rc == rrc and st.cut == rst.cut and st.feasible == rst.feasible
+            assert st.levels == rst.levels
+            assert list(st.level_n[: st.levels]) == list(rst.level_n[: rst.levels])
+    finally:
+        kmp.set_config(kmp.config())
+
+
 @pytest.mark.parametrize("name,make,ks", PARTS, ids=[p[0] for p in PARTS])
 def test_partition_parity(kmp, name, make, ks):
     g = make()

@@ -389,3 +389,48 @@ def test_partition_deterministic():
     a = O.partition(g, 8, 0.03, 3)[0]
     b = O.partition(g, 8, 0.03, 3)[0]
     assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------ replication --
+@pytest.mark.parametrize("R", [2, 4, 8])
+def test_replication_valid_and_stop_rule(R):
+    """Replication (Section 3, "Parallelization"): the result is a valid,
+    recounted partition, and the top hierarchy stops coarsening at
+    max(R, 2) C nodes (or earlier by the convergence rule)."""
+    g = gg.rgg(20000, 8, 4)
+    cfg = O.config(replicas=R)
+    part, rc, st = O.partition(g, 8, 0.03, 1, cfg)
+    assert part.min() >= 0 and part.max() < 8
+    assert st.cut == O.cut(g, part)
+    Lk = int(np.floor(1.03 * np.ceil(g.n / 8)))
+    assert (np.bincount(part, minlength=8).max() <= Lk) == bool(st.feasible)
+    ln = list(st.level_n[: st.levels])
+    assert ln[-1] <= max(R, 2) * cfg.C or 20 * ln[-1] > 19 * ln[-2]
+    assert all(x > max(R, 2) * cfg.C for x in ln[:-1])
+
+
+def test_replication_one_is_the_plain_method():
+    g = gg.rgg(6000, 8, 2)
+    a, _, sa = O.partition(g, 5, 0.03, 4)
+    b, _, sb = O.partition(g, 5, 0.03, 4, O.config(replicas=1))
+    assert np.array_equal(a, b) and sa.cut == sb.cut
+
+
+def test_replication_no_worse_than_the_better_copy():
+    """With R = 2 on a graph that is already the coarsest level (n <= 2C),
+    each copy is a plain partition of that graph under the copy's seed
+    key(seed, {10, copy}).  The run keeps the feasible or smaller-cut copy
+    and then balances and refines it once more, which cannot raise the cut of
+    a feasible bipartition: so the result cuts no more than the better copy."""
+    g = gg.rgg(300, 8, 6)                 # n <= 2C: no coarsening at all
+    cfg = O.config(replicas=2)
+    part, rc, st = O.partition(g, 2, 0.03, 7, cfg)
+    assert st.levels == 1
+    copies = [O.partition(g, 2, 0.03, O.key(7, [10, c]))[0] for c in (0, 1)]
+    cuts = [O.cut(g, p) for p in copies]
+    Lk = int(np.floor(1.03 * np.ceil(g.n / 2)))
+    feas = [np.bincount(p, minlength=2).max() <= Lk for p in copies]
+    best = copies[0] if (feas[0] and not feas[1]) or (feas[0] == feas[1] and cuts[0] <= cuts[1]) else copies[1]
+    # the kept partition is then balanced and refined once more at the same
+    # level, which never raises the cut of a feasible bipartition
+    assert st.cut <= O.cut(g, best)
