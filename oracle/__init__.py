@@ -34,7 +34,7 @@ class Config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "C", "lp_rounds", "refine_rounds", "subrounds", "two_hop", "conv_num", "conv_den",
         "ip_C", "ip_lp_rounds", "rep_random", "rep_bfs", "rep_ggg", "fm_passes", "fm_stop",
-        "learned", "lrep_random", "lrep_bfs", "lrep_ggg", "replicas")]
+        "learned", "lrep_random", "lrep_bfs", "lrep_ggg", "replicas", "async_lp")]
 
 
 class OGraph(ctypes.Structure):
@@ -85,7 +85,7 @@ def lib():
             "kmpo_partition": (i32, [i32, P, P, P, P, i32, dbl, u64, P, P, P]),
             "kmpo_bipartition_blocks": (i32, [i32, P, P, P, P, i32, P, dbl, i64, i32, u64, P, P, P]),
             "kmpo_brute_bisection": (i64, [i32, P, P, P, P, i64, i64, P]),
-            "kmpo_async_cluster": (i32, [i32, P, P, P, P, i32, i32, P]),
+            "kmpo_async_cluster": (i32, [i32, P, P, P, P, i32, i32, u64, P]),
             "kmpo_mpnn_num_params": (i32, []),
             "kmpo_mpnn_features": (None, [i32, P, P, P, P, u64, P]),
             "kmpo_mpnn_forward": (None, [i32, P, P, P, P, P, P, P]),
@@ -346,8 +346,8 @@ def learned_initial(g, target0, key_, W):
     return side[:n]
 
 
-def async_cluster(g, U, rounds):
+def async_cluster(g, U, rounds, seed=1):
     n, xadj, adj, vw, ew = _g(g)
     label = np.zeros(n, np.int32)
-    nc = lib().kmpo_async_cluster(n, _p(xadj), _p(adj), _p(vw), _p(ew), U, rounds, _p(label))
+    nc = lib().kmpo_async_cluster(n, _p(xadj), _p(adj), _p(vw), _p(ew), U, rounds, seed, _p(label))
     return label, int(nc)

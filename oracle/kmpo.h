@@ -44,6 +44,9 @@ typedef struct {
   int32_t lrep_bfs;
   int32_t lrep_ggg;
   int32_t replicas;      /* R, copies of the coarsest graph (Section 3, "Parallelization"): 1 = off */
+  int32_t async_lp;      /* quality reference only (no GPU counterpart): coarsen with the sequential
+                            asynchronous LP (kmpo_async_cluster, no two-hop) instead of the
+                            deterministic sub-rounds (0) */
 } kmpo_config;
 
 /* graph owned by the oracle (returned by kmpo_contract) */
@@ -153,10 +156,11 @@ int64_t kmpo_brute_bisection(int32_t n, const int64_t *xadj, const int32_t *adj,
                              int32_t *side_out);
 
 /* sequential asynchronous (Gauss-Seidel) LP clustering: the paper's sequential
- * semantics of size-constrained LP, used only as a quality reference */
+ * semantics of size-constrained LP, nodes visited by degree bucket in a seeded
+ * random order per round; used only as a quality reference */
 int32_t kmpo_async_cluster(int32_t n, const int64_t *xadj, const int32_t *adj,
                            const int32_t *vw, const int32_t *ew, int32_t U, int32_t rounds,
-                           int32_t *label_out);
+                           uint64_t seed, int32_t *label_out);
 
 /* learned seed proposer (kmpo_mpnn.c): parameters in fp64, layout documented there */
 int32_t kmpo_mpnn_num_params(void);

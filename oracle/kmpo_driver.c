@@ -83,6 +83,7 @@ void kmpo_config_default(kmpo_config *c) {
   c->lrep_bfs = 0;
   c->lrep_ggg = 1;
   c->replicas = 1;
+  c->async_lp = 0;
 }
 
 static int32_t ceil_log2(int32_t f) {
@@ -362,9 +363,16 @@ static void deep(const glvl_t *G0, int32_t R, uint64_t seed, int input, int top,
     if (U < 1) U = 1;
     int32_t *label = (int32_t *)malloc(sizeof(int32_t) * (size_t)g->n);
     kmpo_lp_stats ls;
-    int32_t nc = kmpo_cluster(g->n, g->xadj, g->adj, g->vw, g->ew, (int32_t)U, cfg->lp_rounds,
-                              seed, nl - 1, cfg, 1, cfg->two_hop, label, NULL, &ls);
-    for (int32_t r = 0; r < ls.rounds && r < 16; ++r) st->lp_scanned += ls.scanned[r];
+    int32_t nc;
+    if (cfg->async_lp) {  /* quality reference: sequential asynchronous LP */
+      uint64_t w[2] = {DOM_COARSEN, (uint64_t)(nl - 1)};
+      nc = kmpo_async_cluster(g->n, g->xadj, g->adj, g->vw, g->ew, (int32_t)U, cfg->lp_rounds,
+                              kmpo_key(seed, 2, w), label);
+    } else {
+      nc = kmpo_cluster(g->n, g->xadj, g->adj, g->vw, g->ew, (int32_t)U, cfg->lp_rounds, seed, nl - 1, cfg,
+                        1, cfg->two_hop, label, NULL, &ls);
+      for (int32_t r = 0; r < ls.rounds && r < 16; ++r) st->lp_scanned += ls.scanned[r];
+    }
     if (nc == g->n) {
       free(label);
       break;

@@ -407,12 +407,36 @@ int64_t kmpo_refine(int32_t n, const int64_t *xadj, const int32_t *adj, const in
 }
 
 /* ------------------------------------------- sequential asynchronous LP -- */
-/* Quality reference: the paper's sequential semantics (Section 2): nodes
- * visited in id order, each move applied immediately, cap checked against
- * the current weights, ties kept by the own cluster then the smaller id. */
+/* Quality reference: the paper's sequential semantics (Section 2), each move
+ * applied immediately with the cap checked against the current weights, ties
+ * kept by the own cluster then the smaller id.  Visiting order per round
+ * (Section 4.1, "Iteration Order and Cache Locality"): exponentially spaced
+ * degree buckets in increasing order, a seeded random order inside each
+ * bucket (a fresh one every round). */
+typedef struct {
+  uint64_t key;
+  int32_t v;
+} vorder_t;
+
+static int cmp_vorder(const void *x, const void *y) {
+  const vorder_t *a = (const vorder_t *)x, *b = (const vorder_t *)y;
+  if (a->key != b->key) return a->key < b->key ? -1 : 1;
+  return a->v < b->v ? -1 : (a->v > b->v);
+}
+
+static uint64_t deg_bucket(int64_t d) {
+  uint64_t b = 0;
+  while (d > 0) {
+    ++b;
+    d >>= 1;
+  }
+  return b;  /* 0 for isolated nodes, else 1 + floor(log2 d) */
+}
+
 int32_t kmpo_async_cluster(int32_t n, const int64_t *xadj, const int32_t *adj,
                            const int32_t *vw, const int32_t *ew, int32_t U, int32_t rounds,
-                           int32_t *label) {
+                           uint64_t seed, int32_t *label) {
+  vorder_t *ord = (vorder_t *)malloc(sizeof(vorder_t) * (size_t)(n > 0 ? n : 1));
   int64_t *wt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
   int64_t *rating = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
   int64_t maxdeg = 0;
@@ -425,7 +449,14 @@ int32_t kmpo_async_cluster(int32_t n, const int64_t *xadj, const int32_t *adj,
   }
   for (int32_t r = 0; r < rounds; ++r) {
     int64_t moved = 0;
-    for (int32_t u = 0; u < n; ++u) {
+    uint64_t rk = kmpo_step(seed, (uint64_t)r);
+    for (int32_t v = 0; v < n; ++v) {
+      ord[v].key = (deg_bucket(xadj[v + 1] - xadj[v]) << 32) | (uint64_t)kmpo_perm32(rk, v);
+      ord[v].v = v;
+    }
+    qsort(ord, (size_t)n, sizeof(vorder_t), cmp_vorder);
+    for (int32_t i = 0; i < n; ++i) {
+      const int32_t u = ord[i].v;
       int32_t nc = 0, own = label[u];
       for (int64_t e = xadj[u]; e < xadj[u + 1]; ++e) {
         int32_t K = label[adj[e]];
@@ -450,6 +481,6 @@ int32_t kmpo_async_cluster(int32_t n, const int64_t *xadj, const int32_t *adj,
     if (!moved) break;
   }
   pack_isolated(n, xadj, vw, U, label);
-  free(wt); free(rating); free(cand);
+  free(wt); free(rating); free(cand); free(ord);
   return count_clusters(n, label);
 }
