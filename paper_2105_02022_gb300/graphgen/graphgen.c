@@ -13,6 +13,11 @@
  *
  * Every returned CSR is symmetric, has no self-loops, no duplicate entries,
  * rows sorted by neighbour id, and equal weights on both directions.
+ *
+ * The large loops may run on several host threads (OpenMP, when the build
+ * has it); every value is a pure function of its index and every parallel
+ * step keeps the sequential order, so the output does not depend on the
+ * thread count.
  */
 #include <math.h>
 #include <stdint.h>
@@ -35,21 +40,52 @@ static double unit(uint64_t seed, uint64_t s, uint64_t i) {
   return (double)(draw(seed, s, i) >> 11) * (1.0 / 9007199254740992.0);
 }
 
+#ifdef _OPENMP
+#include <omp.h>
+static int nthreads(int64_t work) { return work < (1 << 20) ? 1 : omp_get_max_threads(); }
+static int thread_id(void) { return omp_get_thread_num(); }
+#else
+static int nthreads(int64_t work) { (void)work; return 1; }
+static int thread_id(void) { return 0; }
+#endif
+
 /* ---------------- LSD radix sort of uint64 keys (host helper) ---------------- */
+/* Stable 16-bit digits; with T threads each thread owns a contiguous chunk
+ * and scatters it to the offsets of (digit, thread) in that order, which is
+ * exactly the sequential placement. */
 static void sort_u64(uint64_t *a, int64_t n) {
   if (n < 2) return;
   uint64_t *tmp = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
-  int64_t cnt[65536];
+  const int T = nthreads(n);
+  int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * 65536 * (size_t)T);
   for (int pass = 0; pass < 4; ++pass) {
     int sh = pass * 16;
-    memset(cnt, 0, sizeof(cnt));
-    for (int64_t i = 0; i < n; ++i) cnt[(a[i] >> sh) & 0xFFFF]++;
+    memset(cnt, 0, sizeof(int64_t) * 65536 * (size_t)T);
+#pragma omp parallel num_threads(T)
+    {
+      const int t = thread_id();
+      const int64_t lo = n * t / T, hi = n * (t + 1) / T;
+      int64_t *c = cnt + (size_t)t * 65536;
+      for (int64_t i = lo; i < hi; ++i) c[(a[i] >> sh) & 0xFFFF]++;
+    }
     int64_t s = 0;
-    for (int d = 0; d < 65536; ++d) { int64_t c = cnt[d]; cnt[d] = s; s += c; }
-    for (int64_t i = 0; i < n; ++i) tmp[cnt[(a[i] >> sh) & 0xFFFF]++] = a[i];
+    for (int d = 0; d < 65536; ++d)
+      for (int t = 0; t < T; ++t) {
+        int64_t c = cnt[(size_t)t * 65536 + d];
+        cnt[(size_t)t * 65536 + d] = s;
+        s += c;
+      }
+#pragma omp parallel num_threads(T)
+    {
+      const int t = thread_id();
+      const int64_t lo = n * t / T, hi = n * (t + 1) / T;
+      int64_t *c = cnt + (size_t)t * 65536;
+      for (int64_t i = lo; i < hi; ++i) tmp[c[(a[i] >> sh) & 0xFFFF]++] = a[i];
+    }
     uint64_t *t = a; a = tmp; tmp = t;
   }
   /* 4 passes: result is back in the original buffer */
+  free(cnt);
   free(tmp);
 }
 
@@ -60,15 +96,33 @@ static void sort_u64(uint64_t *a, int64_t n) {
  */
 static int64_t keys_to_csr(int32_t n, uint64_t *keys, int64_t nk, int64_t *xadj,
                            int32_t **adj_out) {
-  /* symmetrise in place into a doubled buffer */
+  /* symmetrise into a doubled buffer (per-chunk counts keep the order) */
   uint64_t *k2 = (uint64_t *)malloc((size_t)(2 * nk + 1) * sizeof(uint64_t));
-  int64_t m = 0;
-  for (int64_t i = 0; i < nk; ++i) {
-    uint32_t u = (uint32_t)(keys[i] >> 32), v = (uint32_t)keys[i];
-    if (u == v) continue;
-    k2[m++] = ((uint64_t)u << 32) | v;
-    k2[m++] = ((uint64_t)v << 32) | u;
+  const int T = nthreads(nk);
+  int64_t *off = (int64_t *)calloc((size_t)T + 1, sizeof(int64_t));
+#pragma omp parallel num_threads(T)
+  {
+    const int t = thread_id();
+    const int64_t lo = nk * t / T, hi = nk * (t + 1) / T;
+    int64_t c = 0;
+    for (int64_t i = lo; i < hi; ++i) c += (uint32_t)(keys[i] >> 32) != (uint32_t)keys[i];
+    off[t + 1] = 2 * c;
   }
+  for (int t = 0; t < T; ++t) off[t + 1] += off[t];
+  const int64_t m = off[T];
+#pragma omp parallel num_threads(T)
+  {
+    const int t = thread_id();
+    const int64_t lo = nk * t / T, hi = nk * (t + 1) / T;
+    int64_t p = off[t];
+    for (int64_t i = lo; i < hi; ++i) {
+      uint32_t u = (uint32_t)(keys[i] >> 32), v = (uint32_t)keys[i];
+      if (u == v) continue;
+      k2[p++] = ((uint64_t)u << 32) | v;
+      k2[p++] = ((uint64_t)v << 32) | u;
+    }
+  }
+  free(off);
   sort_u64(k2, m);
   int64_t w = 0;
   for (int64_t i = 0; i < m; ++i)
@@ -184,6 +238,7 @@ int64_t gg_rmat(int32_t scale, int32_t edge_factor, double a, double b,
   int64_t ns = (int64_t)edge_factor * (int64_t)n;
   uint64_t *ek = (uint64_t *)malloc((size_t)ns * sizeof(uint64_t));
   double ab = a + b, abc = a + b + c;
+#pragma omp parallel for schedule(static) num_threads(nthreads(ns))
   for (int64_t e = 0; e < ns; ++e) {
     uint32_t u = 0, v = 0;
     for (int32_t l = 0; l < scale; ++l) {
@@ -205,6 +260,7 @@ int64_t gg_rmat(int32_t scale, int32_t edge_factor, double a, double b,
   sort_u64(pk, n);
   int32_t *newid = (int32_t *)malloc((size_t)n * sizeof(int32_t));
   for (int32_t i = 0; i < n; ++i) newid[(uint32_t)pk[i]] = i;
+#pragma omp parallel for schedule(static) num_threads(nthreads(ns))
   for (int64_t e = 0; e < ns; ++e) {
     uint32_t u = (uint32_t)(ek[e] >> 32), v = (uint32_t)ek[e];
     ek[e] = ((uint64_t)(uint32_t)newid[u] << 32) | (uint32_t)newid[v];
