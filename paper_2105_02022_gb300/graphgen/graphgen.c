@@ -44,10 +44,18 @@ static double unit(uint64_t seed, uint64_t s, uint64_t i) {
 #include <omp.h>
 static int nthreads(int64_t work) { return work < (1 << 20) ? 1 : omp_get_max_threads(); }
 static int thread_id(void) { return omp_get_thread_num(); }
+static int team_size(void) { return omp_get_num_threads(); }
 #else
 static int nthreads(int64_t work) { (void)work; return 1; }
 static int thread_id(void) { return 0; }
+static int team_size(void) { return 1; }
 #endif
+
+/* The work is split into T fixed chunks before a parallel region starts.  The
+ * runtime may give the region fewer threads than asked for (a thread limit,
+ * dynamic teams, a nested region), so every region walks all T chunks with
+ * the threads it actually has: chunk t goes to thread t mod (team size). */
+#define FOR_EACH_CHUNK(t, T) for (int t = thread_id(); t < (T); t += team_size())
 
 /* ---------------- LSD radix sort of uint64 keys (host helper) ---------------- */
 /* Stable 16-bit digits; with T threads each thread owns a contiguous chunk
@@ -62,8 +70,7 @@ static void sort_u64(uint64_t *a, int64_t n) {
     int sh = pass * 16;
     memset(cnt, 0, sizeof(int64_t) * 65536 * (size_t)T);
 #pragma omp parallel num_threads(T)
-    {
-      const int t = thread_id();
+    FOR_EACH_CHUNK(t, T) {
       const int64_t lo = n * t / T, hi = n * (t + 1) / T;
       int64_t *c = cnt + (size_t)t * 65536;
       for (int64_t i = lo; i < hi; ++i) c[(a[i] >> sh) & 0xFFFF]++;
@@ -76,8 +83,7 @@ static void sort_u64(uint64_t *a, int64_t n) {
         s += c;
       }
 #pragma omp parallel num_threads(T)
-    {
-      const int t = thread_id();
+    FOR_EACH_CHUNK(t, T) {
       const int64_t lo = n * t / T, hi = n * (t + 1) / T;
       int64_t *c = cnt + (size_t)t * 65536;
       for (int64_t i = lo; i < hi; ++i) tmp[c[(a[i] >> sh) & 0xFFFF]++] = a[i];
@@ -101,8 +107,7 @@ static int64_t keys_to_csr(int32_t n, uint64_t *keys, int64_t nk, int64_t *xadj,
   const int T = nthreads(nk);
   int64_t *off = (int64_t *)calloc((size_t)T + 1, sizeof(int64_t));
 #pragma omp parallel num_threads(T)
-  {
-    const int t = thread_id();
+  FOR_EACH_CHUNK(t, T) {
     const int64_t lo = nk * t / T, hi = nk * (t + 1) / T;
     int64_t c = 0;
     for (int64_t i = lo; i < hi; ++i) c += (uint32_t)(keys[i] >> 32) != (uint32_t)keys[i];
@@ -111,8 +116,7 @@ static int64_t keys_to_csr(int32_t n, uint64_t *keys, int64_t nk, int64_t *xadj,
   for (int t = 0; t < T; ++t) off[t + 1] += off[t];
   const int64_t m = off[T];
 #pragma omp parallel num_threads(T)
-  {
-    const int t = thread_id();
+  FOR_EACH_CHUNK(t, T) {
     const int64_t lo = nk * t / T, hi = nk * (t + 1) / T;
     int64_t p = off[t];
     for (int64_t i = lo; i < hi; ++i) {

@@ -30,6 +30,19 @@ def test_rmat_same_with_one_and_many_threads():
         assert out == here, threads
 
 
+def test_rmat_same_when_the_runtime_gives_fewer_threads():
+    """The work is split into as many chunks as threads were asked for; a
+    runtime that grants fewer (a thread limit, dynamic teams) must still
+    process every chunk."""
+    here = _digest(gg.rmat(17, 16, 5))
+    for env_extra in ({"OMP_NUM_THREADS": "4", "OMP_THREAD_LIMIT": "2"},
+                      {"OMP_NUM_THREADS": "6", "OMP_DYNAMIC": "true", "OMP_THREAD_LIMIT": "3"}):
+        env = dict(os.environ, **env_extra)
+        out = subprocess.run([sys.executable, "-c", _SNIPPET], env=env, capture_output=True, text=True,
+                             check=True).stdout.strip()
+        assert out == here, env_extra
+
+
 def test_rmat_csr_is_symmetric_sorted_and_loop_free():
     g = gg.rmat(14, 16, 3)
     import numpy as np
