@@ -54,7 +54,10 @@ class Stats(ctypes.Structure):
                 ("refine_scanned", ctypes.c_int64), ("cut", ctypes.c_int64),
                 ("feasible", ctypes.c_int32), ("t_coarsen", ctypes.c_double),
                 ("t_ip", ctypes.c_double), ("t_refine", ctypes.c_double),
-                ("t_total", ctypes.c_double)]
+                ("t_total", ctypes.c_double), ("level_kp", ctypes.c_int32 * 64),
+                ("level_U", ctypes.c_int64 * 64), ("level_k", ctypes.c_int32 * 64),
+                ("clustered", ctypes.c_int32), ("t_contract", ctypes.c_double),
+                ("t_balance", ctypes.c_double)]
 
 
 def lib():

@@ -72,7 +72,16 @@ typedef struct {
   int64_t refine_scanned;    /* same for refinement LP */
   int64_t cut;
   int32_t feasible;
-  double t_coarsen, t_ip, t_refine, t_total; /* seconds */
+  double t_coarsen, t_ip, t_refine, t_total; /* seconds (coarsening includes contraction) */
+  /* the schedule of the top hierarchy (D1, D2): k' and U used to cluster
+   * level i (i < levels; the last entry is the clustering that stopped
+   * coarsening, if one ran), and the block count of level i's partition after
+   * its split rounds */
+  int32_t level_kp[64];
+  int64_t level_U[64];
+  int32_t level_k[64];
+  int32_t clustered;         /* number of clusterings run (entries of level_kp/U) */
+  double t_contract, t_balance; /* seconds, parts of t_coarsen and t_refine */
 } kmpo_stats;
 
 void kmpo_config_default(kmpo_config *cfg);

@@ -361,6 +361,11 @@ static void deep(const glvl_t *G0, int32_t R, uint64_t seed, int input, int top,
     int32_t maxc = max_vw(g->n, g->vw);
     if (U < maxc) U = maxc;
     if (U < 1) U = 1;
+    if (top) {
+      st->level_kp[nl - 1] = (int32_t)kp;
+      st->level_U[nl - 1] = U;
+      st->clustered = nl;
+    }
     int32_t *label = (int32_t *)malloc(sizeof(int32_t) * (size_t)g->n);
     kmpo_lp_stats ls;
     int32_t nc;
@@ -379,7 +384,9 @@ static void deep(const glvl_t *G0, int32_t R, uint64_t seed, int input, int top,
     }
     g->map = (int32_t *)malloc(sizeof(int32_t) * (size_t)g->n);
     kmpo_graph cg;
+    double tc = now_s();
     kmpo_contract(g->n, g->xadj, g->adj, g->vw, g->ew, label, g->map, &cg);
+    st->t_contract += now_s() - tc;
     free(label);
     lv[nl].n = cg.n;
     lv[nl].xadj = cg.xadj;
@@ -450,9 +457,12 @@ static void deep(const glvl_t *G0, int32_t R, uint64_t seed, int input, int top,
     }
     double b = now_s();
     *tip += b - a;
+    if (top) st->level_k[l] = nblocks;
     int32_t maxc = max_vw(g->n, g->vw);
     for (int32_t i = 0; i < nblocks; ++i) cap[i] = kmpo_block_cap(eps, cV, k, f[i], maxc);
+    double tb = now_s();
     kmpo_balance(g->n, g->xadj, g->adj, g->vw, g->ew, nblocks, cap, part);
+    st->t_balance += now_s() - tb;
     uint64_t w2[2] = {DOM_REFINE_LEVEL, (uint64_t)l};
     kmpo_lp_stats ls;
     kmpo_refine(g->n, g->xadj, g->adj, g->vw, g->ew, nblocks, cap, cfg->refine_rounds,
