@@ -1,10 +1,16 @@
-"""Benchmark: deep multilevel partitioning of the R-MAT scale-20 workload
-(edge factor 16, a,b,c,d = 0.57,0.19,0.19,0.05, symmetrised, deduplicated,
-self-loops removed, unit weights; k = 256, eps = 0.03) on one GB300.
+"""Benchmark: deep multilevel partitioning on one GB300.
 
-One step = one full kmp_partition_graph call: coarsening (size-constrained LP
-rating + deterministic commit, isolated packing, two-hop, contraction),
-batched initial bipartitioning, balancing, LP refinement, projection, cut.
+Default workload: R-MAT graph, scale 26, edge factor 16,
+(a, b, c, d) = (0.57, 0.19, 0.19, 0.05), symmetrised, deduplicated, self-loops
+removed, unit weights (2^26 nodes, ~2.1e9 directed entries: int32 indices,
+int64 offsets); k = 2^16, eps = 0.03.  This is the largest workload that fits
+one GPU; --workload picks a smaller one (R-MAT scale 20 with k = 256, or the
+2D random geometric graph with 2^24 nodes and k = 2^14).
+
+One step = one full kmp_partition_graph call on the device-resident graph:
+coarsening (size-constrained LP rating + deterministic commit, isolated
+packing, two-hop, contraction), batched initial bipartitioning, balancing,
+LP refinement, projection, cut.
 
 value    = LP edges/s per round: directed CSR entries rated by all LP rounds
            (coarsening and refinement) / device time of those rounds.
@@ -19,10 +25,12 @@ roofline = k_rate, the LP rating kernel (every launch of the timed steps):
            start to its last CTA's end on the device's global timer, stamped
            inside the kernel: the LP rounds run as a replayed CUDA graph, and
            event-record nodes in it would add about 7 us each to the step.
-           traffic = DRAM bytes per launch from the committed ncu capture of
-           one step.
-cpu_baseline = the CPU oracle (single thread) on a bounded sample: level-0
-           coarsening LP of the same graph.
+           rating_stage = the same over the whole rating stage of every
+           sub-round (k_rate and the hub kernels: first CTA start of k_rate to
+           last CTA end of the last hub kernel), hub entries and nodes included.
+cpu_baseline = the CPU oracle (single thread) on a bounded sample of the same
+           graph: the first sub-round of the first round of its level-0
+           coarsening LP.
 
 --impl reference times the CPU oracle itself (the reference arm of this
 project) on the same workload, one bounded sample per step.
@@ -30,9 +38,9 @@ project) on the same workload, one bounded sample per step.
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -44,10 +52,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "LP edges/s per round (HBM GB/s vs peak); end-to-end s at k; cut vs plain"
 UNIT = "edges/s"
-K_BLOCKS = 256
 EPS = 0.03
 SEED = 1
-WORKLOAD = "rmat_scale20_ef16_k256"
+
+# name -> (generator, k, description)
+WORKLOADS = {
+    "rmat_scale26_ef16_k65536": (lambda gg: gg.rmat(26, 16, SEED), 1 << 16,
+                                 "R-MAT scale 26, ef 16, (0.57,0.19,0.19,0.05), unit weights, k=2^16"),
+    "rmat_scale20_ef16_k256": (lambda gg: gg.workload_rmat20(SEED), 256,
+                               "R-MAT scale 20, ef 16, (0.57,0.19,0.19,0.05), unit weights, k=256"),
+    "rgg_2^24_deg16_k16384": (lambda gg: gg.rgg(1 << 24, 16, SEED), 1 << 14,
+                              "2D random geometric graph, n=2^24, average degree 16, unit weights, k=2^14"),
+}
+DEFAULT_WORKLOAD = "rmat_scale26_ef16_k65536"
+ORACLE_SAMPLE_SUBROUNDS = 1
 
 
 def _peaks():
@@ -57,6 +75,17 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
 
 
 class Clocks:
@@ -107,19 +136,60 @@ class Clocks:
         return out
 
 
-def cpu_baseline(g):
-    """The oracle as it stands: level-0 coarsening LP (5 rounds, 8 sub-rounds,
-    isolated packing, two-hop) of the workload graph, single thread."""
+def recorded_rate_traffic(workload):
+    """DRAM bytes per k_rate launch from the committed ncu record of this
+    workload, or None when there is none or the LP source changed since."""
+    import hashlib
+
+    prof = os.path.join(ROOT, "profiles", "lp_rate_traffic.json")
+    try:
+        rec = json.load(open(prof))
+        src = os.path.join(ROOT, "paper_2105_02022_gb300", "csrc", "kmp_lp.cu")
+        if rec.get("workload") != workload:
+            return None
+        if rec.get("kmp_lp_cu_sha256") != hashlib.sha256(open(src, "rb").read()).hexdigest():
+            return None
+        return rec.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        return None
+
+
+def config_of(name, g, k):
+    """The workload description both arms print (identical dicts)."""
+    return {"workload": name, "graph": WORKLOADS[name][2], "n": int(g.n), "m_directed": int(g.m_directed),
+            "k": int(k), "eps": EPS, "seed": SEED, "parallelism": "single",
+            "l2": "inputs larger than L2 (CSR > 129 MB) and a 256 MB write between steps"
+            if g.m_directed * 4 > (129 << 20) else "256 MB write between steps (flushes L2)"}
+
+
+def level0_cap(g, k, C=160):
+    """The cluster cap of the input level (Section 4.1): U = max(floor(eps c(V) / k'),
+    max c(v)) with k' = min(k, floor(n / C)); unit weights here."""
+    kp = max(1, min(k, g.n // C))
+    while kp > 1 and 2 * g.n <= kp * C:
+        kp //= 2
+    return max(1, int(EPS * g.n / kp))
+
+
+def oracle_sample(g, k):
+    """The oracle as it stands on a bounded sample: the first sub-round of the
+    first round of the input level's coarsening LP (single thread)."""
     import oracle as O
 
-    U = int(EPS * g.n / K_BLOCKS)
+    U = level0_cap(g, k)
+    cfg = O.config(sample_subrounds=ORACLE_SAMPLE_SUBROUNDS)
     t = time.perf_counter()
-    _, _, st = O.cluster(g, U, 5, SEED, 0, stats=True)
+    _, _, st = O.cluster(g, U, 1, SEED, 0, cfg=cfg, isolated=False, two_hop=False, stats=True)
     dt = time.perf_counter() - t
-    scanned = sum(st.scanned[r] for r in range(st.rounds))
-    return {"value": scanned / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"level-0 coarsening LP of {WORKLOAD}: {st.rounds} rounds, {scanned} entries rated, "
-                      f"{dt:.1f} s"}
+    scanned = int(st.scanned[0])
+    return scanned, dt
+
+
+def cpu_baseline(name, g, k):
+    scanned, dt = oracle_sample(g, k)
+    return {"value": scanned / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": _cpu_model(),
+            "sample": f"{name}: sub-round 0 of round 0 of the level-0 coarsening LP (U = {level0_cap(g, k)}), "
+                      f"{scanned} entries rated in {dt:.2f} s"}
 
 
 def run_reference(args, rank, world):
@@ -129,24 +199,43 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     O.build()
-    g = gg.workload_rmat20(SEED)
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state; samples are independent
-    vals, secs = [], []
-    base = None
+    make, k, _ = WORKLOADS[args.workload]
+    g = make(gg)
+    # the oracle has no warm-up state: every sample is independent
+    vals, scanned_all, secs = [], 0, 0.0
     for _ in range(args.steps):
-        b = cpu_baseline(g)
-        vals.append(b["value"])
-        base = b
-    v = statistics.mean(vals)
-    base["value"] = v
+        scanned, dt = oracle_sample(g, k)
+        vals.append(scanned / dt)
+        scanned_all += scanned
+        secs += dt
+    v = scanned_all / secs
+    base = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": _cpu_model(),
+            "sample": f"{args.workload}: per step, sub-round 0 of round 0 of the level-0 coarsening LP "
+                      f"(U = {level0_cap(g, k)}), {scanned_all // max(args.steps, 1)} entries rated"}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "k": K_BLOCKS, "eps": EPS, "n": g.n, "m_directed": g.m_directed},
-            "cpu_baseline": base, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
-                                           "d2h_bytes_per_step": 0}}
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / max(args.steps, 1) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": config_of(args.workload, g, k), "cpu_baseline": base,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def oracle_phases():
+    """The oracle's whole partition per phase (coarsening without contraction,
+    contraction, initial bipartitioning, balancing, refinement), single thread,
+    on the small RGG (k = 8) and R-MAT scale 20 (k = 256)."""
+    import oracle as O
+    from paper_2105_02022_gb300 import graphgen as gg
+
+    for name, g, k in (("rgg_2^15_deg8_k8", gg.workload_rgg_small(SEED), 8),
+                       ("rmat_scale20_ef16_k256", gg.workload_rmat20(SEED), 256)):
+        _, rc, st = O.partition(g, k, EPS, SEED)
+        print(json.dumps({"mode": "oracle_phases", "workload": name, "cores": 1, "cpu": _cpu_model(),
+                          "s_total": st.t_total, "s_coarsen_lp": st.t_coarsen - st.t_contract,
+                          "s_contract": st.t_contract, "s_ip": st.t_ip, "s_balance": st.t_balance,
+                          "s_refine": st.t_refine - st.t_balance, "cut": int(st.cut),
+                          "feasible": bool(st.feasible),
+                          "lp_edges_per_s": (st.lp_scanned + st.refine_scanned) / st.t_total}), flush=True)
 
 
 def ksweep(gg, kmp, torch, np):
@@ -181,7 +270,7 @@ def replicas(gg, kmp, torch, np):
     """Replication of the coarsest levels (Section 3, "Parallelization"):
     median of three partitions per R after a warm-up, same seed."""
     kmp.load()
-    for name, g, k in (("rmat_scale20_ef16", gg.workload_rmat20(SEED), K_BLOCKS),
+    for name, g, k in (("rmat_scale20_ef16", gg.workload_rmat20(SEED), 256),
                        ("rgg_2^15_deg8", gg.workload_rgg_small(SEED), 8)):
         dg = kmp.DeviceGraph.from_host(g)
         for R in (1, 2, 4, 8):
@@ -205,16 +294,19 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="partition",
-                    choices=["partition", "coarsen1", "launchlist", "ksweep", "replicas"],
+                    choices=["partition", "coarsen1", "launchlist", "ksweep", "replicas", "oracle_phases"],
                     help="coarsen1: one level-0 coarsening (LP) of the workload graph only; "
                          "launchlist: one warm-up partition and one partition inside the NVTX "
                          "range kmp_step (for ncu launch lists); both are used for kernel profiles; "
                          "ksweep: the large-k sweep k in {2^11, 2^14, 2^17, 2^20} on the 2D random "
                          "geometric graph with 2^24 nodes (average degree 16), one JSON line per k; "
                          "replicas: cut and time with R = 1, 2, 4, 8 copies of the coarsest levels "
-                         "on the benchmark graph (k = 256) and the small RGG (k = 8)")
+                         "on R-MAT scale 20 (k = 256) and the small RGG (k = 8); "
+                         "oracle_phases: the CPU oracle's partition timed per phase on the small RGG "
+                         "and R-MAT scale 20")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -222,6 +314,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.mode == "oracle_phases":
+        oracle_phases()
         return
 
     import numpy as np
@@ -244,10 +339,13 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     kmp.load()
     kmp.set_config(kmp.config())
-    g = gg.workload_rmat20(SEED)
+    make, K_BLOCKS, _ = WORKLOADS[args.workload]
+    t_gen = time.perf_counter()
+    g = make(gg)
+    gen_s = time.perf_counter() - t_gen
     dg = kmp.DeviceGraph.from_host(g)
     if args.mode == "coarsen1":
-        U = int(EPS * g.n / K_BLOCKS)
+        U = level0_cap(g, K_BLOCKS)
         # first call: includes one-time costs (module loading, memory-pool growth)
         t0 = time.perf_counter()
         kmp.coarsen_level(dg, U, 5, SEED, 0)
@@ -261,12 +359,10 @@ def main():
         kmp.coarsen_level(dg, U, 5, SEED, 0)
         e1.record()
         e1.synchronize()
-        ms, by, nl = kmp.profile_read(reset=True)
+        prof = kmp.profile_read(reset=True)
         peak, kind = _peaks()
-        print(json.dumps({"mode": "coarsen1", "workload": WORKLOAD, "ms_level": e0.elapsed_time(e1),
-                          "ms_first_call_host": cold_ms,
-                          "rate_ms": ms, "rate_launches": nl, "rate_bytes": by,
-                          "rate_gbs": by / (ms / 1e3) / 1e9 if ms else None, "peak": peak, "peak_kind": kind}))
+        print(json.dumps({"mode": "coarsen1", "workload": args.workload, "U": U, "ms_level": e0.elapsed_time(e1),
+                          "ms_first_call_host": cold_ms, **prof.as_dict(peak), "peak": peak, "peak_kind": kind}))
         return
     part = torch.empty(g.n, dtype=torch.int32, device="cuda")
     if args.mode == "launchlist":
@@ -276,13 +372,14 @@ def main():
         _, rc, st = kmp.partition_graph(dg, K_BLOCKS, EPS, SEED, part)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-        print(json.dumps({"mode": "launchlist", "workload": WORKLOAD, "gpu_launches": st.gpu_launches,
+        print(json.dumps({"mode": "launchlist", "workload": args.workload, "gpu_launches": st.gpu_launches,
                           "ms_total": st.ms_total, "cut": st.cut}))
         return
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
-    for _ in range(max(args.warmup, 3)):
+    warmup = max(args.warmup, 3)
+    for _ in range(warmup):
         kmp.partition_graph(dg, K_BLOCKS, EPS, SEED, part)
     torch.cuda.synchronize()
 
@@ -293,7 +390,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    step_ms, lp_ms, scanned, launches, cuts, feas, e2e_s = [], [], 0, 0, [], [], []
+    step_ms, lp_ms, scanned, launches, cuts, feas = [], [], 0, 0, [], []
     stats = None
     for _ in range(args.steps):
         flush.fill_(1)
@@ -316,7 +413,7 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     kmp.set_profiling(False)
-    rate_ms, rate_bytes, rate_launches = kmp.profile_read(reset=True)
+    prof = kmp.profile_read(reset=True)
 
     total_lp_s = sum(lp_ms) / 1e3
     total_step_ms = sum(step_ms)
@@ -332,7 +429,7 @@ def main():
     value = scanned_all / total_lp_s
 
     # end to end through the host-buffer entry point (upload + partition + download)
-    e2e_vals = []
+    e2e_vals, e2e_s = [], []
     for _ in range(2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -346,31 +443,21 @@ def main():
     d2h = g.n * 4
 
     peak, peak_kind = _peaks()
-    achieved = (rate_bytes / (rate_ms / 1e3)) / 1e9 if rate_ms > 0 else 0.0
-    # DRAM bytes per k_rate launch from the committed ncu capture of this step,
-    # valid only while the LP source it was taken from is unchanged
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "lp_rate_traffic.json")
-    if os.path.exists(prof):
-        try:
-            rec = json.load(open(prof))
-            src = os.path.join(ROOT, "paper_2105_02022_gb300", "csrc", "kmp_lp.cu")
-            if rec.get("kmp_lp_cu_sha256") == hashlib.sha256(open(src, "rb").read()).hexdigest():
-                traffic = rec.get("dram_bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    # DRAM bytes per k_rate launch from the committed ncu capture, valid only
+    # while the LP source it was taken from is unchanged
+    traffic = recorded_rate_traffic(args.workload)
 
     if rank != 0:
         return
+    pd = prof.as_dict(peak)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": total_step_ms / args.steps, "higher_is_better": True,
+        "warmup": warmup, "ms_per_step": total_step_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": g.n, "m_directed": g.m_directed, "k": K_BLOCKS, "eps": EPS,
-                   "seed": SEED, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "flushed between steps (256 MB write)"},
+        "config": config_of(args.workload, g, K_BLOCKS),
         "end_to_end_s": (total_step_ms / args.steps) / 1e3,
         "end_to_end_s_host_api": statistics.median(e2e_s),
+        "generate_s": gen_s,
         "lp_scanned_per_step": (scanned_all / max(world, 1)) / args.steps,
         "lp_s_per_step": total_lp_s / args.steps,
         "cut": cuts[-1], "feasible": all(feas), "levels": stats.levels,
@@ -379,17 +466,17 @@ def main():
                      "refine": stats.ms_refine, "project": stats.ms_project, "total": stats.ms_total},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": "k_rate (LP rating)", "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak if peak else None,
-                     "traffic": traffic, "launches": int(rate_launches),
-                     "algorithmic_bytes_per_launch": rate_bytes / rate_launches if rate_launches else None,
-                     "algorithmic_bytes": rate_bytes, "ms": rate_ms},
+        "roofline": {"kernel": "k_rate (LP rating)", "bound": "hbm", "achieved": pd["rate_gbs"], "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": pd["rate_frac"], "traffic": traffic,
+                     "launches": pd["rate_launches"], "algorithmic_bytes_per_launch": pd["rate_bytes_per_launch"],
+                     "algorithmic_bytes": pd["rate_bytes"], "ms": pd["rate_ms"],
+                     "rating_stage": {"achieved": pd["stage_gbs"], "frac": pd["stage_frac"],
+                                      "algorithmic_bytes": pd["stage_bytes"], "ms": pd["stage_ms"],
+                                      "spans": pd["stage_spans"]}},
         "clocks": clk,
     }
-    if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(g)
-    elif not args.no_cpu_baseline and rank == 0:
-        line["cpu_baseline"] = cpu_baseline(g)
+    if not args.no_cpu_baseline and rank == 0:
+        line["cpu_baseline"] = cpu_baseline(args.workload, g, K_BLOCKS)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -105,6 +105,14 @@ typedef struct {
   int64_t lp_scanned_level0; /* entries rated there */
   int32_t lp_rounds_level0;
   int32_t gpu_launches;      /* kernels launched by the call */
+  /* the schedule of the top hierarchy (Section 4.1, Algorithm 1): k' and the
+   * cluster cap U used to cluster level i (clustered entries; the last one
+   * may be a clustering that contracted nothing and stopped coarsening), and
+   * the number of blocks of level i's partition after its split rounds */
+  int32_t clustered;
+  int32_t level_kp[64];
+  int64_t level_U[64];
+  int32_t level_k[64];
 } kmp_stats;
 
 /* opaque handle to a CSR graph resident in device memory */
@@ -229,15 +237,24 @@ int kmp_partition_graph(const kmp_graph *g, int32_t k, double eps, uint64_t seed
 int kmp_last_stats(kmp_stats *stats);
 
 /*
- * Live profiling of the LP rating kernel (the dominant kernel of coarsening
- * and refinement): when on, every rating launch is bracketed by CUDA events on
- * the library's stream and its algorithmic bytes are counted (per directed
- * entry rated: adjncy 4 + neighbour label 4 (+ edge weight 4 when weighted);
- * per rated node: xadj 8 + list entry 4 + own label 4 + proposal 8 (+ node
- * weight 4)).  kmp_profile_read returns the sums since the last reset.
+ * Live profiling of the LP rating stage (Section 4.1 and 4.3: the rating of
+ * every LP sub-round, the dominant work of coarsening and refinement).  When
+ * on, the rating kernel k_rate stamps the device's global timer: its first
+ * CTA's start and its last CTA's end give the launch's duration (stamps are
+ * taken inside the kernels, so the replayed CUDA graph of an LP round needs
+ * no extra nodes).  Algorithmic bytes are counted per directed entry rated:
+ * adjncy 4 + neighbour label 4 (+ edge weight 4 when weighted); per rated
+ * node: xadj 8 + list entry 4 + own label 4 + proposal 8 (+ node weight 4).
+ * kmp_profile_read: k_rate alone (nodes rated by the hub kernels excluded),
+ * sums since the last reset (milliseconds, bytes, launches).
+ * kmp_profile_read_stage: the whole rating stage of each sub-round, from
+ * k_rate's first CTA start to the last CTA end of the last hub kernel after
+ * it (hub nodes and entries included): milliseconds, bytes, spans.
+ * Host pointers, each nullable; reset != 0 zeroes the sums after reading.
  */
 int kmp_set_profiling(int on);
 int kmp_profile_read(double *rate_ms, double *rate_bytes, int64_t *rate_launches, int reset);
+int kmp_profile_read_stage(double *stage_ms, double *stage_bytes, int64_t *spans, int reset);
 
 /*
  * Schedule parameters of the GPU kernels.  They decide which kernel variant
@@ -342,23 +359,30 @@ int kmp_sample_sink_close(void);
 
 /*
  * Cut and block weights without any device allocation.  The paper has no
- * counterpart: this is a library-side variant of kmp_cut (the cut of
- * Section 2) for callers that cannot let the library allocate at call time:
- * code whose device memory belongs to another allocator or a fixed arena that
- * must account for every byte, processes that reserve all device memory up
- * front, and loops that cannot take the implicit synchronisation or the
- * possible failure of an allocation.  Its scratch is one fixed device array
- * of KMP_NOALLOC_MAX_K + 2 64-bit words (about 512 KB) inside the library,
- * kept until the process exits.
+ * counterpart: this is a library-side variant of kmp_cut for callers that
+ * cannot let the library allocate device memory at call time: code whose
+ * device memory belongs to another allocator or to a fixed arena that must
+ * account for every byte, processes that reserve all device memory up front,
+ * and loops that cannot take the implicit synchronisation or the possible
+ * failure of an allocation.  Its scratch is one fixed device array of
+ * KMP_NOALLOC_MAX_K + 2 64-bit words (about 512 KB) inside the library, held
+ * on every device that loads the library until the process exits.
  *
  * g: graph handle; part: DEVICE int32[n] with values in [0, k); k in
  * [1, KMP_NOALLOC_MAX_K] (else KMP_ERR_ARG, nothing launched); cut_out (host,
  * nullable): the cut; block_weights_out (host int64[k], nullable): c(V_b).
  * A part value outside [0, k) gives KMP_ERR_ARG (outputs unspecified).
- * Runs on the stream of kmp_set_stream and returns after it drained.  The
- * first call on a device looks the array's device address up once.
- * Overlapping calls (from several host threads or streams) share the one
- * array and race: serialise them.
+ * Runs on the stream of kmp_set_stream and returns after it drained.
+ *
+ * Set-up: the array's module is loaded, and its device address looked up,
+ * while the library initialises on a device (the first library call there,
+ * e.g. kmp_graph_create).  That module load is the only device memory this
+ * entry point ever causes to be committed, and it happens before the first
+ * kmp_cut_noalloc call; make that first library call before any stream
+ * capture.  If the device's context is recreated (cudaDeviceReset), the next
+ * call looks the address up again.  Each call clears the part of the array it
+ * accumulates into; overlapping calls (from several host threads or streams)
+ * share the one array and race: serialise them.
  */
 #define KMP_NOALLOC_MAX_K 65536
 int kmp_cut_noalloc(const kmp_graph *g, const kmp_vid *part, int32_t k, int64_t *cut_out,

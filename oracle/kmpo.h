@@ -47,6 +47,8 @@ typedef struct {
   int32_t async_lp;      /* quality reference only (no GPU counterpart): coarsen with the sequential
                             asynchronous LP (kmpo_async_cluster, no two-hop) instead of the
                             deterministic sub-rounds (0) */
+  int32_t sample_subrounds; /* timing samples only: kmpo_cluster's LP ends after this many
+                               sub-rounds (0: no limit); the sub-rounds that run are unchanged */
 } kmpo_config;
 
 /* graph owned by the oracle (returned by kmpo_contract) */

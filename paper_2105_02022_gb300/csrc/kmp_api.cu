@@ -256,6 +256,11 @@ static void deep(const Graph &g0, int32_t R, uint64_t seed, bool input, bool top
     int64_t U = (int64_t)std::floor(eps * (double)cV / (double)kp);
     if (U < cur.max_vw) U = cur.max_vw;
     if (U < 1) U = 1;
+    if (top) {
+      st->level_kp[lv.size() - 1] = (int32_t)kp;
+      st->level_U[lv.size() - 1] = U;
+      st->clustered = (int32_t)lv.size();
+    }
     DBuf<int32_t> label(cur.n);
     LPStats ls;
     float ms_other = 0;
@@ -338,6 +343,7 @@ static void deep(const Graph &g0, int32_t R, uint64_t seed, bool input, bool top
       }
       st->ms_ip += ti.stop();
     }
+    if (top) st->level_k[l] = nblocks;
     std::vector<int32_t> caps(nblocks);
     for (int b = 0; b < nblocks; ++b) caps[b] = block_cap(eps, cV, k, f[b], g.max_vw);
     {
@@ -749,6 +755,20 @@ int kmp_profile_read(double *rate_ms, double *rate_bytes, int64_t *rate_launches
       C.prof_rate_ms = 0;
       C.prof_rate_bytes = 0;
       C.prof_rate_launches = 0;
+    }
+  });
+}
+
+int kmp_profile_read_stage(double *stage_ms, double *stage_bytes, int64_t *spans, int reset) {
+  return guarded([&] {
+    Context &C = ctx();
+    if (stage_ms) *stage_ms = C.prof_stage_ms;
+    if (stage_bytes) *stage_bytes = C.prof_stage_bytes;
+    if (spans) *spans = C.prof_stage_spans;
+    if (reset) {
+      C.prof_stage_ms = 0;
+      C.prof_stage_bytes = 0;
+      C.prof_stage_spans = 0;
     }
   });
 }

@@ -62,13 +62,21 @@ constexpr int SPEC_MAX = 16;
 
 __device__ __forceinline__ int32_t bw_node(const BalArgs &A, int32_t v) { return A.vw ? A.vw[v] : 1; }
 
+// table size for v's connectivity: a power of two >= 2 * (distinct blocks
+// among its neighbours, at most min(degree, k)), at least 32
+__device__ __forceinline__ uint32_t conn_cap(const BalArgs &A, int32_t v) {
+  int64_t d = A.xadj[v + 1] - A.xadj[v];
+  if (d > A.k) d = A.k;
+  uint32_t cap = 32;
+  while ((int64_t)cap < 2 * d) cap <<= 1;
+  return cap;
+}
+
 // connectivity of v to the blocks of its neighbours, aggregated by one warp
 __device__ int64_t conn_table(const BalArgs &A, int32_t v, int32_t *K, int32_t *V, uint32_t &mask) {
   int lane = threadIdx.x & 31;
   int64_t b = A.xadj[v], e = A.xadj[v + 1];
-  int64_t d = e - b < A.k ? e - b : A.k;
-  uint32_t cap = 32;
-  while ((int64_t)cap < 2 * d) cap <<= 1;
+  uint32_t cap = conn_cap(A, v);
   mask = cap - 1;
   for (uint32_t i = lane; i < cap; i += 32) {
     K[i] = HT_EMPTY;
@@ -133,18 +141,22 @@ __global__ void __launch_bounds__(1024) k_bal_slack(BalArgs A, int32_t Pk) {
     }
 }
 
-__global__ void __launch_bounds__(BAL_T) k_bal_cand(BalArgs A) {
+// Candidates of the overloaded blocks.  big = 0: the nodes whose table fits
+// the warp's shared-memory table (full grid); big = 1: the others, each warp
+// with its own region of A.gtab (a grid bounded by that memory).
+__global__ void __launch_bounds__(BAL_T) k_bal_cand(BalArgs A, int big) {
   __shared__ int32_t sk[BAL_W][BAL_STAB], sv[BAL_W][BAL_STAB];
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int64_t gw = (int64_t)blockIdx.x * BAL_W + w, nw = (int64_t)gridDim.x * BAL_W;
   int32_t *K = sk[w], *V = sv[w];
-  if (A.gtab) {
+  if (big) {
     K = A.gtab + gw * 2ll * A.gcap;
     V = K + A.gcap;
   }
   for (int64_t v = gw; v < A.n; v += nw) {
     int32_t B = A.part[v];
     if (!A.over[B]) continue;
+    if ((conn_cap(A, (int32_t)v) > (uint32_t)BAL_STAB) != (big != 0)) continue;
     uint32_t mask;
     int64_t cown = conn_table(A, (int32_t)v, K, V, mask);
     int64_t c = bw_node(A, (int32_t)v);
@@ -260,10 +272,6 @@ __global__ void __launch_bounds__(BAL_T) k_bal_spec(BalArgs A) {
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int64_t gw = (int64_t)blockIdx.x * BAL_W + w, nw = (int64_t)gridDim.x * BAL_W;
   int32_t *K = sk[w], *V = sv[w];
-  if (A.gtab) {
-    K = A.gtab + gw * 2ll * A.gcap;
-    V = K + A.gcap;
-  }
   uint64_t vmask = (1ull << A.bitsN) - 1ull;
   for (int64_t ob = gw; ob < A.nover; ob += nw) {
     int32_t B = A.olist[ob];
@@ -277,6 +285,8 @@ __global__ void __launch_bounds__(BAL_T) k_bal_spec(BalArgs A) {
       }
       if (nm == SPEC_MAX) break;
       int32_t v = (int32_t)(A.keys[i] & vmask);
+      // a node whose table does not fit shared memory is left to the exact commit
+      if (conn_cap(A, v) > (uint32_t)BAL_STAB) break;
       int64_t c = bw_node(A, v);
       uint32_t mask;
       conn_table(A, v, K, V, mask);
@@ -330,11 +340,11 @@ __global__ void __launch_bounds__(BAL_T) k_bal_spec(BalArgs A) {
 __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch) {
   __shared__ int32_t s_v[BM_W], s_t[BM_W];
   __shared__ int64_t s_c[BM_W], s_eoff[BM_W + 1];
-  __shared__ uint32_t s_adj[BM_W];
+  __shared__ uint32_t s_adj[BM_W], s_mask[BM_W];
   __shared__ int32_t s_nb, s_next, s_stop;
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint64_t vmask = (1ull << A.bitsN) - 1ull;
-  uint32_t gcap = A.gcap, hmask = gcap - 1;
+  const uint32_t gcap = A.gcap;  // stride of the per-member table regions
   __shared__ int32_t s_resume;
   for (int32_t ob = 0; ob < A.nover; ++ob) {
     int32_t B = A.olist[ob];
@@ -377,9 +387,16 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
         unsigned enough = __ballot_sync(0xFFFFFFFFu, lane < avail && c >= A.bw[B] - A.cap[B]);
         int32_t nb = enough ? __ffs(enough) : avail;
         if (lane < nb) {
+          // member table sized by the member's own distinct blocks (at most
+          // min(degree, k)), so low-degree members never touch a hub-sized table
+          int64_t own = A.xadj[v + 1] - A.xadj[v];
+          if (own > A.k) own = A.k;
+          uint32_t cap = 32;
+          while ((int64_t)cap < 2 * own) cap <<= 1;
           s_v[lane] = v;
           s_eoff[lane + 1] = deg;
           s_adj[lane] = 0;
+          s_mask[lane] = cap - 1;
           inbatch[v] = lane + 1;
         }
         if (lane == 0) {
@@ -389,10 +406,12 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
       }
       __syncthreads();
       int32_t nb = s_nb;
-      for (int64_t x = threadIdx.x; x < (int64_t)nb * gcap; x += BM_T) {
-        int32_t *K = A.gtab + (x / gcap) * 2ll * gcap;
-        K[x % gcap] = HT_EMPTY;
-        K[gcap + x % gcap] = 0;
+      if (w < nb) {
+        int32_t *K = A.gtab + (int64_t)w * 2 * gcap;
+        for (uint32_t x = lane; x <= s_mask[w]; x += 32) {
+          K[x] = HT_EMPTY;
+          K[gcap + x] = 0;
+        }
       }
       __syncthreads();
       int64_t E = s_eoff[nb];
@@ -416,7 +435,7 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
         int32_t s = __reduce_add_sync(peers, wt);
         if (ok && lane == __ffs(peers) - 1) {
           int32_t *K = A.gtab + (int64_t)j * 2 * gcap;
-          ht_add(K, K + gcap, hmask, blk, s);
+          ht_add(K, K + gcap, s_mask[j], blk, s);
         }
       }
       __syncthreads();
@@ -425,7 +444,7 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
         int64_t c = bw_node(A, v);
         const int32_t *K = A.gtab + (int64_t)w * 2 * gcap, *V = K + gcap;
         uint64_t bestk = 0;  // (conn, ~block): largest connectivity, then lowest id
-        for (uint32_t x = lane; x < gcap; x += 32) {
+        for (uint32_t x = lane; x <= s_mask[w]; x += 32) {
           int32_t b = K[x];
           if (b == HT_EMPTY || b == B) continue;
           if (A.bw[b] + c > A.cap[b]) continue;
@@ -516,7 +535,8 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   int64_t dmax = std::min<int64_t>(g.maxdeg, k);
   uint32_t gcap = 32;
   while ((int64_t)gcap < 2 * dmax) gcap <<= 1;
-  int grid = grid_for((int64_t)n * 32, BAL_T, 8);
+  const int grid = grid_for((int64_t)n * 32, BAL_T, 8);
+  int grid_big = 0;
   DBuf<int32_t> gtab;
   BalArgs A;
   A.n = n;
@@ -542,18 +562,21 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   A.gtab = nullptr;
   A.gcap = gcap;
   A.moved = moved;
-  if (gcap > BAL_STAB) {
-    // bound the per-warp tables to about 256 MB
-    int64_t per_block = 2ll * gcap * BAL_W * (int64_t)sizeof(int32_t);
-    int64_t gmax = std::max<int64_t>(1, (256ll << 20) / per_block);
-    grid = (int)std::min<int64_t>(grid, gmax);
-    gtab.alloc(2ll * gcap * (int64_t)grid * BAL_W);
-    A.gtab = gtab;
-  }
   k_bal_slack<<<1, 1024, 0, s>>>(A, Pk);
   KMP_LAUNCHED("bal_slack");
-  k_bal_cand<<<grid, BAL_T, 0, s>>>(A);
+  k_bal_cand<<<grid, BAL_T, 0, s>>>(A, 0);
   KMP_LAUNCHED("bal_cand");
+  if (gcap > BAL_STAB) {
+    // nodes with more distinct neighbour blocks than a shared table holds:
+    // per-warp global tables, bounded to about 256 MB
+    int64_t per_block = 2ll * gcap * BAL_W * (int64_t)sizeof(int32_t);
+    int64_t gmax = std::max<int64_t>(1, (256ll << 20) / per_block);
+    grid_big = (int)std::min<int64_t>(grid, gmax);
+    gtab.alloc(2ll * gcap * (int64_t)grid_big * BAL_W);
+    A.gtab = gtab;
+    k_bal_cand<<<grid_big, BAL_T, 0, s>>>(A, 1);
+    KMP_LAUNCHED("bal_cand");
+  }
   int32_t N = read1(ncand.p);
   if (N == 0) return 0;
   radix_sort_u64(keys, tmp, N, bitsN + bitsK);
@@ -572,15 +595,7 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   A.spec_sat = spec_sat;
   {
     int sgrid = (int)ceil_div(nover, BAL_W);
-    DBuf<int32_t> stab;
-    if (gcap > BAL_STAB) {
-      int64_t per_block = 2ll * gcap * BAL_W * (int64_t)sizeof(int32_t);
-      sgrid = (int)std::min<int64_t>(sgrid, std::max<int64_t>(1, (256ll << 20) / per_block));
-      stab.alloc(2ll * gcap * (int64_t)sgrid * BAL_W);
-      A.gtab = stab;
-    } else {
-      A.gtab = nullptr;
-    }
+    A.gtab = nullptr;
     k_bal_spec<<<sgrid, BAL_T, 0, s>>>(A);
     KMP_LAUNCHED("bal_spec");
   }

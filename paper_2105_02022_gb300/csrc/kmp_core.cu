@@ -49,6 +49,9 @@ void ensure_init() {
     KMP_CUDA(cudaMalloc(&p, 64));
     KMP_CUDA(cudaMemset(p, 0, 64));
     g_ctx.d_status = static_cast<int *>(p);
+    // loads the no-allocation entry point's module (and its fixed scratch
+    // array) now, while the library initialises, and records its address
+    noalloc_prepare();
   }
 }
 

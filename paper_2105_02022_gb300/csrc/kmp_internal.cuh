@@ -45,9 +45,12 @@ struct Context {
   cudaStream_t capture_stream = nullptr;  // created on first use: CUDA graph capture of LP rounds
   double prof_rate_ms = 0, prof_rate_bytes = 0;
   int64_t prof_rate_launches = 0;
+  double prof_stage_ms = 0, prof_stage_bytes = 0;  // whole rating stage per sub-round
+  int64_t prof_stage_spans = 0;
 };
 Context &ctx();
 void ensure_init();
+void noalloc_prepare();  // resolves kmp_cut_noalloc's scratch array on the current device
 void sync_and_check(const char *what);  // drain the stream and read the status word
 
 // ---------------------------------------------------------- device memory

@@ -107,6 +107,8 @@ struct LPArgs {
   LPRound *R;                  // current round (written by k_round_begin)
   unsigned long long *tmin;    // profiling (nullable): per k_rate launch (round * S + sub-round)
   unsigned long long *tmax;    // the earliest CTA start and the latest CTA end, global-timer ns
+  unsigned long long *smax;    // latest CTA end of the sub-round's whole rating stage (k_rate
+                               // and the hub kernels after it)
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -507,8 +509,19 @@ __global__ void __launch_bounds__(RATE_T) k_rate(LPArgs A, int s) {
   }
   if (A.tmin) {
     __syncthreads();
-    if (threadIdx.x == 0) atomicMax(&A.tmax[tslot], global_ns());
+    if (threadIdx.x == 0) {
+      unsigned long long t = global_ns();
+      atomicMax(&A.tmax[tslot], t);
+      atomicMax(&A.smax[tslot], t);
+    }
   }
+}
+
+// profiling: the end of the rating stage of sub-round s (its last kernel)
+__device__ __forceinline__ void stamp_stage_end(const LPArgs &A, int s) {
+  if (!A.tmin) return;
+  __syncthreads();
+  if (threadIdx.x == 0) atomicMax(&A.smax[(int64_t)__ldg(&A.R->r) * A.S + s], global_ns());
 }
 
 // ---- hubs (bin 6) with many labels: insert / reduce / emit
@@ -749,6 +762,7 @@ __global__ void __launch_bounds__(256) k_hub_emit(LPArgs A, int s) {
     A.hrown[h] = 0;
     A.hcount[h] = 0;
   }
+  stamp_stage_end(A, s);
 }
 
 // ---- hubs with few labels (refinement): dense rating rows
@@ -830,6 +844,7 @@ __global__ void __launch_bounds__(256) k_hubd_reduce(LPArgs A, int s) {
     }
     __syncthreads();
   }
+  stamp_stage_end(A, s);
 }
 
 __global__ void k_hub_flags(int32_t n, const int64_t *xadj, int64_t huge, uint8_t *flag) {
@@ -1205,15 +1220,18 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   // replayed graph needs no extra nodes) and each round's bin offsets, all
   // read after the run
   DBuf<int32_t> boff_all;
-  DBuf<unsigned long long> tmin, tmax;
+  DBuf<unsigned long long> tmin, tmax, smax;
   if (C.profile) {
     boff_all.alloc((size_t)(S * NB + 1) * rounds);
     tmin.alloc((size_t)S * rounds);
     tmax.alloc((size_t)S * rounds);
+    smax.alloc((size_t)S * rounds);
     tmin.fill_bytes(0xFF);
     tmax.zero();
+    smax.zero();
     A.tmin = tmin;
     A.tmax = tmax;
+    A.smax = smax;
   }
   // one LP round: binning, then per sub-round rating, hub rating and commit
   auto launch_round = [&](cudaStream_t st) {
@@ -1271,18 +1289,22 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   // entry, own label, proposal (target, gain) (+ node weight); hubs rated by
   // the hub kernels are not k_rate's work)
   auto profile_rounds = [&](int nr) {
-    std::vector<unsigned long long> h((size_t)18 * nr), t0((size_t)S * nr), t1((size_t)S * nr);
+    std::vector<unsigned long long> h((size_t)18 * nr), t0((size_t)S * nr), t1((size_t)S * nr),
+        t2((size_t)S * nr);
     std::vector<int32_t> hb((size_t)(S * NB + 1) * nr);
     to_host(h.data(), ctr_all.p, h.size());
     to_host(hb.data(), boff_all.p, hb.size());
     to_host(t0.data(), tmin.p, t0.size());
     to_host(t1.data(), tmax.p, t1.size());
+    to_host(t2.data(), smax.p, t2.size());
     bool hubs_outside = hub_path || dense_hubs;
+    const double per_entry = 8.0 + (g.ew ? 4.0 : 0.0), per_node = 24.0 + (g.vw ? 4.0 : 0.0);
     for (int r = 0; r < nr; ++r) {
       const int32_t *hboff = hb.data() + (size_t)(S * NB + 1) * r;
       for (int s = 0; s < S; ++s) {
-        double V = (double)(hboff[(s + 1) * NB] - hboff[s * NB]);
-        double D = (double)h[18 * r + 2 + s];
+        const double Vall = (double)(hboff[(s + 1) * NB] - hboff[s * NB]);
+        const double Dall = (double)h[18 * r + 2 + s];
+        double V = Vall, D = Dall;
         if (hubs_outside) {
           V -= (double)(hboff[s * NB + 7] - hboff[s * NB + 6]);
           D -= (double)h[18 * r + 10 + s];
@@ -1290,7 +1312,10 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
         size_t i = (size_t)S * r + s;
         C.prof_rate_ms += t1[i] > t0[i] ? (double)(t1[i] - t0[i]) * 1e-6 : 0.0;
         C.prof_rate_launches += 1;
-        C.prof_rate_bytes += D * (8.0 + (g.ew ? 4.0 : 0.0)) + V * (24.0 + (g.vw ? 4.0 : 0.0));
+        C.prof_rate_bytes += D * per_entry + V * per_node;
+        C.prof_stage_ms += t2[i] > t0[i] ? (double)(t2[i] - t0[i]) * 1e-6 : 0.0;
+        C.prof_stage_spans += 1;
+        C.prof_stage_bytes += Dall * per_entry + Vall * per_node;
       }
     }
   };

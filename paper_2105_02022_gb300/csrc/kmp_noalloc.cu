@@ -7,45 +7,94 @@
 // and latency-critical loops that cannot afford the implicit synchronisation
 // and possible failure of an allocation at call time.  kmp_cut_noalloc gives
 // them the same result with its scratch in a fixed file-scope device array.
+//
+// The array lives in this file's module.  With lazy module loading (the CUDA
+// default) the module, and with it the array's memory, is loaded the first
+// time anything in it is used; the library therefore resolves the array's
+// address while it initialises on a device (noalloc_prepare, called from the
+// first library call there), so that the load happens then and not inside a
+// later kmp_cut_noalloc call.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "kmp_internal.cuh"
 
 namespace kmp {
 
-
 // [0] cut, [1] out-of-range flag, [2 .. 2+k) block weights
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[KMP_NOALLOC_MAX_K + 2];
 
 namespace {
 constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned long long *g_ptr[kMaxDevices] = {};
+constexpr int kStagedK = 2048;  // block weights staged in shared memory up to this k
 
-// device address of the scratch array for the current device (looked up once
-// per device; the host-side symbol is only a stand-in, never a device address)
+// one entry per device: the array's device address and the context it was
+// resolved in (a context recreated after cudaDeviceReset has a new id, and the
+// address must be looked up again)
+struct Slot {
+  unsigned long long *ptr = nullptr;
+  unsigned long long ctx_id = 0;
+};
+std::mutex g_mu;
+Slot g_slot[kMaxDevices];
+
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// id of the current context (0 when the driver cannot tell); the entry point
+// is fetched through the runtime so that the library does not link libcuda
+unsigned long long current_ctx_id() {
+  static CtxGetIdFn fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<CtxGetIdFn>(p);
+  }();
+  unsigned long long id = 0;
+  if (fn && fn(nullptr, &id) != CUDA_SUCCESS) id = 0;
+  return id;
+}
+
+// device address of the scratch array on the current device.  The host-side
+// symbol is only a stand-in and never a device address, so it is looked up
+// with cudaGetSymbolAddress: once per device (and again only if the device's
+// context was recreated).
 unsigned long long *scratch_ptr() {
   int dev = 0;
   KMP_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) fail(KMP_ERR_UNSUPPORTED, "device index beyond 64");
+  const unsigned long long id = current_ctx_id();
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_ptr[dev]) {
+  Slot &s = g_slot[dev];
+  if (!s.ptr || s.ctx_id != id) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) fail(KMP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_ptr[dev] = static_cast<unsigned long long *>(p);
+    s.ptr = static_cast<unsigned long long *>(p);
+    s.ctx_id = id;
   }
-  return g_ptr[dev];
+  return s.ptr;
 }
 }  // namespace
 
+// called while the library initialises on the current device
+void noalloc_prepare() { scratch_ptr(); }
+
 // same row walk as the allocating cut kernel: a warp takes 32 consecutive
-// nodes, lanes over each row's entries; block weights go straight to scratch
+// nodes, lanes over each row's entries; for k <= kStagedK each CTA adds its
+// block weights in shared memory first, then once per block into scratch
 __global__ void __launch_bounds__(256) k_cut_noalloc(int32_t n, int32_t k, const int64_t *xadj,
                                                      const int32_t *adj, const int32_t *vw,
                                                      const int32_t *ew, const int32_t *part,
                                                      unsigned long long *scratch) {
+  __shared__ unsigned long long sbw[kStagedK];
   unsigned long long *cut = scratch, *flag = scratch + 1, *bw = scratch + 2;
+  const bool staged = k <= kStagedK;
+  if (staged)
+    for (int i = threadIdx.x; i < k; i += blockDim.x) sbw[i] = 0;
+  __syncthreads();
   int lane = threadIdx.x & 31;
   int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -55,7 +104,11 @@ __global__ void __launch_bounds__(256) k_cut_noalloc(int32_t n, int32_t k, const
     int32_t p = my < n ? part[my] : -1;
     bool ok = p >= 0 && p < k;
     if (my < n && !ok) atomicOr(flag, 1ull);
-    if (ok) atomicAdd(&bw[p], (unsigned long long)(vw ? vw[my] : 1));
+    if (ok) {
+      unsigned long long w = (unsigned long long)(vw ? vw[my] : 1);
+      if (staged) atomicAdd(&sbw[p], w);
+      else atomicAdd(&bw[p], w);
+    }
     int jmax = (int)(n - base < 32 ? n - base : 32);
     for (int j = 0; j < jmax; ++j) {
       int64_t v = base + j;
@@ -69,6 +122,11 @@ __global__ void __launch_bounds__(256) k_cut_noalloc(int32_t n, int32_t k, const
 #pragma unroll
   for (int m = 16; m > 0; m >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, m);
   if (lane == 0 && c) atomicAdd(cut, c);
+  if (staged) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < k; i += blockDim.x)
+      if (sbw[i]) atomicAdd(&bw[i], sbw[i]);
+  }
 }
 
 }  // namespace kmp

@@ -47,14 +47,18 @@ class Stats(ctypes.Structure):
                 ("ms_balance", ctypes.c_float), ("ms_refine", ctypes.c_float),
                 ("ms_project", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("ms_lp_level0", ctypes.c_float), ("lp_scanned_level0", ctypes.c_int64),
-                ("lp_rounds_level0", ctypes.c_int32), ("gpu_launches", ctypes.c_int32)]
+                ("lp_rounds_level0", ctypes.c_int32), ("gpu_launches", ctypes.c_int32),
+                ("clustered", ctypes.c_int32), ("level_kp", ctypes.c_int32 * 64),
+                ("level_U", ctypes.c_int64 * 64), ("level_k", ctypes.c_int32 * 64)]
 
     def as_dict(self):
         d = {}
         for name, _ in self._fields_:
             v = getattr(self, name)
-            if name in ("level_n", "level_m"):
+            if name in ("level_n", "level_m", "level_k"):
                 v = list(v)[: self.levels]
+            elif name in ("level_kp", "level_U"):
+                v = list(v)[: self.clustered]
             d[name] = v
         return d
 
@@ -115,6 +119,7 @@ def load():
         "kmp_get_tuning": (ctypes.c_int, [P]),
         "kmp_autotune": (ctypes.c_int, [P, i32, dbl, u64, P]),
         "kmp_profile_read": (ctypes.c_int, [P, P, P, ctypes.c_int]),
+        "kmp_profile_read_stage": (ctypes.c_int, [P, P, P, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -359,11 +364,36 @@ def set_profiling(on: bool):
     _check(load().kmp_set_profiling(1 if on else 0))
 
 
-def profile_read(reset: bool = False):
-    """Rating-kernel launch sums since the last reset: (ms, algorithmic bytes, launches)."""
+class Profile:
+    """Sums of the live rating profile since the last reset."""
+
+    def __init__(self, rate_ms, rate_bytes, rate_launches, stage_ms, stage_bytes, stage_spans):
+        self.rate_ms, self.rate_bytes, self.rate_launches = rate_ms, rate_bytes, rate_launches
+        self.stage_ms, self.stage_bytes, self.stage_spans = stage_ms, stage_bytes, stage_spans
+
+    def __iter__(self):  # (ms, bytes, launches) of k_rate alone
+        return iter((self.rate_ms, self.rate_bytes, self.rate_launches))
+
+    def as_dict(self, peak_gbs=None):
+        gbs = lambda by, ms: by / (ms / 1e3) / 1e9 if ms > 0 else None
+        d = {"rate_ms": self.rate_ms, "rate_bytes": self.rate_bytes, "rate_launches": self.rate_launches,
+             "rate_bytes_per_launch": self.rate_bytes / self.rate_launches if self.rate_launches else None,
+             "rate_gbs": gbs(self.rate_bytes, self.rate_ms), "stage_ms": self.stage_ms,
+             "stage_bytes": self.stage_bytes, "stage_spans": self.stage_spans,
+             "stage_gbs": gbs(self.stage_bytes, self.stage_ms)}
+        d["rate_frac"] = d["rate_gbs"] / peak_gbs if peak_gbs and d["rate_gbs"] else None
+        d["stage_frac"] = d["stage_gbs"] / peak_gbs if peak_gbs and d["stage_gbs"] else None
+        return d
+
+
+def profile_read(reset: bool = False) -> Profile:
+    """Rating profile sums since the last reset; unpacks as (ms, bytes, launches) of k_rate."""
     ms, by, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
-    _check(load().kmp_profile_read(ctypes.byref(ms), ctypes.byref(by), ctypes.byref(n), 1 if reset else 0))
-    return ms.value, by.value, n.value
+    sms, sby, sn = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    L = load()
+    _check(L.kmp_profile_read(ctypes.byref(ms), ctypes.byref(by), ctypes.byref(n), 1 if reset else 0))
+    _check(L.kmp_profile_read_stage(ctypes.byref(sms), ctypes.byref(sby), ctypes.byref(sn), 1 if reset else 0))
+    return Profile(ms.value, by.value, n.value, sms.value, sby.value, sn.value)
 
 
 # ------------------------------------------------------------ learned proposer

@@ -81,15 +81,21 @@ def test_bipartition_config_variants(kmp, cfgkw):
         kmp.set_config(kmp.config())
 
 
-@pytest.mark.parametrize("case", ["rgg", "weighted", "rmat"])
+@pytest.mark.parametrize("case", ["rgg", "weighted", "rmat", "hubs_k1024"])
 def test_balance_parity(kmp, case):
+    k = 6
     if case == "rgg":
         g = gg.rgg(5000, 8, 3)
     elif case == "weighted":
         g = gg.with_weights(gg.rgg(5000, 8, 4), 9, 5, 4)
-    else:
+    elif case == "rmat":
         g = gg.rmat(13, 8, 5)
-    k = 6
+    else:
+        # hubs with more than 256 distinct neighbour blocks: their connectivity
+        # tables exceed a warp's shared table (global-table candidate pass,
+        # speculation hands them to the exact commit, per-member commit tables)
+        g = gg.hubs(30000, [3000, 12000, 700, 2500], 60000, 8)
+        k = 1024
     part = (np.arange(g.n) * k // g.n).astype(np.int32)
     part[g.n // 6: g.n // 3] = 0
     part[g.n // 2: g.n // 2 + 300] = 5
@@ -121,13 +127,23 @@ def test_balance_many_adjacent_overloaded_blocks(kmp):
     assert np.array_equal(pt.cpu().numpy(), rp)
 
 
+def _same_schedule(st, rst):
+    """Level sizes, k', U and block counts per level equal the oracle's."""
+    assert st.levels == rst.levels
+    assert list(st.level_n[: st.levels]) == list(rst.level_n[: rst.levels])
+    assert list(st.level_k[: st.levels]) == list(rst.level_k[: rst.levels])
+    assert st.clustered == rst.clustered
+    assert list(st.level_kp[: st.clustered]) == list(rst.level_kp[: rst.clustered])
+    assert list(st.level_U[: st.clustered]) == list(rst.level_U[: rst.clustered])
+
+
 PARTS = [
     ("path", lambda: gg.path(700), [2, 5]),
     ("grid", lambda: gg.grid(40, 60), [2, 4, 7]),
     ("rgg15", lambda: gg.workload_rgg_small(1), [8, 3, 64]),
     ("rgg_w", lambda: gg.with_weights(gg.rgg(12000, 8, 6), 5, 9, 6), [7, 16]),
     ("rmat14", lambda: gg.rmat(14, 16, 2), [32, 5]),
-    ("hubs", lambda: gg.hubs(30000, [3000, 12000], 60000, 8), [16]),
+    ("hubs", lambda: gg.hubs(30000, [3000, 12000], 60000, 8), [16, 600]),
     # 16 nodes per block: L_k leaves no slack, so the result may be infeasible
     # (both sides must agree on that too)
     ("rgg15_k2048", lambda: gg.workload_rgg_small(1), [2048]),
@@ -155,8 +171,7 @@ def test_replication_parity(kmp, name, make, k, Rs):
             rp, rrc, rst = O.partition(g, k, 0.03, 1, O.config(replicas=R))
             assert np.array_equal(part.cpu().numpy(), rp), (name, R)
             assert rc == rrc and st.cut == rst.cut and st.feasible == rst.feasible
-            assert st.levels == rst.levels
-            assert list(st.level_n[: st.levels]) == list(rst.level_n[: rst.levels])
+            _same_schedule(st, rst)
     finally:
         kmp.set_config(kmp.config())
 
@@ -172,8 +187,25 @@ def test_partition_parity(kmp, name, make, ks):
             got = part.cpu().numpy()
             assert np.array_equal(got, rp), (name, k, seed)
             assert rc == rrc and st.cut == rst.cut and st.feasible == rst.feasible
-            assert st.levels == rst.levels
-            assert list(st.level_n[: st.levels]) == list(rst.level_n[: rst.levels])
+            _same_schedule(st, rst)
+
+
+def test_schedule_halving_chain_on_isolated_nodes(kmp):
+    """2^15 isolated unit nodes, k = 128, eps = 0.0157: every level is known
+    in closed form (Section 4.1 and Algorithm 1, readings D1 and D2; the
+    derivation is in the oracle's pin of the same name).  The GPU partition
+    is bit-exact with the oracle and its schedule equals the hand values."""
+    n = 1 << 15
+    g = gg.Graph(n, np.zeros(n + 1, np.int64), np.zeros(0, np.int32), None, None)
+    dg = kmp.DeviceGraph.from_host(g)
+    part, rc, st = kmp.partition_graph(dg, 128, 0.0157, 1)
+    rp, rrc, rst = O.partition(g, 128, 0.0157, 1)
+    assert np.array_equal(part.cpu().numpy(), rp) and rc == rrc
+    assert list(st.level_n[:7]) == [32768, 8192, 4096, 2048, 1024, 512, 256] and st.levels == 7
+    assert list(st.level_kp[:6]) == [128, 64, 32, 16, 8, 4]
+    assert list(st.level_U[:6]) == [4, 8, 16, 32, 64, 128]
+    assert list(st.level_k[:7]) == [128, 64, 32, 16, 8, 4, 2]
+    _same_schedule(st, rst)
 
 
 @pytest.mark.parametrize("tune", [(4, 1024, 1024, 2, 600, 0), (8, 2048, 4096, 8, 1 << 30, 1),

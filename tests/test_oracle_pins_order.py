@@ -174,3 +174,16 @@ def test_schedule_cap_is_at_least_the_heaviest_node():
     assert st.level_kp[0] == 6 and st.level_U[0] == 500
     assert st.levels == 2 and list(st.level_n)[:2] == [1000, 3]
     assert list(st.level_k)[:2] == [8, 2]
+
+
+def test_balance_order_is_fixed_by_the_starting_state():
+    """Block 0 = {x = 0, y = 1, z = 2, anchor a = 3 (c 10, isolated)}, unit
+    x, y, z; block 1 = {p = 4}, block 2 = {q = 5}; edges x-p (5), x-y (1),
+    y-p (1), z-q (1); cap0 = 11 < 13, so two unit nodes must leave.
+    Starting-state relative gains: x: 5 - 1 = 4; y: 1 - 1 = 0; z: 1; a: 0.
+    Order x, z, y, a: x goes to block 1, then z to block 2, and block 0 fits.
+    (Re-rating after x's move would give y: 2 - 0 = 2 > z and move y.)"""
+    g = gg.from_edges(6, [(0, 4, 5), (0, 1, 1), (1, 4, 1), (2, 5, 1)], vwgt=[1, 1, 1, 10, 1, 1])
+    part = np.array([0, 0, 0, 0, 1, 2], np.int32)
+    out, mv = O.balance(g, 3, np.array([11, 100, 100], np.int32), part)
+    assert out.tolist() == [1, 0, 2, 0, 1, 2] and mv == 2
