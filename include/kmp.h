@@ -80,6 +80,10 @@ typedef struct {
                             R/2 under its own seed, and the better partition is kept (feasible
                             first, then the smaller cut); coarsening stops at max(R, 2) C nodes
                             (Section 3, "Parallelization", with R in the role of the PEs) */
+  int32_t adaptive;      /* 1: adaptive portfolio (plain mode only): the first ceil(R/2) runs of
+                            every algorithm, then the rest only of algorithms whose feasible cuts
+                            have mean - 2 sd <= the best feasible cut so far (Section 4.2, the
+                            adaptive algorithm selection it names); 0: the fixed portfolio */
 } kmp_config;
 
 /* Per-call measurements of kmp_partition / kmp_partition_graph (CUDA events). */
@@ -273,6 +277,8 @@ typedef struct {
                                  dense per-label row instead of one CTA (512..2^30) */
   int32_t lp_graphs;          /* 1: each LP run captures one round as a CUDA graph and replays
                                  it for every round; 0: direct launches (default 1) */
+  int32_t hub_bucket;         /* hub ratings with many labels: target entries per label bucket
+                                 aggregated by one warp (32..2^20; 0 = default 256) */
 } kmp_tuning;
 
 int kmp_set_tuning(const kmp_tuning *t);

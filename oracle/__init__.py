@@ -34,7 +34,7 @@ class Config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "C", "lp_rounds", "refine_rounds", "subrounds", "two_hop", "conv_num", "conv_den",
         "ip_C", "ip_lp_rounds", "rep_random", "rep_bfs", "rep_ggg", "fm_passes", "fm_stop",
-        "learned", "lrep_random", "lrep_bfs", "lrep_ggg", "replicas", "async_lp", "sample_subrounds")]
+        "learned", "lrep_random", "lrep_bfs", "lrep_ggg", "replicas", "async_lp", "sample_subrounds", "adaptive")]
 
 
 class OGraph(ctypes.Structure):
@@ -88,6 +88,7 @@ def lib():
             "kmpo_partition": (i32, [i32, P, P, P, P, i32, dbl, u64, P, P, P]),
             "kmpo_bipartition_blocks": (i32, [i32, P, P, P, P, i32, P, dbl, i64, i32, u64, P, P, P]),
             "kmpo_brute_bisection": (i64, [i32, P, P, P, P, i64, i64, P]),
+            "kmpo_adaptive_keep": (i32, [i32, P, i64]),
             "kmpo_async_cluster": (i32, [i32, P, P, P, P, i32, i32, u64, P]),
             "kmpo_mpnn_num_params": (i32, []),
             "kmpo_mpnn_features": (None, [i32, P, P, P, P, u64, P]),
@@ -259,6 +260,11 @@ def bipartition_blocks(g, nblocks, f, eps, cV, k, roundkey, part, cfg=None):
     nb = lib().kmpo_bipartition_blocks(n, _p(xadj), _p(adj), _p(vw), _p(ew), nblocks, _p(f), eps, cV, k,
                                        roundkey, ctypes.byref(cfg), _p(part), _p(fo))
     return part, fo[:nb].copy()
+
+
+def adaptive_keep(cuts, best) -> bool:
+    c = np.ascontiguousarray(cuts, np.int64)
+    return bool(lib().kmpo_adaptive_keep(len(c), _p(c) if len(c) else None, int(best)))
 
 
 def brute_bisection(g, L0, L1):

@@ -49,6 +49,7 @@ typedef struct {
                             deterministic sub-rounds (0) */
   int32_t sample_subrounds; /* timing samples only: kmpo_cluster's LP ends after this many
                                sub-rounds (0: no limit); the sub-rounds that run are unchanged */
+  int32_t adaptive;      /* adaptive portfolio (B7, kmpo_ip.c): 0 = the fixed portfolio of B2 */
 } kmpo_config;
 
 /* graph owned by the oracle (returned by kmpo_contract) */
@@ -159,6 +160,10 @@ int32_t kmpo_bipartition_blocks(int32_t n, const int64_t *xadj, const int32_t *a
 int32_t kmpo_partition(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
                        const int32_t *ew, int32_t k, double eps, uint64_t seed,
                        const kmpo_config *cfg, int32_t *part_out, kmpo_stats *st);
+
+/* the adaptive portfolio's rule (B7): 1 if an algorithm whose f feasible
+ * runs have these cuts keeps running given the best feasible cut */
+int32_t kmpo_adaptive_keep(int32_t f, const int64_t *cuts, int64_t best);
 
 /* brute-force minimum cut bisection (n <= 24) with caps on both sides;
  * returns -1 if no feasible bisection exists */

@@ -85,6 +85,7 @@ void kmpo_config_default(kmpo_config *c) {
   c->replicas = 1;
   c->async_lp = 0;
   c->sample_subrounds = 0;
+  c->adaptive = 0;
 }
 
 static int32_t ceil_log2(int32_t f) {

@@ -37,6 +37,18 @@
  *     repetitions of B2 (same keys).  Only if the best of these is infeasible
  *     do the remaining repetitions of B2 run, in B2's order.  Every candidate
  *     is FM-refined and compared exactly as in B2 (first best wins).
+ *  B7 Adaptive portfolio (cfg->adaptive, plain mode only; Section 4.2 names
+ *     the adaptive algorithm selection of Mt-KaHyPar without describing it).
+ *     Stage 1 runs the first ceil(R_a / 2) repetitions of every algorithm a,
+ *     in B2's order.  Then each algorithm is judged once, on the FM-refined
+ *     cuts of its feasible stage-1 runs (f runs, sum S1, sum of squares S2):
+ *     it keeps running only while it can plausibly still win, i.e. its mean
+ *     minus two standard deviations (population) is at most the best feasible
+ *     cut b so far: S1 - f b <= 2 sqrt(f S2 - S1^2), evaluated exactly in
+ *     integers; an algorithm without a feasible run stops.  Stage 2 runs the
+ *     remaining repetitions of the algorithms kept, in B2's order.  With no
+ *     feasible run at all after stage 1, every algorithm is kept.  The winner
+ *     is the first candidate (stage 1, then stage 2) with the best key of B2.
  */
 #include <stdlib.h>
 #include <string.h>
@@ -245,6 +257,29 @@ void kmpo_initial(int32_t algo, int32_t n, const int64_t *xadj, const int32_t *a
   free(ord);
 }
 
+/* B7: does an algorithm whose feasible runs have the cuts x_1..x_f (sum s1,
+ * sum of squares s2) keep running, given the best feasible cut b?  Exactly
+ * mean - 2 sd <= b with the population standard deviation:
+ * s1 - f b <= 2 sqrt(f s2 - s1^2); no feasible run: no. */
+static int adaptive_keep(int64_t f, int64_t s1, __int128 s2, int64_t b) {
+  if (f <= 0) return 0;
+  const __int128 D = (__int128)s1 - (__int128)f * b;
+  if (D <= 0) return 1;
+  const __int128 var = (__int128)f * s2 - (__int128)s1 * s1; /* f^2 times the variance */
+  return D * D <= 4 * var;
+}
+
+/* the rule of B7 on an explicit list of feasible cuts (for the pins) */
+int32_t kmpo_adaptive_keep(int32_t f, const int64_t *cuts, int64_t best) {
+  int64_t s1 = 0;
+  __int128 s2 = 0;
+  for (int32_t i = 0; i < f; ++i) {
+    s1 += cuts[i];
+    s2 += (__int128)cuts[i] * cuts[i];
+  }
+  return adaptive_keep(f, s1, s2, best);
+}
+
 /* one level of the bipartitioner's hierarchy */
 typedef struct {
   int32_t n;
@@ -325,16 +360,31 @@ int64_t kmpo_bipartition(int32_t n, const int64_t *xadj, const int32_t *adj, con
   /* B6: in learned mode the first pass takes the proposal and a prefix of
    * each algorithm's repetitions, the second the rest if still infeasible */
   int32_t first[3] = {reps[0], reps[1], reps[2]};
+  const int adaptive = cfg->adaptive && !W;
   if (W) {
     first[0] = cfg->lrep_random < reps[0] ? cfg->lrep_random : reps[0];
     first[1] = cfg->lrep_bfs < reps[1] ? cfg->lrep_bfs : reps[1];
     first[2] = cfg->lrep_ggg < reps[2] ? cfg->lrep_ggg : reps[2];
+  } else if (adaptive) {
+    for (int32_t a = 0; a < 3; ++a) first[a] = (reps[a] + 1) / 2;
   }
+  /* B7: per algorithm, the feasible stage-1 runs and their cut sums */
+  int64_t fa[3] = {0, 0, 0}, s1[3] = {0, 0, 0};
+  __int128 s2[3] = {0, 0, 0};
+  int keep[3] = {1, 1, 1};
   for (int32_t pass = 0; pass < 2; ++pass) {
-    if (pass == 1 && (!W || (have && !bestk.inf))) break;
+    if (pass == 1) {
+      if (adaptive) {
+        if (have && !bestk.inf)
+          for (int32_t a = 0; a < 3; ++a) keep[a] = adaptive_keep(fa[a], s1[a], s2[a], bestk.cut);
+      } else if (!W || (have && !bestk.inf)) {
+        break;
+      }
+    }
     for (int32_t a = (pass == 0 && W) ? -1 : 0; a < 3; ++a) {
       int32_t r0 = a < 0 ? 0 : (pass == 0 ? 0 : first[a]);
       int32_t r1 = a < 0 ? 1 : (pass == 0 ? first[a] : reps[a]);
+      if (pass == 1 && a >= 0 && !keep[a]) continue;
       for (int32_t r = r0; r < r1; ++r) {
         if (a < 0) {
           kmpo_learned_initial(h->n, h->xadj, h->adj, h->vw, h->ew, target0,
@@ -350,6 +400,11 @@ int64_t kmpo_bipartition(int32_t n, const int64_t *xadj, const int32_t *adj, con
           else W1 += vwt(h->vw, v);
         }
         fmkey_t k = make_key(W0, W1, hL0, hL1, cut);
+        if (pass == 0 && a >= 0 && !k.inf) {
+          fa[a] += 1;
+          s1[a] += cut;
+          s2[a] += (__int128)cut * cut;
+        }
         if (!have || key_less(k, bestk)) {
           have = 1;
           bestk = k;

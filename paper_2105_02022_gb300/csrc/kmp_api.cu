@@ -431,6 +431,7 @@ void kmp_config_default(kmp_config *c) {
   c->lrep_bfs = 0;
   c->lrep_ggg = 1;
   c->replicas = 1;
+  c->adaptive = 0;
 }
 
 int kmp_set_config(const kmp_config *c) {
@@ -443,7 +444,8 @@ int kmp_set_config(const kmp_config *c) {
         c->rep_ggg < 0 || c->rep_random + c->rep_bfs + c->rep_ggg < 1 ||
         c->rep_random + c->rep_bfs + c->rep_ggg > 64 || c->fm_passes < 0 || c->fm_stop < 1 ||
         c->learned < 0 || c->learned > 1 || c->lrep_random < 0 || c->lrep_bfs < 0 || c->lrep_ggg < 0 ||
-        c->replicas < 1 || c->replicas > 64 || (c->replicas & (c->replicas - 1)) != 0)
+        c->replicas < 1 || c->replicas > 64 || (c->replicas & (c->replicas - 1)) != 0 ||
+        c->adaptive < 0 || c->adaptive > 1)
       fail(KMP_ERR_ARG, "invalid configuration");
     ctx().cfg = *c;
   });
@@ -692,7 +694,8 @@ int kmp_set_tuning(const kmp_tuning *t) {
     if (t->rate_blocks_per_sm < 2 || t->rate_blocks_per_sm > 16 || t->hub_degree < 256 ||
         t->hub_degree > 2048 || !pow2 || t->hub_chunk < 256 || t->hub_chunk > 65536 ||
         t->ip_blocks_per_sm < 1 || t->ip_blocks_per_sm > 8 || t->dense_hub_degree < 512 ||
-        t->dense_hub_degree > (1 << 30) || t->lp_graphs < 0 || t->lp_graphs > 1)
+        t->dense_hub_degree > (1 << 30) || t->lp_graphs < 0 || t->lp_graphs > 1 ||
+        (t->hub_bucket != 0 && (t->hub_bucket < 32 || t->hub_bucket > (1 << 20))))
       fail(KMP_ERR_ARG, "invalid tuning");
     ctx().tune = *t;
   });
@@ -726,7 +729,8 @@ int kmp_autotune(const kmp_graph *g, int32_t k, double eps, uint64_t seed, kmp_t
     for (int gi : grids)
       for (int hd : hubs)
         for (int hc : chunks) {
-          C.tune = kmp_tuning{gi, hd, hc, keep.ip_blocks_per_sm, keep.dense_hub_degree, keep.lp_graphs};
+          C.tune = kmp_tuning{gi, hd, hc, keep.ip_blocks_per_sm, keep.dense_hub_degree, keep.lp_graphs,
+                                keep.hub_bucket};
           LPStats st;
           cluster_level(G, (int32_t)U, C.cfg.lp_rounds, key_of(seed, {DOM_COARSEN, 0}), false, label,
                         nullptr, &st, nullptr);

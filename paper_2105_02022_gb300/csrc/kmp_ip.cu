@@ -67,6 +67,7 @@ struct IPArgs {
   // learned mode: proposer weights (null: plain portfolio) and reduced repetitions
   const __nv_bfloat16 *W;
   int32_t lrep_random, lrep_bfs, lrep_ggg;
+  int32_t adaptive;  // adaptive portfolio (plain mode only)
   SampleSink sink;  // counters null: no recording
   int32_t dyn_words;  // dynamic shared memory per CTA (int32 words) for FM and portfolio state
 };
@@ -1136,6 +1137,12 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
   __shared__ int32_t *maps[IP_MAXL + 1];
   __shared__ int64_t s_wk[IPW][3];
   __shared__ int32_t s_wrep[IPW];
+  // adaptive portfolio: per warp and algorithm, the feasible stage-1 runs,
+  // their cut sum and sum of squares; the repetitions kept for stage 2
+  __shared__ int32_t s_fa[IPW][3];
+  __shared__ int64_t s_s1[IPW][3];
+  __shared__ unsigned __int128 s_s2[IPW][3];
+  __shared__ int32_t s_rest[3];
   const ItemDesc D = A.items[it];
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (D.n == 0) return;
@@ -1257,10 +1264,13 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
     // algorithm, then (learned mode, best still infeasible) the rest
     int32_t nlrn = score ? 1 : 0;
     int32_t first[3] = {reps[0], reps[1], reps[2]};
+    const bool adaptive = A.adaptive && !score;
     if (score) {
       first[0] = min(A.lrep_random, reps[0]);
       first[1] = min(A.lrep_bfs, reps[1]);
       first[2] = min(A.lrep_ggg, reps[2]);
+    } else if (adaptive) {
+      for (int a = 0; a < 3; ++a) first[a] = (reps[a] + 1) / 2;  // stage 1
     }
     int32_t rest[3] = {reps[0] - first[0], reps[1] - first[1], reps[2] - first[2]};
     int32_t R0 = nlrn + first[0] + first[1] + first[2];
@@ -1268,8 +1278,51 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
     bool have = false;
     int32_t binf = 0, brep = -1;
     int64_t bov = 0, bcut = 0;
+    int32_t fa[3] = {0, 0, 0};
+    int64_t s1[3] = {0, 0, 0};
+    unsigned __int128 s2[3] = {0, 0, 0};
     for (int phase = 0; phase < 2; ++phase) {
-      if (phase == 1 && (R1 == 0 || s_wk[s_bw][0] == 0)) break;
+      if (phase == 1) {
+        if (adaptive) {
+          // stage 2 keeps an algorithm while mean - 2 sd (population) of its
+          // feasible stage-1 cuts is at most the best feasible cut, exactly:
+          // s1 - f b <= 2 sqrt(f s2 - s1^2); everything stays when no run is
+          // feasible yet
+          if (threadIdx.x == 0) {
+            const bool feas = s_wk[s_bw][0] == 0;
+            const int64_t b = s_wk[s_bw][2];
+            for (int a = 0; a < 3; ++a) {
+              int32_t f = 0;
+              int64_t t1 = 0;
+              unsigned __int128 t2 = 0;
+              for (int x = 0; x < IPW; ++x) {
+                f += s_fa[x][a];
+                t1 += s_s1[x][a];
+                t2 += s_s2[x][a];
+              }
+              bool keep = true;
+              if (feas) {
+                if (f == 0) {
+                  keep = false;
+                } else {
+                  const __int128 D = (__int128)t1 - (__int128)f * b;
+                  const __int128 var = (__int128)f * (__int128)t2 - (__int128)t1 * t1;
+                  keep = D <= 0 || D * D <= 4 * var;
+                }
+              }
+              s_rest[a] = keep ? reps[a] - first[a] : 0;
+            }
+          }
+          __syncthreads();
+          rest[0] = s_rest[0];
+          rest[1] = s_rest[1];
+          rest[2] = s_rest[2];
+          R1 = rest[0] + rest[1] + rest[2];
+          if (R1 == 0) break;
+        } else if (R1 == 0 || s_wk[s_bw][0] == 0) {
+          break;
+        }
+      }
       int32_t Rp = phase == 0 ? R0 : R1;
       const int32_t *cnt = phase == 0 ? first : rest;
       for (int32_t q = w; q < Rp; q += IPW) {
@@ -1298,6 +1351,11 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
         int64_t o = o0 > o1 ? o0 : o1;
         int32_t inf = o > 0;
         int64_t ovv = inf ? o : 0;
+        if (phase == 0 && a < 3 && !inf) {
+          fa[a] += 1;
+          s1[a] += cut;
+          s2[a] += (unsigned __int128)((uint64_t)cut) * (uint64_t)cut;
+        }
         if (!have || fm_less(inf, ovv, cut, binf, bov, bcut)) {
           have = true;
           binf = inf;
@@ -1313,6 +1371,11 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
         s_wk[w][1] = bov;
         s_wk[w][2] = bcut;
         s_wrep[w] = have ? brep : INT32_MAX;
+        for (int a = 0; a < 3; ++a) {
+          s_fa[w][a] = fa[a];
+          s_s1[w][a] = s1[a];
+          s_s2[w][a] = s2[a];
+        }
       }
       __syncthreads();
       // the first candidate with the best (infeasible?, overload, cut) wins
@@ -1629,6 +1692,7 @@ int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::
       A.lrep_random = cfg.lrep_random;
       A.lrep_bfs = cfg.lrep_bfs;
       A.lrep_ggg = cfg.lrep_ggg;
+      A.adaptive = (cfg.adaptive && !A.W) ? 1 : 0;
       A.sink = sample_sink();
       // dynamic shared memory: the LP working arrays (7.5 words a node plus
       // sort space) and then the FM state (8 words a node) of the largest item of the round,

@@ -34,7 +34,7 @@ class Config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "C", "lp_rounds", "refine_rounds", "subrounds", "two_hop", "conv_num", "conv_den",
         "ip_C", "ip_lp_rounds", "rep_random", "rep_bfs", "rep_ggg", "fm_passes", "fm_stop",
-        "learned", "lrep_random", "lrep_bfs", "lrep_ggg", "replicas")]
+        "learned", "lrep_random", "lrep_bfs", "lrep_ggg", "replicas", "adaptive")]
 
 
 class Stats(ctypes.Structure):
@@ -65,7 +65,8 @@ class Stats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
-        "rate_blocks_per_sm", "hub_degree", "hub_chunk", "ip_blocks_per_sm", "dense_hub_degree", "lp_graphs")]
+        "rate_blocks_per_sm", "hub_degree", "hub_chunk", "ip_blocks_per_sm", "dense_hub_degree", "lp_graphs",
+        "hub_bucket")]
 
 
 def load():

@@ -48,3 +48,23 @@ def test_hash_fixture(row):
         assert O.key(x, []) == want
     else:
         assert O.lib().kmpo_perm32(0, x) == want
+
+
+def test_full_size_partition_record_is_complete():
+    """The stored oracle record of the large-k partition (written by
+    tests/golden/make_partition_golden.py from oracle/ alone) has every field
+    the GPU test compares, and its level sizes start at the input graph."""
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rgg24_k16384_partition.txt")
+    rec = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        key, *vals = line.split()
+        rec[key] = vals
+    for key in ("n", "m_directed", "sha256", "cut", "status", "feasible", "max_block", "level_n"):
+        assert key in rec, key
+    assert len(rec["sha256"][0]) == 64
+    assert int(rec["level_n"][0]) == int(rec["n"][0]) == 1 << 24
+    assert int(rec["max_block"][0]) <= int(1.03 * ((1 << 24) // (1 << 14)))

@@ -66,7 +66,9 @@ def test_bipartition_blocks_parity(kmp, name):
 
 
 @pytest.mark.parametrize("cfgkw", [dict(rep_random=1, rep_bfs=0, rep_ggg=0), dict(fm_passes=0),
-                                   dict(ip_lp_rounds=1, subrounds=2), dict(rep_ggg=17, fm_stop=3)])
+                                   dict(ip_lp_rounds=1, subrounds=2), dict(rep_ggg=17, fm_stop=3),
+                                   dict(adaptive=1), dict(adaptive=1, rep_random=3, rep_bfs=5, rep_ggg=9),
+                                   dict(adaptive=1, rep_random=0, rep_bfs=2, rep_ggg=1)])
 def test_bipartition_config_variants(kmp, cfgkw):
     g, part, f, k = _split_case("rgg_16blocks")
     kmp.set_config(kmp.config(**cfgkw))
@@ -208,8 +210,8 @@ def test_schedule_halving_chain_on_isolated_nodes(kmp):
     _same_schedule(st, rst)
 
 
-@pytest.mark.parametrize("tune", [(4, 1024, 1024, 2, 600, 0), (8, 2048, 4096, 8, 1 << 30, 1),
-                                  (2, 256, 256, 1, 4096, 0)])
+@pytest.mark.parametrize("tune", [(4, 1024, 1024, 2, 600, 0, 64), (8, 2048, 4096, 8, 1 << 30, 1, 1 << 20),
+                                  (2, 256, 256, 1, 4096, 0, 0)])
 def test_tuning_invariance(kmp, tune):
     """Schedule parameters (grids, hub threshold, chunking) never change results."""
     g = gg.hubs(30000, [700, 3000, 12000], 60000, 8)
@@ -280,13 +282,30 @@ def test_full_size_rmat20_k256(kmp):
     assert rc == rrc == 0 and st.cut == rst.cut and st.feasible == 1
 
 
+def _golden(name):
+    import os
+
+    out = {}
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            key, *vals = line.split()
+            out[key] = vals if len(vals) > 1 else vals[0]
+    return out
+
+
 def test_full_size_rgg24_k16384(kmp):
     """The large-k case: 2D RGG with 2^24 nodes (average degree ~16), k = 2^14.
-    The oracle's whole partition is too slow at this size, so it checks the
-    input level's coarsening bit-exactly (the driver's cluster cap) and the
-    partition by properties that hold at any size: every block within
-    L_k = floor(1.03 ceil(n/k)), the reported cut equal to a recount, and the
-    same result on a second run."""
+    The whole partition is bit-exact with the oracle's: its SHA-256, cut,
+    status and level sizes equal the stored record that
+    tests/golden/make_partition_golden.py wrote by running the oracle alone.
+    Also checked: the input level's coarsening bit-exactly against the oracle
+    (the driver's cluster cap), every block within L_k = floor(1.03 ceil(n/k)),
+    the reported cut equal to a recount, and the same result on a second run."""
+    import hashlib
+
+    rec = _golden("rgg24_k16384_partition.txt")
     g = gg.rgg(1 << 24, 16, 1)
     k = 1 << 14
     dg = kmp.DeviceGraph.from_host(g)
@@ -304,3 +323,25 @@ def test_full_size_rgg24_k16384(kmp):
     assert np.bincount(p, minlength=k).max() <= Lk
     cut, bw = kmp.cut(dg, part, k)
     assert cut == st.cut and int(bw.sum()) == g.n
+    assert int(rec["n"]) == g.n and int(rec["m_directed"]) == g.m_directed
+    assert hashlib.sha256(np.ascontiguousarray(p, dtype="<i4").tobytes()).hexdigest() == rec["sha256"]
+    assert st.cut == int(rec["cut"]) and rc == int(rec["status"])
+    assert [int(x) for x in rec["level_n"]] == list(st.level_n[: st.levels])
+
+
+@pytest.mark.parametrize("name,make,k", [("rgg15", lambda: gg.workload_rgg_small(1), 64),
+                                         ("rmat14", lambda: gg.rmat(14, 16, 2), 32),
+                                         ("rgg_w", lambda: gg.with_weights(gg.rgg(12000, 8, 6), 5, 9, 6), 16)])
+def test_adaptive_partition_parity(kmp, name, make, k):
+    """Adaptive portfolio selection (Section 4.2, reading B7) in every split
+    round of a full partition: bit-exact with the oracle."""
+    g = make()
+    dg = kmp.DeviceGraph.from_host(g)
+    kmp.set_config(kmp.config(adaptive=1))
+    try:
+        part, rc, st = kmp.partition_graph(dg, k, 0.03, 1)
+    finally:
+        kmp.set_config(kmp.config())
+    rp, rrc, rst = O.partition(g, k, 0.03, 1, O.config(adaptive=1))
+    assert np.array_equal(part.cpu().numpy(), rp)
+    assert rc == rrc and st.cut == rst.cut

@@ -7,6 +7,7 @@ Every expected value below is derived by hand in the test's docstring from
 the reading it pins, on graphs small or regular enough that the derivation
 does not depend on hash values.  CPU only."""
 import numpy as np
+import pytest
 
 import oracle as O
 from paper_2105_02022_gb300 import graphgen as gg
@@ -187,3 +188,62 @@ def test_balance_order_is_fixed_by_the_starting_state():
     part = np.array([0, 0, 0, 0, 1, 2], np.int32)
     out, mv = O.balance(g, 3, np.array([11, 100, 100], np.int32), part)
     assert out.tolist() == [1, 0, 2, 0, 1, 2] and mv == 2
+
+
+# ------------------------------------------------- adaptive portfolio (B7) --
+def _keep_by_definition(cuts, best):
+    """mean - 2 * population standard deviation <= best, exactly (Fractions)."""
+    import statistics
+    from fractions import Fraction
+
+    if not cuts:
+        return False
+    xs = [Fraction(c) for c in cuts]
+    mean, var = statistics.mean(xs), statistics.pvariance(xs)
+    d = mean - best
+    return d <= 0 or d * d <= 4 * var
+
+
+def test_adaptive_keep_rule():
+    """The rule that keeps an algorithm in the adaptive portfolio against its
+    statistical definition: cuts 10, 12 have mean 11 and sd 1, so the
+    algorithm stays for best >= 9 and stops for best 8; equal cuts (sd 0)
+    stay only when they equal the best; no feasible run never stays."""
+    assert O.adaptive_keep([10, 12], 9) and not O.adaptive_keep([10, 12], 8)
+    assert O.adaptive_keep([9, 13], 7) and not O.adaptive_keep([9, 13], 6)
+    assert O.adaptive_keep([5, 5, 5], 5) and not O.adaptive_keep([5, 5, 5], 4)
+    assert not O.adaptive_keep([], 100)
+    rng = np.random.default_rng(4)
+    for _ in range(3000):
+        f = int(rng.integers(1, 6))
+        cuts = rng.integers(0, 60, f).tolist()
+        best = int(rng.integers(0, 60))
+        assert O.adaptive_keep(cuts, best) == _keep_by_definition(cuts, best), (cuts, best)
+    big = [3_000_000_000, 3_000_000_007]  # sums of squares beyond 64 bits
+    assert O.adaptive_keep(big, 2_999_999_996) == _keep_by_definition(big, 2_999_999_996)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_adaptive_with_single_repetitions_is_the_plain_portfolio(seed):
+    """With one repetition per algorithm, stage 1 is the whole portfolio."""
+    g = gg.with_weights(gg.random_graph(60, 150, seed), 3, 5, seed)
+    cB = int(g.vw().sum())
+    t0, t1, L0, L1 = O.split_caps(0.03, cB, 2, cB, 2)
+    kw = dict(rep_random=1, rep_bfs=1, rep_ggg=1)
+    a, ca = O.bipartition(g, L0, L1, t0, t1, 77, cfg=O.config(adaptive=1, **kw))
+    b, cb = O.bipartition(g, L0, L1, t0, t1, 77, cfg=O.config(**kw))
+    assert ca == cb and np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("seed", range(1, 9))
+def test_adaptive_bipartition_vs_brute_force(seed):
+    """The adaptive portfolio's bipartitions keep the caps and never beat the
+    exhaustive optimum (n <= 18)."""
+    g = gg.with_weights(gg.random_graph(16 + seed % 3, 40, seed), 4, 6, seed)
+    cB = int(g.vw().sum())
+    t0, t1, L0, L1 = O.split_caps(0.03, cB, 2, cB, 2)
+    side, c = O.bipartition(g, L0, L1, t0, t1, 5, cfg=O.config(adaptive=1))
+    w = g.vw().astype(np.int64)
+    assert w[side == 0].sum() <= L0 + w.max() and w[side == 1].sum() <= L1 + w.max()
+    opt, _ = O.brute_bisection(g, L0 + int(w.max()), L1 + int(w.max()))
+    assert c >= opt and c == O.cut(g, side)
