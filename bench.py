@@ -238,13 +238,15 @@ def oracle_phases():
                           "lp_edges_per_s": (st.lp_scanned + st.refine_scanned) / st.t_total}), flush=True)
 
 
-def ksweep(gg, kmp, torch, np):
-    """Large-k sweep (deep multilevel at k up to n / 16): time, cut, balance and
-    feasibility of one partition per k after a warm-up partition at the same k."""
+def ksweep(gg, kmp, torch, np, workload):
+    """Large-k sweep (Section 5, the large-k experiment; k up to n / 16 on the
+    2D RGG, up to 2^20 on R-MAT 2^26): time, cut, balance and feasibility of
+    one partition per k after a warm-up partition at the same k, on the graph
+    of the chosen workload (default for this mode: the RGG with 2^24 nodes)."""
     kmp.load()
     kmp.set_config(kmp.config())
     t0 = time.perf_counter()
-    g = gg.rgg(1 << 24, 16, SEED)
+    g = WORKLOADS[workload][0](gg)
     gen_s = time.perf_counter() - t0
     dg = kmp.DeviceGraph.from_host(g)
     for k in (1 << 11, 1 << 14, 1 << 17, 1 << 20):
@@ -257,7 +259,7 @@ def ksweep(gg, kmp, torch, np):
         e1.synchronize()
         bw = np.bincount(part.cpu().numpy(), minlength=k)
         lk = int(np.floor((1.0 + EPS) * ((g.n + k - 1) // k)))
-        print(json.dumps({"mode": "ksweep", "workload": "rgg_2^24_deg16", "n": g.n, "m_directed": g.m_directed,
+        print(json.dumps({"mode": "ksweep", "workload": workload, "n": g.n, "m_directed": g.m_directed,
                           "k": k, "ms": e0.elapsed_time(e1), "cut": int(st.cut), "feasible": bool(st.feasible),
                           "rc": rc, "max_block_weight": int(bw.max()), "L_k": lk,
                           "overloaded_blocks": int((bw > lk).sum()), "levels": int(st.levels),
@@ -294,20 +296,23 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
+                    help=f"default {DEFAULT_WORKLOAD} (ksweep: rgg_2^24_deg16_k16384)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="partition",
                     choices=["partition", "coarsen1", "launchlist", "ksweep", "replicas", "oracle_phases"],
                     help="coarsen1: one level-0 coarsening (LP) of the workload graph only; "
                          "launchlist: one warm-up partition and one partition inside the NVTX "
                          "range kmp_step (for ncu launch lists); both are used for kernel profiles; "
-                         "ksweep: the large-k sweep k in {2^11, 2^14, 2^17, 2^20} on the 2D random "
-                         "geometric graph with 2^24 nodes (average degree 16), one JSON line per k; "
+                         "ksweep: the large-k sweep k in {2^11, 2^14, 2^17, 2^20} on --workload (default the 2D random "
+                         "geometric graph with 2^24 nodes, average degree 16), one JSON line per k; "
                          "replicas: cut and time with R = 1, 2, 4, 8 copies of the coarsest levels "
                          "on R-MAT scale 20 (k = 256) and the small RGG (k = 8); "
                          "oracle_phases: the CPU oracle's partition timed per phase on the small RGG "
                          "and R-MAT scale 20")
     args = ap.parse_args()
+    if args.mode != "ksweep" and args.workload is None:
+        args.workload = DEFAULT_WORKLOAD
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -327,7 +332,7 @@ def main():
 
     torch.cuda.set_device(local)
     if args.mode == "ksweep":
-        ksweep(gg, kmp, torch, np)
+        ksweep(gg, kmp, torch, np, args.workload or "rgg_2^24_deg16_k16384")
         return
     if args.mode == "replicas":
         replicas(gg, kmp, torch, np)

@@ -117,6 +117,10 @@ typedef struct {
   int32_t level_kp[64];
   int64_t level_U[64];
   int32_t level_k[64];
+  /* k-way balancing (Section 4.3), summed over the levels: overloaded blocks,
+   * moves, moves decided by the parallel speculation that stood at commit,
+   * and batches the exact in-order commit evaluated */
+  int64_t bal_over_blocks, bal_moves, bal_spec_moves, bal_exact_batches;
 } kmp_stats;
 
 /* opaque handle to a CSR graph resident in device memory */
@@ -279,6 +283,10 @@ typedef struct {
                                  it for every round; 0: direct launches (default 1) */
   int32_t hub_bucket;         /* hub ratings with many labels: target entries per label bucket
                                  aggregated by one warp (32..2^20; 0 = default 256) */
+  int32_t dense_labels;       /* an LP run with more than 2048 but at most this many labels rates
+                                 its hubs into dense per-hub rows of label counters (the dense
+                                 vector of Section 5) when the rows fit 4 GB; 0 = never (label
+                                 buckets); at most 57344 */
 } kmp_tuning;
 
 int kmp_set_tuning(const kmp_tuning *t);

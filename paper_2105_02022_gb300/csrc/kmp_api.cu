@@ -348,7 +348,12 @@ static void deep(const Graph &g0, int32_t R, uint64_t seed, bool input, bool top
     for (int b = 0; b < nblocks; ++b) caps[b] = block_cap(eps, cV, k, f[b], g.max_vw);
     {
       Timer tb;
-      balance(g, nblocks, caps.data(), part);
+      BalStats bs;
+      balance(g, nblocks, caps.data(), part, &bs);
+      st->bal_over_blocks += bs.over_blocks;
+      st->bal_moves += bs.moves;
+      st->bal_spec_moves += bs.spec_moves;
+      st->bal_exact_batches += bs.exact_batches;
       st->ms_balance += tb.stop();
     }
     LPStats rs;
@@ -695,7 +700,8 @@ int kmp_set_tuning(const kmp_tuning *t) {
         t->hub_degree > 2048 || !pow2 || t->hub_chunk < 256 || t->hub_chunk > 65536 ||
         t->ip_blocks_per_sm < 1 || t->ip_blocks_per_sm > 8 || t->dense_hub_degree < 512 ||
         t->dense_hub_degree > (1 << 30) || t->lp_graphs < 0 || t->lp_graphs > 1 ||
-        (t->hub_bucket != 0 && (t->hub_bucket < 32 || t->hub_bucket > (1 << 20))))
+        (t->hub_bucket != 0 && (t->hub_bucket < 32 || t->hub_bucket > (1 << 20))) ||
+        t->dense_labels < 0 || t->dense_labels > 57344)
       fail(KMP_ERR_ARG, "invalid tuning");
     ctx().tune = *t;
   });
@@ -730,7 +736,7 @@ int kmp_autotune(const kmp_graph *g, int32_t k, double eps, uint64_t seed, kmp_t
       for (int hd : hubs)
         for (int hc : chunks) {
           C.tune = kmp_tuning{gi, hd, hc, keep.ip_blocks_per_sm, keep.dense_hub_degree, keep.lp_graphs,
-                                keep.hub_bucket};
+                                keep.hub_bucket, keep.dense_labels};
           LPStats st;
           cluster_level(G, (int32_t)U, C.cfg.lp_rounds, key_of(seed, {DOM_COARSEN, 0}), false, label,
                         nullptr, &st, nullptr);

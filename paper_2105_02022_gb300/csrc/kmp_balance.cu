@@ -141,22 +141,21 @@ __global__ void __launch_bounds__(1024) k_bal_slack(BalArgs A, int32_t Pk) {
     }
 }
 
-// Candidates of the overloaded blocks.  big = 0: the nodes whose table fits
-// the warp's shared-memory table (full grid); big = 1: the others, each warp
-// with its own region of A.gtab (a grid bounded by that memory).
-__global__ void __launch_bounds__(BAL_T) k_bal_cand(BalArgs A, int big) {
+// Candidates of the overloaded blocks, one warp per node with the warp's
+// shared-memory table.  Nodes whose table would not fit it are listed in
+// big[] for k_bal_cand_big.
+__global__ void __launch_bounds__(BAL_T) k_bal_cand(BalArgs A, int32_t *big, int32_t *nbig) {
   __shared__ int32_t sk[BAL_W][BAL_STAB], sv[BAL_W][BAL_STAB];
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int64_t gw = (int64_t)blockIdx.x * BAL_W + w, nw = (int64_t)gridDim.x * BAL_W;
   int32_t *K = sk[w], *V = sv[w];
-  if (big) {
-    K = A.gtab + gw * 2ll * A.gcap;
-    V = K + A.gcap;
-  }
   for (int64_t v = gw; v < A.n; v += nw) {
     int32_t B = A.part[v];
     if (!A.over[B]) continue;
-    if ((conn_cap(A, (int32_t)v) > (uint32_t)BAL_STAB) != (big != 0)) continue;
+    if (conn_cap(A, (int32_t)v) > (uint32_t)BAL_STAB) {
+      if (lane == 0) big[atomicAdd(nbig, 1)] = (int32_t)v;
+      continue;
+    }
     uint32_t mask;
     int64_t cown = conn_table(A, (int32_t)v, K, V, mask);
     int64_t c = bw_node(A, (int32_t)v);
@@ -182,6 +181,80 @@ __global__ void __launch_bounds__(BAL_T) k_bal_cand(BalArgs A, int big) {
       A.keys[p] = ((uint64_t)(uint32_t)B << A.bitsN) | (uint64_t)v;
     }
     __syncwarp();
+  }
+}
+
+// Candidates among the listed high-degree nodes: one CTA per node, the node's
+// row spread over all threads into the CTA's own global table region
+// (2 * gcap words; the node uses the power of two >= 2 min(degree, k)).
+__global__ void __launch_bounds__(BAL_T) k_bal_cand_big(BalArgs A, const int32_t *big, const int32_t *nbig) {
+  __shared__ int64_t s_best[BAL_W];
+  __shared__ int32_t s_nadj[BAL_W];
+  __shared__ int64_t s_cown;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t *K = A.gtab + (int64_t)blockIdx.x * 2 * A.gcap, *V = K + A.gcap;
+  const int32_t nb = *nbig;
+  for (int32_t i = blockIdx.x; i < nb; i += gridDim.x) {
+    const int32_t v = big[i], B = A.part[v];
+    const uint32_t cap = conn_cap(A, v), mask = cap - 1;
+    for (uint32_t x = threadIdx.x; x < cap; x += BAL_T) {
+      K[x] = HT_EMPTY;
+      V[x] = 0;
+    }
+    if (threadIdx.x == 0) s_cown = 0;
+    __syncthreads();
+    const int64_t b = A.xadj[v], e = A.xadj[v + 1];
+    for (int64_t base = b + 32 * w; base < e; base += BAL_T) {
+      const int64_t q = base + lane;
+      const bool ok = q < e;
+      const int32_t u = ok ? A.adj[q] : -1;
+      const int32_t wt = ok ? (A.ew ? A.ew[q] : 1) : 0;
+      const int32_t blk = ok ? A.part[u] : HT_EMPTY;
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, blk);
+      const int32_t sm = __reduce_add_sync(peers, wt);
+      if (blk != HT_EMPTY && lane == __ffs(peers) - 1) ht_add(K, V, mask, blk, sm);
+    }
+    __syncthreads();
+    const int64_t c = bw_node(A, v);
+    int64_t best = -1;
+    int32_t nadj = 0;
+    for (uint32_t x = threadIdx.x; x < cap; x += BAL_T) {
+      const int32_t blk = K[x];
+      if (blk == HT_EMPTY) continue;
+      if (blk == B) {
+        s_cown = V[x];
+        continue;
+      }
+      if (A.bw[blk] + c > A.cap[blk]) continue;
+      ++nadj;
+      if (V[x] > best) best = V[x];
+    }
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+      int64_t o = (int64_t)shfl_xor64((uint64_t)best, m);
+      best = o > best ? o : best;
+      nadj += __shfl_xor_sync(0xFFFFFFFFu, nadj, m);
+    }
+    if (lane == 0) {
+      s_best[w] = best;
+      s_nadj[w] = nadj;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int64_t bb = -1;
+      int32_t na = 0;
+      for (int x = 0; x < BAL_W; ++x) {
+        bb = s_best[x] > bb ? s_best[x] : bb;
+        na += s_nadj[x];
+      }
+      if (bb < 0 && count_fit(A, c) > na) bb = 0;  // an admissible block without neighbours
+      if (bb >= 0) {
+        A.cand_d[v] = bb - s_cown;
+        int32_t p = atomicAdd(A.ncand, 1);
+        A.keys[p] = ((uint64_t)(uint32_t)B << A.bitsN) | (uint64_t)v;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -339,33 +412,68 @@ __global__ void __launch_bounds__(BAL_T) k_bal_spec(BalArgs A) {
 
 __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch) {
   __shared__ int32_t s_v[BM_W], s_t[BM_W];
-  __shared__ int64_t s_c[BM_W], s_eoff[BM_W + 1];
+  __shared__ int64_t s_c[BM_W], s_eoff[BM_W + 1], s_beg[BM_W], s_bwt[BM_W], s_capt[BM_W];
   __shared__ uint32_t s_adj[BM_W], s_mask[BM_W];
   __shared__ int32_t s_nb, s_next, s_stop;
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint64_t vmask = (1ull << A.bitsN) - 1ull;
   const uint32_t gcap = A.gcap;  // stride of the per-member table regions
-  __shared__ int32_t s_resume;
-  for (int32_t ob = 0; ob < A.nover; ++ob) {
-    int32_t B = A.olist[ob];
-    int32_t lo = A.seg_lo[B], hi = A.seg_hi[B];
-    // the speculated moves, in order, while their targets still fit under the
-    // weights left by the blocks before; then the exact batches from there
-    if (threadIdx.x == 0) {
-      int32_t nm = A.spec_n[ob], j = 0;
-      for (; j < nm; ++j) {
-        int32_t v = A.spec_v[ob * SPEC_MAX + j], t = A.spec_t[ob * SPEC_MAX + j];
-        int64_t c = bw_node(A, v);
-        if (A.bw[t] + c > A.cap[t]) break;
-        A.part[v] = t;
-        A.bw[B] -= c;
-        A.bw[t] += c;
-        atomicAdd(A.moved, 1ull);
+  __shared__ int32_t s_resume, s_ob;
+  for (int32_t ob = 0;; ++ob) {
+    // Warp 0 runs ahead over the blocks: a block's speculated moves stand, in
+    // order, while their targets still fit under the weights left by the
+    // blocks before.  One lane per move checks its target against the current
+    // weight plus what the block's earlier moves add to it; the moves before
+    // the first that does not fit are applied at once.  Warp 0 stops at the
+    // first block that still needs the exact commit (the whole CTA).
+    if (w == 0) {
+      int32_t o = ob, resume = 0;
+      for (; o < A.nover; ++o) {
+        const int32_t B = A.olist[o];
+        const int32_t lo = A.seg_lo[B], hi = A.seg_hi[B];
+        const int32_t nm = A.spec_n[o];
+        int32_t v = 0, t = 0;
+        int64_t c = 0, bt = 0, ct = 0;
+        if (lane < nm) {
+          v = A.spec_v[(int64_t)o * SPEC_MAX + lane];
+          t = A.spec_t[(int64_t)o * SPEC_MAX + lane];
+          c = bw_node(A, v);
+          bt = A.bw[t];
+          ct = A.cap[t];
+        }
+        int64_t pre = 0;  // this block's earlier moves into the same target
+#pragma unroll
+        for (int j = 0; j < SPEC_MAX; ++j) {
+          const int32_t tj = __shfl_sync(0xFFFFFFFFu, t, j);
+          const long long cj = __shfl_sync(0xFFFFFFFFu, (long long)c, j);
+          if (j < lane && j < nm && tj == t) pre += cj;
+        }
+        const unsigned bad = __ballot_sync(0xFFFFFFFFu, lane < nm && bt + pre + c > ct);
+        const int32_t f = bad ? __ffs(bad) - 1 : nm;  // moves [0, f) stand
+        if (lane < f) {
+          A.part[v] = t;
+          atomicAdd(reinterpret_cast<unsigned long long *>(&A.bw[t]), (unsigned long long)c);
+        }
+        const int64_t gone = warp_sum64(lane < f ? c : 0);
+        if (lane == 0 && f > 0) {
+          A.bw[B] -= gone;
+          atomicAdd(A.moved, (unsigned long long)f);
+          atomicAdd(A.moved + 1, (unsigned long long)f);  // speculated moves that stood
+        }
+        __syncwarp();
+        resume = f < nm ? lo + f : (A.spec_sat[o] ? hi : A.spec_end[o]);
+        if (resume < hi && A.bw[B] > A.cap[B]) break;  // the exact commit takes over here
       }
-      s_resume = (j == nm && A.spec_sat[ob]) ? hi : lo + j;
-      if (j == nm && !A.spec_sat[ob]) s_resume = A.spec_end[ob];
+      if (lane == 0) {
+        s_ob = o;
+        s_resume = resume;
+      }
     }
     __syncthreads();
+    ob = s_ob;
+    if (ob >= A.nover) break;
+    const int32_t B = A.olist[ob];
+    const int32_t hi = A.seg_hi[B];
     int32_t i = s_resume;
     while (i < hi) {
       if (A.bw[B] <= A.cap[B]) break;
@@ -373,7 +481,9 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
         int32_t avail = hi - i < BM_W ? hi - i : BM_W;
         int32_t v = lane < avail ? (int32_t)(A.keys[i + lane] & vmask) : 0;
         int64_t c = lane < avail ? bw_node(A, v) : 0;
-        int64_t deg = lane < avail ? A.xadj[v + 1] - A.xadj[v] : 0;
+        const int64_t rb = lane < avail ? A.xadj[v] : 0;
+        int64_t deg = lane < avail ? A.xadj[v + 1] - rb : 0;
+        const int64_t own = deg < A.k ? deg : A.k;
         // inclusive prefix sums of weights and degrees
 #pragma unroll
         for (int m = 1; m < 32; m <<= 1) {
@@ -389,11 +499,10 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
         if (lane < nb) {
           // member table sized by the member's own distinct blocks (at most
           // min(degree, k)), so low-degree members never touch a hub-sized table
-          int64_t own = A.xadj[v + 1] - A.xadj[v];
-          if (own > A.k) own = A.k;
           uint32_t cap = 32;
           while ((int64_t)cap < 2 * own) cap <<= 1;
           s_v[lane] = v;
+          s_beg[lane] = rb;
           s_eoff[lane + 1] = deg;
           s_adj[lane] = 0;
           s_mask[lane] = cap - 1;
@@ -423,7 +532,7 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
           while (s_eoff[j + 1] <= t) ++j;
         int32_t blk = HT_EMPTY, wt = 0;
         if (ok) {
-          int64_t q = A.xadj[s_v[j]] + (t - s_eoff[j]);
+          int64_t q = s_beg[j] + (t - s_eoff[j]);
           int32_t u = A.adj[q];
           blk = A.part[u];
           wt = A.ew ? A.ew[q] : 1;
@@ -464,29 +573,45 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
         if (lane == 0) {
           s_t[w] = t;
           s_c[w] = c;
+          s_bwt[w] = t >= 0 ? A.bw[t] : 0;  // the target's weight at the start of the batch
+          s_capt[w] = t >= 0 ? A.cap[t] : 0;
         }
       }
       __syncthreads();
       if (threadIdx.x == 0) {
+        // in order; only this CTA changes weights, so the block's and the
+        // targets' weights are tracked here (a target's weight is its start
+        // weight plus the moves of this batch into it)
         uint32_t moved_mask = 0;
-        int32_t j = 0;
+        int32_t j = 0, moves = 0;
         s_stop = 0;
+        int64_t wB = A.bw[B];
+        const int64_t capB = A.cap[B];
         for (; j < nb; ++j) {
-          if (A.bw[B] <= A.cap[B]) {
+          if (wB <= capB) {
             s_stop = 1;
             break;
           }
-          int32_t t = s_t[j];
-          int64_t c = s_c[j];
-          if (j > 0 && ((s_adj[j] & moved_mask) || (t >= 0 && A.bw[t] + c > A.cap[t]))) break;
+          const int32_t t = s_t[j];
+          const int64_t c = s_c[j];
+          int64_t wt = 0;
+          if (t >= 0) {
+            wt = s_bwt[j];
+            for (int32_t x = 0; x < j; ++x)
+              if (((moved_mask >> x) & 1u) && s_t[x] == t) wt += s_c[x];
+          }
+          if (j > 0 && ((s_adj[j] & moved_mask) || (t >= 0 && wt + c > s_capt[j]))) break;
           if (t >= 0) {
             A.part[s_v[j]] = t;
-            A.bw[B] -= c;
-            A.bw[t] += c;
-            atomicAdd(A.moved, 1ull);
+            A.bw[t] = wt + c;
+            wB -= c;
+            ++moves;
             moved_mask |= 1u << j;
           }
         }
+        A.bw[B] = wB;
+        if (moves) atomicAdd(A.moved, (unsigned long long)moves);
+        atomicAdd(A.moved + 2, 1ull);  // an exact batch
         s_next = j;
       }
       __syncthreads();
@@ -498,7 +623,7 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
   }
 }
 
-int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *part) {
+int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *part, BalStats *bs) {
   Context &C = ctx();
   cudaStream_t s = C.stream;
   int32_t n = g.n;
@@ -523,7 +648,7 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   DBuf<uint8_t> over(k);
   DBuf<int64_t> cand_d(n);
   DBuf<uint64_t> keys(n), tmp(n), sortbuf(2ll * n);
-  DBuf<unsigned long long> moved(1);
+  DBuf<unsigned long long> moved(3);  // moves, speculated moves that stood, exact batches
   to_dev(cap.p, caps_host, k);
   to_dev(over.p, hover.data(), k);
   DBuf<int32_t> olist(holist.size());
@@ -564,22 +689,31 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   A.moved = moved;
   k_bal_slack<<<1, 1024, 0, s>>>(A, Pk);
   KMP_LAUNCHED("bal_slack");
-  k_bal_cand<<<grid, BAL_T, 0, s>>>(A, 0);
+  // nodes with more distinct neighbour blocks than a warp's shared table
+  // holds have degree > BAL_STAB / 2, so there are at most m / 257 of them
+  DBuf<int32_t> big(g.m / (BAL_STAB / 2 + 1) + 1), nbig(1);
+  nbig.zero();
+  k_bal_cand<<<grid, BAL_T, 0, s>>>(A, big, nbig);
   KMP_LAUNCHED("bal_cand");
   if (gcap > BAL_STAB) {
-    // nodes with more distinct neighbour blocks than a shared table holds:
-    // per-warp global tables, bounded to about 256 MB
-    int64_t per_block = 2ll * gcap * BAL_W * (int64_t)sizeof(int32_t);
-    int64_t gmax = std::max<int64_t>(1, (256ll << 20) / per_block);
-    grid_big = (int)std::min<int64_t>(grid, gmax);
-    gtab.alloc(2ll * gcap * (int64_t)grid_big * BAL_W);
-    A.gtab = gtab;
-    k_bal_cand<<<grid_big, BAL_T, 0, s>>>(A, 1);
-    KMP_LAUNCHED("bal_cand");
+    const int32_t nb = read1(nbig.p);
+    if (nb > 0) {
+      // one CTA per listed node, each with its own global table region,
+      // bounded to about 256 MB in all
+      int64_t per_cta = 2ll * gcap * (int64_t)sizeof(int32_t);
+      int64_t gmax = std::max<int64_t>(1, (256ll << 20) / per_cta);
+      grid_big = (int)std::min<int64_t>(std::min<int64_t>(nb, gmax), (int64_t)C.sms * 8);
+      gtab.alloc(2ll * gcap * (int64_t)grid_big);
+      A.gtab = gtab;
+      k_bal_cand_big<<<grid_big, BAL_T, 0, s>>>(A, big, nbig);
+      KMP_LAUNCHED("bal_cand_big");
+    }
   }
   int32_t N = read1(ncand.p);
   if (N == 0) return 0;
-  radix_sort_u64(keys, tmp, N, bitsN + bitsK);
+  // grouped by block only: k_bal_sort orders every block's candidates by a
+  // strict total order (relative gain, then id), whatever order they arrive in
+  radix_sort_u64(keys, tmp, N, bitsK, bitsN);
   k_bal_segments<<<grid_for(N, 256), 256, 0, s>>>(A, N);
   KMP_LAUNCHED("bal_segments");
   k_bal_sort<<<A.nover, BAL_T, 0, s>>>(A);
@@ -605,7 +739,15 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   A.gtab = gtab1;
   k_bal_moves<<<1, BM_T, 0, s>>>(A, inbatch);
   KMP_LAUNCHED("bal_moves");
-  return (int64_t)read1(moved.p);
+  unsigned long long hm[3];
+  to_host(hm, moved.p, 3);
+  if (bs) {
+    bs->over_blocks += nover;
+    bs->moves += (int64_t)hm[0];
+    bs->spec_moves += (int64_t)hm[1];
+    bs->exact_batches += (int64_t)hm[2];
+  }
+  return (int64_t)hm[0];
 }
 
 }  // namespace kmp

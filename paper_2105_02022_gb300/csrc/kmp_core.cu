@@ -226,61 +226,79 @@ void scan_excl_u8_to_i32(const uint8_t *in, int32_t *out, int64_t n, int32_t *to
 
 // ------------------------------------------------------------ radix sort
 constexpr int RS_T = 256;
+constexpr int RS_SUB = 8;                // sub-tiles of RS_T keys per tile
+constexpr int RS_TILE = RS_T * RS_SUB;   // keys per tile (one CTA)
 
+// digit histogram of every tile (2048 keys)
 __global__ void __launch_bounds__(RS_T) k_rs_hist(const uint64_t *keys, int64_t n, int sh,
                                                   int32_t *cnt, int64_t ntiles) {
   __shared__ int32_t h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
-  int64_t j = (int64_t)blockIdx.x * RS_T + threadIdx.x;
-  if (j < n) atomicAdd(&h[(keys[j] >> sh) & 255u], 1);
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll
+  for (int r = 0; r < RS_SUB; ++r) {
+    const int64_t j = base + r * RS_T + threadIdx.x;
+    if (j < n) atomicAdd(&h[(keys[j] >> sh) & 255u], 1);
+  }
   __syncthreads();
   cnt[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
+// Stable scatter of one tile: its sub-tiles in order, inside a sub-tile warps
+// in order and lanes in order (ranks from match-any groups), on top of the
+// digit's running count over the tile's earlier sub-tiles.
 __global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t *keys, uint64_t *out,
                                                      int64_t n, int sh, const int32_t *off,
                                                      int64_t ntiles, const int32_t *vin = nullptr,
                                                      int32_t *vout = nullptr) {
   __shared__ int32_t wc[RS_T / 32][256];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < (RS_T / 32) * 256; i += RS_T) (&wc[0][0])[i] = 0;
-  __syncthreads();
-  int64_t j = (int64_t)blockIdx.x * RS_T + threadIdx.x;
-  bool ok = j < n;
-  uint64_t k = ok ? keys[j] : 0;
-  int d = ok ? (int)((k >> sh) & 255u) : 256 + lane;  // unique dummy digit for padding lanes
-  unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
-  int rank = __popc(peers & ((1u << lane) - 1u));
-  if (ok && rank == 0) wc[w][d] = __popc(peers);
-  __syncthreads();
-  // exclusive prefix over warps, per digit (thread t handles digit t)
-  {
-    int dd = threadIdx.x;
-    int32_t s = 0;
-    for (int ww = 0; ww < RS_T / 32; ++ww) {
-      int32_t c = wc[ww][dd];
-      wc[ww][dd] = s;
-      s += c;
+  __shared__ int32_t run[256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  run[threadIdx.x] = off[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_SUB; ++r) {
+    for (int i = threadIdx.x; i < (RS_T / 32) * 256; i += RS_T) (&wc[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t j = base + r * RS_T + threadIdx.x;
+    const bool ok = j < n;
+    const uint64_t k = ok ? keys[j] : 0;
+    const int d = ok ? (int)((k >> sh) & 255u) : 256 + lane;  // unique dummy digit for padding lanes
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (ok && rank == 0) wc[w][d] = __popc(peers);
+    __syncthreads();
+    // per digit (thread t handles digit t): exclusive prefix over warps on
+    // top of the running position, which then moves past this sub-tile
+    {
+      const int dd = threadIdx.x;
+      int32_t s = run[dd];
+      for (int ww = 0; ww < RS_T / 32; ++ww) {
+        const int32_t c = wc[ww][dd];
+        wc[ww][dd] = s;
+        s += c;
+      }
+      run[dd] = s;
     }
-  }
-  __syncthreads();
-  if (ok) {
-    int64_t p = off[(int64_t)d * ntiles + blockIdx.x] + wc[w][d] + rank;
-    out[p] = k;
-    if (vin) vout[p] = vin[j];
+    __syncthreads();
+    if (ok) {
+      const int64_t p = (int64_t)wc[w][d] + rank;
+      out[p] = k;
+      if (vin) vout[p] = vin[j];
+    }
+    __syncthreads();  // wc is cleared for the next sub-tile
   }
 }
 
-void radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t n, int bits) {
+void radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t n, int bits, int lo_bit) {
   if (n <= 1 || bits <= 0) return;
-  int64_t ntiles = ceil_div(n, RS_T);
+  int64_t ntiles = ceil_div(n, RS_TILE);
   DBuf<int32_t> cnt(256 * ntiles), off(256 * ntiles);
   cudaStream_t s = ctx().stream;
   uint64_t *a = keys, *b = tmp;
   int passes = (bits + 7) / 8;
   for (int p = 0; p < passes; ++p) {
-    int sh = 8 * p;
+    int sh = lo_bit + 8 * p;
     k_rs_hist<<<(unsigned)ntiles, RS_T, 0, s>>>(a, n, sh, cnt, ntiles);
     KMP_LAUNCHED("rs_hist");
     scan_excl_i32(cnt, off, 256 * ntiles, nullptr);
@@ -293,7 +311,7 @@ void radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t n, int bits) {
 
 void radix_sort_kv(uint64_t *keys, int32_t *vals, uint64_t *tmpk, int32_t *tmpv, int64_t n, int bits) {
   if (n <= 1 || bits <= 0) return;
-  int64_t ntiles = ceil_div(n, RS_T);
+  int64_t ntiles = ceil_div(n, RS_TILE);
   DBuf<int32_t> cnt(256 * ntiles), off(256 * ntiles);
   cudaStream_t s = ctx().stream;
   uint64_t *a = keys, *b = tmpk;

@@ -39,7 +39,7 @@ struct Context {
   int64_t launches = 0;
   int *d_status = nullptr;  // device status word: 0 ok, else KMP_ERR_* set by kernels
   // schedule parameters (never change results); see kmp_autotune
-  kmp_tuning tune{8, 2048, 512, 4, 8192, 1};
+  kmp_tuning tune{8, 2048, 512, 4, 8192, 1, 256, 0};
   // live profiling of the LP rating launches (CUDA events on `stream`)
   bool profile = false;
   cudaStream_t capture_stream = nullptr;  // created on first use: CUDA graph capture of LP rounds
@@ -243,8 +243,9 @@ void scan_excl_i32_on(const int32_t *in, int32_t *out, int64_t n, int32_t *total
                       cudaStream_t s);
 void scan_excl_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total_dev);
 void scan_excl_u8_to_i32(const uint8_t *in, int32_t *out, int64_t n, int32_t *total_dev);
-// stable LSD radix sort of 64-bit keys over the low `bits` bits (in place via tmp)
-void radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t n, int bits);
+// stable LSD radix sort of 64-bit keys by bits [lo_bit, lo_bit + bits) (in place via tmp);
+// keys equal in those bits keep their order
+void radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t n, int bits, int lo_bit = 0);
 // same with an int32 payload moved along with each key
 void radix_sort_kv(uint64_t *keys, int32_t *vals, uint64_t *tmpk, int32_t *tmpv, int64_t n, int bits);
 int grid_for(int64_t work, int per_block, int max_blocks_per_sm = 8);
@@ -278,7 +279,11 @@ void block_weights(const Graph &g, const int32_t *part, int32_t k, int64_t *bw_d
 // refinement wrapper: caps host int32[k]; returns the cut when want_cut, else 0
 int64_t refine(const Graph &g, int32_t k, const int32_t *caps_host, int32_t rounds,
                uint64_t seed, int32_t *part, LPStats *st, bool want_cut = true);
-int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *part);
+struct BalStats {
+  int64_t over_blocks = 0, moves = 0, spec_moves = 0, exact_batches = 0;
+};
+// k-way balancing; bs (nullable) accumulates where the work went
+int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *part, BalStats *bs = nullptr);
 // Algorithm 2, one split round; f in/out (host), returns new block count
 int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::vector<int32_t> &f,
                            double eps, int64_t cV, int32_t k, uint64_t roundkey,

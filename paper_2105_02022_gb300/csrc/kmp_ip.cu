@@ -1586,7 +1586,9 @@ int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::
   DBuf<uint64_t> keys(n), tmp(n);
   k_block_keys<<<grid, 256, 0, s>>>(n, part, bitsN, keys);
   KMP_LAUNCHED("block_keys");
-  radix_sort_u64(keys, tmp, n, bitsN + bitsB);
+  // keys are written in ascending node order, so a stable sort by the block
+  // bits alone leaves every block's members in ascending id
+  radix_sort_u64(keys, tmp, n, bitsB, bitsN);
   DBuf<int32_t> members(n), bcount(nblocks + 1), ideg(n), boff(nblocks + 1), loc(n);
   DBuf<unsigned long long> bweight(nblocks), becount(nblocks);
   bcount.zero();

@@ -81,22 +81,26 @@ struct LPArgs {
   int32_t *bigmove;            // high-degree nodes that moved in this sub-round
   unsigned long long *ctr64;   // 18 per round: [0] scanned entries, [1] moved nodes, [2+s]
                                // degree sum of sub-round s, [10+s] the same over bin 6 (hubs)
-  // bin 6 (degree > huge_deg) with many labels: per-hub global tables filled
-  // by many CTAs in parallel
+  // bin 6 (degree > huge_deg) with many labels: the sub-round's hub entries
+  // are hashed by label into buckets of about hub_bucket entries, scattered
+  // into bucket order and aggregated one bucket per warp in shared memory
   const int32_t *hubs;         // hub node ids, ascending
   int32_t nhubs;
-  const int64_t *hoff;         // table offset of each hub
-  int32_t *hkeys;
-  int32_t *hvals;
   unsigned long long *hkc;     // best admissible key per hub
   unsigned long long *hku;     // best key per hub
   int32_t *hrown;              // rating of the hub's own cluster
-  int32_t *hlist;              // occupied table slots of each hub (same offsets as the table)
-  int32_t *hcount;             // number of occupied slots per hub
+  int32_t *hlab;               // neighbour labels of the sub-round's hub entries (entry order)
+  int32_t *hslab;              // the same in bucket order (~label once aggregated)
+  int32_t *hsw;                // their edge weights in bucket order (weighted graphs)
+  int32_t *hbcnt;              // entries per bucket (zeroed by the bucket kernel after use)
+  int32_t *hbcur;              // scatter cursor per bucket (zeroed likewise)
+  int32_t *hboff;              // bucket offsets: exclusive scan of hbcnt
+  int32_t hub_bucket;          // target entries per bucket
   int32_t *plan_h;             // per sub-round hub plan: hub index of each bin-6 entry,
   int64_t *plan_e;             // exclusive prefix of its edge chunks,
-  int64_t *plan_t;             // exclusive prefix of its table chunks,
-  int64_t *plan_tot;           // [0] edge chunks, [1] table chunks
+  int64_t *plan_x;             // of its entries (degree),
+  int64_t *plan_b;             // of its buckets,
+  int64_t *plan_tot;           // [0] edge chunks, [1] buckets, [2] entries
   int32_t small_labels;        // all labels fit a CTA table: bin 6 handled like bin 5
   int32_t *hdense;             // few labels: bin-6 entry i of a sub-round owns row i of
                                // a [hubs][nlab] rating array filled by many CTAs
@@ -525,7 +529,6 @@ __device__ __forceinline__ void stamp_stage_end(const LPArgs &A, int s) {
 }
 
 // ---- hubs (bin 6) with many labels: insert / reduce / emit
-constexpr int64_t HUB_RCHUNK = 4096;  // occupied-slot list entries per reduce work unit
 
 __device__ __forceinline__ int32_t hub_index(const LPArgs &A, int32_t u) {
   int32_t lo = 0, hi = A.nhubs - 1;
@@ -547,201 +550,280 @@ __device__ __forceinline__ int32_t find_seg(const int64_t *off, int32_t cnt, int
   return lo;
 }
 
+// buckets of a hub of degree deg, and the bucket of label L among them
+__device__ __forceinline__ int64_t hub_nbuckets(const LPArgs &A, int64_t deg) {
+  return ceil_div(deg, (int64_t)A.hub_bucket);
+}
+__device__ __forceinline__ int64_t hub_bucket_of(int32_t L, int64_t nb) {
+  // a mix decorrelated from the table slots' fmix32(L)
+  return (int64_t)(((uint64_t)fmix32((uint32_t)L ^ 0x5BD1E995u) * (uint64_t)nb) >> 32);
+}
+
 // work plan of one sub-round: the hubs it rates, with exclusive prefixes of
-// their edge chunks and table chunks (one block, any number of hubs)
+// their edge chunks, entries and buckets (one block, any number of hubs)
 __global__ void __launch_bounds__(1024) k_hub_plan(LPArgs A, int s) {
-  __shared__ int64_t we[32], wt2[32];
-  __shared__ int64_t carry_e, carry_t;
+  __shared__ int64_t we[32], wx[32], wb[32];
+  __shared__ int64_t carry_e, carry_x, carry_b;
   const int32_t *bo = A.boff + s * NB;
   int32_t lo = bo[6], cnt = bo[7] - bo[6];
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (threadIdx.x == 0) { carry_e = 0; carry_t = 0; }
+  if (threadIdx.x == 0) { carry_e = 0; carry_x = 0; carry_b = 0; }
   __syncthreads();
   for (int32_t base = 0; base < cnt; base += blockDim.x) {
     int32_t i = base + threadIdx.x;
-    int64_t ne = 0, nt = 0;
+    int64_t ne = 0, nx = 0, nb = 0;
     int32_t h = 0;
     if (i < cnt) {
       int32_t u = A.vlist[lo + i];
       h = A.hubs ? hub_index(A, u) : i;
       int64_t deg = A.xadj[u + 1] - A.xadj[u];
       ne = ceil_div(deg, A.hub_chunk);
-      nt = ceil_div((int64_t)next_pow2_dev(2 * deg), HUB_RCHUNK);
+      nx = deg;
+      nb = A.hub_bucket > 0 ? hub_nbuckets(A, deg) : 0;
     }
-    int64_t xe = ne, xt = nt;
+    int64_t xe = ne, xx = nx, xb = nb;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       int64_t ye = (int64_t)__shfl_up_sync(0xFFFFFFFFu, (unsigned long long)xe, d);
-      int64_t yt = (int64_t)__shfl_up_sync(0xFFFFFFFFu, (unsigned long long)xt, d);
-      if (lane >= d) { xe += ye; xt += yt; }
+      int64_t yx = (int64_t)__shfl_up_sync(0xFFFFFFFFu, (unsigned long long)xx, d);
+      int64_t yb = (int64_t)__shfl_up_sync(0xFFFFFFFFu, (unsigned long long)xb, d);
+      if (lane >= d) { xe += ye; xx += yx; xb += yb; }
     }
-    if (lane == 31) { we[w] = xe; wt2[w] = xt; }
+    if (lane == 31) { we[w] = xe; wx[w] = xx; wb[w] = xb; }
     __syncthreads();
-    int64_t pe = carry_e, pt = carry_t, te = 0, tt = 0;
+    int64_t pe = carry_e, px = carry_x, pb = carry_b, te = 0, tx = 0, tb = 0;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-      if (k < w) { pe += we[k]; pt += wt2[k]; }
+      if (k < w) { pe += we[k]; px += wx[k]; pb += wb[k]; }
       te += we[k];
-      tt += wt2[k];
+      tx += wx[k];
+      tb += wb[k];
     }
     if (i < cnt) {
       A.plan_h[i] = h;
       A.plan_e[i] = pe + xe - ne;
-      A.plan_t[i] = pt + xt - nt;
+      A.plan_x[i] = px + xx - nx;
+      A.plan_b[i] = pb + xb - nb;
     }
     __syncthreads();
-    if (threadIdx.x == 0) { carry_e += te; carry_t += tt; }
+    if (threadIdx.x == 0) { carry_e += te; carry_x += tx; carry_b += tb; }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     A.plan_tot[0] = carry_e;
-    A.plan_tot[1] = carry_t;
+    A.plan_tot[1] = carry_b;
+    A.plan_tot[2] = carry_x;
   }
 }
 
-// work units: edge chunks of the sub-round's hubs
-__global__ void __launch_bounds__(256) k_hub_insert(LPArgs A, int s) {
+// lanes of a warp that hit the same bucket add their counts first
+__device__ __forceinline__ int32_t warp_bucket_claim(int32_t *ctr, bool ok, int64_t g, int lane) {
+  uint64_t key = ok ? (uint64_t)g : (0xFFFFFFFF00000000ull | (uint32_t)lane);
+  unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+  int leader = __ffs(peers) - 1;
+  int32_t base = 0;
+  if (ok && lane == leader) base = atomicAdd(&ctr[g], __popc(peers));
+  base = __shfl_sync(0xFFFFFFFFu, base, leader);
+  return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+// work units: edge chunks of the sub-round's hubs; every entry's neighbour
+// label is gathered once (kept in entry order) and counted in its bucket
+// The hub of every work unit: each CTA (warp) takes a contiguous range of
+// units, finds the first one's hub by binary search and then only moves
+// forward (the units of one hub are consecutive).
+struct HubCursor {
+  int32_t i = -1;   // hub position in the sub-round's plan
+  int64_t next = 0; // first unit of hub i + 1
+  int32_t u = 0;
+  int64_t b = 0, deg = 0, nb = 0, gb = 0, xo = 0, e_first = 0;
+  __device__ void seek(const LPArgs &A, const int64_t *units, int32_t cnt, int64_t total, int64_t c) {
+    if (i < 0 || c >= next) {
+      if (i < 0 || c >= next + 64) {
+        i = find_seg(units, cnt, c);
+      } else {
+        do ++i;
+        while (i + 1 < cnt && units[i + 1] <= c);
+      }
+      next = i + 1 < cnt ? units[i + 1] : total;
+      u = A.hubs[A.plan_h[i]];
+      b = A.xadj[u];
+      deg = A.xadj[u + 1] - b;
+      nb = A.hub_bucket > 0 ? hub_nbuckets(A, deg) : 0;
+      gb = A.plan_b[i];
+      xo = A.plan_x[i] - b;
+      e_first = units[i];
+    }
+  }
+};
+
+__global__ void __launch_bounds__(256) k_hub_count(LPArgs A, int s) {
   const int32_t *bo = A.boff + s * NB;
   int32_t cnt = bo[7] - bo[6];
   int64_t total = A.plan_tot[0];
-  for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
-    int32_t i = find_seg(A.plan_e, cnt, c);
-    int32_t h = A.plan_h[i];
-    int32_t u = A.hubs[h];
-    int64_t b = A.xadj[u], deg = A.xadj[u + 1] - b;
-    uint32_t mask = next_pow2_dev(2 * deg) - 1;
-    int32_t *keys = A.hkeys + A.hoff[h], *vals = A.hvals + A.hoff[h];
-    int32_t *list = A.hlist + A.hoff[h];
-    int64_t cc = c - A.plan_e[i];
-    int64_t e0 = b + cc * A.hub_chunk, e1 = e0 + A.hub_chunk < b + deg ? e0 + A.hub_chunk : b + deg;
-    int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
+  const int64_t per = ceil_div(total, (int64_t)gridDim.x);
+  const int64_t c0 = (int64_t)blockIdx.x * per, c1 = c0 + per < total ? c0 + per : total;
+  HubCursor H;
+  for (int64_t c = c0; c < c1; ++c) {
+    H.seek(A, A.plan_e, cnt, total, c);
+    const int64_t b = H.b, deg = H.deg, nb = H.nb, gb = H.gb, xo = H.xo;
+    int64_t e0 = b + (c - H.e_first) * A.hub_chunk, e1 = e0 + A.hub_chunk < b + deg ? e0 + A.hub_chunk : b + deg;
     for (int64_t base = e0 + (threadIdx.x & ~31); base < e1; base += blockDim.x) {
       int64_t e = base + lane;
-      int32_t fresh = -1;  // slot this lane occupied first
-      if (e < e1) {
-        int32_t K = A.label[A.adj[e]], x = edge_w(A, e);
-        uint32_t t = fmix32((uint32_t)K) & mask;
-        // the table holds >= 2 deg slots, so a free one is always found
-        for (uint32_t probe = 0; probe <= mask; ++probe) {
-          int32_t old = atomicCAS(&keys[t], HT_EMPTY, K);
-          if (old == HT_EMPTY || old == K) {
-            atomicAdd(&vals[t], x);
-            if (old == HT_EMPTY) fresh = (int32_t)t;
-            break;
-          }
-          t = (t + 1) & mask;
+      bool ok = e < e1;
+      int32_t L = ok ? A.label[A.adj[e]] : 0;
+      if (ok) A.hlab[xo + e] = L;
+      warp_bucket_claim(A.hbcnt, ok, gb + hub_bucket_of(L, nb), lane);
+    }
+  }
+}
+
+// the same work units: entries into bucket order (positions inside a bucket
+// are arbitrary; the aggregation below does not depend on them)
+__global__ void __launch_bounds__(256) k_hub_scatter(LPArgs A, int s) {
+  const int32_t *bo = A.boff + s * NB;
+  int32_t cnt = bo[7] - bo[6];
+  int64_t total = A.plan_tot[0];
+  const int lane = threadIdx.x & 31;
+  const int64_t per = ceil_div(total, (int64_t)gridDim.x);
+  const int64_t c0 = (int64_t)blockIdx.x * per, c1 = c0 + per < total ? c0 + per : total;
+  HubCursor H;
+  for (int64_t c = c0; c < c1; ++c) {
+    H.seek(A, A.plan_e, cnt, total, c);
+    const int64_t b = H.b, deg = H.deg, nb = H.nb, gb = H.gb, xo = H.xo;
+    int64_t e0 = b + (c - H.e_first) * A.hub_chunk, e1 = e0 + A.hub_chunk < b + deg ? e0 + A.hub_chunk : b + deg;
+    for (int64_t base = e0 + (threadIdx.x & ~31); base < e1; base += blockDim.x) {
+      int64_t e = base + lane;
+      bool ok = e < e1;
+      int32_t L = ok ? A.hlab[xo + e] : 0;
+      int64_t g = gb + hub_bucket_of(L, nb);
+      int32_t r = warp_bucket_claim(A.hbcur, ok, g, lane);
+      if (ok) {
+        int64_t pos = (int64_t)A.hboff[g] + r;
+        A.hslab[pos] = L;
+        if (A.ew) A.hsw[pos] = A.ew[e];
+      }
+    }
+  }
+}
+
+// add w to key k's slot if k is in the table (no insert)
+__device__ __forceinline__ bool ht_find_add(int32_t *keys, int32_t *vals, uint32_t mask, int32_t k, int32_t w) {
+  uint32_t h = fmix32((uint32_t)k) & mask;
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    int32_t c = keys[h];
+    if (c == k) {
+      atomicAdd(&vals[h], w);
+      return true;
+    }
+    if (c == HT_EMPTY) return false;
+    h = (h + 1) & mask;
+  }
+  return false;
+}
+
+constexpr int64_t DENSE_ROWS_MAX_BYTES = 4ll << 30;  // dense hub rows of one LP run
+constexpr int DENSE_LABELS_MAX = 57344;              // a CTA's shared counters (224 KB)
+
+constexpr int HB_TAB = 1024;             // per-warp table of the bucket kernel
+constexpr int HB_LIMIT = HB_TAB / 2 - 32;  // labels admitted per round (load <= 1/2)
+
+// One warp per bucket: its entries are aggregated by label in the warp's
+// shared table.  A round admits new labels while fewer than HB_LIMIT are
+// held and keeps adding to labels already held after that; entries whose
+// label came too late wait for the next round (a label's entries therefore
+// all land in the round that admitted it).  Every round ends with the
+// selection pass over the occupied slots; the bucket's best keys go to its
+// hub by atomicMax, the own cluster's rating (in exactly one bucket) is
+// stored.  Counts and cursors are cleared for the next sub-round.
+constexpr int HB_W = 8;  // warps per CTA of k_hub_bucket
+constexpr size_t HB_SMEM = (size_t)HB_W * (2 * HB_TAB * sizeof(int32_t) + HB_TAB / 2 * sizeof(uint16_t));
+
+__global__ void __launch_bounds__(HB_W * 32) k_hub_bucket(LPArgs A, int s) {
+  constexpr int W = HB_W;
+  extern __shared__ __align__(16) unsigned char hb_smem[];  // HB_SMEM bytes (opt-in above 48 KB)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t *keys = reinterpret_cast<int32_t *>(hb_smem) + (size_t)w * 2 * HB_TAB;
+  int32_t *vals = keys + HB_TAB;
+  uint16_t *list = reinterpret_cast<uint16_t *>(hb_smem + (size_t)W * 2 * HB_TAB * sizeof(int32_t)) +
+                   (size_t)w * (HB_TAB / 2);
+  for (int x = lane; x < HB_TAB; x += 32) {
+    keys[x] = HT_EMPTY;
+    vals[x] = 0;
+  }
+  __syncwarp();
+  const int32_t *bo = A.boff + s * NB;
+  const int32_t cnt = bo[7] - bo[6];
+  const int64_t NBt = A.plan_tot[1];
+  const uint32_t mask = HB_TAB - 1;
+  const int64_t gw = (int64_t)blockIdx.x * W + w, nw = (int64_t)gridDim.x * W;
+  const int64_t per = ceil_div(NBt, nw);
+  const int64_t g0 = gw * per, g1 = g0 + per < NBt ? g0 + per : NBt;
+  HubCursor H;
+  int32_t h = -1, own = 0, cu = 0;
+  for (int64_t g = g0; g < g1; ++g) {
+    const int32_t ne = A.hbcnt[g];
+    if (ne == 0) continue;
+    H.seek(A, A.plan_b, cnt, NBt, g);
+    if (A.plan_h[H.i] != h) {
+      h = A.plan_h[H.i];
+      own = A.label[H.u];
+      cu = node_w(A, H.u);
+    }
+    const int64_t beg = A.hboff[g];
+    uint64_t kc = 0, ku = 0;
+    bool left = true;
+    while (left) {
+      int32_t held = 0;
+      bool full = false, mine_left = false;
+      for (int32_t e0 = 0; e0 < ne; e0 += 32) {
+        const int32_t e = e0 + lane;
+        int32_t L = e < ne ? A.hslab[beg + e] : -1;
+        const bool live = L >= 0;
+        const int32_t wt = live ? (A.ew ? A.hsw[beg + e] : 1) : 0;
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, live ? L : -1 - lane);
+        const int32_t sum = __reduce_add_sync(peers, wt);
+        const int leader = __ffs(peers) - 1;
+        if (!full) {
+          int32_t sl = (live && lane == leader) ? ht_add_fresh(keys, vals, mask, L, sum) : -1;
+          unsigned m = __ballot_sync(0xFFFFFFFFu, sl >= 0);
+          if (sl >= 0) list[held + __popc(m & ((1u << lane) - 1u))] = (uint16_t)sl;
+          held += __popc(m);
+          if (live) A.hslab[beg + e] = ~L;
+          full = held > HB_LIMIT;
+        } else {
+          bool found = (live && lane == leader) ? ht_find_add(keys, vals, mask, L, sum) : false;
+          found = __shfl_sync(0xFFFFFFFFu, found, leader);
+          if (live && found) A.hslab[beg + e] = ~L;
+          if (live && !found) mine_left = true;
         }
       }
-      // one list reservation per warp
-      unsigned m = __ballot_sync(0xFFFFFFFFu, fresh >= 0);
-      if (m) {
-        int32_t at = 0;
-        if (lane == __ffs(m) - 1) at = atomicAdd(&A.hcount[h], __popc(m));
-        at = __shfl_sync(0xFFFFFFFFu, at, __ffs(m) - 1);
-        if (fresh >= 0) list[at + __popc(m & ((1u << lane) - 1))] = fresh;
-      }
-    }
-  }
-}
-
-// reduce work units: chunks of each hub's occupied-slot list (known only
-// after the inserts)
-__global__ void __launch_bounds__(1024) k_hub_plan_list(LPArgs A, int s) {
-  __shared__ int64_t wt2[32];
-  __shared__ int64_t carry;
-  const int32_t *bo = A.boff + s * NB;
-  int32_t cnt = bo[7] - bo[6];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int32_t base = 0; base < cnt; base += blockDim.x) {
-    int32_t i = base + threadIdx.x;
-    int64_t nt = i < cnt ? ceil_div(A.hcount[A.plan_h[i]], HUB_RCHUNK) : 0;
-    int64_t xt = nt;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      int64_t yt = (int64_t)__shfl_up_sync(0xFFFFFFFFu, (unsigned long long)xt, d);
-      if (lane >= d) xt += yt;
-    }
-    if (lane == 31) wt2[w] = xt;
-    __syncthreads();
-    int64_t pt = carry, tt = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-      if (k < w) pt += wt2[k];
-      tt += wt2[k];
-    }
-    if (i < cnt) A.plan_t[i] = pt + xt - nt;
-    __syncthreads();
-    if (threadIdx.x == 0) carry += tt;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) A.plan_tot[1] = carry;
-}
-
-// work units: table chunks of the sub-round's hubs
-__global__ void __launch_bounds__(256) k_hub_reduce(LPArgs A, int s) {
-  __shared__ unsigned long long red_c[8], red_u[8];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int32_t *bo = A.boff + s * NB;
-  int32_t cnt = bo[7] - bo[6];
-  int64_t total = A.plan_tot[1];
-  for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
-    int32_t i = find_seg(A.plan_t, cnt, c);
-    int32_t h = A.plan_h[i];
-    int32_t u = A.hubs[h];
-    int32_t own = A.label[u], cu = node_w(A, u);
-    int32_t *keys = A.hkeys + A.hoff[h], *vals = A.hvals + A.hoff[h];
-    const int32_t *list = A.hlist + A.hoff[h];
-    int64_t cc = c - A.plan_t[i];
-    {
-      uint64_t kc = 0, ku = 0;
-      int64_t e0 = cc * HUB_RCHUNK;
-      int64_t occ = A.hcount[h];
-      int64_t e1 = e0 + HUB_RCHUNK < occ ? e0 + HUB_RCHUNK : occ;
-      // all loads of this thread's entries first (independent, overlapped),
-      // then the cluster weights, then the clears
-      constexpr int PER = HUB_RCHUNK / 256;
-      int32_t Tv[PER], Kv[PER], Rv[PER], Wv[PER];
-#pragma unroll
-      for (int j = 0; j < PER; ++j) {
-        int64_t x = e0 + threadIdx.x + (int64_t)j * blockDim.x;
-        Tv[j] = x < e1 ? list[x] : -1;
-      }
-#pragma unroll
-      for (int j = 0; j < PER; ++j) {
-        Kv[j] = Tv[j] >= 0 ? keys[Tv[j]] : HT_EMPTY;
-        Rv[j] = Tv[j] >= 0 ? vals[Tv[j]] : 0;
-      }
-#pragma unroll
-      for (int j = 0; j < PER; ++j)
-        Wv[j] = (Kv[j] != HT_EMPTY && Kv[j] != own) ? A.wt[Kv[j]] : 0;
-#pragma unroll
-      for (int j = 0; j < PER; ++j) {
-        int32_t K = Kv[j];
-        if (K == HT_EMPTY) continue;
-        keys[Tv[j]] = HT_EMPTY;  // leave the table empty for its next use
-        vals[Tv[j]] = 0;
+      left = __any_sync(0xFFFFFFFFu, mine_left);
+      __syncwarp();
+      for (int32_t x = lane; x < held; x += 32) {
+        const int32_t sl = list[x];
+        const int32_t K = keys[sl], r = vals[sl];
+        keys[sl] = HT_EMPTY;
+        vals[sl] = 0;
         if (K == own) {
-          A.hrown[h] = Rv[j];
+          A.hrown[h] = r;
           continue;
         }
-        uint64_t k = rate_key(A, K, Rv[j]);
+        const uint64_t k = rate_key(A, K, r);
         ku = k > ku ? k : ku;
-        if ((int64_t)Wv[j] + cu <= cap_of(A, K) && k > kc) kc = k;
+        if ((int64_t)A.wt[K] + cu <= cap_of(A, K) && k > kc) kc = k;
       }
-      kc = group_max64<32>(kc);
-      ku = group_max64<32>(ku);
-      if (lane == 0) { red_c[w] = kc; red_u[w] = ku; }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
-          kc = red_c[i] > kc ? red_c[i] : kc;
-          ku = red_u[i] > ku ? red_u[i] : ku;
-        }
-        if (kc) atomicMax(&A.hkc[h], kc);
-        if (ku) atomicMax(&A.hku[h], ku);
-      }
-      __syncthreads();
+      __syncwarp();
     }
+    kc = group_max64<32>(kc);
+    ku = group_max64<32>(ku);
+    if (lane == 0) {
+      if (kc) atomicMax(&A.hkc[h], kc);
+      if (ku) atomicMax(&A.hku[h], ku);
+      A.hbcnt[g] = 0;
+      A.hbcur[g] = 0;
+    }
+    __syncwarp();
   }
 }
 
@@ -760,29 +842,54 @@ __global__ void __launch_bounds__(256) k_hub_emit(LPArgs A, int s) {
     A.hkc[h] = 0;
     A.hku[h] = 0;
     A.hrown[h] = 0;
-    A.hcount[h] = 0;
   }
   stamp_stage_end(A, s);
 }
 
 // ---- hubs with few labels (refinement): dense rating rows
-// work units: edge chunks of the sub-round's hubs; a CTA sums its chunk per
-// label in shared memory (lanes of a warp that hit the same label add first)
-// and adds the non-zero sums to the hub's row
+// work units: edge chunks of the sub-round's hubs; every CTA takes a
+// contiguous range of chunks and sums them per label in shared memory (lanes
+// of a warp that hit the same label add first); the non-zero sums go to the
+// hub's row whenever the next chunk belongs to another hub, and at the end
 __global__ void __launch_bounds__(256) k_hubd_insert(LPArgs A, int s) {
   extern __shared__ int32_t cnt_s[];
   const int32_t *bo = A.boff + s * NB;
-  int32_t lo = bo[6], cnt = bo[7] - bo[6];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int64_t total = A.plan_tot[0];
-  for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
-    int32_t i = find_seg(A.plan_e, cnt, c);
-    int32_t u = A.vlist[lo + i];
-    int64_t b = A.xadj[u], deg = A.xadj[u + 1] - b;
-    int64_t e0 = b + (c - A.plan_e[i]) * A.hub_chunk;
-    int64_t e1 = e0 + A.hub_chunk < b + deg ? e0 + A.hub_chunk : b + deg;
-    for (int32_t l = threadIdx.x; l < A.nlab; l += blockDim.x) cnt_s[l] = 0;
+  const int32_t lo = bo[6], cnt = bo[7] - bo[6];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t total = A.plan_tot[0];
+  const int64_t per = ceil_div(total, (int64_t)gridDim.x);
+  const int64_t c0 = (int64_t)blockIdx.x * per, c1 = c0 + per < total ? c0 + per : total;
+  for (int32_t l = threadIdx.x; l < A.nlab; l += blockDim.x) cnt_s[l] = 0;
+  __syncthreads();
+  int32_t i = -1;
+  int64_t next = 0, b = 0, deg = 0, efirst = 0;
+  auto flush = [&]() {
     __syncthreads();
+    int32_t *row = A.hdense + (int64_t)i * A.nlab;
+    for (int32_t l = threadIdx.x; l < A.nlab; l += blockDim.x)
+      if (cnt_s[l]) {
+        atomicAdd(&row[l], cnt_s[l]);
+        cnt_s[l] = 0;
+      }
+    __syncthreads();
+  };
+  for (int64_t c = c0; c < c1; ++c) {
+    if (i < 0 || c >= next) {
+      if (i >= 0) flush();
+      if (i < 0 || c >= next + 64) {
+        i = find_seg(A.plan_e, cnt, c);
+      } else {
+        do ++i;
+        while (i + 1 < cnt && A.plan_e[i + 1] <= c);
+      }
+      next = i + 1 < cnt ? A.plan_e[i + 1] : total;
+      const int32_t u = A.vlist[lo + i];
+      b = A.xadj[u];
+      deg = A.xadj[u + 1] - b;
+      efirst = A.plan_e[i];
+    }
+    const int64_t e0 = b + (c - efirst) * A.hub_chunk;
+    const int64_t e1 = e0 + A.hub_chunk < b + deg ? e0 + A.hub_chunk : b + deg;
     for (int64_t base = e0 + 32 * w; base < e1; base += blockDim.x) {
       int64_t e = base + lane;
       bool ok = e < e1;
@@ -792,12 +899,8 @@ __global__ void __launch_bounds__(256) k_hubd_insert(LPArgs A, int s) {
       int32_t sum = __reduce_add_sync(peers, x);
       if (ok && lane == __ffs(peers) - 1) atomicAdd(&cnt_s[L], sum);
     }
-    __syncthreads();
-    int32_t *row = A.hdense + (int64_t)i * A.nlab;
-    for (int32_t l = threadIdx.x; l < A.nlab; l += blockDim.x)
-      if (cnt_s[l]) atomicAdd(&row[l], cnt_s[l]);
-    __syncthreads();
   }
+  if (i >= 0) flush();
 }
 
 // one CTA per hub of the sub-round: best labels from its row (cleared for
@@ -853,13 +956,14 @@ __global__ void k_hub_flags(int32_t n, const int64_t *xadj, int64_t huge, uint8_
     flag[v] = (xadj[v + 1] - xadj[v]) > huge ? 1 : 0;
 }
 
+// hub ids in ascending order and their degrees
 __global__ void k_hub_list(int32_t n, const int64_t *xadj, const uint8_t *flag, const int32_t *pos,
-                           int32_t *hubs, int64_t *hsz) {
+                           int32_t *hubs, int64_t *hdeg) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x)
     if (flag[v]) {
       hubs[pos[v]] = (int32_t)v;
-      hsz[pos[v]] = (int64_t)next_pow2_dev(2 * (xadj[v + 1] - xadj[v]));
+      hdeg[pos[v]] = xadj[v + 1] - xadj[v];
     }
 }
 
@@ -1100,14 +1204,33 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   ctr.zero();
 
   // hubs: with few labels (refinement) a shared-memory table always fits;
-  // otherwise every hub gets its own global table region for the whole run
+  // otherwise every sub-round's hub entries are aggregated in label buckets
+  // (entry buffers sized by the hubs' total degree, one count, cursor and
+  // offset per bucket)
   bool small_labels = 2 * (int64_t)nlab <= CTA_TAB;
   const int64_t huge = small_labels ? C.tune.dense_hub_degree : C.tune.hub_degree;
   bool hub_path = !small_labels && g.maxdeg > huge;
   bool dense_hubs = small_labels && g.maxdeg > huge;
+  // with more labels than a CTA table holds but at most tune.dense_labels of
+  // them, hubs may rate into dense rows of nlab counters (the paper's dense
+  // vector for high-degree nodes) when all rows fit DENSE_ROWS_MAX_BYTES
+  if (hub_path && C.tune.dense_labels > 0 && nlab <= C.tune.dense_labels) {
+    DBuf<uint8_t> flag(n);
+    DBuf<int32_t> pos(n), cnt(1);
+    k_hub_flags<<<grid_for(n, 256), 256, 0, stream>>>(n, g.xadj, huge, flag);
+    KMP_LAUNCHED("hub_flags");
+    scan_excl_u8_to_i32(flag, pos, n, cnt);
+    const int64_t nh = read1(cnt.p);
+    if (nh * (int64_t)nlab * (int64_t)sizeof(int32_t) <= DENSE_ROWS_MAX_BYTES) {
+      hub_path = false;
+      dense_hubs = true;
+    }
+  }
+  const int32_t hub_bucket = C.tune.hub_bucket > 0 ? C.tune.hub_bucket : 256;
   int32_t nhubs = 0;
-  DBuf<int32_t> hubs, hkeys, hvals, hrown, plan_h, hdense, hlist, hcount;
-  DBuf<int64_t> hoff, plan_e, plan_t, plan_tot;
+  int64_t nbmax = 0;
+  DBuf<int32_t> hubs, hrown, plan_h, hdense, hlab, hslab, hsw, hbcnt, hbcur, hboff, hbsum;
+  DBuf<int64_t> plan_e, plan_x, plan_b, plan_tot;
   DBuf<unsigned long long> hkc, hku;
   if (hub_path) {
     DBuf<uint8_t> flag(n);
@@ -1117,19 +1240,21 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
     scan_excl_u8_to_i32(flag, pos, n, cnt);
     nhubs = read1(cnt.p);
     hubs.alloc(nhubs);
-    DBuf<int64_t> hsz(nhubs), tot(1);
-    hoff.alloc(nhubs);
-    k_hub_list<<<grid_for(n, 256), 256, 0, stream>>>(n, g.xadj, flag, pos, hubs, hsz);
+    DBuf<int64_t> hdeg(nhubs), hdoff(nhubs), tot(1);
+    k_hub_list<<<grid_for(n, 256), 256, 0, stream>>>(n, g.xadj, flag, pos, hubs, hdeg);
     KMP_LAUNCHED("hub_list");
-    scan_excl_i64(hsz, hoff, nhubs, tot);
-    int64_t T = read1(tot.p);
-    hkeys.alloc(T);
-    hvals.alloc(T);
-    hlist.alloc(T);
-    hcount.alloc(nhubs);
-    hkeys.fill_bytes(0xFF);
-    hvals.zero();
-    hcount.zero();
+    scan_excl_i64(hdeg, hdoff, nhubs, tot);
+    const int64_t Dhub = read1(tot.p);  // bounds the entries of any sub-round
+    nbmax = Dhub / hub_bucket + nhubs;  // bounds its buckets (ceil per hub)
+    hlab.alloc(Dhub);
+    hslab.alloc(Dhub);
+    if (g.ew) hsw.alloc(Dhub);
+    hbcnt.alloc(nbmax);
+    hbcur.alloc(nbmax);
+    hboff.alloc(nbmax);
+    hbsum.alloc(scan_tmp_count(nbmax));
+    hbcnt.zero();
+    hbcur.zero();
     hkc.alloc(nhubs);
     hku.alloc(nhubs);
     hrown.alloc(nhubs);
@@ -1138,8 +1263,14 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
     hrown.zero();
     plan_h.alloc(nhubs);
     plan_e.alloc(nhubs + 1);
-    plan_t.alloc(nhubs + 1);
-    plan_tot.alloc(2);
+    plan_x.alloc(nhubs + 1);
+    plan_b.alloc(nhubs + 1);
+    plan_tot.alloc(3);
+    static bool hb_attr = false;  // before any capture: the bucket kernel's tables exceed 48 KB
+    if (!hb_attr) {
+      KMP_CUDA(cudaFuncSetAttribute(k_hub_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HB_SMEM));
+      hb_attr = true;
+    }
   } else if (dense_hubs) {
     DBuf<uint8_t> flag(n);
     DBuf<int32_t> pos(n), cnt(1);
@@ -1149,10 +1280,17 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
     nhubs = read1(cnt.p);
     hdense.alloc((int64_t)nhubs * nlab);
     hdense.zero();
+    static bool hd_attr = false;  // before any capture: counters of up to DENSE_LABELS_MAX labels
+    if (!hd_attr) {
+      KMP_CUDA(cudaFuncSetAttribute(k_hubd_insert, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    DENSE_LABELS_MAX * (int)sizeof(int32_t)));
+      hd_attr = true;
+    }
     plan_h.alloc(nhubs);
     plan_e.alloc(nhubs + 1);
-    plan_t.alloc(nhubs + 1);
-    plan_tot.alloc(2);
+    plan_x.alloc(nhubs + 1);
+    plan_b.alloc(nhubs + 1);
+    plan_tot.alloc(3);
   }
 
   LPArgs A{};
@@ -1185,17 +1323,21 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
   A.bigmove = bigmove;
   A.hubs = hubs.p;
   A.nhubs = nhubs;
-  A.hoff = hoff.p;
-  A.hkeys = hkeys.p;
-  A.hvals = hvals.p;
+
   A.hkc = hkc.p;
   A.hku = hku.p;
   A.hrown = hrown.p;
-  A.hlist = hlist.p;
-  A.hcount = hcount.p;
+  A.hlab = hlab.p;
+  A.hslab = hslab.p;
+  A.hsw = hsw.p;
+  A.hbcnt = hbcnt.p;
+  A.hbcur = hbcur.p;
+  A.hboff = hboff.p;
+  A.hub_bucket = dense_hubs ? 0 : hub_bucket;
   A.plan_h = plan_h.p;
   A.plan_e = plan_e.p;
-  A.plan_t = plan_t.p;
+  A.plan_x = plan_x.p;
+  A.plan_b = plan_b.p;
   A.plan_tot = plan_tot.p;
   A.small_labels = small_labels ? 1 : 0;
   A.hdense = dense_hubs ? hdense.p : nullptr;
@@ -1206,6 +1348,7 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
 
   int grid_rate = C.tune.rate_blocks_per_sm * C.sms;
   int grid_hub = 4 * C.sms;
+  int grid_bucket = 3 * C.sms;  // k_hub_bucket: 72 KB of tables per CTA
   int grid_commit = grid_for(ceil_div(n, S), 256, 8);
   // per-round state and counters in device memory (18 counters a round)
   DBuf<LPRound> rstate(1);
@@ -1254,12 +1397,13 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
       if (hub_path) {
         k_hub_plan<<<1, 1024, 0, st>>>(A, s);
         KMP_LAUNCHED("hub_plan");
-        k_hub_insert<<<grid_hub, 256, 0, st>>>(A, s);
-        KMP_LAUNCHED("hub_insert");
-        k_hub_plan_list<<<1, 1024, 0, st>>>(A, s);
-        KMP_LAUNCHED("hub_plan_list");
-        k_hub_reduce<<<grid_hub, 256, 0, st>>>(A, s);
-        KMP_LAUNCHED("hub_reduce");
+        k_hub_count<<<grid_hub, 256, 0, st>>>(A, s);
+        KMP_LAUNCHED("hub_count");
+        scan_excl_i32_on(hbcnt, hboff, nbmax, nullptr, hbsum, st);
+        k_hub_scatter<<<grid_hub, 256, 0, st>>>(A, s);
+        KMP_LAUNCHED("hub_scatter");
+        k_hub_bucket<<<grid_bucket, HB_W * 32, HB_SMEM, st>>>(A, s);
+        KMP_LAUNCHED("hub_bucket");
         k_hub_emit<<<grid_for(nhubs, 256), 256, 0, st>>>(A, s);
         KMP_LAUNCHED("hub_emit");
       } else if (dense_hubs) {

@@ -49,7 +49,9 @@ class Stats(ctypes.Structure):
                 ("ms_lp_level0", ctypes.c_float), ("lp_scanned_level0", ctypes.c_int64),
                 ("lp_rounds_level0", ctypes.c_int32), ("gpu_launches", ctypes.c_int32),
                 ("clustered", ctypes.c_int32), ("level_kp", ctypes.c_int32 * 64),
-                ("level_U", ctypes.c_int64 * 64), ("level_k", ctypes.c_int32 * 64)]
+                ("level_U", ctypes.c_int64 * 64), ("level_k", ctypes.c_int32 * 64),
+                ("bal_over_blocks", ctypes.c_int64), ("bal_moves", ctypes.c_int64),
+                ("bal_spec_moves", ctypes.c_int64), ("bal_exact_batches", ctypes.c_int64)]
 
     def as_dict(self):
         d = {}
@@ -66,7 +68,7 @@ class Stats(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "rate_blocks_per_sm", "hub_degree", "hub_chunk", "ip_blocks_per_sm", "dense_hub_degree", "lp_graphs",
-        "hub_bucket")]
+        "hub_bucket", "dense_labels")]
 
 
 def load():

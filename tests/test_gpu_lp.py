@@ -218,7 +218,7 @@ def test_rating_profile_is_consistent(kmp, graphs):
     U = int(np.floor(0.03 * g.n / 64))
     old = kmp.get_tuning()
     t = kmp.Tuning(old.rate_blocks_per_sm, old.hub_degree, old.hub_chunk, old.ip_blocks_per_sm,
-                   old.dense_hub_degree, graphs)
+                   old.dense_hub_degree, graphs, old.hub_bucket, old.dense_labels)
     kmp.set_tuning(t)
     try:
         plain = kmp.coarsen_level(dg, U, 5, 7, 0)
@@ -229,7 +229,8 @@ def test_rating_profile_is_consistent(kmp, graphs):
         prof = kmp.coarsen_level(dg, U, 5, 7, 0)
         e1.record()
         e1.synchronize()
-        ms, by, nl = kmp.profile_read(reset=True)
+        p = kmp.profile_read(reset=True)
+        ms, by, nl = p
     finally:
         kmp.set_profiling(False)
         kmp.set_tuning(old)
@@ -238,3 +239,88 @@ def test_rating_profile_is_consistent(kmp, graphs):
     assert nl > 0 and nl % S == 0 and nl <= 5 * S
     assert by > 0
     assert 0 < ms <= e0.elapsed_time(e1)
+    # the whole rating stage (k_rate and the hub kernels after it) spans at
+    # least k_rate's time, one span per sub-round, hub entries included
+    assert p.stage_spans == nl and ms <= p.stage_ms <= e0.elapsed_time(e1)
+    assert p.stage_bytes > by
+
+
+@pytest.mark.parametrize("bucket", [32, 256, 1 << 20])
+def test_hub_buckets_any_size(kmp, bucket):
+    """Hub ratings with many labels aggregate each hub's entries in label
+    buckets of about `bucket` entries, one warp each, in rounds of at most a
+    table's worth of new labels.  One bucket per hub (2^20) forces several
+    rounds for every hub with more distinct neighbour labels than a round
+    admits; 32 makes many small buckets.  The bucket size is a schedule
+    parameter: labels and favoured clusters stay bit-exact with the oracle."""
+    old = kmp.get_tuning()
+    t = kmp.Tuning(old.rate_blocks_per_sm, 256, old.hub_chunk, old.ip_blocks_per_sm, old.dense_hub_degree,
+                   old.lp_graphs, bucket, 0)
+    kmp.set_tuning(t)
+    try:
+        for name in ("hubs", "hubs_w", "rmat14"):
+            g = CASES[name]
+            U = _U(g, 0.004)
+            dg = kmp.DeviceGraph.from_host(g)
+            label, fav = kmp.coarsen_level(dg, U, 5, 4, 0, fav=True)
+            rl, rf, _ = O.cluster(g, U, 5, 4, 0, stats=True)
+            assert np.array_equal(label.cpu().numpy(), rl), (name, bucket)
+            assert np.array_equal(fav.cpu().numpy(), rf), (name, bucket)
+    finally:
+        kmp.set_tuning(old)
+
+
+@pytest.mark.parametrize("name", ["hubs_w", "rmat14"])
+def test_refine_parity_many_blocks(kmp, name):
+    """Refinement with more blocks than a shared table holds labels (k = 3000):
+    hub ratings take the bucketed path with blocks as labels."""
+    g = CASES[name]
+    k = 3000
+    rng = np.random.default_rng(5)
+    part = rng.integers(0, k, g.n).astype(np.int32)
+    bw = np.bincount(part, weights=g.vw(), minlength=k)
+    caps = (np.maximum(bw, 1.03 * g.vw().sum() / k) + int(g.vw().max())).astype(np.int64)
+    dg = kmp.DeviceGraph.from_host(g)
+    pt = torch.from_numpy(part).cuda()
+    old = kmp.get_tuning()
+    kmp.set_tuning(kmp.Tuning(old.rate_blocks_per_sm, 256, old.hub_chunk, old.ip_blocks_per_sm,
+                              old.dense_hub_degree, old.lp_graphs, 64, 0))
+    try:
+        cut = kmp.refine(dg, k, caps, 5, 11, pt)
+    finally:
+        kmp.set_tuning(old)
+    rp, rc = O.refine(g, k, caps.astype(np.int32), 5, 11, part)
+    assert np.array_equal(pt.cpu().numpy(), rp)
+    assert cut == rc
+
+
+@pytest.mark.parametrize("dense_labels", [0, 57344])
+def test_dense_hub_rows_for_mid_size_label_sets(kmp, dense_labels):
+    """With at most `dense_labels` labels (here every graph of the test), hubs
+    rate into dense per-hub rows of label counters instead of label buckets:
+    coarsening labels, favoured clusters and a many-block refinement stay
+    bit-exact with the oracle either way."""
+    old = kmp.get_tuning()
+    t = kmp.Tuning(old.rate_blocks_per_sm, 256, old.hub_chunk, old.ip_blocks_per_sm, old.dense_hub_degree,
+                   old.lp_graphs, old.hub_bucket, dense_labels)
+    kmp.set_tuning(t)
+    try:
+        for name in ("hubs_w", "rmat14"):
+            g = CASES[name]
+            U = _U(g, 0.004)
+            dg = kmp.DeviceGraph.from_host(g)
+            label, fav = kmp.coarsen_level(dg, U, 5, 4, 0, fav=True)
+            rl, rf, _ = O.cluster(g, U, 5, 4, 0, stats=True)
+            assert np.array_equal(label.cpu().numpy(), rl), name
+            assert np.array_equal(fav.cpu().numpy(), rf), name
+            k = 3000
+            rng = np.random.default_rng(7)
+            part = rng.integers(0, k, g.n).astype(np.int32)
+            bw = np.bincount(part, weights=g.vw(), minlength=k)
+            caps = (np.maximum(bw, 1.03 * g.vw().sum() / k) + int(g.vw().max())).astype(np.int64)
+            pt = torch.from_numpy(part).cuda()
+            cut = kmp.refine(dg, k, caps, 5, 11, pt)
+            rp, rc = O.refine(g, k, caps.astype(np.int32), 5, 11, part)
+            assert np.array_equal(pt.cpu().numpy(), rp) and cut == rc, name
+    finally:
+        kmp.set_tuning(old)

@@ -210,7 +210,7 @@ def test_schedule_halving_chain_on_isolated_nodes(kmp):
     _same_schedule(st, rst)
 
 
-@pytest.mark.parametrize("tune", [(4, 1024, 1024, 2, 600, 0, 64), (8, 2048, 4096, 8, 1 << 30, 1, 1 << 20),
+@pytest.mark.parametrize("tune", [(4, 1024, 1024, 2, 600, 0, 64, 57344), (8, 2048, 4096, 8, 1 << 30, 1, 1 << 20, 0),
                                   (2, 256, 256, 1, 4096, 0, 0)])
 def test_tuning_invariance(kmp, tune):
     """Schedule parameters (grids, hub threshold, chunking) never change results."""
