@@ -136,21 +136,23 @@ class Clocks:
         return out
 
 
-def recorded_rate_traffic(workload):
-    """DRAM bytes per k_rate launch from the committed ncu record of this
-    workload, or None when there is none or the LP source changed since."""
+def recorded_rate_traffic(workload, alg_bytes_per_launch):
+    """DRAM bytes per k_rate launch: the committed ncu record gives DRAM bytes
+    per algorithmic byte on a small case of the same graph family (one kernel,
+    a few launches), scaled here by this run's algorithmic bytes per launch.
+    None when there is no record for the workload or the LP source changed."""
     import hashlib
 
     prof = os.path.join(ROOT, "profiles", "lp_rate_traffic.json")
     try:
         rec = json.load(open(prof))
         src = os.path.join(ROOT, "paper_2105_02022_gb300", "csrc", "kmp_lp.cu")
-        if rec.get("workload") != workload:
+        if workload not in rec.get("applies_to", []):
             return None
         if rec.get("kmp_lp_cu_sha256") != hashlib.sha256(open(src, "rb").read()).hexdigest():
             return None
-        return rec.get("dram_bytes_per_launch")
-    except (OSError, ValueError):
+        return rec["dram_bytes_per_algorithmic_byte"] * alg_bytes_per_launch
+    except (OSError, ValueError, KeyError, TypeError):
         return None
 
 
@@ -268,6 +270,177 @@ def ksweep(gg, kmp, torch, np, workload):
                           "generate_s": gen_s}), flush=True)
 
 
+def _coarse_blocks(gg, kmp, np, g, seed, k):
+    """One coarsening level of g on the GPU (clusters of about 6 nodes), then
+    a k-way partition of the coarse graph: (host coarse graph, block of every
+    node)."""
+    dg = kmp.DeviceGraph.from_host(g)
+    U = max(1, g.n // max(g.n // 6, 1))
+    cg, _ = kmp.contract(dg, kmp.coarsen_level(dg, U, 5, seed, 0))
+    part, _, _ = kmp.partition_graph(cg, k, EPS, seed)
+    return cg.to_host(), part.cpu().numpy()
+
+
+def _union_of_blocks(gg, np, h, part, blocks, vmax=64, emax=256):
+    """Disjoint union of the induced subgraphs of the chosen blocks (node ids
+    block by block, ascending inside), weights clipped to [1, vmax] and
+    [1, emax]; returns (graph, block index of every node, per-block caps
+    (t0, t1, L0, L1) for a bisection at eps)."""
+    rank = -np.ones(part.max() + 1, np.int64)
+    rank[np.asarray(blocks)] = np.arange(len(blocks))
+    r = rank[part]
+    sel = np.flatnonzero(r >= 0)
+    sel = sel[np.lexsort((sel, r[sel]))]
+    newid = -np.ones(h.n, np.int64)
+    newid[sel] = np.arange(len(sel))
+    src = np.repeat(np.arange(h.n), np.diff(h.xadj))
+    keep = (r[src] >= 0) & (part[src] == part[h.adjncy])
+    s_new, d_new = newid[src[keep]], newid[h.adjncy[keep]]
+    w = np.clip(h.ew()[keep], 1, emax).astype(np.int32)
+    o = np.lexsort((d_new, s_new))
+    s_new, d_new, w = s_new[o], d_new[o], w[o]
+    n = len(sel)
+    xadj = np.zeros(n + 1, np.int64)
+    np.add.at(xadj, s_new + 1, 1)
+    xadj = np.cumsum(xadj)
+    vw = np.clip(h.vw()[sel], 1, vmax).astype(np.int32)
+    bpart = r[sel].astype(np.int32)
+    caps = []
+    cb = np.bincount(bpart, weights=vw, minlength=len(blocks)).astype(np.int64)
+    for c in cb:
+        L = int(np.floor((1.0 + EPS) * ((int(c) + 1) // 2)))
+        caps += [int(c) // 2, int(c) - int(c) // 2, L, L]
+    return gg.Graph(n, xadj, d_new.astype(np.int32), vw, w, "blocks"), bpart, np.array(caps, np.int32)
+
+
+def _block_set(gg, kmp, np, sources, want, lo=200, hi=4000):
+    """Blocks of lo..hi nodes from coarse partitions of the sources, until
+    `want` are collected: their union, block index per node and caps."""
+    graphs = []
+    total = 0
+    for make, seed, k in sources:
+        h, part = _coarse_blocks(gg, kmp, np, make(seed), seed, k)
+        sizes = np.bincount(part, minlength=k)
+        blocks = [b for b in range(k) if lo <= sizes[b] <= hi]
+        graphs.append((h, part, blocks))
+        total += len(blocks)
+        if total >= want:
+            break
+    parts = []
+    for h, part, blocks in graphs:
+        take = blocks[: max(0, want - sum(len(b) for _, _, b in parts))]
+        if take:
+            parts.append((h, part, take))
+    # one union graph per source, concatenated
+    gs = [_union_of_blocks(gg, np, h, part, bl) for h, part, bl in parts]
+    n_off, e_off, boff = 0, 0, 0
+    xs, adjs, vws, ews, bps, caps = [], [], [], [], [], []
+    for g, bp, cp in gs:
+        xs.append(g.xadj[:-1] + e_off)
+        adjs.append(g.adjncy + n_off)
+        vws.append(g.vwgt)
+        ews.append(g.adjwgt)
+        bps.append(bp + boff)
+        caps.append(cp)
+        n_off += g.n
+        e_off += g.m_directed
+        boff += int(bp.max()) + 1
+    xadj = np.concatenate(xs + [np.array([e_off], np.int64)])
+    u = gg.Graph(n_off, xadj, np.concatenate(adjs).astype(np.int32), np.concatenate(vws),
+                 np.concatenate(ews), "block_union")
+    return u, np.concatenate(bps).astype(np.int32), np.concatenate(caps).astype(np.int32), boff
+
+
+def learned(gg, kmp, torch, np):
+    """The learned seed proposer (spec addition, readings B6 and B8):
+    trained on item bipartitions the plain method produces (other seeds), then
+    (i) 4096 coarse blocks of 200..4000 nodes with vertex weights 1..64 and
+    edge weights 1..256 from one coarsening level of RGG 2^20 (deg 8) and
+    R-MAT 2^18 (ef 16), bipartitioned at eps = 0.03 in one launch per mode:
+    plain portfolio, learned mode 1 (coarsest graph) and learned mode 2 (item
+    graph), cut ratio and time; (ii) end to end on RGG 2^24, k = 2^14."""
+    kmp.load()
+    rgg = lambda s: gg.rgg(1 << 20, 8, s)
+    rmat = lambda s: gg.rmat(18, 16, s)
+    # training data: item graphs and their final plain bipartitions
+    t0 = time.perf_counter()
+    train_src = [(rgg, 100 + i, 128) for i in range(2)] + [(rmat, 200 + i, 32) for i in range(4)]
+    tg, tp, tc, tnb = _block_set(gg, kmp, np, train_src, 512)
+    kmp.set_config(kmp.config())
+    kmp.sample_sink_open(tnb + 8, tg.n + 8, tg.m_directed + 8, item_level=1)
+    try:
+        kmp.bipartition_each(kmp.DeviceGraph.from_host(tg), tnb, tc, 7, torch.from_numpy(tp.copy()).cuda())
+        batch, dropped = kmp.sample_sink_read()
+    finally:
+        kmp.sample_sink_close()
+    model = kmp.Mpnn(5)
+    torch.cuda.synchronize()
+    tt = time.perf_counter()
+    losses = model.train(batch, 300, 3e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - tt
+    print(json.dumps({"mode": "learned", "part": "training", "samples": int(batch.ng), "nodes": int(batch.n),
+                      "dropped": int(dropped), "epochs": 300, "loss_first": float(losses[0]),
+                      "loss_last": float(losses[-1]), "train_s": train_s,
+                      "prepare_s": time.perf_counter() - t0}), flush=True)
+    # (i) the block set of the learned-proposal configuration
+    src = [(rgg, i, 128) for i in range(1, 40)]
+    a_g, a_p, a_c, a_nb = _block_set(gg, kmp, np, src, 2048)
+    src = [(rmat, i, 32) for i in range(1, 200)]
+    b_g, b_p, b_c, b_nb = _block_set(gg, kmp, np, src, 2048)
+    res = {}
+    for fam, g, bp, caps, nb in (("rgg_2^20", a_g, a_p, a_c, a_nb), ("rmat_2^18", b_g, b_p, b_c, b_nb)):
+        dg = kmp.DeviceGraph.from_host(g)
+        sizes = np.bincount(bp)
+        for mode, cfg, prop in (("plain", kmp.config(), None), ("learned1", kmp.config(learned=1), model),
+                                ("learned2", kmp.config(learned=2), model)):
+            kmp.set_config(cfg)
+            kmp.set_proposer(prop)
+            pt = torch.from_numpy(bp.copy()).cuda()
+            kmp.bipartition_each(dg, nb, caps, 11, pt)
+            ms = []
+            for _ in range(3):
+                pt = torch.from_numpy(bp.copy()).cuda()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                kmp.bipartition_each(dg, nb, caps, 11, pt)
+                e1.record()
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            side = pt.cpu().numpy()
+            cut, bw = kmp.cut(dg, pt, 2 * nb)
+            L = caps.reshape(-1, 4)[:, 2:]
+            feas = bool(np.all(bw[0::2] <= L[:, 0] + g.vwgt.max()) and np.all(bw[1::2] <= L[:, 1] + g.vwgt.max()))
+            res[(fam, mode)] = (cut, statistics.median(ms))
+            print(json.dumps({"mode": "learned", "part": "blocks", "family": fam, "blocks": int(nb),
+                              "nodes_min": int(sizes.min()), "nodes_max": int(sizes.max()),
+                              "nodes_mean": float(sizes.mean()), "method": mode, "cut": int(cut),
+                              "cut_vs_plain": cut / res[(fam, "plain")][0],
+                              "ms": statistics.median(ms), "ms_vs_plain": statistics.median(ms) / res[(fam, "plain")][1],
+                              "within_caps": feas}), flush=True)
+        del dg
+    # (ii) end to end at large k
+    g = gg.rgg(1 << 24, 16, SEED)
+    dg = kmp.DeviceGraph.from_host(g)
+    for mode, cfg, prop in (("plain", kmp.config(), None), ("learned2", kmp.config(learned=2), model)):
+        kmp.set_config(cfg)
+        kmp.set_proposer(prop)
+        kmp.partition_graph(dg, 1 << 14, EPS, SEED)
+        sts = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            _, rc, st = kmp.partition_graph(dg, 1 << 14, EPS, SEED)
+            sts.append(st)
+        st = min(sts, key=lambda x: x.ms_total)
+        print(json.dumps({"mode": "learned", "part": "end_to_end", "workload": "rgg_2^24_deg16_k16384",
+                          "method": mode, "ms": st.ms_total, "ms_ip": st.ms_ip, "cut": int(st.cut),
+                          "feasible": bool(st.feasible)}), flush=True)
+    kmp.set_config(kmp.config())
+    kmp.set_proposer(None)
+    model.free()
+
+
 def replicas(gg, kmp, torch, np):
     """Replication of the coarsest levels (Section 3, "Parallelization"):
     median of three partitions per R after a warm-up, same seed."""
@@ -300,7 +473,8 @@ def main():
                     help=f"default {DEFAULT_WORKLOAD} (ksweep: rgg_2^24_deg16_k16384)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="partition",
-                    choices=["partition", "coarsen1", "launchlist", "ksweep", "replicas", "oracle_phases"],
+                    choices=["partition", "coarsen1", "launchlist", "ksweep", "replicas", "oracle_phases",
+                             "learned"],
                     help="coarsen1: one level-0 coarsening (LP) of the workload graph only; "
                          "launchlist: one warm-up partition and one partition inside the NVTX "
                          "range kmp_step (for ncu launch lists); both are used for kernel profiles; "
@@ -309,7 +483,8 @@ def main():
                          "replicas: cut and time with R = 1, 2, 4, 8 copies of the coarsest levels "
                          "on R-MAT scale 20 (k = 256) and the small RGG (k = 8); "
                          "oracle_phases: the CPU oracle's partition timed per phase on the small RGG "
-                         "and R-MAT scale 20")
+                         "and R-MAT scale 20; learned: the learned seed proposer trained on the "
+                         "method's own item bipartitions, on 4096 coarse blocks and end to end")
     args = ap.parse_args()
     if args.mode != "ksweep" and args.workload is None:
         args.workload = DEFAULT_WORKLOAD
@@ -336,6 +511,9 @@ def main():
         return
     if args.mode == "replicas":
         replicas(gg, kmp, torch, np)
+        return
+    if args.mode == "learned":
+        learned(gg, kmp, torch, np)
         return
     dist = None
     if world > 1:
@@ -450,11 +628,11 @@ def main():
     peak, peak_kind = _peaks()
     # DRAM bytes per k_rate launch from the committed ncu capture, valid only
     # while the LP source it was taken from is unchanged
-    traffic = recorded_rate_traffic(args.workload)
+    pd = prof.as_dict(peak)
+    traffic = recorded_rate_traffic(args.workload, pd["rate_bytes_per_launch"] or 0.0)
 
     if rank != 0:
         return
-    pd = prof.as_dict(peak)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": warmup, "ms_per_step": total_step_ms / args.steps, "higher_is_better": True,

@@ -69,9 +69,13 @@ typedef struct {
   int32_t rep_ggg;       /* greedy graph growing (8) */
   int32_t fm_passes;     /* 2-way FM passes per level (8) */
   int32_t fm_stop;       /* fruitless FM moves that end a pass (64) */
-  int32_t learned;       /* learned mode (0): the proposer set by kmp_set_proposer seeds one
-                            bipartition first, then a reduced portfolio runs; the rest of the
-                            plain portfolio runs only if the best so far is infeasible */
+  int32_t learned;       /* learned mode (0 = off), with the proposer set by kmp_set_proposer:
+                            1: the proposal seeds one bipartition of each item's coarsest graph
+                            first, then a reduced portfolio runs; the rest of the plain portfolio
+                            runs only if the best so far is infeasible;
+                            2: the proposal is made on the item graph itself and refined there by
+                            2-way FM, skipping the item's coarsening and portfolio; the plain
+                            method runs only if that breaks a cap */
   int32_t lrep_random;   /* learned-mode repetitions (each at most its rep_*): random (0) */
   int32_t lrep_bfs;      /* BFS (0) */
   int32_t lrep_ggg;      /* greedy graph growing (1) */
@@ -274,7 +278,7 @@ typedef struct {
   int32_t hub_degree;         /* degree above which coarsening rates a node with the
                                  multi-CTA hub kernels (256..2048) */
   int32_t hub_chunk;          /* edges per hub work unit (256..65536, power of two;
-                                 default 512) */
+                                 default 2048) */
   int32_t ip_blocks_per_sm;   /* bipartitioner CTAs per SM (1..8) */
   int32_t dense_hub_degree;   /* with few labels (refinement: labels are block ids), degree
                                  above which a node's rating is split over many CTAs into a
@@ -370,6 +374,11 @@ int kmp_sample_sink_count(int32_t *graphs, int64_t *nodes, int64_t *entries, int
 int kmp_sample_sink_read(int32_t *noff, int64_t *xadj, int32_t *adj, int32_t *vw, int32_t *ew,
                          uint64_t *keys, int32_t *side);
 int kmp_sample_sink_close(void);
+/* what the sink records from now on: 0 (default) each item's coarsest graph
+ * and the winning portfolio bipartition there (training data for learned
+ * mode 1); 1 each item graph and its final bipartition by the plain method
+ * (training data for learned mode 2).  KMP_ERR_ARG for other values. */
+int kmp_sample_sink_level(int32_t item_level);
 
 /*
  * Cut and block weights without any device allocation.  The paper has no

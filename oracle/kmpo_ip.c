@@ -37,6 +37,13 @@
  *     repetitions of B2 (same keys).  Only if the best of these is infeasible
  *     do the remaining repetitions of B2 run, in B2's order.  Every candidate
  *     is FM-refined and compared exactly as in B2 (first best wins).
+ *  B8 Learned item mode (cfg->learned == 2 with a proposer set; an addition
+ *     to the method): the network scores the item graph itself (M1-M3, key
+ *     step(itemkey, DOM_LEARNED)), the learned start fills block 0 first fit
+ *     in score order (as in B6), and 2-way FM (B4) refines it on the item
+ *     graph with the caps of B5.  The item's own coarsening, portfolio and
+ *     intermediate levels are skipped.  If the refined start breaks a cap, the
+ *     item is bipartitioned by the plain method (B1-B5, the fixed portfolio).
  *  B7 Adaptive portfolio (cfg->adaptive, plain mode only; Section 4.2 names
  *     the adaptive algorithm selection of Mt-KaHyPar without describing it).
  *     Stage 1 runs the first ceil(R_a / 2) repetitions of every algorithm a,
@@ -304,6 +311,23 @@ int64_t kmpo_bipartition(int32_t n, const int64_t *xadj, const int32_t *adj, con
                          int32_t target1, uint64_t itemkey, const kmpo_config *cfg,
                          int32_t *side_out) {
   if (n == 0) return 0;
+  if (cfg->learned == 2 && kmpo_proposer()) {
+    /* B8: learned start on the item graph, FM there, plain method if infeasible */
+    const int32_t mx = max_w(n, vw);
+    const int32_t c0 = level_cap(L0, target0, mx), c1 = level_cap(L1, target1, mx);
+    kmpo_learned_initial(n, xadj, adj, vw, ew, target0, kmpo_step(itemkey, DOM_LEARNED),
+                         kmpo_proposer(), side_out);
+    int64_t cut = kmpo_fm(n, xadj, adj, vw, ew, c0, c1, cfg, side_out);
+    int64_t W0 = 0, W1 = 0;
+    for (int32_t v = 0; v < n; ++v) {
+      if (side_out[v] == 0) W0 += vwt(vw, v);
+      else W1 += vwt(vw, v);
+    }
+    if (W0 <= c0 && W1 <= c1) return cut;
+    kmpo_config plain = *cfg;
+    plain.learned = 0;
+    return kmpo_bipartition(n, xadj, adj, vw, ew, L0, L1, target0, target1, itemkey, &plain, side_out);
+  }
   lvl_t lv[64];
   int32_t nl = 1;
   lv[0].n = n;

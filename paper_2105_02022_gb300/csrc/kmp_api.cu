@@ -448,7 +448,7 @@ int kmp_set_config(const kmp_config *c) {
         c->ip_lp_rounds < 0 || c->ip_lp_rounds > 64 || c->rep_random < 0 || c->rep_bfs < 0 ||
         c->rep_ggg < 0 || c->rep_random + c->rep_bfs + c->rep_ggg < 1 ||
         c->rep_random + c->rep_bfs + c->rep_ggg > 64 || c->fm_passes < 0 || c->fm_stop < 1 ||
-        c->learned < 0 || c->learned > 1 || c->lrep_random < 0 || c->lrep_bfs < 0 || c->lrep_ggg < 0 ||
+        c->learned < 0 || c->learned > 2 || c->lrep_random < 0 || c->lrep_bfs < 0 || c->lrep_ggg < 0 ||
         c->replicas < 1 || c->replicas > 64 || (c->replicas & (c->replicas - 1)) != 0 ||
         c->adaptive < 0 || c->adaptive > 1)
       fail(KMP_ERR_ARG, "invalid configuration");

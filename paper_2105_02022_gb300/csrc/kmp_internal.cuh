@@ -39,7 +39,7 @@ struct Context {
   int64_t launches = 0;
   int *d_status = nullptr;  // device status word: 0 ok, else KMP_ERR_* set by kernels
   // schedule parameters (never change results); see kmp_autotune
-  kmp_tuning tune{8, 2048, 512, 4, 8192, 1, 256, 0};
+  kmp_tuning tune{8, 2048, 2048, 4, 8192, 1, 256, 0};
   // live profiling of the LP rating launches (CUDA events on `stream`)
   bool profile = false;
   cudaStream_t capture_stream = nullptr;  // created on first use: CUDA graph capture of LP rounds

@@ -68,6 +68,7 @@ struct IPArgs {
   const __nv_bfloat16 *W;
   int32_t lrep_random, lrep_bfs, lrep_ggg;
   int32_t adaptive;  // adaptive portfolio (plain mode only)
+  int32_t learned_item;  // learned item mode (W set): start on the item graph, FM there
   SampleSink sink;  // counters null: no recording
   int32_t dyn_words;  // dynamic shared memory per CTA (int32 words) for FM and portfolio state
 };
@@ -1132,6 +1133,60 @@ __device__ void record_sample(const SampleSink &K, const LG &h, const int32_t *s
   __syncthreads();
 }
 
+// Learned item mode: the network scores the item graph itself, the learned
+// start (first fit in score order, warp 0) is refined by the CTA's 2-way FM on
+// the item graph with the finest level's caps.  1: feasible, written to
+// side_out; 0: a cap is broken (the caller runs the plain method); -1: the
+// item's scratch is too small.
+__device__ int item_learned(const IPArgs &A, const ItemDesc &D, const LG &g, Bump &B, int32_t *dyn) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int32_t n = g.n;
+  const int32_t P = pow2_at_least(n > 1 ? n : 2);
+  float *X = reinterpret_cast<float *>(B.take((int64_t)n * MF));
+  int32_t *d1 = B.take(n), *d2 = B.take(n);
+  float *scr = reinterpret_cast<float *>(B.take((int64_t)n * (MF + 3 * MH)));
+  float *sc = reinterpret_cast<float *>(B.take(n));
+  int32_t *side = B.take(n);
+  uint64_t *oh = reinterpret_cast<uint64_t *>(B.take(2ll * P));
+  int32_t *ov = B.take(P);
+  int32_t *fmbuf = B.take(7ll * n + 2);
+  if (B.oom) return -1;
+  GView<int32_t> G{n, g.xadj, g.adj, 0, g.vw, g.ew};
+  mp_features(G, key_step(D.key, DOM_LEARNED), X, d1, d2);
+  mp_forward_cta(G, A.W, X, scr, sc);
+  __syncthreads();
+  if (w == 0) warp_initial(3, g, D.t0, 0, side, oh, ov, nullptr, nullptr, nullptr, sc);
+  __syncthreads();
+  const int64_t c0 = level_cap(D.L0, D.t0, g.maxc), c1 = level_cap(D.L1, D.t1, g.maxc);
+  // FM's state (sides, gains, locks, moves) in shared memory when it fits
+  const bool in_smem = 8ll * n + 2 <= A.dyn_words;
+  int32_t *fs = in_smem ? dyn : side;
+  if (in_smem) {
+    for (int32_t v = threadIdx.x; v < n; v += IPT) fs[v] = side[v];
+    __syncthreads();
+  }
+  {
+    uint64_t *k0 = reinterpret_cast<uint64_t *>(dyn + 4ll * n + 2 - ((4ll * n) & 1));
+    FMBuf sb{dyn + n, dyn + 2ll * n, dyn + 3ll * n, k0, k0 + n};
+    FMBuf fb{fmbuf, fmbuf + n, fmbuf + 2ll * n, reinterpret_cast<uint64_t *>(fmbuf + 3ll * n + (n & 1)),
+             reinterpret_cast<uint64_t *>(fmbuf + 3ll * n + (n & 1)) + n};
+    cta_fm(A, g, fs, c0, c1, in_smem ? sb : fb);
+  }
+  __syncthreads();
+  int64_t W0 = 0, W1 = 0;
+  for (int32_t v = threadIdx.x; v < n; v += IPT) {
+    if (fs[v] == 0) W0 += g.vw[v];
+    else W1 += g.vw[v];
+  }
+  W0 = block_sum64(W0);
+  W1 = block_sum64(W1);
+  if (W0 > c0 || W1 > c1) return 0;
+  for (int32_t v = threadIdx.x; v < n; v += IPT) A.side_out[D.vbase + v] = fs[v];
+  __syncthreads();
+  (void)lane;
+  return 1;
+}
+
 __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *wvals, int32_t *dyn) {
   __shared__ LG lv[IP_MAXL + 1];
   __shared__ int32_t *maps[IP_MAXL + 1];
@@ -1178,6 +1233,16 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
     lv[0] = g0;
   }
   __syncthreads();
+  if (A.learned_item) {
+    const int64_t mark = B.top;
+    const int r = item_learned(A, D, lv[0], B, dyn);
+    if (r < 0) {
+      if (threadIdx.x == 0) atomicExch(A.oom, 1);
+      return;
+    }
+    if (r == 1) return;
+    B.top = mark;  // infeasible: the plain method from here, in the same scratch
+  }
   // 1. coarsen
   uint64_t lpkey = key_step(D.key, DOM_IP_LP);
   int32_t nl = 1;
@@ -1233,7 +1298,7 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
   }
   // learned mode: scores of the coarsest graph's nodes (whole CTA)
   const float *score = nullptr;
-  if (A.W) {
+  if (A.W && !A.learned_item) {
     float *X = reinterpret_cast<float *>(B.take((int64_t)nH * MF));
     int32_t *d1 = B.take(nH), *d2 = B.take(nH);
     float *scr = reinterpret_cast<float *>(B.take((int64_t)nH * (MF + 3 * MH)));
@@ -1398,7 +1463,7 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
     for (int32_t v = threadIdx.x; v < nH; v += IPT) fin[v] = bsrc[v];
   }
   __syncthreads();
-  if (A.sink.counters) record_sample(A.sink, h, fin, D.key);
+  if (A.sink.counters && !A.sink.item_level) record_sample(A.sink, h, fin, D.key);
   // 3. uncoarsen with FM on every level (warp 0)
   int32_t *cur = fin;
   int32_t *fmbuf = B.take(7ll * n0 + 2);
@@ -1436,6 +1501,7 @@ __device__ void run_item(const IPArgs &A, int32_t it, int32_t *wkeys, int32_t *w
   }
   for (int32_t v = threadIdx.x; v < n0; v += IPT) A.side_out[D.vbase + v] = cur[v];
   __syncthreads();
+  if (A.sink.counters && A.sink.item_level) record_sample(A.sink, lv[0], cur, D.key);
 }
 
 __global__ void __launch_bounds__(IPT) k_ip_items(IPArgs A) {
@@ -1695,6 +1761,7 @@ int32_t bipartition_blocks(const Graph &g, int32_t *part, int32_t nblocks, std::
       A.lrep_bfs = cfg.lrep_bfs;
       A.lrep_ggg = cfg.lrep_ggg;
       A.adaptive = (cfg.adaptive && !A.W) ? 1 : 0;
+      A.learned_item = (cfg.learned == 2 && A.W) ? 1 : 0;
       A.sink = sample_sink();
       // dynamic shared memory: the LP working arrays (7.5 words a node plus
       // sort space) and then the FM state (8 words a node) of the largest item of the round,

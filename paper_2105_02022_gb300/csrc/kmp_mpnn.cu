@@ -537,6 +537,13 @@ int kmp_set_proposer(const kmp_mpnn *m) {
   return guarded_mp([&] { proposer().W = m ? m->wbf : nullptr; });
 }
 
+int kmp_sample_sink_level(int32_t item_level) {
+  return guarded_mp([&] {
+    if (item_level < 0 || item_level > 1) fail(KMP_ERR_ARG, "sink level must be 0 or 1");
+    sample_sink().item_level = item_level;
+  });
+}
+
 int kmp_sample_sink_open(int32_t max_graphs, int64_t max_nodes, int64_t max_entries) {
   return guarded_mp([&] {
     if (max_graphs < 1 || max_nodes < 1 || max_entries < 0) fail(KMP_ERR_ARG, "invalid sink capacity");

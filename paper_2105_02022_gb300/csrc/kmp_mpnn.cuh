@@ -222,6 +222,8 @@ struct SampleSink {
   int32_t *adj = nullptr, *ew = nullptr;   // per entry, graph-local ids
   int32_t max_graphs = 0;
   int64_t max_nodes = 0, max_entries = 0;
+  int32_t item_level = 0;  // 0: each item's coarsest graph and portfolio winner; 1: the item
+                           // graph and its final bipartition
 };
 SampleSink &sample_sink();
 

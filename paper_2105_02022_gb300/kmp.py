@@ -118,6 +118,7 @@ def load():
         "kmp_sample_sink_count": (ctypes.c_int, [P, P, P, P]),
         "kmp_sample_sink_read": (ctypes.c_int, [P, P, P, P, P, P, P]),
         "kmp_sample_sink_close": (ctypes.c_int, []),
+        "kmp_sample_sink_level": (ctypes.c_int, [i32]),
         "kmp_set_tuning": (ctypes.c_int, [P]),
         "kmp_get_tuning": (ctypes.c_int, [P]),
         "kmp_autotune": (ctypes.c_int, [P, i32, dbl, u64, P]),
@@ -494,9 +495,11 @@ def set_proposer(m: "Mpnn | None"):
     _check(load().kmp_set_proposer(m.h if m is not None else None))
 
 
-def sample_sink_open(max_graphs: int, max_nodes: int, max_entries: int):
+def sample_sink_open(max_graphs: int, max_nodes: int, max_entries: int, item_level: int = 0):
+    """Open the sink; item_level 1 records item graphs with their final bipartitions."""
     _stream()
     _check(load().kmp_sample_sink_open(int(max_graphs), int(max_nodes), int(max_entries)))
+    _check(load().kmp_sample_sink_level(int(item_level)))
 
 
 def sample_sink_read():

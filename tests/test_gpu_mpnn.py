@@ -139,7 +139,7 @@ def _oracle_each(g, part, nb, caps, roundkey, cfg):
 
 
 @pytest.mark.parametrize("name", ["rgg_blocks", "rmat_blocks", "grid_blocks"])
-@pytest.mark.parametrize("learned", [0, 1])
+@pytest.mark.parametrize("learned", [0, 1, 2])
 def test_bipartition_each_parity(kmp, name, learned):
     g, part, nb, caps = _blocks_case(name)
     P = _params(11)
@@ -169,8 +169,11 @@ LEARNED_PARTS = [
 ]
 
 
+@pytest.mark.parametrize("learned", [1, 2])
 @pytest.mark.parametrize("name,make,ks", LEARNED_PARTS, ids=[p[0] for p in LEARNED_PARTS])
-def test_learned_partition_parity(kmp, name, make, ks):
+def test_learned_partition_parity(kmp, name, make, ks, learned):
+    """Learned mode on the coarsest graph of every item (1) and on the item
+    graph itself (2): full partitions bit-exact with the oracle."""
     g = make()
     P = _params(17)
     m = kmp.Mpnn(4)
@@ -178,11 +181,11 @@ def test_learned_partition_parity(kmp, name, make, ks):
         m.set_params(P)
         kmp.set_proposer(m)
         O.set_proposer(P)
-        kmp.set_config(kmp.config(learned=1))
+        kmp.set_config(kmp.config(learned=learned))
         dg = kmp.DeviceGraph.from_host(g)
         for k in ks:
             part, rc, st = kmp.partition_graph(dg, k, 0.03, 5)
-            rp, rrc, rst = O.partition(g, k, 0.03, 5, O.config(learned=1))
+            rp, rrc, rst = O.partition(g, k, 0.03, 5, O.config(learned=learned))
             assert np.array_equal(part.cpu().numpy(), rp), (name, k)
             assert rc == rrc and st.cut == rst.cut
     finally:
@@ -232,6 +235,33 @@ def test_sample_sink_records_every_item(kmp):
         fw = set(zip(rows.tolist(), cols.tolist(), b.ew[b.xadj[lo]:b.xadj[hi]].tolist()))
         bw = set(zip(cols.tolist(), rows.tolist(), b.ew[b.xadj[lo]:b.xadj[hi]].tolist()))
         assert fw == bw
+
+
+def test_sample_sink_item_level_records_items_and_their_bipartitions(kmp):
+    """With the sink at item level, every item is recorded once: its own
+    graph (the block's induced subgraph, nodes in ascending id) and the final
+    bipartition that the call returned for it."""
+    g, part, nb, caps = _blocks_case("rgg_blocks")
+    dg = kmp.DeviceGraph.from_host(g)
+    kmp.sample_sink_open(nb, 10**6, 10**7, item_level=1)
+    try:
+        pt = torch.from_numpy(part.copy()).cuda()
+        kmp.bipartition_each(dg, nb, caps, 99, pt)
+        b, dropped = kmp.sample_sink_read()
+    finally:
+        kmp.sample_sink_close()
+    out = pt.cpu().numpy()
+    assert dropped == 0 and b.ng == nb
+    for i in range(b.ng):
+        bl = [x for x in range(nb) if O.step(99, x) == int(b.keys[i])][0]
+        vs = np.flatnonzero(part == bl)
+        lo, hi = b.noff[i], b.noff[i + 1]
+        assert hi - lo == len(vs)
+        sub = gg.subgraph(g, vs)
+        assert np.array_equal(b.xadj[lo:hi + 1] - b.xadj[lo], sub.xadj)
+        assert np.array_equal(b.adj[b.xadj[lo]:b.xadj[hi]] - lo, sub.adjncy)
+        assert np.array_equal(b.vw[lo:hi], sub.vw())
+        assert np.array_equal(b.side[lo:hi], out[vs] - 2 * bl)
 
 
 def test_sink_capacity_drops_and_counts(kmp):

@@ -160,3 +160,61 @@ def test_learned_mode_without_a_proposer_is_the_plain_method():
     cfg.learned = 1
     p1, _, _ = O.partition(g, 8, 0.03, 2, cfg)
     assert np.array_equal(p0, p1)
+
+
+def test_item_mode_bipartition_is_optimal_on_a_path():
+    """Learned item mode (reading B8): the distance network's start on the
+    item graph itself, FM there, no coarsening: one cut edge on a path, the
+    brute-force optimum of a balanced path bisection."""
+    g = gg.path(20)
+    cfg = O.config(learned=2)
+    O.set_proposer(_distance_net())
+    try:
+        side, cut = O.bipartition(g, 10, 10, 10, 10, O.key(3, [5]), cfg)
+    finally:
+        O.set_proposer(None)
+    assert cut == O.brute_bisection(g, 10, 10)[0] == 1
+    assert cut == O.cut(g, side)
+
+
+def test_item_mode_is_fm_of_the_learned_start_when_feasible():
+    """Where the refined learned start keeps the caps, it is the result: the
+    same as the learned start refined by FM on the item graph directly."""
+    g = gg.with_weights(gg.rgg(400, 8, 4), 3, 5, 4)
+    cB = int(g.vw().sum())
+    t0, t1, L0, L1 = O.split_caps(0.03, cB, 2, cB, 2)
+    key = O.key(9, [1])
+    P = _params(4).astype(np.float32)
+    cfg = O.config(learned=2)
+    O.set_proposer(P)
+    try:
+        side, cut = O.bipartition(g, L0, L1, t0, t1, key, cfg)
+        start = O.learned_initial(g, t0, O.step(key, 9), P)
+    finally:
+        O.set_proposer(None)
+    mx = int(g.vw().max())
+    c0, c1 = max(L0, t0 + mx), max(L1, t1 + mx)
+    ref, rcut = O.fm(g, c0, c1, start, cfg)
+    w = g.vw().astype(np.int64)
+    assert w[ref == 0].sum() <= c0 and w[ref == 1].sum() <= c1
+    assert np.array_equal(side, ref) and cut == rcut
+
+
+def test_item_mode_falls_back_to_the_plain_method_when_infeasible():
+    """Three nodes of weight 10 with targets 1: no bipartition keeps the caps
+    (11 each), so learned item mode returns the plain method's result."""
+    g = gg.from_edges(3, [(0, 1, 1), (1, 2, 1)], vwgt=[10, 10, 10])
+    O.set_proposer(_distance_net())
+    try:
+        a, ca = O.bipartition(g, 1, 1, 1, 1, O.key(2, [1]), O.config(learned=2))
+    finally:
+        O.set_proposer(None)
+    b, cb = O.bipartition(g, 1, 1, 1, 1, O.key(2, [1]), O.config())
+    assert np.array_equal(a, b) and ca == cb
+
+
+def test_item_mode_without_a_proposer_is_the_plain_method():
+    g = gg.with_weights(gg.rgg(3000, 8, 3), 4, 6, 3)
+    p0, _, _ = O.partition(g, 8, 0.03, 2, O.config())
+    p1, _, _ = O.partition(g, 8, 0.03, 2, O.config(learned=2))
+    assert np.array_equal(p0, p1)
