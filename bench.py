@@ -63,6 +63,12 @@ WORKLOADS = {
                                "R-MAT scale 20, ef 16, (0.57,0.19,0.19,0.05), unit weights, k=256"),
     "rgg_2^24_deg16_k16384": (lambda gg: gg.rgg(1 << 24, 16, SEED), 1 << 14,
                               "2D random geometric graph, n=2^24, average degree 16, unit weights, k=2^14"),
+    # smaller cases of the R-MAT family for kernel profiles (inputs larger than
+    # L2, a few GB on the device)
+    "rmat_scale24_ef16_k16384": (lambda gg: gg.rmat(24, 16, SEED), 1 << 14,
+                                 "R-MAT scale 24, ef 16, (0.57,0.19,0.19,0.05), unit weights, k=2^14"),
+    "rmat_scale22_ef16_k4096": (lambda gg: gg.rmat(22, 16, SEED), 1 << 12,
+                                "R-MAT scale 22, ef 16, (0.57,0.19,0.19,0.05), unit weights, k=2^12"),
 }
 DEFAULT_WORKLOAD = "rmat_scale26_ef16_k65536"
 ORACLE_SAMPLE_SUBROUNDS = 1
@@ -240,6 +246,14 @@ def oracle_phases():
                           "lp_edges_per_s": (st.lp_scanned + st.refine_scanned) / st.t_total}), flush=True)
 
 
+def balancer_stats(st):
+    """Work of the k-way balancer over one partition: overloaded blocks it
+    emptied, nodes it moved, moves that stood as speculated, exact batches."""
+    return {"overloaded_blocks": int(st.bal_over_blocks), "moves": int(st.bal_moves),
+            "speculated_moves": int(st.bal_spec_moves), "exact_batches": int(st.bal_exact_batches),
+            "exact_candidates": int(st.bal_exact_cands), "exact_entries": int(st.bal_exact_entries)}
+
+
 def ksweep(gg, kmp, torch, np, workload):
     """Large-k sweep (Section 5, the large-k experiment; k up to n / 16 on the
     2D RGG, up to 2^20 on R-MAT 2^26): time, cut, balance and feasibility of
@@ -267,7 +281,7 @@ def ksweep(gg, kmp, torch, np, workload):
                           "overloaded_blocks": int((bw > lk).sum()), "levels": int(st.levels),
                           "ip_items": int(st.ip_items), "phase_ms": {"lp": st.ms_lp, "contract": st.ms_contract,
                           "ip": st.ms_ip, "balance": st.ms_balance, "refine": st.ms_refine},
-                          "generate_s": gen_s}), flush=True)
+                          "balancer": balancer_stats(st), "generate_s": gen_s}), flush=True)
 
 
 def _coarse_blocks(gg, kmp, np, g, seed, k):
@@ -647,6 +661,7 @@ def main():
         "phase_ms": {"lp": stats.ms_lp, "cluster_other": stats.ms_cluster_other,
                      "contract": stats.ms_contract, "ip": stats.ms_ip, "balance": stats.ms_balance,
                      "refine": stats.ms_refine, "project": stats.ms_project, "total": stats.ms_total},
+        "balancer": balancer_stats(stats),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "roofline": {"kernel": "k_rate (LP rating)", "bound": "hbm", "achieved": pd["rate_gbs"], "peak": peak,

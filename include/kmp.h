@@ -125,6 +125,8 @@ typedef struct {
    * moves, moves decided by the parallel speculation that stood at commit,
    * and batches the exact in-order commit evaluated */
   int64_t bal_over_blocks, bal_moves, bal_spec_moves, bal_exact_batches;
+  /* candidates the exact batches evaluated, and the adjacency entries they read */
+  int64_t bal_exact_cands, bal_exact_entries;
 } kmp_stats;
 
 /* opaque handle to a CSR graph resident in device memory */

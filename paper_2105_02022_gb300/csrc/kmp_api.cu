@@ -354,6 +354,8 @@ static void deep(const Graph &g0, int32_t R, uint64_t seed, bool input, bool top
       st->bal_moves += bs.moves;
       st->bal_spec_moves += bs.spec_moves;
       st->bal_exact_batches += bs.exact_batches;
+      st->bal_exact_cands += bs.exact_cands;
+      st->bal_exact_entries += bs.exact_entries;
       st->ms_balance += tb.stop();
     }
     LPStats rs;

@@ -413,7 +413,8 @@ __global__ void __launch_bounds__(BAL_T) k_bal_spec(BalArgs A) {
 __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch) {
   __shared__ int32_t s_v[BM_W], s_t[BM_W];
   __shared__ int64_t s_c[BM_W], s_eoff[BM_W + 1], s_beg[BM_W], s_bwt[BM_W], s_capt[BM_W];
-  __shared__ uint32_t s_adj[BM_W], s_mask[BM_W];
+  __shared__ uint32_t s_adj[BM_W], s_mask[BM_W], s_toff[BM_W + 1];
+  __shared__ unsigned long long s_best[BM_W];
   __shared__ int32_t s_nb, s_next, s_stop;
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint64_t vmask = (1ull << A.bitsN) - 1ull;
@@ -496,71 +497,101 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
         }
         unsigned enough = __ballot_sync(0xFFFFFFFFu, lane < avail && c >= A.bw[B] - A.cap[B]);
         int32_t nb = enough ? __ffs(enough) : avail;
+        // member table sized by the member's own distinct blocks (at most
+        // min(degree, k)), so low-degree members never touch a hub-sized
+        // table; the tables' slots are numbered across the batch (s_toff) so
+        // that the whole CTA clears and scans them
+        uint32_t cap = 32;
+        while ((int64_t)cap < 2 * own) cap <<= 1;
+        uint32_t tpre = lane < nb ? cap : 0;
+#pragma unroll
+        for (int m = 1; m < 32; m <<= 1) {
+          const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, tpre, m);
+          if (lane >= m) tpre += o;
+        }
         if (lane < nb) {
-          // member table sized by the member's own distinct blocks (at most
-          // min(degree, k)), so low-degree members never touch a hub-sized table
-          uint32_t cap = 32;
-          while ((int64_t)cap < 2 * own) cap <<= 1;
           s_v[lane] = v;
           s_beg[lane] = rb;
           s_eoff[lane + 1] = deg;
           s_adj[lane] = 0;
           s_mask[lane] = cap - 1;
+          s_toff[lane + 1] = tpre;
+          s_best[lane] = 0;
           inbatch[v] = lane + 1;
         }
         if (lane == 0) {
           s_eoff[0] = 0;
+          s_toff[0] = 0;
           s_nb = nb;
         }
       }
       __syncthreads();
       int32_t nb = s_nb;
-      if (w < nb) {
-        int32_t *K = A.gtab + (int64_t)w * 2 * gcap;
-        for (uint32_t x = lane; x <= s_mask[w]; x += 32) {
+      // every table size is a multiple of 32, so a warp's 32 slots lie in one table
+      const uint32_t TT = s_toff[nb];
+      {
+        int32_t j = 0;
+        for (uint32_t t = threadIdx.x; t < TT; t += BM_T) {
+          while (s_toff[j + 1] <= t) ++j;
+          int32_t *K = A.gtab + (int64_t)j * 2 * gcap;
+          const uint32_t x = t - s_toff[j];
           K[x] = HT_EMPTY;
           K[gcap + x] = 0;
         }
       }
       __syncthreads();
       int64_t E = s_eoff[nb];
+      int32_t jm = 0;  // this thread's entries only move forward through the members
       for (int64_t base = 0; base < E; base += BM_T) {
         int64_t t = base + threadIdx.x;
         bool ok = t < E;
-        int32_t j = 0;
         if (ok)
-          while (s_eoff[j + 1] <= t) ++j;
+          while (s_eoff[jm + 1] <= t) ++jm;
         int32_t blk = HT_EMPTY, wt = 0;
         if (ok) {
-          int64_t q = s_beg[j] + (t - s_eoff[j]);
+          int64_t q = s_beg[jm] + (t - s_eoff[jm]);
           int32_t u = A.adj[q];
           blk = A.part[u];
           wt = A.ew ? A.ew[q] : 1;
           int32_t jj = inbatch[u];
-          if (jj > 0) atomicOr(&s_adj[j], 1u << (jj - 1));
+          if (jj > 0) atomicOr(&s_adj[jm], 1u << (jj - 1));
         }
-        uint64_t key = ok ? ((uint64_t)(uint32_t)j << 32) | (uint32_t)blk : ~0ull;
+        uint64_t key = ok ? ((uint64_t)(uint32_t)jm << 32) | (uint32_t)blk : ~0ull;
         unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
         int32_t s = __reduce_add_sync(peers, wt);
         if (ok && lane == __ffs(peers) - 1) {
-          int32_t *K = A.gtab + (int64_t)j * 2 * gcap;
-          ht_add(K, K + gcap, s_mask[j], blk, s);
+          int32_t *K = A.gtab + (int64_t)jm * 2 * gcap;
+          ht_add(K, K + gcap, s_mask[jm], blk, s);
+        }
+      }
+      __syncthreads();
+      {
+        // best admissible block of every member: (conn, ~block), largest
+        // connectivity, then lowest id; a warp's slots belong to one member
+        int32_t jj = 0;
+        for (uint32_t base = 0; base < TT; base += BM_T) {
+          const uint32_t t = base + threadIdx.x;
+          if (base + (threadIdx.x & ~31u) >= TT) break;  // warp-uniform
+          const bool ok = t < TT;
+          if (ok)
+            while (s_toff[jj + 1] <= t) ++jj;
+          uint64_t key = 0;
+          if (ok) {
+            const int32_t *K = A.gtab + (int64_t)jj * 2 * gcap;
+            const uint32_t x = t - s_toff[jj];
+            const int32_t b = K[x];
+            if (b != HT_EMPTY && b != B && A.bw[b] + bw_node(A, s_v[jj]) <= A.cap[b])
+              key = ((uint64_t)(uint32_t)K[gcap + x] << 32) | (0xFFFFFFFFu - (uint32_t)b);
+          }
+          key = group_max64<32>(key);
+          if (lane == 0 && key) atomicMax(&s_best[jj], key);
         }
       }
       __syncthreads();
       if (w < nb) {
         int32_t v = s_v[w];
         int64_t c = bw_node(A, v);
-        const int32_t *K = A.gtab + (int64_t)w * 2 * gcap, *V = K + gcap;
-        uint64_t bestk = 0;  // (conn, ~block): largest connectivity, then lowest id
-        for (uint32_t x = lane; x <= s_mask[w]; x += 32) {
-          int32_t b = K[x];
-          if (b == HT_EMPTY || b == B) continue;
-          if (A.bw[b] + c > A.cap[b]) continue;
-          uint64_t key = ((uint64_t)(uint32_t)V[x] << 32) | (0xFFFFFFFFu - (uint32_t)b);
-          bestk = key > bestk ? key : bestk;
-        }
-        bestk = group_max64<32>(bestk);
+        const uint64_t bestk = s_best[w];
         int32_t t = bestk ? (int32_t)(0xFFFFFFFFu - (uint32_t)bestk) : -1;
         if (t < 0) {
           int32_t low = INT32_MAX;
@@ -612,6 +643,8 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
         A.bw[B] = wB;
         if (moves) atomicAdd(A.moved, (unsigned long long)moves);
         atomicAdd(A.moved + 2, 1ull);  // an exact batch
+        atomicAdd(A.moved + 3, (unsigned long long)nb);
+        atomicAdd(A.moved + 4, (unsigned long long)E);
         s_next = j;
       }
       __syncthreads();
@@ -648,7 +681,8 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   DBuf<uint8_t> over(k);
   DBuf<int64_t> cand_d(n);
   DBuf<uint64_t> keys(n), tmp(n), sortbuf(2ll * n);
-  DBuf<unsigned long long> moved(3);  // moves, speculated moves that stood, exact batches
+  // moves, speculated moves that stood, exact batches, their candidates and adjacency entries
+  DBuf<unsigned long long> moved(5);
   to_dev(cap.p, caps_host, k);
   to_dev(over.p, hover.data(), k);
   DBuf<int32_t> olist(holist.size());
@@ -739,13 +773,15 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   A.gtab = gtab1;
   k_bal_moves<<<1, BM_T, 0, s>>>(A, inbatch);
   KMP_LAUNCHED("bal_moves");
-  unsigned long long hm[3];
-  to_host(hm, moved.p, 3);
+  unsigned long long hm[5];
+  to_host(hm, moved.p, 5);
   if (bs) {
     bs->over_blocks += nover;
     bs->moves += (int64_t)hm[0];
     bs->spec_moves += (int64_t)hm[1];
     bs->exact_batches += (int64_t)hm[2];
+    bs->exact_cands += (int64_t)hm[3];
+    bs->exact_entries += (int64_t)hm[4];
   }
   return (int64_t)hm[0];
 }

@@ -465,10 +465,11 @@ __global__ void k_large_tiles(const int32_t *large_list, const int32_t *nlarge, 
   }
 }
 
-// distinct entries of all large rows into one (row << bits | neighbour, weight) list
+// distinct entries of every large row into its own temporary row (positions
+// within the row from its entry counter; the row is sorted afterwards)
 __global__ void __launch_bounds__(256) k_large_compact(int64_t LT, const int32_t *tile_row,
-                                                       const int32_t *lk, const int32_t *lv, int bits,
-                                                       uint64_t *ek, int32_t *ev, int32_t *cnt,
+                                                       const int32_t *lk, const int32_t *lv,
+                                                       const int64_t *toff, int32_t *tadj, int32_t *tw,
                                                        int32_t *cdeg) {
   int lane = threadIdx.x & 31;
   int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -481,37 +482,108 @@ __global__ void __launch_bounds__(256) k_large_compact(int64_t LT, const int32_t
     unsigned bal = __ballot_sync(0xFFFFFFFFu, has);
     if (bal == 0) continue;
     int32_t p0 = 0;
-    if (lane == 0) {
-      p0 = atomicAdd(cnt, __popc(bal));
-      atomicAdd(&cdeg[x], __popc(bal));
-    }
+    if (lane == 0) p0 = atomicAdd(&cdeg[x], __popc(bal));
     p0 = __shfl_sync(0xFFFFFFFFu, p0, 0);
     if (has) {
-      int32_t p = p0 + __popc(bal & ((1u << lane) - 1u));
-      ek[p] = ((uint64_t)(uint32_t)x << bits) | (uint64_t)(uint32_t)y;
-      ev[p] = lv[e + lane];
+      const int64_t p = toff[x] + p0 + __popc(bal & ((1u << lane) - 1u));
+      tadj[p] = y;
+      tw[p] = lv[e + lane];
     }
   }
 }
 
-__global__ void k_large_seg(int32_t N, const uint64_t *ek, int bits, int32_t *seglo) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+// large rows by their distinct entries: up to SORT_S (one CTA of 256 threads
+// sorts in shared memory), up to SORT_L (1024 threads), more (radix sort)
+constexpr int32_t SORT_S = 2048;
+constexpr int32_t SORT_L = 16384;
+__global__ void k_large_split(const int32_t *rows, const int32_t *nrows, const int32_t *cdeg, int32_t cap,
+                              int32_t *lists, int32_t *counts) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < *nrows;
        i += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t x = ek[i] >> bits;
-    if (i == 0 || (ek[i - 1] >> bits) != x) seglo[x] = (int32_t)i;
+    const int32_t x = rows[i], d = cdeg[x];
+    const int c = d <= SORT_S ? 0 : d <= SORT_L ? 1 : 2;
+    lists[(int64_t)c * cap + atomicAdd(&counts[c], 1)] = x;
   }
 }
 
-__global__ void k_large_place(int32_t N, const uint64_t *ek, const int32_t *ev, int bits,
-                              const int32_t *seglo, const int64_t *toff, int32_t *tadj, int32_t *tw) {
-  uint64_t mask = (1ull << bits) - 1ull;
+// one CTA per row: (neighbour << 32 | weight) sorted in shared memory; the
+// neighbours of a row are distinct, so the order is by neighbour
+template <int P, int NT>
+__global__ void __launch_bounds__(NT) k_large_sort_smem(const int32_t *rows, int32_t nrows, const int64_t *toff,
+                                                        const int32_t *cdeg, int32_t *tadj, int32_t *tw) {
+  extern __shared__ uint64_t srt[];  // P entries
+  const uint32_t tid = threadIdx.x;
+  for (int64_t i = blockIdx.x; i < nrows; i += gridDim.x) {
+    const int32_t x = rows[i];
+    const int64_t o = toff[x];
+    const int32_t d = cdeg[x];
+    uint32_t Q = 32;
+    while ((int32_t)Q < d) Q <<= 1;
+    for (uint32_t j = tid; j < Q; j += NT)
+      srt[j] = (int32_t)j < d ? ((uint64_t)(uint32_t)tadj[o + j] << 32) | (uint32_t)tw[o + j] : ~0ull;
+    __syncthreads();
+    bitonic<true>(srt, Q, tid, NT);
+    for (uint32_t j = tid; (int32_t)j < d; j += NT) {
+      tadj[o + j] = (int32_t)(srt[j] >> 32);
+      tw[o + j] = (int32_t)(uint32_t)srt[j];
+    }
+    __syncthreads();  // the next row reuses the array
+  }
+}
+
+template <int P, int NT>
+void launch_large_sort_smem(const int32_t *rows, int32_t nrows, const int64_t *toff, const int32_t *cdeg,
+                            int32_t *tadj, int32_t *tw) {
+  constexpr size_t bytes = (size_t)P * sizeof(uint64_t);
+  static bool attr = false;
+  if (!attr) {
+    KMP_CUDA(cudaFuncSetAttribute(k_large_sort_smem<P, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)bytes));
+    attr = true;
+  }
+  int per_sm = (int)((227u << 10) / (bytes + 1024));
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 2048 / NT) per_sm = 2048 / NT;
+  int blocks = std::min<int64_t>(nrows, (int64_t)ctx().sms * per_sm);
+  k_large_sort_smem<P, NT><<<blocks, NT, bytes, ctx().stream>>>(rows, nrows, toff, cdeg, tadj, tw);
+  KMP_LAUNCHED("large_sort_smem");
+}
+
+// rows too long for shared memory: their entries as (rank << bits | neighbour,
+// weight), a warp per row, at the row's offset among them
+__global__ void k_large_gather(const int32_t *rows, int32_t nrows, const int64_t *boff, const int64_t *toff,
+                               const int32_t *tadj, const int32_t *tw, const int32_t *cdeg, int bits,
+                               uint64_t *ek, int32_t *ev) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = gw; r < nrows; r += nw) {
+    const int32_t x = rows[r], d = cdeg[x];
+    const int64_t o = toff[x], b = boff[r];
+    for (int32_t j = lane; j < d; j += 32) {
+      ek[b + j] = ((uint64_t)r << bits) | (uint64_t)(uint32_t)tadj[o + j];
+      ev[b + j] = tw[o + j];
+    }
+  }
+}
+
+// sorted entries back into their rows (rank r's entries fill [boff[r], boff[r + 1]))
+__global__ void k_large_place(int64_t N, const uint64_t *ek, const int32_t *ev, int bits, const int32_t *rows,
+                              const int64_t *boff, const int64_t *toff, int32_t *tadj, int32_t *tw) {
+  const uint64_t mask = (1ull << bits) - 1ull;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
-    int32_t x = (int32_t)(ek[i] >> bits);
-    int64_t p = toff[x] + (i - seglo[x]);
+    const int64_t r = (int64_t)(ek[i] >> bits);
+    const int64_t p = toff[rows[r]] + (i - boff[r]);
     tadj[p] = (int32_t)(ek[i] & mask);
     tw[p] = ev[i];
   }
+}
+
+__global__ void k_gather_deg(const int32_t *rows, int32_t nrows, const int32_t *cdeg, int64_t *out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nrows;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = cdeg[rows[i]];
 }
 
 // rows from their upper-bound offsets into the final CSR; four loads per lane
@@ -653,8 +725,10 @@ Graph contract_graph(const Graph &g, const int32_t *label, int32_t *map) {
   if (hc[3] > 0) launch_aggregate_warp<1024, 4>(L(3), hc[3], cub, g, map, members, moff, toff, tadj, tw, cdeg);
   if (hc[CLS_GLOBAL] > 0) {
     // large rows: every member inserts in parallel into its coarse node's global
-    // table; the distinct entries of all large rows are then ordered by one
-    // key-value radix sort of (row, neighbour) and placed into their rows
+    // table; each row's distinct entries are compacted into its temporary row
+    // and sorted there by neighbour: in shared memory by one CTA per row when
+    // they fit, else by one key-value radix sort of (row rank, neighbour) over
+    // all such rows
     int bits = 1;
     while ((1ll << bits) < (int64_t)nc) ++bits;
     DBuf<int64_t> tsz(nc), ltoff(nc), ltot(1);
@@ -662,10 +736,9 @@ Graph contract_graph(const Graph &g, const int32_t *label, int32_t *map) {
     KMP_LAUNCHED("large_sizes");
     scan_excl_i64(tsz, ltoff, nc, ltot);
     int64_t LT = read1(ltot.p);
-    DBuf<int32_t> lk(LT), lv(LT), lcnt(1);
+    DBuf<int32_t> lk(LT), lv(LT);
     lk.fill_bytes(0xFF);
     lv.zero();
-    lcnt.zero();
     DBuf<int64_t> nch(n), choff(n), chtot(1);
     k_large_chunks<<<grid, 256, 0, s>>>(n, g.xadj, map, cub, nch);
     KMP_LAUNCHED("large_chunks");
@@ -677,21 +750,41 @@ Graph contract_graph(const Graph &g, const int32_t *label, int32_t *map) {
     k_large_insert<<<grid_for(CT * 32, 256, 8), 256, 0, s>>>(CT, owner, choff, g.xadj, g.adj, g.ew, map,
                                                              ltoff, tsz, lk, lv);
     KMP_LAUNCHED("large_insert");
-    int64_t cap_entries = LT / 2 + 1;
-    DBuf<uint64_t> ek(cap_entries), ektmp(cap_entries);
-    DBuf<int32_t> ev(cap_entries), evtmp(cap_entries), seglo(nc);
     DBuf<int32_t> tile_row(LT / 32 + 1);
     k_large_tiles<<<grid_for((int64_t)hc[CLS_GLOBAL] * 32, 256), 256, 0, s>>>(large_list, counts.p + CLS_GLOBAL, ltoff, tsz,
                                                                      tile_row);
     KMP_LAUNCHED("large_tiles");
-    k_large_compact<<<grid_for(LT, 256, 8), 256, 0, s>>>(LT, tile_row, lk, lv, bits, ek, ev, lcnt, cdeg);
+    k_large_compact<<<grid_for(LT, 256, 8), 256, 0, s>>>(LT, tile_row, lk, lv, toff, tadj, tw, cdeg);
     KMP_LAUNCHED("large_compact");
-    int32_t NE = read1(lcnt.p);
-    radix_sort_kv(ek, ev, ektmp, evtmp, NE, 2 * bits);
-    k_large_seg<<<grid_for(NE, 256), 256, 0, s>>>(NE, ek, bits, seglo);
-    KMP_LAUNCHED("large_seg");
-    k_large_place<<<grid_for(NE, 256), 256, 0, s>>>(NE, ek, ev, bits, seglo, toff, tadj, tw);
-    KMP_LAUNCHED("large_place");
+    const int32_t nlarge = hc[CLS_GLOBAL];
+    DBuf<int32_t> slists(3ll * nlarge), scounts(3);
+    scounts.zero();
+    k_large_split<<<grid_for(nlarge, 256), 256, 0, s>>>(large_list, counts.p + CLS_GLOBAL, cdeg, nlarge, slists,
+                                                       scounts);
+    KMP_LAUNCHED("large_split");
+    int32_t sc[3];
+    to_host(sc, scounts.p, 3);
+    if (sc[0] > 0) launch_large_sort_smem<SORT_S, 256>(slists.p, sc[0], toff, cdeg, tadj, tw);
+    if (sc[1] > 0) launch_large_sort_smem<SORT_L, 1024>(slists.p + nlarge, sc[1], toff, cdeg, tadj, tw);
+    if (sc[2] > 0) {
+      const int32_t nbig = sc[2];
+      const int32_t *brows = slists.p + 2ll * nlarge;
+      DBuf<int64_t> bdeg(nbig), boff(nbig), btot(1);
+      k_gather_deg<<<grid_for(nbig, 256), 256, 0, s>>>(brows, nbig, cdeg, bdeg);
+      KMP_LAUNCHED("gather_deg");
+      scan_excl_i64(bdeg, boff, nbig, btot);
+      const int64_t NE = read1(btot.p);
+      int rbits = 1;
+      while ((1ll << rbits) < (int64_t)nbig) ++rbits;
+      DBuf<uint64_t> ek(NE), ektmp(NE);
+      DBuf<int32_t> ev(NE), evtmp(NE);
+      k_large_gather<<<grid_for((int64_t)nbig * 32, 256), 256, 0, s>>>(brows, nbig, boff, toff, tadj, tw, cdeg,
+                                                                      bits, ek, ev);
+      KMP_LAUNCHED("large_gather");
+      radix_sort_kv(ek, ev, ektmp, evtmp, NE, rbits + bits);
+      k_large_place<<<grid_for(NE, 256), 256, 0, s>>>(NE, ek, ev, bits, brows, boff, toff, tadj, tw);
+      KMP_LAUNCHED("large_place");
+    }
   }
   DBuf<int64_t> mtot(1);
   out.xadj = static_cast<int64_t *>(dmalloc((nc + 1) * sizeof(int64_t)));

@@ -280,7 +280,7 @@ void block_weights(const Graph &g, const int32_t *part, int32_t k, int64_t *bw_d
 int64_t refine(const Graph &g, int32_t k, const int32_t *caps_host, int32_t rounds,
                uint64_t seed, int32_t *part, LPStats *st, bool want_cut = true);
 struct BalStats {
-  int64_t over_blocks = 0, moves = 0, spec_moves = 0, exact_batches = 0;
+  int64_t over_blocks = 0, moves = 0, spec_moves = 0, exact_batches = 0, exact_cands = 0, exact_entries = 0;
 };
 // k-way balancing; bs (nullable) accumulates where the work went
 int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *part, BalStats *bs = nullptr);

@@ -615,19 +615,45 @@ __global__ void __launch_bounds__(1024) k_hub_plan(LPArgs A, int s) {
   }
 }
 
-// lanes of a warp that hit the same bucket add their counts first
-__device__ __forceinline__ int32_t warp_bucket_claim(int32_t *ctr, bool ok, int64_t g, int lane) {
-  uint64_t key = ok ? (uint64_t)g : (0xFFFFFFFF00000000ull | (uint32_t)lane);
-  unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
-  int leader = __ffs(peers) - 1;
-  int32_t base = 0;
-  if (ok && lane == leader) base = atomicAdd(&ctr[g], __popc(peers));
-  base = __shfl_sync(0xFFFFFFFFu, base, leader);
-  return base + __popc(peers & ((1u << lane) - 1u));
+// A CTA takes its work units in pieces of HP entries (HP_PER per thread) and
+// counts each piece's entries per bucket in a shared table first, so one
+// global atomic serves all of a piece's entries of one bucket.
+constexpr int HP_PER = 8;
+constexpr int HP_T = 256;
+constexpr int HP = HP_T * HP_PER;
+constexpr int HP_TAB = 2 * HP;  // bucket slots (at most HP keys: load <= 1/2)
+struct HubPieceTable {
+  int32_t key[HP_TAB];  // bucket (relative to the hub's first) or HT_EMPTY
+  int32_t val[HP_TAB];  // entries of the piece in it; then their first position
+  uint16_t list[HP];    // occupied slots
+  int32_t n;
+};
+
+__device__ void hp_clear_all(HubPieceTable &T) {
+  for (int x = threadIdx.x; x < HP_TAB; x += blockDim.x) {
+    T.key[x] = HT_EMPTY;
+    T.val[x] = 0;
+  }
+  if (threadIdx.x == 0) T.n = 0;
 }
 
-// work units: edge chunks of the sub-round's hubs; every entry's neighbour
-// label is gathered once (kept in entry order) and counted in its bucket
+// slot of bucket b (inserted if new) and the entry's rank among the piece's
+// entries of b
+__device__ __forceinline__ int32_t hp_insert(HubPieceTable &T, int32_t b, int32_t &rank) {
+  uint32_t h = (uint32_t)b & (HP_TAB - 1);
+  for (int probe = 0; probe < HP_TAB; ++probe) {
+    const int32_t old = atomicCAS(&T.key[h], HT_EMPTY, b);
+    if (old == HT_EMPTY || old == b) {
+      rank = atomicAdd(&T.val[h], 1);
+      if (old == HT_EMPTY) T.list[atomicAdd(&T.n, 1)] = (uint16_t)h;
+      return (int32_t)h;
+    }
+    h = (h + 1) & (HP_TAB - 1);
+  }
+  rank = 0;
+  return -1;  // unreachable: a piece has at most HP_TAB / 2 buckets
+}
+
 // The hub of every work unit: each CTA (warp) takes a contiguous range of
 // units, finds the first one's hub by binary search and then only moves
 // forward (the units of one hub are consecutive).
@@ -656,11 +682,15 @@ struct HubCursor {
   }
 };
 
-__global__ void __launch_bounds__(256) k_hub_count(LPArgs A, int s) {
+// work units: edge chunks of the sub-round's hubs; every entry's neighbour
+// label is gathered once (kept in entry order) and counted in its bucket
+__global__ void __launch_bounds__(HP_T) k_hub_count(LPArgs A, int s) {
+  __shared__ HubPieceTable T;
+  hp_clear_all(T);
+  __syncthreads();
   const int32_t *bo = A.boff + s * NB;
   int32_t cnt = bo[7] - bo[6];
   int64_t total = A.plan_tot[0];
-  const int lane = threadIdx.x & 31;
   const int64_t per = ceil_div(total, (int64_t)gridDim.x);
   const int64_t c0 = (int64_t)blockIdx.x * per, c1 = c0 + per < total ? c0 + per : total;
   HubCursor H;
@@ -668,23 +698,46 @@ __global__ void __launch_bounds__(256) k_hub_count(LPArgs A, int s) {
     H.seek(A, A.plan_e, cnt, total, c);
     const int64_t b = H.b, deg = H.deg, nb = H.nb, gb = H.gb, xo = H.xo;
     int64_t e0 = b + (c - H.e_first) * A.hub_chunk, e1 = e0 + A.hub_chunk < b + deg ? e0 + A.hub_chunk : b + deg;
-    for (int64_t base = e0 + (threadIdx.x & ~31); base < e1; base += blockDim.x) {
-      int64_t e = base + lane;
-      bool ok = e < e1;
-      int32_t L = ok ? A.label[A.adj[e]] : 0;
-      if (ok) A.hlab[xo + e] = L;
-      warp_bucket_claim(A.hbcnt, ok, gb + hub_bucket_of(L, nb), lane);
+    for (int64_t p0 = e0; p0 < e1; p0 += HP) {
+      int32_t nbr[HP_PER], L[HP_PER];
+#pragma unroll
+      for (int r = 0; r < HP_PER; ++r) {
+        const int64_t e = p0 + r * HP_T + threadIdx.x;
+        nbr[r] = e < e1 ? A.adj[e] : -1;
+      }
+#pragma unroll
+      for (int r = 0; r < HP_PER; ++r) L[r] = nbr[r] >= 0 ? A.label[nbr[r]] : -1;
+#pragma unroll
+      for (int r = 0; r < HP_PER; ++r)
+        if (nbr[r] >= 0) {
+          A.hlab[xo + p0 + r * HP_T + threadIdx.x] = L[r];
+          int32_t rk;
+          hp_insert(T, (int32_t)hub_bucket_of(L[r], nb), rk);
+        }
+      __syncthreads();
+      const int32_t nt = T.n;
+      for (int32_t x = threadIdx.x; x < nt; x += HP_T) {
+        const int32_t h = T.list[x];
+        atomicAdd(&A.hbcnt[gb + T.key[h]], T.val[h]);
+        T.key[h] = HT_EMPTY;
+        T.val[h] = 0;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) T.n = 0;
+      __syncthreads();
     }
   }
 }
 
 // the same work units: entries into bucket order (positions inside a bucket
 // are arbitrary; the aggregation below does not depend on them)
-__global__ void __launch_bounds__(256) k_hub_scatter(LPArgs A, int s) {
+__global__ void __launch_bounds__(HP_T) k_hub_scatter(LPArgs A, int s) {
+  __shared__ HubPieceTable T;
+  hp_clear_all(T);
+  __syncthreads();
   const int32_t *bo = A.boff + s * NB;
   int32_t cnt = bo[7] - bo[6];
   int64_t total = A.plan_tot[0];
-  const int lane = threadIdx.x & 31;
   const int64_t per = ceil_div(total, (int64_t)gridDim.x);
   const int64_t c0 = (int64_t)blockIdx.x * per, c1 = c0 + per < total ? c0 + per : total;
   HubCursor H;
@@ -692,17 +745,40 @@ __global__ void __launch_bounds__(256) k_hub_scatter(LPArgs A, int s) {
     H.seek(A, A.plan_e, cnt, total, c);
     const int64_t b = H.b, deg = H.deg, nb = H.nb, gb = H.gb, xo = H.xo;
     int64_t e0 = b + (c - H.e_first) * A.hub_chunk, e1 = e0 + A.hub_chunk < b + deg ? e0 + A.hub_chunk : b + deg;
-    for (int64_t base = e0 + (threadIdx.x & ~31); base < e1; base += blockDim.x) {
-      int64_t e = base + lane;
-      bool ok = e < e1;
-      int32_t L = ok ? A.hlab[xo + e] : 0;
-      int64_t g = gb + hub_bucket_of(L, nb);
-      int32_t r = warp_bucket_claim(A.hbcur, ok, g, lane);
-      if (ok) {
-        int64_t pos = (int64_t)A.hboff[g] + r;
-        A.hslab[pos] = L;
-        if (A.ew) A.hsw[pos] = A.ew[e];
+    for (int64_t p0 = e0; p0 < e1; p0 += HP) {
+      int32_t L[HP_PER], sl[HP_PER], rk[HP_PER];
+#pragma unroll
+      for (int r = 0; r < HP_PER; ++r) {
+        const int64_t e = p0 + r * HP_T + threadIdx.x;
+        L[r] = e < e1 ? A.hlab[xo + e] : -1;
       }
+#pragma unroll
+      for (int r = 0; r < HP_PER; ++r)
+        sl[r] = L[r] >= 0 ? hp_insert(T, (int32_t)hub_bucket_of(L[r], nb), rk[r]) : -1;
+      __syncthreads();
+      // one claim per bucket; the slot's count becomes its first position
+      const int32_t nt = T.n;
+      for (int32_t x = threadIdx.x; x < nt; x += HP_T) {
+        const int32_t h = T.list[x];
+        const int64_t g = gb + T.key[h];
+        T.val[h] = A.hboff[g] + atomicAdd(&A.hbcur[g], T.val[h]);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < HP_PER; ++r)
+        if (sl[r] >= 0) {
+          const int64_t pos = (int64_t)T.val[sl[r]] + rk[r];
+          A.hslab[pos] = L[r];
+          if (A.ew) A.hsw[pos] = A.ew[p0 + r * HP_T + threadIdx.x];
+        }
+      __syncthreads();
+      for (int32_t x = threadIdx.x; x < nt; x += HP_T) {
+        const int32_t h = T.list[x];
+        T.key[h] = HT_EMPTY;
+        T.val[h] = 0;
+      }
+      if (threadIdx.x == 0) T.n = 0;
+      __syncthreads();
     }
   }
 }
@@ -725,14 +801,17 @@ __device__ __forceinline__ bool ht_find_add(int32_t *keys, int32_t *vals, uint32
 constexpr int64_t DENSE_ROWS_MAX_BYTES = 4ll << 30;  // dense hub rows of one LP run
 constexpr int DENSE_LABELS_MAX = 57344;              // a CTA's shared counters (224 KB)
 
-constexpr int HB_TAB = 1024;             // per-warp table of the bucket kernel
+constexpr int HB_TAB = 1024;               // per-warp table of the bucket kernel
 constexpr int HB_LIMIT = HB_TAB / 2 - 32;  // labels admitted per round (load <= 1/2)
 
 // One warp per bucket: its entries are aggregated by label in the warp's
-// shared table.  A round admits new labels while fewer than HB_LIMIT are
-// held and keeps adding to labels already held after that; entries whose
-// label came too late wait for the next round (a label's entries therefore
-// all land in the round that admitted it).  Every round ends with the
+// shared table, every lane adding its own entry (shared-memory atomics; a
+// warp-level pre-aggregation was slower).  A round admits new labels while
+// fewer than HB_LIMIT are held and keeps adding to labels already held after
+// that; entries whose label came too late wait for the next round (a label's
+// entries therefore all land in the round that admitted it).  The next round
+// starts at the first chunk that came after the table filled, so only the
+// entries consumed after that point are marked.  Every round ends with the
 // selection pass over the occupied slots; the bucket's best keys go to its
 // hub by atomicMax, the own cluster's rating (in exactly one bucket) is
 // stored.  Counts and cursors are cleared for the next sub-round.
@@ -772,33 +851,31 @@ __global__ void __launch_bounds__(HB_W * 32) k_hub_bucket(LPArgs A, int s) {
     }
     const int64_t beg = A.hboff[g];
     uint64_t kc = 0, ku = 0;
-    bool left = true;
-    while (left) {
-      int32_t held = 0;
-      bool full = false, mine_left = false;
-      for (int32_t e0 = 0; e0 < ne; e0 += 32) {
+    int32_t start = 0;  // first entry of this round; every entry before it is consumed
+    while (start < ne) {
+      int32_t held = 0, next = ne;
+      bool mine_left = false;
+      for (int32_t e0 = start; e0 < ne; e0 += 32) {
         const int32_t e = e0 + lane;
         int32_t L = e < ne ? A.hslab[beg + e] : -1;
         const bool live = L >= 0;
         const int32_t wt = live ? (A.ew ? A.hsw[beg + e] : 1) : 0;
-        const unsigned peers = __match_any_sync(0xFFFFFFFFu, live ? L : -1 - lane);
-        const int32_t sum = __reduce_add_sync(peers, wt);
-        const int leader = __ffs(peers) - 1;
-        if (!full) {
-          int32_t sl = (live && lane == leader) ? ht_add_fresh(keys, vals, mask, L, sum) : -1;
+        if (next == ne) {
+          // admitting: every entry of the chunk lands in this round
+          int32_t sl = live ? ht_add_fresh(keys, vals, mask, L, wt) : -1;
           unsigned m = __ballot_sync(0xFFFFFFFFu, sl >= 0);
           if (sl >= 0) list[held + __popc(m & ((1u << lane) - 1u))] = (uint16_t)sl;
           held += __popc(m);
-          if (live) A.hslab[beg + e] = ~L;
-          full = held > HB_LIMIT;
+          if (held > HB_LIMIT) next = e0 + 32;
         } else {
-          bool found = (live && lane == leader) ? ht_find_add(keys, vals, mask, L, sum) : false;
-          found = __shfl_sync(0xFFFFFFFFu, found, leader);
+          // full: only labels already held; those entries are marked, as the
+          // next round starts at `next`
+          const bool found = live && ht_find_add(keys, vals, mask, L, wt);
           if (live && found) A.hslab[beg + e] = ~L;
           if (live && !found) mine_left = true;
         }
       }
-      left = __any_sync(0xFFFFFFFFu, mine_left);
+      start = __any_sync(0xFFFFFFFFu, mine_left) ? next : ne;
       __syncwarp();
       for (int32_t x = lane; x < held; x += 32) {
         const int32_t sl = list[x];
@@ -1397,10 +1474,10 @@ void lp_run(const Graph &g, int32_t *label, int32_t *wt, int32_t nlab, const int
       if (hub_path) {
         k_hub_plan<<<1, 1024, 0, st>>>(A, s);
         KMP_LAUNCHED("hub_plan");
-        k_hub_count<<<grid_hub, 256, 0, st>>>(A, s);
+        k_hub_count<<<grid_hub, HP_T, 0, st>>>(A, s);
         KMP_LAUNCHED("hub_count");
         scan_excl_i32_on(hbcnt, hboff, nbmax, nullptr, hbsum, st);
-        k_hub_scatter<<<grid_hub, 256, 0, st>>>(A, s);
+        k_hub_scatter<<<grid_hub, HP_T, 0, st>>>(A, s);
         KMP_LAUNCHED("hub_scatter");
         k_hub_bucket<<<grid_bucket, HB_W * 32, HB_SMEM, st>>>(A, s);
         KMP_LAUNCHED("hub_bucket");

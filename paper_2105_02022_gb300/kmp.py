@@ -51,7 +51,8 @@ class Stats(ctypes.Structure):
                 ("clustered", ctypes.c_int32), ("level_kp", ctypes.c_int32 * 64),
                 ("level_U", ctypes.c_int64 * 64), ("level_k", ctypes.c_int32 * 64),
                 ("bal_over_blocks", ctypes.c_int64), ("bal_moves", ctypes.c_int64),
-                ("bal_spec_moves", ctypes.c_int64), ("bal_exact_batches", ctypes.c_int64)]
+                ("bal_spec_moves", ctypes.c_int64), ("bal_exact_batches", ctypes.c_int64),
+                ("bal_exact_cands", ctypes.c_int64), ("bal_exact_entries", ctypes.c_int64)]
 
     def as_dict(self):
         d = {}

@@ -123,6 +123,45 @@ def test_contract_row_classes(kmp, n, m):
     _contract_check(kmp, g, lab)
 
 
+def _large_rows_by_distinct(g, lab, rg, rmp):
+    """Distinct-entry counts of the coarse rows whose members' total degree is
+    above the block path's bound (8192): the rows of the global path"""
+    ub = np.bincount(rmp, weights=np.diff(g.xadj), minlength=rg.n)
+    return np.diff(rg.xadj)[ub > 8192]
+
+
+@pytest.mark.parametrize("family", ["rgg_blocks", "random_clusters"])
+def test_contract_large_rows_every_sort_class(kmp, family):
+    """Rows of the global path whose distinct entries fall in each of its
+    three sort classes: at most 2048 (sorted by one CTA of 256 threads in
+    shared memory), at most 16384 (1024 threads) and more (key-value radix
+    sort over all such rows).  Spatially consecutive RGG nodes give rows with
+    a large total degree but few distinct neighbours (only the cluster's
+    boundary); clusters of random nodes give about as many as their degree."""
+    if family == "rgg_blocks":
+        g = gg.with_weights(gg.rgg(300000, 16, 6), 3, 7, 2)
+        lab = ((np.arange(g.n) // 1500) * 1500).astype(np.int32)
+    else:
+        g = gg.with_weights(gg.random_graph(240000, 1500000, 12), 5, 9, 4)
+        deg = np.diff(g.xadj)
+        order = np.random.default_rng(5).permutation(g.n)
+        lab = np.arange(g.n, dtype=np.int32)  # singletons by default
+        pos = 0
+        for t in [9000, 12000, 20000, 40000, 90000] * 2:
+            s, start = 0, pos
+            while pos < g.n and s + deg[order[pos]] <= t:
+                s += deg[order[pos]]
+                pos += 1
+            lab[order[start:pos]] = order[start]
+    rg, rmp = O.contract(g, lab)
+    d = _large_rows_by_distinct(g, lab, rg, rmp)
+    if family == "rgg_blocks":
+        assert (d <= 2048).any()
+    else:
+        assert ((d > 2048) & (d <= 16384)).any() and (d > 16384).any()
+    _contract_check(kmp, g, lab)
+
+
 @pytest.mark.parametrize("group", [40, 100, 700])
 def test_contract_many_members(kmp, group):
     """Clusters of `group` consecutive nodes of a sparse graph with many

@@ -110,6 +110,29 @@ def test_balance_parity(kmp, case):
     assert np.array_equal(pt.cpu().numpy(), rp)
 
 
+@pytest.mark.parametrize("name,k", [("rmat15", 512), ("rgg", 2000), ("rmat15_w", 300)])
+def test_balance_random_partitions_many_overloaded_blocks(kmp, name, k):
+    """A random k-way partition overloads about half of the blocks, nearly all
+    of them neighbours (R-MAT) or spatially close (RGG), so most speculated
+    moves are fragile and go through the exact commit; bit-exact with the
+    oracle."""
+    if name == "rmat15":
+        g = gg.rmat(15, 16, 3)
+    elif name == "rgg":
+        g = gg.rgg(40000, 8, 5)
+    else:
+        g = gg.with_weights(gg.rmat(15, 16, 4), 4, 9, 4)
+    rng = np.random.default_rng(k)
+    part = rng.integers(0, k, g.n).astype(np.int32)
+    cap = np.full(k, int(1.03 * g.vw().sum() / k) + int(g.vw().max()), np.int64)
+    dg = kmp.DeviceGraph.from_host(g)
+    pt = torch.from_numpy(part).cuda()
+    mv = kmp.balance(dg, k, cap, pt)
+    rp, rmv = O.balance(g, k, cap.astype(np.int32), part)
+    assert mv == rmv and mv > 0
+    assert np.array_equal(pt.cpu().numpy(), rp)
+
+
 def test_balance_many_adjacent_overloaded_blocks(kmp):
     """480 blocks of 15 and 10 nodes alternating over an RGG whose ids are
     spatially local, cap 12: half the blocks are overloaded and most border
