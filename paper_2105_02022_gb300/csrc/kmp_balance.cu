@@ -410,137 +410,346 @@ __global__ void __launch_bounds__(BAL_T) k_bal_spec(BalArgs A) {
   }
 }
 
+// A batch with at most WS_E adjacency entries and WS_T table slots is
+// evaluated by warp 0 alone, in shared-memory tables, with no CTA barrier.
+constexpr int WS_E = 256;
+constexpr int WS_T = 2048;
+constexpr int WS_R = 4;  // entries per lane whose loads are issued together
+
+// Lowest-id admissible block for a member of weight c (>= 1) with no
+// admissible neighbouring block (one warp).  *hint is the lowest block that
+// may have room: every block below it has cap - weight < 1.  Blocks only gain
+// weight during the commit, except the block being emptied (the commit lowers
+// the hint to it when it gets room), so the scan starts there and moves the
+// hint up past the full blocks it passes.  The overloaded block B has no room.
+constexpr int LA_U = 8;  // chunks of 32 blocks checked per round trip
+__device__ int32_t lowest_admissible(const BalArgs &A, int32_t B, int64_t c, int lane, int32_t *hint) {
+  int32_t h1 = -1, res = -1;
+  for (int32_t base = *hint & ~31; base < A.k && res < 0; base += 32 * LA_U) {
+    int32_t room[LA_U];  // cap - weight, clamped to int32 (only >= 1 and >= c matter)
+#pragma unroll
+    for (int u = 0; u < LA_U; ++u) {
+      const int32_t b = base + 32 * u + lane;
+      const int32_t bb = b < A.k ? b : A.k - 1;
+      const int64_t r = (int64_t)A.cap[bb] - A.bw[bb];
+      room[u] = r < INT32_MIN ? INT32_MIN : (r > INT32_MAX ? INT32_MAX : (int32_t)r);
+    }
+#pragma unroll
+    for (int u = 0; u < LA_U; ++u) {
+      const int32_t b = base + 32 * u + lane;
+      const unsigned m1 = __ballot_sync(0xFFFFFFFFu, b < A.k && room[u] >= 1);
+      const unsigned mc = __ballot_sync(0xFFFFFFFFu, b < A.k && b != B && (int64_t)room[u] >= c);
+      if (h1 < 0 && m1) h1 = base + 32 * u + __ffs(m1) - 1;
+      if (res < 0 && mc) res = base + 32 * u + __ffs(mc) - 1;
+    }
+  }
+  // blocks in [*hint, h1) were seen without room (h1 = k: none has room)
+  if (lane == 0) atomicMax(hint, h1 >= 0 ? h1 : A.k);
+  __syncwarp();
+  return res;
+}
+
+// the block being emptied lost weight: the hint comes down to it if it has room
+__device__ __forceinline__ void hint_lower(const BalArgs &A, int32_t B, int32_t *hint) {
+  if ((int64_t)A.cap[B] - A.bw[B] >= 1 && B < *hint) *hint = B;
+}
+
+// the in-order commit of an evaluated batch (one thread); returns the members
+// decided, `stop` when the block fits
+__device__ int32_t commit_batch(const BalArgs &A, int32_t B, int32_t nb, const int32_t *s_v, const int32_t *s_t,
+                                const int64_t *s_c, const int64_t *s_bwt, const int64_t *s_capt,
+                                const uint32_t *s_adj, int64_t E, int32_t &stop, int32_t *hint) {
+  // only this CTA changes weights, so the block's and the targets' weights are
+  // tracked here (a target's weight is its start weight plus the moves of this
+  // batch into it)
+  uint32_t moved_mask = 0;
+  int32_t j = 0, moves = 0;
+  stop = 0;
+  int64_t wB = A.bw[B];
+  const int64_t capB = A.cap[B];
+  for (; j < nb; ++j) {
+    if (wB <= capB) {
+      stop = 1;
+      break;
+    }
+    const int32_t t = s_t[j];
+    const int64_t c = s_c[j];
+    int64_t wt = 0;
+    if (t >= 0) {
+      wt = s_bwt[j];
+      for (int32_t x = 0; x < j; ++x)
+        if (((moved_mask >> x) & 1u) && s_t[x] == t) wt += s_c[x];
+    }
+    if (j > 0 && ((s_adj[j] & moved_mask) || (t >= 0 && wt + c > s_capt[j]))) break;
+    if (t >= 0) {
+      A.part[s_v[j]] = t;
+      A.bw[t] = wt + c;
+      wB -= c;
+      ++moves;
+      moved_mask |= 1u << j;
+    }
+  }
+  A.bw[B] = wB;
+  hint_lower(A, B, hint);
+  if (moves) atomicAdd(A.moved, (unsigned long long)moves);
+  atomicAdd(A.moved + 2, 1ull);  // an exact batch
+  atomicAdd(A.moved + 3, (unsigned long long)nb);
+  atomicAdd(A.moved + 4, (unsigned long long)E);
+  return j;
+}
+
+// Warp 0 drives the commit: it applies the speculated moves that stand,
+// sets up every exact batch, and evaluates and commits the small ones alone;
+// the whole CTA joins only for a batch beyond WS_E entries or WS_T slots.
 __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch) {
   __shared__ int32_t s_v[BM_W], s_t[BM_W];
   __shared__ int64_t s_c[BM_W], s_eoff[BM_W + 1], s_beg[BM_W], s_bwt[BM_W], s_capt[BM_W];
   __shared__ uint32_t s_adj[BM_W], s_mask[BM_W], s_toff[BM_W + 1];
   __shared__ unsigned long long s_best[BM_W];
-  __shared__ int32_t s_nb, s_next, s_stop;
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint64_t vmask = (1ull << A.bitsN) - 1ull;
+  __shared__ int32_t wk[WS_T], wv[WS_T];  // warp 0's tables (empty between batches)
+  __shared__ int32_t s_nb, s_B, s_ob, s_i, s_phase, s_done, s_hint;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint64_t vmask = (1ull << A.bitsN) - 1ull;
   const uint32_t gcap = A.gcap;  // stride of the per-member table regions
-  __shared__ int32_t s_resume, s_ob;
-  for (int32_t ob = 0;; ++ob) {
-    // Warp 0 runs ahead over the blocks: a block's speculated moves stand, in
-    // order, while their targets still fit under the weights left by the
-    // blocks before.  One lane per move checks its target against the current
-    // weight plus what the block's earlier moves add to it; the moves before
-    // the first that does not fit are applied at once.  Warp 0 stops at the
-    // first block that still needs the exact commit (the whole CTA).
+  for (int x = threadIdx.x; x < WS_T; x += BM_T) {
+    wk[x] = HT_EMPTY;
+    wv[x] = 0;
+  }
+  if (threadIdx.x == 0) {
+    s_ob = 0;
+    s_i = 0;
+    s_phase = 0;
+    s_done = 0;
+    s_hint = 0;
+  }
+  __syncthreads();
+  for (;;) {
     if (w == 0) {
-      int32_t o = ob, resume = 0;
-      for (; o < A.nover; ++o) {
-        const int32_t B = A.olist[o];
-        const int32_t lo = A.seg_lo[B], hi = A.seg_hi[B];
-        const int32_t nm = A.spec_n[o];
-        int32_t v = 0, t = 0;
-        int64_t c = 0, bt = 0, ct = 0;
-        if (lane < nm) {
-          v = A.spec_v[(int64_t)o * SPEC_MAX + lane];
-          t = A.spec_t[(int64_t)o * SPEC_MAX + lane];
-          c = bw_node(A, v);
-          bt = A.bw[t];
-          ct = A.cap[t];
-        }
-        int64_t pre = 0;  // this block's earlier moves into the same target
+      int32_t ob = s_ob, i = s_i, phase = s_phase;
+      for (;;) {
+        if (phase == 0) {
+          // Run ahead over the blocks: a block's speculated moves stand, in
+          // order, while their targets still fit under the weights left by
+          // the blocks before.  One lane per move checks its target against
+          // the current weight plus what the block's earlier moves add to
+          // it; the moves before the first that does not fit are applied at
+          // once.  Stop at the first block that still needs exact batches.
+          int32_t o = ob, resume = 0;
+          for (; o < A.nover; ++o) {
+            const int32_t B = A.olist[o];
+            const int32_t lo = A.seg_lo[B], hi = A.seg_hi[B];
+            const int32_t nm = A.spec_n[o];
+            int32_t v = 0, t = 0;
+            int64_t c = 0, bt = 0, ct = 0;
+            if (lane < nm) {
+              v = A.spec_v[(int64_t)o * SPEC_MAX + lane];
+              t = A.spec_t[(int64_t)o * SPEC_MAX + lane];
+              c = bw_node(A, v);
+              bt = A.bw[t];
+              ct = A.cap[t];
+            }
+            int64_t pre = 0;  // this block's earlier moves into the same target
 #pragma unroll
-        for (int j = 0; j < SPEC_MAX; ++j) {
-          const int32_t tj = __shfl_sync(0xFFFFFFFFu, t, j);
-          const long long cj = __shfl_sync(0xFFFFFFFFu, (long long)c, j);
-          if (j < lane && j < nm && tj == t) pre += cj;
+            for (int j = 0; j < SPEC_MAX; ++j) {
+              const int32_t tj = __shfl_sync(0xFFFFFFFFu, t, j);
+              const long long cj = __shfl_sync(0xFFFFFFFFu, (long long)c, j);
+              if (j < lane && j < nm && tj == t) pre += cj;
+            }
+            const unsigned bad = __ballot_sync(0xFFFFFFFFu, lane < nm && bt + pre + c > ct);
+            const int32_t f = bad ? __ffs(bad) - 1 : nm;  // moves [0, f) stand
+            if (lane < f) {
+              A.part[v] = t;
+              atomicAdd(reinterpret_cast<unsigned long long *>(&A.bw[t]), (unsigned long long)c);
+            }
+            const int64_t gone = warp_sum64(lane < f ? c : 0);
+            if (lane == 0 && f > 0) {
+              A.bw[B] -= gone;
+              hint_lower(A, B, &s_hint);
+              atomicAdd(A.moved, (unsigned long long)f);
+              atomicAdd(A.moved + 1, (unsigned long long)f);  // speculated moves that stood
+            }
+            __syncwarp();
+            resume = f < nm ? lo + f : (A.spec_sat[o] ? hi : A.spec_end[o]);
+            if (resume < hi && A.bw[B] > A.cap[B]) break;  // exact batches take over here
+          }
+          if (o >= A.nover) {
+            if (lane == 0) s_done = 1;
+            break;
+          }
+          ob = o;
+          i = resume;
+          phase = 1;
         }
-        const unsigned bad = __ballot_sync(0xFFFFFFFFu, lane < nm && bt + pre + c > ct);
-        const int32_t f = bad ? __ffs(bad) - 1 : nm;  // moves [0, f) stand
-        if (lane < f) {
-          A.part[v] = t;
-          atomicAdd(reinterpret_cast<unsigned long long *>(&A.bw[t]), (unsigned long long)c);
+        const int32_t B = A.olist[ob];
+        const int32_t hi = A.seg_hi[B];
+        if (i >= hi || A.bw[B] <= A.cap[B]) {
+          ++ob;
+          phase = 0;
+          continue;
         }
-        const int64_t gone = warp_sum64(lane < f ? c : 0);
-        if (lane == 0 && f > 0) {
-          A.bw[B] -= gone;
-          atomicAdd(A.moved, (unsigned long long)f);
-          atomicAdd(A.moved + 1, (unsigned long long)f);  // speculated moves that stood
+        // the next batch: the shortest prefix of the remaining candidates
+        // whose weights cover the overload
+        {
+          int32_t avail = hi - i < BM_W ? hi - i : BM_W;
+          int32_t v = lane < avail ? (int32_t)(A.keys[i + lane] & vmask) : 0;
+          int64_t c = lane < avail ? bw_node(A, v) : 0;
+          const int64_t rb = lane < avail ? A.xadj[v] : 0;
+          int64_t deg = lane < avail ? A.xadj[v + 1] - rb : 0;
+          const int64_t own = deg < A.k ? deg : A.k;
+          // inclusive prefix sums of weights and degrees
+#pragma unroll
+          for (int m = 1; m < 32; m <<= 1) {
+            int64_t oc = (int64_t)__shfl_up_sync(0xFFFFFFFFu, (unsigned long long)c, m);
+            int64_t od = (int64_t)__shfl_up_sync(0xFFFFFFFFu, (unsigned long long)deg, m);
+            if (lane >= m) {
+              c += oc;
+              deg += od;
+            }
+          }
+          unsigned enough = __ballot_sync(0xFFFFFFFFu, lane < avail && c >= A.bw[B] - A.cap[B]);
+          int32_t nb = enough ? __ffs(enough) : avail;
+          // member table sized by the member's own distinct blocks (at most
+          // min(degree, k)), so low-degree members never touch a hub-sized
+          // table; the tables' slots are numbered across the batch (s_toff)
+          uint32_t cap = 32;
+          while ((int64_t)cap < 2 * own) cap <<= 1;
+          uint32_t tpre = lane < nb ? cap : 0;
+#pragma unroll
+          for (int m = 1; m < 32; m <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, tpre, m);
+            if (lane >= m) tpre += o;
+          }
+          if (lane < nb) {
+            s_v[lane] = v;
+            s_beg[lane] = rb;
+            s_eoff[lane + 1] = deg;
+            s_adj[lane] = 0;
+            s_mask[lane] = cap - 1;
+            s_toff[lane + 1] = tpre;
+            s_best[lane] = 0;
+            inbatch[v] = lane + 1;
+          }
+          if (lane == 0) {
+            s_eoff[0] = 0;
+            s_toff[0] = 0;
+            s_nb = nb;
+          }
         }
         __syncwarp();
-        resume = f < nm ? lo + f : (A.spec_sat[o] ? hi : A.spec_end[o]);
-        if (resume < hi && A.bw[B] > A.cap[B]) break;  // the exact commit takes over here
-      }
-      if (lane == 0) {
-        s_ob = o;
-        s_resume = resume;
+        const int32_t nb = s_nb;
+        const int64_t E = s_eoff[nb];
+        const uint32_t TT = s_toff[nb];
+        if (E > WS_E || TT > WS_T) {
+          if (lane == 0) {
+            s_B = B;
+            s_ob = ob;
+            s_i = i;
+          }
+          break;  // the whole CTA evaluates this batch
+        }
+        // ---- warp 0 alone: connectivity tables in shared memory, entries in
+        // rounds of WS_R per lane (their loads issued together)
+        {
+          int32_t j = 0;
+          for (int64_t t0 = 0; t0 < E; t0 += 32 * WS_R) {
+            int32_t uu[WS_R], wt[WS_R], jm[WS_R];
+#pragma unroll
+            for (int r = 0; r < WS_R; ++r) {
+              const int64_t t = t0 + lane + 32 * r;
+              uu[r] = -1;
+              if (t < E) {
+                while (s_eoff[j + 1] <= t) ++j;
+                const int64_t q = s_beg[j] + (t - s_eoff[j]);
+                uu[r] = A.adj[q];
+                wt[r] = A.ew ? A.ew[q] : 1;
+                jm[r] = j;
+              }
+            }
+            int32_t bk[WS_R], ib[WS_R];
+#pragma unroll
+            for (int r = 0; r < WS_R; ++r)
+              if (uu[r] >= 0) {
+                bk[r] = A.part[uu[r]];
+                ib[r] = inbatch[uu[r]];
+              }
+#pragma unroll
+            for (int r = 0; r < WS_R; ++r)
+              if (uu[r] >= 0) {
+                if (ib[r] > 0) atomicOr(&s_adj[jm[r]], 1u << (ib[r] - 1));
+                ht_add(wk + s_toff[jm[r]], wv + s_toff[jm[r]], s_mask[jm[r]], bk[r], wt[r]);
+              }
+          }
+        }
+        __syncwarp();
+        // best admissible block of every member, (conn, ~block); the tables
+        // are emptied on the way (every table spans whole 32-slot chunks)
+        {
+          int32_t j = 0;
+          for (uint32_t base = 0; base < TT; base += 32) {
+            while (s_toff[j + 1] <= base) ++j;
+            const uint32_t x = base + lane;
+            const int32_t b = wk[x], cv = wv[x];
+            wk[x] = HT_EMPTY;
+            wv[x] = 0;
+            uint64_t key = 0;
+            if (b != HT_EMPTY && b != B && A.bw[b] + bw_node(A, s_v[j]) <= A.cap[b])
+              key = ((uint64_t)(uint32_t)cv << 32) | (0xFFFFFFFFu - (uint32_t)b);
+            key = group_max64<32>(key);
+            if (lane == 0 && key > s_best[j]) s_best[j] = key;
+            __syncwarp();
+          }
+        }
+        if (lane < nb) {
+          const uint64_t bkey = s_best[lane];
+          s_t[lane] = bkey ? (int32_t)(0xFFFFFFFFu - (uint32_t)bkey) : -1;
+          s_c[lane] = bw_node(A, s_v[lane]);
+        }
+        __syncwarp();
+        for (int32_t j = 0; j < nb; ++j)
+          if (s_t[j] < 0) {
+            const int32_t t = lowest_admissible(A, B, s_c[j], lane, &s_hint);
+            __syncwarp();
+            if (lane == 0) s_t[j] = t;
+            __syncwarp();
+          }
+        if (lane < nb) {
+          const int32_t t = s_t[lane];
+          s_bwt[lane] = t >= 0 ? A.bw[t] : 0;  // the target's weight at the start of the batch
+          s_capt[lane] = t >= 0 ? A.cap[t] : 0;
+        }
+        __syncwarp();
+        int32_t next = 0, stop = 0;
+        if (lane == 0) next = commit_batch(A, B, nb, s_v, s_t, s_c, s_bwt, s_capt, s_adj, E, stop, &s_hint);
+        next = __shfl_sync(0xFFFFFFFFu, next, 0);
+        stop = __shfl_sync(0xFFFFFFFFu, stop, 0);
+        if (lane < nb) inbatch[s_v[lane]] = 0;
+        __syncwarp();
+        i += next;
+        if (stop) {
+          ++ob;
+          phase = 0;
+        }
       }
     }
     __syncthreads();
-    ob = s_ob;
-    if (ob >= A.nover) break;
-    const int32_t B = A.olist[ob];
-    const int32_t hi = A.seg_hi[B];
-    int32_t i = s_resume;
-    while (i < hi) {
-      if (A.bw[B] <= A.cap[B]) break;
-      if (w == 0) {
-        int32_t avail = hi - i < BM_W ? hi - i : BM_W;
-        int32_t v = lane < avail ? (int32_t)(A.keys[i + lane] & vmask) : 0;
-        int64_t c = lane < avail ? bw_node(A, v) : 0;
-        const int64_t rb = lane < avail ? A.xadj[v] : 0;
-        int64_t deg = lane < avail ? A.xadj[v + 1] - rb : 0;
-        const int64_t own = deg < A.k ? deg : A.k;
-        // inclusive prefix sums of weights and degrees
-#pragma unroll
-        for (int m = 1; m < 32; m <<= 1) {
-          int64_t oc = (int64_t)__shfl_up_sync(0xFFFFFFFFu, (unsigned long long)c, m);
-          int64_t od = (int64_t)__shfl_up_sync(0xFFFFFFFFu, (unsigned long long)deg, m);
-          if (lane >= m) {
-            c += oc;
-            deg += od;
-          }
-        }
-        unsigned enough = __ballot_sync(0xFFFFFFFFu, lane < avail && c >= A.bw[B] - A.cap[B]);
-        int32_t nb = enough ? __ffs(enough) : avail;
-        // member table sized by the member's own distinct blocks (at most
-        // min(degree, k)), so low-degree members never touch a hub-sized
-        // table; the tables' slots are numbered across the batch (s_toff) so
-        // that the whole CTA clears and scans them
-        uint32_t cap = 32;
-        while ((int64_t)cap < 2 * own) cap <<= 1;
-        uint32_t tpre = lane < nb ? cap : 0;
-#pragma unroll
-        for (int m = 1; m < 32; m <<= 1) {
-          const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, tpre, m);
-          if (lane >= m) tpre += o;
-        }
-        if (lane < nb) {
-          s_v[lane] = v;
-          s_beg[lane] = rb;
-          s_eoff[lane + 1] = deg;
-          s_adj[lane] = 0;
-          s_mask[lane] = cap - 1;
-          s_toff[lane + 1] = tpre;
-          s_best[lane] = 0;
-          inbatch[v] = lane + 1;
-        }
-        if (lane == 0) {
-          s_eoff[0] = 0;
-          s_toff[0] = 0;
-          s_nb = nb;
-        }
+    if (s_done) break;
+    // ---- a large batch, evaluated by the whole CTA
+    const int32_t B = s_B, nb = s_nb;
+    // every table size is a multiple of 32, so a warp's 32 slots lie in one table
+    const uint32_t TT = s_toff[nb];
+    {
+      int32_t j = 0;
+      for (uint32_t t = threadIdx.x; t < TT; t += BM_T) {
+        while (s_toff[j + 1] <= t) ++j;
+        int32_t *K = A.gtab + (int64_t)j * 2 * gcap;
+        const uint32_t x = t - s_toff[j];
+        K[x] = HT_EMPTY;
+        K[gcap + x] = 0;
       }
-      __syncthreads();
-      int32_t nb = s_nb;
-      // every table size is a multiple of 32, so a warp's 32 slots lie in one table
-      const uint32_t TT = s_toff[nb];
-      {
-        int32_t j = 0;
-        for (uint32_t t = threadIdx.x; t < TT; t += BM_T) {
-          while (s_toff[j + 1] <= t) ++j;
-          int32_t *K = A.gtab + (int64_t)j * 2 * gcap;
-          const uint32_t x = t - s_toff[j];
-          K[x] = HT_EMPTY;
-          K[gcap + x] = 0;
-        }
-      }
-      __syncthreads();
-      int64_t E = s_eoff[nb];
+    }
+    __syncthreads();
+    const int64_t E = s_eoff[nb];
+    {
       int32_t jm = 0;  // this thread's entries only move forward through the members
       for (int64_t base = 0; base < E; base += BM_T) {
         int64_t t = base + threadIdx.x;
@@ -564,95 +773,54 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
           ht_add(K, K + gcap, s_mask[jm], blk, s);
         }
       }
-      __syncthreads();
-      {
-        // best admissible block of every member: (conn, ~block), largest
-        // connectivity, then lowest id; a warp's slots belong to one member
-        int32_t jj = 0;
-        for (uint32_t base = 0; base < TT; base += BM_T) {
-          const uint32_t t = base + threadIdx.x;
-          if (base + (threadIdx.x & ~31u) >= TT) break;  // warp-uniform
-          const bool ok = t < TT;
-          if (ok)
-            while (s_toff[jj + 1] <= t) ++jj;
-          uint64_t key = 0;
-          if (ok) {
-            const int32_t *K = A.gtab + (int64_t)jj * 2 * gcap;
-            const uint32_t x = t - s_toff[jj];
-            const int32_t b = K[x];
-            if (b != HT_EMPTY && b != B && A.bw[b] + bw_node(A, s_v[jj]) <= A.cap[b])
-              key = ((uint64_t)(uint32_t)K[gcap + x] << 32) | (0xFFFFFFFFu - (uint32_t)b);
-          }
-          key = group_max64<32>(key);
-          if (lane == 0 && key) atomicMax(&s_best[jj], key);
-        }
-      }
-      __syncthreads();
-      if (w < nb) {
-        int32_t v = s_v[w];
-        int64_t c = bw_node(A, v);
-        const uint64_t bestk = s_best[w];
-        int32_t t = bestk ? (int32_t)(0xFFFFFFFFu - (uint32_t)bestk) : -1;
-        if (t < 0) {
-          int32_t low = INT32_MAX;
-          for (int32_t b = lane; b < A.k; b += 32)
-            if (b != B && A.bw[b] + c <= A.cap[b]) { low = b; break; }
-#pragma unroll
-          for (int m = 16; m > 0; m >>= 1) low = min(low, __shfl_xor_sync(0xFFFFFFFFu, low, m));
-          t = low == INT32_MAX ? -1 : low;
-        }
-        if (lane == 0) {
-          s_t[w] = t;
-          s_c[w] = c;
-          s_bwt[w] = t >= 0 ? A.bw[t] : 0;  // the target's weight at the start of the batch
-          s_capt[w] = t >= 0 ? A.cap[t] : 0;
-        }
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        // in order; only this CTA changes weights, so the block's and the
-        // targets' weights are tracked here (a target's weight is its start
-        // weight plus the moves of this batch into it)
-        uint32_t moved_mask = 0;
-        int32_t j = 0, moves = 0;
-        s_stop = 0;
-        int64_t wB = A.bw[B];
-        const int64_t capB = A.cap[B];
-        for (; j < nb; ++j) {
-          if (wB <= capB) {
-            s_stop = 1;
-            break;
-          }
-          const int32_t t = s_t[j];
-          const int64_t c = s_c[j];
-          int64_t wt = 0;
-          if (t >= 0) {
-            wt = s_bwt[j];
-            for (int32_t x = 0; x < j; ++x)
-              if (((moved_mask >> x) & 1u) && s_t[x] == t) wt += s_c[x];
-          }
-          if (j > 0 && ((s_adj[j] & moved_mask) || (t >= 0 && wt + c > s_capt[j]))) break;
-          if (t >= 0) {
-            A.part[s_v[j]] = t;
-            A.bw[t] = wt + c;
-            wB -= c;
-            ++moves;
-            moved_mask |= 1u << j;
-          }
-        }
-        A.bw[B] = wB;
-        if (moves) atomicAdd(A.moved, (unsigned long long)moves);
-        atomicAdd(A.moved + 2, 1ull);  // an exact batch
-        atomicAdd(A.moved + 3, (unsigned long long)nb);
-        atomicAdd(A.moved + 4, (unsigned long long)E);
-        s_next = j;
-      }
-      __syncthreads();
-      if (threadIdx.x < nb) inbatch[s_v[threadIdx.x]] = 0;
-      __syncthreads();
-      i += s_next;
-      if (s_stop) break;
     }
+    __syncthreads();
+    {
+      // best admissible block of every member: (conn, ~block), largest
+      // connectivity, then lowest id; a warp's slots belong to one member
+      int32_t jj = 0;
+      for (uint32_t base = 0; base < TT; base += BM_T) {
+        const uint32_t t = base + threadIdx.x;
+        if (base + (threadIdx.x & ~31u) >= TT) break;  // warp-uniform
+        while (s_toff[jj + 1] <= t) ++jj;
+        const int32_t *K = A.gtab + (int64_t)jj * 2 * gcap;
+        const uint32_t x = t - s_toff[jj];
+        const int32_t b = K[x];
+        uint64_t key = 0;
+        if (b != HT_EMPTY && b != B && A.bw[b] + bw_node(A, s_v[jj]) <= A.cap[b])
+          key = ((uint64_t)(uint32_t)K[gcap + x] << 32) | (0xFFFFFFFFu - (uint32_t)b);
+        key = group_max64<32>(key);
+        if (lane == 0 && key) atomicMax(&s_best[jj], key);
+      }
+    }
+    __syncthreads();
+    if (w < nb) {
+      const int64_t c = bw_node(A, s_v[w]);
+      const uint64_t bestk = s_best[w];
+      int32_t t = bestk ? (int32_t)(0xFFFFFFFFu - (uint32_t)bestk) : -1;
+      if (t < 0) t = lowest_admissible(A, B, c, lane, &s_hint);
+      if (lane == 0) {
+        s_t[w] = t;
+        s_c[w] = c;
+        s_bwt[w] = t >= 0 ? A.bw[t] : 0;  // the target's weight at the start of the batch
+        s_capt[w] = t >= 0 ? A.cap[t] : 0;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int32_t stop = 0;
+      const int32_t next = commit_batch(A, B, nb, s_v, s_t, s_c, s_bwt, s_capt, s_adj, E, stop, &s_hint);
+      s_i += next;
+      if (stop) {
+        ++s_ob;
+        s_phase = 0;
+      } else {
+        s_phase = 1;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < nb) inbatch[s_v[threadIdx.x]] = 0;
+    __syncthreads();
   }
 }
 

@@ -731,10 +731,20 @@ __global__ void __launch_bounds__(HP_T) k_hub_count(LPArgs A, int s) {
 
 // the same work units: entries into bucket order (positions inside a bucket
 // are arbitrary; the aggregation below does not depend on them)
+// one piece in bucket order: each staged entry's index in the piece and its
+// table slot (the label and weight are read again, from cache, when written)
+struct HubPieceStage {
+  uint16_t idx[HP];
+  uint16_t slot[HP];
+  int32_t wsum[HP_T / 32];
+};
+
 __global__ void __launch_bounds__(HP_T) k_hub_scatter(LPArgs A, int s) {
   __shared__ HubPieceTable T;
+  __shared__ HubPieceStage P;
   hp_clear_all(T);
   __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int32_t *bo = A.boff + s * NB;
   int32_t cnt = bo[7] - bo[6];
   int64_t total = A.plan_tot[0];
@@ -746,6 +756,7 @@ __global__ void __launch_bounds__(HP_T) k_hub_scatter(LPArgs A, int s) {
     const int64_t b = H.b, deg = H.deg, nb = H.nb, gb = H.gb, xo = H.xo;
     int64_t e0 = b + (c - H.e_first) * A.hub_chunk, e1 = e0 + A.hub_chunk < b + deg ? e0 + A.hub_chunk : b + deg;
     for (int64_t p0 = e0; p0 < e1; p0 += HP) {
+      const int32_t pc = e1 - p0 < HP ? (int32_t)(e1 - p0) : HP;  // entries of the piece
       int32_t L[HP_PER], sl[HP_PER], rk[HP_PER];
 #pragma unroll
       for (int r = 0; r < HP_PER; ++r) {
@@ -756,21 +767,57 @@ __global__ void __launch_bounds__(HP_T) k_hub_scatter(LPArgs A, int s) {
       for (int r = 0; r < HP_PER; ++r)
         sl[r] = L[r] >= 0 ? hp_insert(T, (int32_t)hub_bucket_of(L[r], nb), rk[r]) : -1;
       __syncthreads();
-      // one claim per bucket; the slot's count becomes its first position
+      // the occupied slots in list order get consecutive staging ranges
+      // (exclusive prefix of their counts) and one global claim each; the
+      // slot's key becomes the claimed position, its value the staging offset
       const int32_t nt = T.n;
-      for (int32_t x = threadIdx.x; x < nt; x += HP_T) {
-        const int32_t h = T.list[x];
-        const int64_t g = gb + T.key[h];
-        T.val[h] = A.hboff[g] + atomicAdd(&A.hbcur[g], T.val[h]);
+      {
+        int32_t cnts[HP_PER], sum = 0;
+#pragma unroll
+        for (int q = 0; q < HP_PER; ++q) {
+          const int32_t x = threadIdx.x * HP_PER + q;
+          cnts[q] = x < nt ? T.val[T.list[x]] : 0;
+          sum += cnts[q];
+        }
+        int32_t inc = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int32_t o = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+          if (lane >= d) inc += o;
+        }
+        if (lane == 31) P.wsum[wid] = inc;
+        __syncthreads();
+        int32_t run = inc - sum;
+        for (int k = 0; k < wid; ++k) run += P.wsum[k];
+#pragma unroll
+        for (int q = 0; q < HP_PER; ++q) {
+          const int32_t x = threadIdx.x * HP_PER + q;
+          if (x < nt) {
+            const int32_t h = T.list[x];
+            const int64_t g = gb + T.key[h];
+            T.key[h] = A.hboff[g] + atomicAdd(&A.hbcur[g], cnts[q]);
+            T.val[h] = run;
+            run += cnts[q];
+          }
+        }
       }
       __syncthreads();
 #pragma unroll
       for (int r = 0; r < HP_PER; ++r)
         if (sl[r] >= 0) {
-          const int64_t pos = (int64_t)T.val[sl[r]] + rk[r];
-          A.hslab[pos] = L[r];
-          if (A.ew) A.hsw[pos] = A.ew[p0 + r * HP_T + threadIdx.x];
+          const int32_t lp = T.val[sl[r]] + rk[r];
+          P.idx[lp] = (uint16_t)(r * HP_T + threadIdx.x);
+          P.slot[lp] = (uint16_t)sl[r];
         }
+      __syncthreads();
+      // consecutive threads write consecutive positions of a bucket's run
+      for (int32_t t = threadIdx.x; t < pc; t += HP_T) {
+        const int32_t h = P.slot[t];
+        const int64_t pos = (int64_t)T.key[h] + (t - T.val[h]);
+        const int64_t e = p0 + P.idx[t];
+        A.hslab[pos] = A.hlab[xo + e];
+        if (A.ew) A.hsw[pos] = A.ew[e];
+      }
       __syncthreads();
       for (int32_t x = threadIdx.x; x < nt; x += HP_T) {
         const int32_t h = T.list[x];
