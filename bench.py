@@ -17,17 +17,22 @@ value    = LP edges/s per round: directed CSR entries rated by all LP rounds
 e2e      = the same quantity through kmp_partition with host buffers: entries
            rated / wall time of the call (CSR upload and partition download
            included).
-roofline = k_rate, the LP rating kernel (every launch of the timed steps):
-           algorithmic bytes (per rated entry adjncy + neighbour label, per
-           rated node 24 B; hubs rated by the hub kernels excluded) / summed
-           launch time, live in the timed region, against the measured HBM
-           copy bandwidth.  A launch's time is the span from its first CTA's
-           start to its last CTA's end on the device's global timer, stamped
-           inside the kernel: the LP rounds run as a replayed CUDA graph, and
+roofline = the LP rating stage, the dominant part of the step: in every
+           sub-round of every LP round of the timed steps, k_rate and the hub
+           kernels (k_hub_plan, k_hub_count, k_hub_scatter, k_hub_bucket,
+           k_hub_emit; k_hubd_insert/k_hubd_reduce in refinement).
+           achieved = algorithmic bytes (per rated directed entry adjncy +
+           neighbour label, + 4 B edge weight when weighted; per rated node
+           24 B, + 4 B node weight) / summed stage spans, live in the timed
+           region, against the measured HBM copy bandwidth.  A span runs from
+           the first CTA start of k_rate to the last CTA end of the stage's
+           last kernel on the device's global timer, stamped inside the
+           kernels: the LP rounds run as a replayed CUDA graph, and
            event-record nodes in it would add about 7 us each to the step.
-           rating_stage = the same over the whole rating stage of every
-           sub-round (k_rate and the hub kernels: first CTA start of k_rate to
-           last CTA end of the last hub kernel), hub entries and nodes included.
+           k_rate = the same for k_rate alone (hub entries excluded).
+           traffic = DRAM bytes per span from the committed ncu record of the
+           same workload (profiles/lp_rate_traffic.json), null when the LP
+           source changed since.
 cpu_baseline = the CPU oracle (single thread) on a bounded sample of the same
            graph: the first sub-round of the first round of its level-0
            coarsening LP.
@@ -142,11 +147,12 @@ class Clocks:
         return out
 
 
-def recorded_rate_traffic(workload, alg_bytes_per_launch):
-    """DRAM bytes per k_rate launch: the committed ncu record gives DRAM bytes
-    per algorithmic byte on a small case of the same graph family (one kernel,
-    a few launches), scaled here by this run's algorithmic bytes per launch.
-    None when there is no record for the workload or the LP source changed."""
+def recorded_rate_traffic(workload, alg_bytes_per_span, key="stage"):
+    """DRAM bytes per rating-stage span (key "stage") or per k_rate launch
+    (key "k_rate"): the committed ncu record of one partition step of the
+    workload gives DRAM bytes per algorithmic byte, scaled here by this run's
+    algorithmic bytes per span.  None when there is no record for the workload
+    or the LP source changed."""
     import hashlib
 
     prof = os.path.join(ROOT, "profiles", "lp_rate_traffic.json")
@@ -157,7 +163,7 @@ def recorded_rate_traffic(workload, alg_bytes_per_launch):
             return None
         if rec.get("kmp_lp_cu_sha256") != hashlib.sha256(open(src, "rb").read()).hexdigest():
             return None
-        return rec["dram_bytes_per_algorithmic_byte"] * alg_bytes_per_launch
+        return rec[key]["dram_bytes_per_algorithmic_byte"] * alg_bytes_per_span
     except (OSError, ValueError, KeyError, TypeError):
         return None
 
@@ -477,6 +483,57 @@ def replicas(gg, kmp, torch, np):
     kmp.set_config(kmp.config())
 
 
+def _partition_variants(kmp, torch, dg, k, variants, mode, name):
+    """One partition per variant (config, tuning) after a warm-up at the same
+    variant; best of two; one JSON line each."""
+    base_cfg, base_tune = kmp.config(), kmp.get_tuning()
+    for label, cfg, tune in variants:
+        kmp.set_config(cfg if cfg is not None else base_cfg)
+        kmp.set_tuning(tune if tune is not None else base_tune)
+        kmp.partition_graph(dg, k, EPS, SEED)
+        best = None
+        for _ in range(2):
+            torch.cuda.synchronize()
+            _, rc, st = kmp.partition_graph(dg, k, EPS, SEED)
+            if best is None or st.ms_total < best.ms_total:
+                best = st
+        print(json.dumps({"mode": mode, "workload": name, "k": k, "variant": label, "ms": best.ms_total,
+                          "cut": int(best.cut), "feasible": bool(best.feasible),
+                          "phase_ms": {"lp": best.ms_lp, "contract": best.ms_contract, "ip": best.ms_ip,
+                                       "balance": best.ms_balance, "refine": best.ms_refine}}), flush=True)
+    kmp.set_config(base_cfg)
+    kmp.set_tuning(base_tune)
+
+
+def adaptive(gg, kmp, torch, np):
+    """Adaptive portfolio selection (Section 4.2) against the fixed portfolio:
+    time and cut of full partitions at large k (RGG 2^24, k = 2^14) and on
+    R-MAT 2^22 (k = 2^12)."""
+    kmp.load()
+    for name in ("rgg_2^24_deg16_k16384", "rmat_scale22_ef16_k4096"):
+        make, k, _ = WORKLOADS[name]
+        dg = kmp.DeviceGraph.from_host(make(gg))
+        _partition_variants(kmp, torch, dg, k, [("fixed", kmp.config(adaptive=0), None),
+                                                ("adaptive", kmp.config(adaptive=1), None)], "adaptive", name)
+        del dg
+
+
+def dense_rows(gg, kmp, torch, np):
+    """Dense per-hub rating rows for label sets up to 57344 (tuning
+    dense_labels) against label buckets, on full partitions of R-MAT 2^20
+    (k = 256) and R-MAT 2^26 (k = 2^16)."""
+    kmp.load()
+    for name in ("rmat_scale20_ef16_k256", "rmat_scale26_ef16_k65536"):
+        make, k, _ = WORKLOADS[name]
+        dg = kmp.DeviceGraph.from_host(make(gg))
+        b = kmp.get_tuning()
+        dense = kmp.Tuning(b.rate_blocks_per_sm, b.hub_degree, b.hub_chunk, b.ip_blocks_per_sm, b.dense_hub_degree,
+                           b.lp_graphs, b.hub_bucket, 57344)
+        _partition_variants(kmp, torch, dg, k, [("buckets", None, None), ("dense_rows", None, dense)],
+                            "dense_rows", name)
+        del dg
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -488,7 +545,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="partition",
                     choices=["partition", "coarsen1", "launchlist", "ksweep", "replicas", "oracle_phases",
-                             "learned"],
+                             "learned", "adaptive", "dense_rows"],
                     help="coarsen1: one level-0 coarsening (LP) of the workload graph only; "
                          "launchlist: one warm-up partition and one partition inside the NVTX "
                          "range kmp_step (for ncu launch lists); both are used for kernel profiles; "
@@ -498,7 +555,10 @@ def main():
                          "on R-MAT scale 20 (k = 256) and the small RGG (k = 8); "
                          "oracle_phases: the CPU oracle's partition timed per phase on the small RGG "
                          "and R-MAT scale 20; learned: the learned seed proposer trained on the "
-                         "method's own item bipartitions, on 4096 coarse blocks and end to end")
+                         "method's own item bipartitions, on 4096 coarse blocks and end to end; "
+                         "adaptive: adaptive against fixed portfolio on RGG 2^24 (k = 2^14) and "
+                         "R-MAT 2^22 (k = 2^12); dense_rows: dense per-hub rating rows against label "
+                         "buckets on R-MAT 2^20 (k = 256) and 2^26 (k = 2^16)")
     args = ap.parse_args()
     if args.mode != "ksweep" and args.workload is None:
         args.workload = DEFAULT_WORKLOAD
@@ -528,6 +588,12 @@ def main():
         return
     if args.mode == "learned":
         learned(gg, kmp, torch, np)
+        return
+    if args.mode == "adaptive":
+        adaptive(gg, kmp, torch, np)
+        return
+    if args.mode == "dense_rows":
+        dense_rows(gg, kmp, torch, np)
         return
     dist = None
     if world > 1:
@@ -640,10 +706,13 @@ def main():
     d2h = g.n * 4
 
     peak, peak_kind = _peaks()
-    # DRAM bytes per k_rate launch from the committed ncu capture, valid only
-    # while the LP source it was taken from is unchanged
+    # DRAM bytes per span from the committed ncu capture, valid only while the
+    # LP source it was taken from is unchanged
     pd = prof.as_dict(peak)
-    traffic = recorded_rate_traffic(args.workload, pd["rate_bytes_per_launch"] or 0.0)
+    stage_per_span = pd["stage_bytes"] / pd["stage_spans"] if pd["stage_spans"] else 0.0
+    stage_span_ms = pd["stage_ms"] / pd["stage_spans"] if pd["stage_spans"] else None
+    traffic = recorded_rate_traffic(args.workload, stage_per_span, "stage")
+    rate_traffic = recorded_rate_traffic(args.workload, pd["rate_bytes_per_launch"] or 0.0, "k_rate")
 
     if rank != 0:
         return
@@ -664,13 +733,15 @@ def main():
         "balancer": balancer_stats(stats),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": "k_rate (LP rating)", "bound": "hbm", "achieved": pd["rate_gbs"], "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": pd["rate_frac"], "traffic": traffic,
-                     "launches": pd["rate_launches"], "algorithmic_bytes_per_launch": pd["rate_bytes_per_launch"],
-                     "algorithmic_bytes": pd["rate_bytes"], "ms": pd["rate_ms"],
-                     "rating_stage": {"achieved": pd["stage_gbs"], "frac": pd["stage_frac"],
-                                      "algorithmic_bytes": pd["stage_bytes"], "ms": pd["stage_ms"],
-                                      "spans": pd["stage_spans"]}},
+        "roofline": {"kernel": "LP rating stage (k_rate + hub kernels, one span per sub-round)",
+                     "bound": "hbm", "achieved": pd["stage_gbs"], "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": pd["stage_frac"], "traffic": traffic,
+                     "spans": pd["stage_spans"], "algorithmic_bytes_per_span": stage_per_span,
+                     "ms_per_span": stage_span_ms, "algorithmic_bytes": pd["stage_bytes"], "ms": pd["stage_ms"],
+                     "k_rate": {"achieved": pd["rate_gbs"], "frac": pd["rate_frac"], "traffic": rate_traffic,
+                                "launches": pd["rate_launches"],
+                                "algorithmic_bytes_per_launch": pd["rate_bytes_per_launch"],
+                                "algorithmic_bytes": pd["rate_bytes"], "ms": pd["rate_ms"]}},
         "clocks": clk,
     }
     if not args.no_cpu_baseline and rank == 0:

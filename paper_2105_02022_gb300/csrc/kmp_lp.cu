@@ -353,6 +353,64 @@ __device__ __forceinline__ int32_t ht_add_fresh(int32_t *keys, int32_t *vals, ui
 // hashing are unchanged, so per-node work scales with the distinct labels,
 // not with the table capacity.
 
+// Best keys over a table's held slots (one thread's share: list[i0], i0 +
+// step, ... < held): ku over every label but `own`, kc over the admissible
+// ones (target weight + c(u) <= cap).  Admissibility needs the target's
+// weight, a random read, so a thread checks its own best label first; the
+// caller reduces those to kc0, the best admissible top of the group, and only
+// a thread whose top failed then checks its other labels above kc0
+// (select_rest).  The result is the plain maximum over admissible labels:
+// a thread whose top passed holds nothing above it.
+struct SelTop {
+  uint64_t ku = 0, kc = 0;
+  int32_t lu = -1, lc = -1;
+  bool failed = false;  // the thread's top label is not admissible
+};
+__device__ __forceinline__ SelTop select_top(const LPArgs &A, const int32_t *keys, const int32_t *vals,
+                                             const uint16_t *list, int32_t i0, int32_t step, int32_t held,
+                                             int32_t own, int32_t cu, int32_t &rown) {
+  SelTop T;
+  for (int32_t i = i0; i < held; i += step) {
+    const int32_t sl = list[i];
+    const int32_t K = keys[sl], r = vals[sl];
+    if (K == own) {
+      rown = r;
+      continue;
+    }
+    const uint64_t k = rate_key(A, K, r);
+    if (k > T.ku) {
+      T.ku = k;
+      T.lu = K;
+    }
+  }
+  if (T.lu >= 0) {
+    if ((int64_t)A.wt[T.lu] + cu <= cap_of(A, T.lu)) {
+      T.kc = T.ku;
+      T.lc = T.lu;
+    } else {
+      T.failed = true;
+    }
+  }
+  return T;
+}
+// the labels above kc0 of a thread whose top failed; the slots are cleared
+__device__ __forceinline__ void select_rest(const LPArgs &A, int32_t *keys, int32_t *vals, const uint16_t *list,
+                                            int32_t i0, int32_t step, int32_t held, int32_t own, int32_t cu,
+                                            uint64_t kc0, SelTop &T) {
+  for (int32_t i = i0; i < held; i += step) {
+    const int32_t sl = list[i];
+    const int32_t K = keys[sl], r = vals[sl];
+    keys[sl] = HT_EMPTY;
+    vals[sl] = 0;
+    if (!T.failed || K == own || K == T.lu) continue;
+    const uint64_t k = rate_key(A, K, r);
+    if (k > kc0 && (int64_t)A.wt[K] + cu <= cap_of(A, K) && k > T.kc) {
+      T.kc = k;
+      T.lc = K;
+    }
+  }
+}
+
 // one node per warp, neighbours aggregated in a shared-memory table of WARP_TAB
 __device__ __forceinline__ void rate_warp(const LPArgs &A, int32_t u, int32_t pos, int lane,
                                           int32_t *keys, int32_t *vals, uint16_t *list) {
@@ -370,21 +428,10 @@ __device__ __forceinline__ void rate_warp(const LPArgs &A, int32_t u, int32_t po
   }
   __syncwarp();
   int32_t rown = 0;
-  uint64_t kc = 0, ku = 0;
-  int32_t lc = -1, lu = -1;
-  for (int32_t i = lane; i < cnt; i += 32) {
-    int32_t sl = list[i];
-    int32_t K = keys[sl], r = vals[sl];
-    keys[sl] = HT_EMPTY;
-    vals[sl] = 0;
-    if (K == own) {
-      rown = r;
-      continue;
-    }
-    uint64_t k = rate_key(A, K, r);
-    if (k > ku) { ku = k; lu = K; }
-    if ((int64_t)A.wt[K] + cu <= cap_of(A, K) && k > kc) { kc = k; lc = K; }
-  }
+  SelTop T = select_top(A, keys, vals, list, lane, 32, cnt, own, cu, rown);
+  select_rest(A, keys, vals, list, lane, 32, cnt, own, cu, group_max64<32>(T.kc), T);
+  const uint64_t kc = T.kc, ku = T.ku;
+  int32_t lc = T.lc, lu = T.lu;
   rown = (int32_t)__reduce_max_sync(0xFFFFFFFFu, (uint32_t)rown);
   uint64_t mc = group_max64<32>(kc), mu = group_max64<32>(ku);
   unsigned bc = __ballot_sync(0xFFFFFFFFu, mc != 0 && kc == mc);
@@ -424,21 +471,20 @@ __device__ void rate_cta(const LPArgs &A, int32_t u, int32_t pos, int32_t *keys,
   }
   __syncthreads();
   const int32_t cnt = s_cnt;
-  uint64_t kc = 0, ku = 0;
-  int32_t lc = -1, lu = -1;
-  for (int32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-    int32_t sl = list[i];
-    int32_t K = keys[sl], r = vals[sl];
-    keys[sl] = HT_EMPTY;
-    vals[sl] = 0;
-    if (K == own) {
-      s_rown = r;
-      continue;
-    }
-    uint64_t k = rate_key(A, K, r);
-    if (k > ku) { ku = k; lu = K; }
-    if ((int64_t)A.wt[K] + cu <= cap_of(A, K) && k > kc) { kc = k; lc = K; }
+  int32_t rown = -1;
+  SelTop T = select_top(A, keys, vals, list, threadIdx.x, blockDim.x, cnt, own, cu, rown);
+  if (rown >= 0) s_rown = rown;
+  {
+    const uint64_t w0 = group_max64<32>(T.kc);
+    if (lane == 0) red_c[w] = w0;
+    __syncthreads();
+    uint64_t kc0 = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) kc0 = red_c[i] > kc0 ? red_c[i] : kc0;
+    select_rest(A, keys, vals, list, threadIdx.x, blockDim.x, cnt, own, cu, kc0, T);
+    __syncthreads();  // red_c is reused below
   }
+  const uint64_t kc = T.kc, ku = T.ku;
+  const int32_t lc = T.lc, lu = T.lu;
   uint64_t wc = group_max64<32>(kc), wu = group_max64<32>(ku);
   if (lane == 0) { red_c[w] = wc; red_u[w] = wu; }
   __syncthreads();
@@ -456,7 +502,7 @@ __device__ void rate_cta(const LPArgs &A, int32_t u, int32_t pos, int32_t *keys,
 
 __device__ __forceinline__ int32_t hub_index(const LPArgs &A, int32_t u);
 
-__global__ void __launch_bounds__(RATE_T) k_rate(LPArgs A, int s) {
+__global__ void __launch_bounds__(RATE_T, 6) k_rate(LPArgs A, int s) {
   __shared__ int32_t tkeys[CTA_TAB];
   __shared__ int32_t tvals[CTA_TAB];
   __shared__ uint16_t tlist[CTA_TAB / 2];
@@ -924,19 +970,13 @@ __global__ void __launch_bounds__(HB_W * 32) k_hub_bucket(LPArgs A, int s) {
       }
       start = __any_sync(0xFFFFFFFFu, mine_left) ? next : ne;
       __syncwarp();
-      for (int32_t x = lane; x < held; x += 32) {
-        const int32_t sl = list[x];
-        const int32_t K = keys[sl], r = vals[sl];
-        keys[sl] = HT_EMPTY;
-        vals[sl] = 0;
-        if (K == own) {
-          A.hrown[h] = r;
-          continue;
-        }
-        const uint64_t k = rate_key(A, K, r);
-        ku = k > ku ? k : ku;
-        if ((int64_t)A.wt[K] + cu <= cap_of(A, K) && k > kc) kc = k;
-      }
+      int32_t rown = -1;
+      SelTop T = select_top(A, keys, vals, list, lane, 32, held, own, cu, rown);
+      if (rown >= 0) A.hrown[h] = rown;
+      const uint64_t thr = group_max64<32>(T.kc > kc ? T.kc : kc);  // best admissible so far
+      select_rest(A, keys, vals, list, lane, 32, held, own, cu, thr, T);
+      ku = T.ku > ku ? T.ku : ku;
+      kc = T.kc > kc ? T.kc : kc;
       __syncwarp();
     }
     kc = group_max64<32>(kc);
