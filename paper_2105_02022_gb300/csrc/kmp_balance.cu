@@ -458,15 +458,14 @@ __device__ __forceinline__ void hint_lower(const BalArgs &A, int32_t B, int32_t 
 // decided, `stop` when the block fits
 __device__ int32_t commit_batch(const BalArgs &A, int32_t B, int32_t nb, const int32_t *s_v, const int32_t *s_t,
                                 const int64_t *s_c, const int64_t *s_bwt, const int64_t *s_capt,
-                                const uint32_t *s_adj, int64_t E, int32_t &stop, int32_t *hint) {
+                                const uint32_t *s_adj, int64_t E, int32_t &stop, int32_t *hint, int64_t &wB,
+                                int32_t capB) {
   // only this CTA changes weights, so the block's and the targets' weights are
   // tracked here (a target's weight is its start weight plus the moves of this
   // batch into it)
   uint32_t moved_mask = 0;
   int32_t j = 0, moves = 0;
   stop = 0;
-  int64_t wB = A.bw[B];
-  const int64_t capB = A.cap[B];
   for (; j < nb; ++j) {
     if (wB <= capB) {
       stop = 1;
@@ -490,7 +489,7 @@ __device__ int32_t commit_batch(const BalArgs &A, int32_t B, int32_t nb, const i
     }
   }
   A.bw[B] = wB;
-  hint_lower(A, B, hint);
+  if ((int64_t)capB - wB >= 1 && B < *hint) *hint = B;
   if (moves) atomicAdd(A.moved, (unsigned long long)moves);
   atomicAdd(A.moved + 2, 1ull);  // an exact batch
   atomicAdd(A.moved + 3, (unsigned long long)nb);
@@ -507,7 +506,8 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
   __shared__ uint32_t s_adj[BM_W], s_mask[BM_W], s_toff[BM_W + 1];
   __shared__ unsigned long long s_best[BM_W];
   __shared__ int32_t wk[WS_T], wv[WS_T];  // warp 0's tables (empty between batches)
-  __shared__ int32_t s_nb, s_B, s_ob, s_i, s_phase, s_done, s_hint;
+  __shared__ int32_t s_nb, s_B, s_ob, s_i, s_phase, s_done, s_hint, s_capB;
+  __shared__ int64_t s_wB;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint64_t vmask = (1ull << A.bitsN) - 1ull;
   const uint32_t gcap = A.gcap;  // stride of the per-member table regions
@@ -582,10 +582,16 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
         }
         const int32_t B = A.olist[ob];
         const int32_t hi = A.seg_hi[B];
-        if (i >= hi || A.bw[B] <= A.cap[B]) {
+        const int64_t wB = A.bw[B];
+        const int32_t capB = A.cap[B];
+        if (i >= hi || wB <= capB) {
           ++ob;
           phase = 0;
           continue;
+        }
+        if (lane == 0) {
+          s_wB = wB;  // for the commit, which comes after several warp barriers
+          s_capB = capB;
         }
         // the next batch: the shortest prefix of the remaining candidates
         // whose weights cover the overload
@@ -606,7 +612,7 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
               deg += od;
             }
           }
-          unsigned enough = __ballot_sync(0xFFFFFFFFu, lane < avail && c >= A.bw[B] - A.cap[B]);
+          unsigned enough = __ballot_sync(0xFFFFFFFFu, lane < avail && c >= wB - capB);
           int32_t nb = enough ? __ffs(enough) : avail;
           // member table sized by the member's own distinct blocks (at most
           // min(degree, k)), so low-degree members never touch a hub-sized
@@ -719,7 +725,10 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
         }
         __syncwarp();
         int32_t next = 0, stop = 0;
-        if (lane == 0) next = commit_batch(A, B, nb, s_v, s_t, s_c, s_bwt, s_capt, s_adj, E, stop, &s_hint);
+        if (lane == 0) {
+          int64_t w = s_wB;
+          next = commit_batch(A, B, nb, s_v, s_t, s_c, s_bwt, s_capt, s_adj, E, stop, &s_hint, w, s_capB);
+        }
         next = __shfl_sync(0xFFFFFFFFu, next, 0);
         stop = __shfl_sync(0xFFFFFFFFu, stop, 0);
         if (lane < nb) inbatch[s_v[lane]] = 0;
@@ -809,7 +818,9 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
     __syncthreads();
     if (threadIdx.x == 0) {
       int32_t stop = 0;
-      const int32_t next = commit_batch(A, B, nb, s_v, s_t, s_c, s_bwt, s_capt, s_adj, E, stop, &s_hint);
+      int64_t wB = A.bw[B];
+      const int32_t next =
+          commit_batch(A, B, nb, s_v, s_t, s_c, s_bwt, s_capt, s_adj, E, stop, &s_hint, wB, A.cap[B]);
       s_i += next;
       if (stop) {
         ++s_ob;
