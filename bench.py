@@ -77,6 +77,7 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "rmat_scale26_ef16_k65536"
 ORACLE_SAMPLE_SUBROUNDS = 1
+REFERENCE_SAMPLES_PER_BUDGET = 6  # full-sub-round samples the reference arm may spend per run
 
 
 def _peaks():
@@ -185,13 +186,14 @@ def level0_cap(g, k, C=160):
     return max(1, int(EPS * g.n / kp))
 
 
-def oracle_sample(g, k):
+def oracle_sample(g, k, nodes=0):
     """The oracle as it stands on a bounded sample: the first sub-round of the
-    first round of the input level's coarsening LP (single thread)."""
+    first round of the input level's coarsening LP (single thread), over the
+    nodes below `nodes` only when it is positive."""
     import oracle as O
 
     U = level0_cap(g, k)
-    cfg = O.config(sample_subrounds=ORACLE_SAMPLE_SUBROUNDS)
+    cfg = O.config(sample_subrounds=ORACLE_SAMPLE_SUBROUNDS, sample_nodes=nodes)
     t = time.perf_counter()
     _, _, st = O.cluster(g, U, 1, SEED, 0, cfg=cfg, isolated=False, two_hop=False, stats=True)
     dt = time.perf_counter() - t
@@ -215,17 +217,23 @@ def run_reference(args, rank, world):
     O.build()
     make, k, _ = WORKLOADS[args.workload]
     g = make(gg)
-    # the oracle has no warm-up state: every sample is independent
+    # the oracle has no warm-up state: every sample is independent.  A step
+    # rates the first sub-round over a share of the nodes that keeps the whole
+    # run near REFERENCE_BUDGET_S (the full sub-round of R-MAT 2^26 takes
+    # about 25 s on one core)
+    share = min(1.0, REFERENCE_SAMPLES_PER_BUDGET / max(args.steps, 1))
+    nodes = g.n if share >= 1.0 else max(1, int(g.n * share))
     vals, scanned_all, secs = [], 0, 0.0
     for _ in range(args.steps):
-        scanned, dt = oracle_sample(g, k)
+        scanned, dt = oracle_sample(g, k, nodes)
         vals.append(scanned / dt)
         scanned_all += scanned
         secs += dt
     v = scanned_all / secs
     base = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": _cpu_model(),
             "sample": f"{args.workload}: per step, sub-round 0 of round 0 of the level-0 coarsening LP "
-                      f"(U = {level0_cap(g, k)}), {scanned_all // max(args.steps, 1)} entries rated"}
+                      f"(U = {level0_cap(g, k)}) over nodes 0..{nodes - 1}, "
+                      f"{scanned_all // max(args.steps, 1)} entries rated"}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / max(args.steps, 1) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",

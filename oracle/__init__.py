@@ -34,7 +34,8 @@ class Config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in (
         "C", "lp_rounds", "refine_rounds", "subrounds", "two_hop", "conv_num", "conv_den",
         "ip_C", "ip_lp_rounds", "rep_random", "rep_bfs", "rep_ggg", "fm_passes", "fm_stop",
-        "learned", "lrep_random", "lrep_bfs", "lrep_ggg", "replicas", "async_lp", "sample_subrounds", "adaptive")]
+        "learned", "lrep_random", "lrep_bfs", "lrep_ggg", "replicas", "async_lp", "sample_subrounds", "adaptive",
+        "sample_nodes")]
 
 
 class OGraph(ctypes.Structure):

@@ -50,6 +50,8 @@ typedef struct {
   int32_t sample_subrounds; /* timing samples only: kmpo_cluster's LP ends after this many
                                sub-rounds (0: no limit); the sub-rounds that run are unchanged */
   int32_t adaptive;      /* adaptive portfolio (B7, kmpo_ip.c): 0 = the fixed portfolio of B2 */
+  int32_t sample_nodes;  /* timing samples only: with sample_subrounds, the sampled sub-rounds rate
+                            only nodes u < sample_nodes (0: all) */
 } kmpo_config;
 
 /* graph owned by the oracle (returned by kmpo_contract) */

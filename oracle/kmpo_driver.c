@@ -85,6 +85,7 @@ void kmpo_config_default(kmpo_config *c) {
   c->replicas = 1;
   c->async_lp = 0;
   c->sample_subrounds = 0;
+  c->sample_nodes = 0;
   c->adaptive = 0;
 }
 

@@ -111,7 +111,8 @@ static int cmp_prop(const void *a, const void *b) {
 static int32_t lp_run(int32_t n, const int64_t *xadj, const int32_t *adj, const int32_t *vw,
                       const int32_t *ew, int32_t *label, int64_t *wt, int32_t nlab,
                       const int32_t *cap, int32_t U, int32_t rounds, int32_t S,
-                      uint64_t basekey, int32_t *fav, kmpo_lp_stats *st, int32_t sample) {
+                      uint64_t basekey, int32_t *fav, kmpo_lp_stats *st, int32_t sample,
+                      int32_t sample_nodes) {
   int64_t *rating = (int64_t *)calloc((size_t)(nlab > 0 ? nlab : 1), sizeof(int64_t));
   char *active = (char *)malloc((size_t)(n > 0 ? n : 1));
   char *moved = (char *)malloc((size_t)(n > 0 ? n : 1));
@@ -130,7 +131,8 @@ static int32_t lp_run(int32_t n, const int64_t *xadj, const int32_t *adj, const 
     for (int32_t s = 0; s < S; ++s) {
       if (sample > 0 && r * S + s >= sample) break;
       int32_t np = 0;
-      for (int32_t u = 0; u < n; ++u) {
+      const int32_t un = sample > 0 && sample_nodes > 0 && sample_nodes < n ? sample_nodes : n;
+      for (int32_t u = 0; u < un; ++u) {
         if (!active[u] || kmpo_subround(rk, u, S) != s) continue;
         int64_t deg = xadj[u + 1] - xadj[u];
         if (deg == 0) continue;
@@ -305,7 +307,7 @@ int32_t kmpo_cluster(int32_t n, const int64_t *xadj, const int32_t *adj, const i
     fav[v] = -1;
   }
   lp_run(n, xadj, adj, vw, ew, label, wt, n, NULL, U, rounds, cfg->subrounds, basekey, fav, st,
-         cfg->sample_subrounds);
+         cfg->sample_subrounds, cfg->sample_nodes);
   if (do_isolated) pack_isolated(n, xadj, vw, U, label);
   if (do_two_hop) two_hop(n, vw, U, fav, label);
   if (fav_out) memcpy(fav_out, fav, sizeof(int32_t) * (size_t)n);
@@ -323,7 +325,7 @@ int32_t kmpo_cluster_key(int32_t n, const int64_t *xadj, const int32_t *adj, con
     label[v] = v;
     wt[v] = vwt(vw, v);
   }
-  lp_run(n, xadj, adj, vw, ew, label, wt, n, NULL, U, rounds, S, basekey, NULL, NULL, 0);
+  lp_run(n, xadj, adj, vw, ew, label, wt, n, NULL, U, rounds, S, basekey, NULL, NULL, 0, 0);
   pack_isolated(n, xadj, vw, U, label);
   free(wt);
   return count_clusters(n, label);
@@ -403,7 +405,7 @@ int64_t kmpo_refine(int32_t n, const int64_t *xadj, const int32_t *adj, const in
   uint64_t basekey = kmpo_key(seed, 1, w);
   int64_t *bw = (int64_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int64_t));
   for (int32_t v = 0; v < n; ++v) bw[part[v]] += vwt(vw, v);
-  lp_run(n, xadj, adj, vw, ew, part, bw, k, cap, 0, rounds, cfg->subrounds, basekey, NULL, st, 0);
+  lp_run(n, xadj, adj, vw, ew, part, bw, k, cap, 0, rounds, cfg->subrounds, basekey, NULL, st, 0, 0);
   free(bw);
   return kmpo_cut(n, xadj, adj, ew, part);
 }

@@ -356,20 +356,19 @@ __device__ __forceinline__ int32_t ht_add_fresh(int32_t *keys, int32_t *vals, ui
 // Best keys over a table's held slots (one thread's share: list[i0], i0 +
 // step, ... < held): ku over every label but `own`, kc over the admissible
 // ones (target weight + c(u) <= cap).  Admissibility needs the target's
-// weight, a random read, so it is checked top-first: the group's best label
-// alone (select_keys, then select_check by its holder); only if that one is
-// full does every other thread check its own best; the caller reduces those
-// to kc0, and a thread whose best failed then checks its other labels above
-// kc0 (select_rest).  The result is the plain maximum over admissible
-// labels: a thread whose best passed holds nothing above it.
+// weight, a random read, so a thread checks its own best label first; the
+// caller reduces those to kc0, the best admissible top of the group, and only
+// a thread whose top failed then checks its other labels above kc0
+// (select_rest).  The result is the plain maximum over admissible labels:
+// a thread whose top passed holds nothing above it.
 struct SelTop {
   uint64_t ku = 0, kc = 0;
   int32_t lu = -1, lc = -1;
-  bool failed = false;  // the thread's best label is not admissible
+  bool failed = false;  // the thread's top label is not admissible
 };
-__device__ __forceinline__ SelTop select_keys(const LPArgs &A, const int32_t *keys, const int32_t *vals,
-                                              const uint16_t *list, int32_t i0, int32_t step, int32_t held,
-                                              int32_t own, int32_t &rown) {
+__device__ __forceinline__ SelTop select_top(const LPArgs &A, const int32_t *keys, const int32_t *vals,
+                                             const uint16_t *list, int32_t i0, int32_t step, int32_t held,
+                                             int32_t own, int32_t cu, int32_t &rown) {
   SelTop T;
   for (int32_t i = i0; i < held; i += step) {
     const int32_t sl = list[i];
@@ -384,26 +383,15 @@ __device__ __forceinline__ SelTop select_keys(const LPArgs &A, const int32_t *ke
       T.lu = K;
     }
   }
-  return T;
-}
-// the thread's best label: admissible (kc) or not (failed)
-__device__ __forceinline__ void select_check(const LPArgs &A, int32_t cu, SelTop &T) {
-  if (T.lu < 0) return;
-  if ((int64_t)A.wt[T.lu] + cu <= cap_of(A, T.lu)) {
-    T.kc = T.ku;
-    T.lc = T.lu;
-  } else {
-    T.failed = true;
+  if (T.lu >= 0) {
+    if ((int64_t)A.wt[T.lu] + cu <= cap_of(A, T.lu)) {
+      T.kc = T.ku;
+      T.lc = T.lu;
+    } else {
+      T.failed = true;
+    }
   }
-}
-// a warp's share of the top-first check (group = the warp); best admissible
-// labels above `floor` only (0: all)
-__device__ __forceinline__ void select_check_warp(const LPArgs &A, int32_t cu, uint64_t floor, SelTop &T) {
-  const uint64_t gtop = group_max64<32>(T.ku);
-  if (gtop <= floor) return;  // nothing here beats what is held already
-  const bool holder = T.ku == gtop;
-  if (holder) select_check(A, cu, T);
-  if (!__any_sync(0xFFFFFFFFu, holder && !T.failed) && !holder && T.ku > floor) select_check(A, cu, T);
+  return T;
 }
 // the labels above kc0 of a thread whose top failed; the slots are cleared
 __device__ __forceinline__ void select_rest(const LPArgs &A, int32_t *keys, int32_t *vals, const uint16_t *list,
@@ -440,8 +428,7 @@ __device__ __forceinline__ void rate_warp(const LPArgs &A, int32_t u, int32_t po
   }
   __syncwarp();
   int32_t rown = 0;
-  SelTop T = select_keys(A, keys, vals, list, lane, 32, cnt, own, rown);
-  select_check_warp(A, cu, 0, T);
+  SelTop T = select_top(A, keys, vals, list, lane, 32, cnt, own, cu, rown);
   select_rest(A, keys, vals, list, lane, 32, cnt, own, cu, group_max64<32>(T.kc), T);
   const uint64_t kc = T.kc, ku = T.ku;
   int32_t lc = T.lc, lu = T.lu;
@@ -485,31 +472,16 @@ __device__ void rate_cta(const LPArgs &A, int32_t u, int32_t pos, int32_t *keys,
   __syncthreads();
   const int32_t cnt = s_cnt;
   int32_t rown = -1;
-  SelTop T = select_keys(A, keys, vals, list, threadIdx.x, blockDim.x, cnt, own, rown);
+  SelTop T = select_top(A, keys, vals, list, threadIdx.x, blockDim.x, cnt, own, cu, rown);
   if (rown >= 0) s_rown = rown;
   {
-    // the CTA's best label first; every thread's best only if it is full
-    uint64_t w0 = group_max64<32>(T.ku);
-    if (lane == 0) red_u[w] = w0;
-    if (threadIdx.x == 0) lab_c = 0;  // flag: the CTA's best is admissible
-    __syncthreads();
-    uint64_t gtop = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) gtop = red_u[i] > gtop ? red_u[i] : gtop;
-    const bool holder = gtop != 0 && T.ku == gtop;
-    if (holder) {
-      select_check(A, cu, T);
-      if (!T.failed) lab_c = 1;
-    }
-    __syncthreads();
-    if (lab_c == 0 && !holder) select_check(A, cu, T);
-    w0 = group_max64<32>(T.kc);
+    const uint64_t w0 = group_max64<32>(T.kc);
     if (lane == 0) red_c[w] = w0;
     __syncthreads();
     uint64_t kc0 = 0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) kc0 = red_c[i] > kc0 ? red_c[i] : kc0;
     select_rest(A, keys, vals, list, threadIdx.x, blockDim.x, cnt, own, cu, kc0, T);
-    __syncthreads();  // red_c, red_u and lab_c are reused below
-    if (threadIdx.x == 0) lab_c = -1;
+    __syncthreads();  // red_c is reused below
   }
   const uint64_t kc = T.kc, ku = T.ku;
   const int32_t lc = T.lc, lu = T.lu;
@@ -999,11 +971,9 @@ __global__ void __launch_bounds__(HB_W * 32) k_hub_bucket(LPArgs A, int s) {
       start = __any_sync(0xFFFFFFFFu, mine_left) ? next : ne;
       __syncwarp();
       int32_t rown = -1;
-      SelTop T = select_keys(A, keys, vals, list, lane, 32, held, own, rown);
+      SelTop T = select_top(A, keys, vals, list, lane, 32, held, own, cu, rown);
       if (rown >= 0) A.hrown[h] = rown;
-      const uint64_t kcw = group_max64<32>(kc);  // best admissible of earlier rounds
-      select_check_warp(A, cu, kcw, T);
-      const uint64_t thr = group_max64<32>(T.kc > kcw ? T.kc : kcw);
+      const uint64_t thr = group_max64<32>(T.kc > kc ? T.kc : kc);  // best admissible so far
       select_rest(A, keys, vals, list, lane, 32, held, own, cu, thr, T);
       ku = T.ku > ku ? T.ku : ku;
       kc = T.kc > kc ? T.kc : kc;
