@@ -449,10 +449,6 @@ __device__ int32_t lowest_admissible(const BalArgs &A, int32_t B, int64_t c, int
   return res;
 }
 
-// the block being emptied lost weight: the hint comes down to it if it has room
-__device__ __forceinline__ void hint_lower(const BalArgs &A, int32_t B, int32_t *hint) {
-  if ((int64_t)A.cap[B] - A.bw[B] >= 1 && B < *hint) *hint = B;
-}
 
 // the in-order commit of an evaluated batch (one thread); returns the members
 // decided, `stop` when the block fits
@@ -537,8 +533,10 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
           int32_t o = ob, resume = 0;
           for (; o < A.nover; ++o) {
             const int32_t B = A.olist[o];
+            const int32_t nm = A.spec_n[o], sat = A.spec_sat[o], send = A.spec_end[o];
             const int32_t lo = A.seg_lo[B], hi = A.seg_hi[B];
-            const int32_t nm = A.spec_n[o];
+            const int64_t bwB = A.bw[B];  // no move below targets B
+            const int32_t capB = A.cap[B];
             int32_t v = 0, t = 0;
             int64_t c = 0, bt = 0, ct = 0;
             if (lane < nm) {
@@ -561,16 +559,16 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
               A.part[v] = t;
               atomicAdd(reinterpret_cast<unsigned long long *>(&A.bw[t]), (unsigned long long)c);
             }
-            const int64_t gone = warp_sum64(lane < f ? c : 0);
+            const int64_t bwB2 = bwB - warp_sum64(lane < f ? c : 0);
             if (lane == 0 && f > 0) {
-              A.bw[B] -= gone;
-              hint_lower(A, B, &s_hint);
+              A.bw[B] = bwB2;
+              if ((int64_t)capB - bwB2 >= 1 && B < s_hint) s_hint = B;  // the block got room
               atomicAdd(A.moved, (unsigned long long)f);
               atomicAdd(A.moved + 1, (unsigned long long)f);  // speculated moves that stood
             }
             __syncwarp();
-            resume = f < nm ? lo + f : (A.spec_sat[o] ? hi : A.spec_end[o]);
-            if (resume < hi && A.bw[B] > A.cap[B]) break;  // exact batches take over here
+            resume = f < nm ? lo + f : (sat ? hi : send);
+            if (resume < hi && bwB2 > capB) break;  // exact batches take over here
           }
           if (o >= A.nover) {
             if (lane == 0) s_done = 1;
@@ -689,6 +687,8 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
         __syncwarp();
         // best admissible block of every member, (conn, ~block); the tables
         // are emptied on the way (every table spans whole 32-slot chunks)
+        // (the lane that holds a member's best so far also records that
+        // block's weight and cap, the target's state at the start of the batch)
         {
           int32_t j = 0;
           for (uint32_t base = 0; base < TT; base += 32) {
@@ -698,10 +698,20 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
             wk[x] = HT_EMPTY;
             wv[x] = 0;
             uint64_t key = 0;
-            if (b != HT_EMPTY && b != B && A.bw[b] + bw_node(A, s_v[j]) <= A.cap[b])
-              key = ((uint64_t)(uint32_t)cv << 32) | (0xFFFFFFFFu - (uint32_t)b);
-            key = group_max64<32>(key);
-            if (lane == 0 && key > s_best[j]) s_best[j] = key;
+            int64_t bwb = 0;
+            int32_t capb = 0;
+            if (b != HT_EMPTY && b != B) {
+              bwb = A.bw[b];
+              capb = A.cap[b];
+              if (bwb + bw_node(A, s_v[j]) <= capb)
+                key = ((uint64_t)(uint32_t)cv << 32) | (0xFFFFFFFFu - (uint32_t)b);
+            }
+            const uint64_t top = group_max64<32>(key);
+            if (top != 0 && key == top && top > s_best[j]) {
+              s_best[j] = top;
+              s_bwt[j] = bwb;
+              s_capt[j] = capb;
+            }
             __syncwarp();
           }
         }
@@ -715,15 +725,13 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
           if (s_t[j] < 0) {
             const int32_t t = lowest_admissible(A, B, s_c[j], lane, &s_hint);
             __syncwarp();
-            if (lane == 0) s_t[j] = t;
+            if (lane == 0) {
+              s_t[j] = t;
+              s_bwt[j] = t >= 0 ? A.bw[t] : 0;
+              s_capt[j] = t >= 0 ? A.cap[t] : 0;
+            }
             __syncwarp();
           }
-        if (lane < nb) {
-          const int32_t t = s_t[lane];
-          s_bwt[lane] = t >= 0 ? A.bw[t] : 0;  // the target's weight at the start of the batch
-          s_capt[lane] = t >= 0 ? A.cap[t] : 0;
-        }
-        __syncwarp();
         int32_t next = 0, stop = 0;
         if (lane == 0) {
           int64_t w = s_wB;
