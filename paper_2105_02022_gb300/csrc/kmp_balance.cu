@@ -493,6 +493,21 @@ __device__ int32_t commit_batch(const BalArgs &A, int32_t B, int32_t nb, const i
   return j;
 }
 
+// the fixed data of overloaded block o's speculation (lane j: its move j)
+struct SpecAhead {
+  int32_t B = 0, nm = 0, v = 0, t = 0;
+};
+__device__ __forceinline__ SpecAhead spec_ahead(const BalArgs &A, int32_t o, int lane) {
+  SpecAhead S;
+  S.B = A.olist[o];
+  S.nm = A.spec_n[o];
+  if (lane < S.nm) {
+    S.v = A.spec_v[(int64_t)o * SPEC_MAX + lane];
+    S.t = A.spec_t[(int64_t)o * SPEC_MAX + lane];
+  }
+  return S;
+}
+
 // Warp 0 drives the commit: it applies the speculated moves that stand,
 // sets up every exact batch, and evaluates and commits the small ones alone;
 // the whole CTA joins only for a batch beyond WS_E entries or WS_T slots.
@@ -530,18 +545,21 @@ __global__ void __launch_bounds__(BM_T) k_bal_moves(BalArgs A, int32_t *inbatch)
           // the current weight plus what the block's earlier moves add to
           // it; the moves before the first that does not fit are applied at
           // once.  Stop at the first block that still needs exact batches.
+          // What does not change during the commit (the block, its speculated
+          // moves, caps, node weights) is read one block ahead; only the
+          // weights are read when the block's turn comes.
           int32_t o = ob, resume = 0;
+          SpecAhead nx;
+          if (o < A.nover) nx = spec_ahead(A, o, lane);
           for (; o < A.nover; ++o) {
-            const int32_t B = A.olist[o];
-            const int32_t nm = A.spec_n[o], sat = A.spec_sat[o], send = A.spec_end[o];
-            const int32_t lo = A.seg_lo[B], hi = A.seg_hi[B];
+            const SpecAhead cur = nx;
+            if (o + 1 < A.nover) nx = spec_ahead(A, o + 1, lane);
+            const int32_t B = cur.B, nm = cur.nm, v = cur.v, t = cur.t;
+            const int32_t lo = A.seg_lo[B], hi = A.seg_hi[B], capB = A.cap[B];
+            const int32_t sat = A.spec_sat[o], send = A.spec_end[o];
             const int64_t bwB = A.bw[B];  // no move below targets B
-            const int32_t capB = A.cap[B];
-            int32_t v = 0, t = 0;
             int64_t c = 0, bt = 0, ct = 0;
             if (lane < nm) {
-              v = A.spec_v[(int64_t)o * SPEC_MAX + lane];
-              t = A.spec_t[(int64_t)o * SPEC_MAX + lane];
               c = bw_node(A, v);
               bt = A.bw[t];
               ct = A.cap[t];
