@@ -19,6 +19,7 @@
 // whose members are evaluated at once and committed while they provably do
 // not interact.
 #include <algorithm>
+#include <climits>
 
 #include "kmp_internal.cuh"
 
@@ -40,7 +41,7 @@ struct BalArgs {
   const uint8_t *over;
   const int32_t *olist;  // the overloaded blocks, ascending
   int32_t nover;
-  int32_t *slack;        // sorted cap - weight of all blocks (Pk entries)
+  int64_t max_room;      // the largest cap - weight over all blocks at the start
   int64_t *cand_d;       // [n] d of candidate nodes
   uint64_t *keys;        // (block << bitsN | node) of candidates
   int32_t *ncand;
@@ -108,38 +109,9 @@ __device__ int64_t conn_table(const BalArgs &A, int32_t v, int32_t *K, int32_t *
   return ht_get(K, V, mask, A.part[v]);
 }
 
-// blocks whose slack is at least c (B itself has negative slack)
-__device__ int32_t count_fit(const BalArgs &A, int64_t c) {
-  int32_t lo = 0, hi = A.k;
-  while (lo < hi) {
-    int32_t mid = (lo + hi) >> 1;
-    if ((int64_t)A.slack[mid] >= c) hi = mid;
-    else lo = mid + 1;
-  }
-  return A.k - lo;
-}
-
-__global__ void __launch_bounds__(1024) k_bal_slack(BalArgs A, int32_t Pk) {
-  for (int32_t i = threadIdx.x; i < Pk; i += blockDim.x) {
-    int64_t s = i < A.k ? (int64_t)A.cap[i] - A.bw[i] : (int64_t)INT32_MAX;
-    A.slack[i] = (int32_t)(s < INT32_MIN ? INT32_MIN : (s > INT32_MAX ? INT32_MAX : s));
-  }
-  __syncthreads();
-  for (int32_t kk = 2; kk <= Pk; kk <<= 1)
-    for (int32_t j = kk >> 1; j > 0; j >>= 1) {
-      for (int32_t i = threadIdx.x; i < Pk; i += blockDim.x) {
-        int32_t l = i ^ j;
-        if (l > i) {
-          int32_t x = A.slack[i], y = A.slack[l];
-          if ((x > y) == ((i & kk) == 0)) {
-            A.slack[i] = y;
-            A.slack[l] = x;
-          }
-        }
-      }
-      __syncthreads();
-    }
-}
+// some block has room for weight c (the overloaded block itself has none);
+// candidates are rated from the starting state, so the starting room decides
+__device__ __forceinline__ bool room_somewhere(const BalArgs &A, int64_t c) { return A.max_room >= c; }
 
 // Candidates of the overloaded blocks, one warp per node with the warp's
 // shared-memory table.  Nodes whose table would not fit it are listed in
@@ -174,7 +146,7 @@ __global__ void __launch_bounds__(BAL_T) k_bal_cand(BalArgs A, int32_t *big, int
       best = o > best ? o : best;
       nadj += __shfl_xor_sync(0xFFFFFFFFu, nadj, m);
     }
-    if (best < 0 && count_fit(A, c) > nadj) best = 0;  // an admissible block without neighbours
+    if (best < 0 && room_somewhere(A, c)) best = 0;  // an admissible block without neighbours
     if (lane == 0 && best >= 0) {
       A.cand_d[v] = best - cown;
       int32_t p = atomicAdd(A.ncand, 1);
@@ -247,7 +219,7 @@ __global__ void __launch_bounds__(BAL_T) k_bal_cand_big(BalArgs A, const int32_t
         bb = s_best[x] > bb ? s_best[x] : bb;
         na += s_nadj[x];
       }
-      if (bb < 0 && count_fit(A, c) > na) bb = 0;  // an admissible block without neighbours
+      if (bb < 0 && room_somewhere(A, c)) bb = 0;  // an admissible block without neighbours
       if (bb >= 0) {
         A.cand_d[v] = bb - s_cown;
         int32_t p = atomicAdd(A.ncand, 1);
@@ -871,18 +843,20 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   to_host(hbw.data(), bw.p, k);
   std::vector<uint8_t> hover(k, 0);
   std::vector<int32_t> holist;
-  for (int32_t b = 0; b < k; ++b)
+  int64_t max_room = INT64_MIN;
+  for (int32_t b = 0; b < k; ++b) {
     if (hbw[b] > caps_host[b]) {
       hover[b] = 1;
       holist.push_back(b);
     }
+    max_room = std::max<int64_t>(max_room, (int64_t)caps_host[b] - hbw[b]);
+  }
   if (holist.empty() || n == 0) return 0;
-  int32_t Pk = (int32_t)next_pow2((uint64_t)std::max(k, 2));
   int bitsN = 1;
   while ((1ll << bitsN) < (int64_t)n) ++bitsN;
   int bitsK = 1;
   while ((1ll << bitsK) < (int64_t)k) ++bitsK;
-  DBuf<int32_t> cap(k), slack(Pk), ncand(1), seg_lo(k), seg_hi(k);
+  DBuf<int32_t> cap(k), ncand(1), seg_lo(k), seg_hi(k);
   DBuf<uint8_t> over(k);
   DBuf<int64_t> cand_d(n);
   DBuf<uint64_t> keys(n), tmp(n), sortbuf(2ll * n);
@@ -915,7 +889,7 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   A.over = over;
   A.olist = olist;
   A.nover = (int32_t)holist.size();
-  A.slack = slack;
+  A.max_room = max_room;
   A.cand_d = cand_d;
   A.keys = keys;
   A.ncand = ncand;
@@ -926,8 +900,6 @@ int64_t balance(const Graph &g, int32_t k, const int32_t *caps_host, int32_t *pa
   A.gtab = nullptr;
   A.gcap = gcap;
   A.moved = moved;
-  k_bal_slack<<<1, 1024, 0, s>>>(A, Pk);
-  KMP_LAUNCHED("bal_slack");
   // nodes with more distinct neighbour blocks than a warp's shared table
   // holds have degree > BAL_STAB / 2, so there are at most m / 257 of them
   DBuf<int32_t> big(g.m / (BAL_STAB / 2 + 1) + 1), nbig(1);
