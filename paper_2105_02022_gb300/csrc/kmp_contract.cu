@@ -567,6 +567,84 @@ __global__ void k_large_gather(const int32_t *rows, int32_t nrows, const int64_t
   }
 }
 
+// The longer rows' entries (rank r << bits | neighbour) are ordered by a
+// counting sort on (r, neighbour >> SEG_LO): every such segment holds at most
+// 2^SEG_LO distinct neighbours of one row, and one CTA then sorts it in shared
+// memory by the low bits.
+constexpr int SEG_LO = 14;
+static_assert((1 << SEG_LO) == SORT_L, "a segment fits the larger shared-memory sort");
+__global__ void k_seg_hist(int64_t N, const uint64_t *ek, int bits, int32_t *hist) {
+  const int hb = bits - SEG_LO;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = ek[i];
+    atomicAdd(&hist[((k >> bits) << hb) | ((k & ((1ull << bits) - 1ull)) >> SEG_LO)], 1);
+  }
+}
+__global__ void k_seg_scatter(int64_t N, const uint64_t *ek, const int32_t *ev, int bits, const int32_t *off,
+                              int32_t *cur, uint64_t *ek2, int32_t *ev2) {
+  const int hb = bits - SEG_LO;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = ek[i];
+    const int64_t x = (int64_t)(((k >> bits) << hb) | ((k & ((1ull << bits) - 1ull)) >> SEG_LO));
+    const int64_t p = (int64_t)off[x] + atomicAdd(&cur[x], 1);
+    ek2[p] = k;
+    ev2[p] = ev[i];
+  }
+}
+// non-empty segments by size: up to SORT_S entries (list 0) and up to SORT_L (list 1)
+__global__ void k_seg_split(int64_t X, const int32_t *hist, int32_t *lists, int32_t *counts, int64_t cap) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < X;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t len = hist[x];
+    if (len == 0) continue;
+    const int c = len <= SORT_S ? 0 : 1;
+    lists[(int64_t)c * cap + atomicAdd(&counts[c], 1)] = (int32_t)x;
+  }
+}
+// one CTA per segment: (low SEG_LO bits << 32 | weight) sorted in shared memory
+template <int P, int NT>
+__global__ void __launch_bounds__(NT) k_seg_sort(const int32_t *segs, int32_t nseg, const int32_t *off,
+                                                 const int32_t *hist, uint64_t *ek, int32_t *ev) {
+  extern __shared__ uint64_t srt[];  // P entries
+  const uint32_t tid = threadIdx.x;
+  const uint64_t lo_mask = (1ull << SEG_LO) - 1ull;
+  for (int64_t i = blockIdx.x; i < nseg; i += gridDim.x) {
+    const int32_t x = segs[i];
+    const int64_t o = off[x];
+    const int32_t d = hist[x];
+    const uint64_t hi = ek[o] & ~lo_mask;
+    uint32_t Q = 32;
+    while ((int32_t)Q < d) Q <<= 1;
+    for (uint32_t j = tid; j < Q; j += NT)
+      srt[j] = (int32_t)j < d ? ((ek[o + j] & lo_mask) << 32) | (uint32_t)ev[o + j] : ~0ull;
+    __syncthreads();
+    bitonic<true>(srt, Q, tid, NT);
+    for (uint32_t j = tid; (int32_t)j < d; j += NT) {
+      ek[o + j] = hi | (srt[j] >> 32);
+      ev[o + j] = (int32_t)(uint32_t)srt[j];
+    }
+    __syncthreads();  // the next segment reuses the array
+  }
+}
+template <int P, int NT>
+void launch_seg_sort(const int32_t *segs, int32_t nseg, const int32_t *off, const int32_t *hist, uint64_t *ek,
+                     int32_t *ev) {
+  constexpr size_t bytes = (size_t)P * sizeof(uint64_t);
+  static bool attr = false;
+  if (!attr) {
+    KMP_CUDA(cudaFuncSetAttribute(k_seg_sort<P, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    attr = true;
+  }
+  int per_sm = (int)((227u << 10) / (bytes + 1024));
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 2048 / NT) per_sm = 2048 / NT;
+  int blocks = std::min<int64_t>(nseg, (int64_t)ctx().sms * per_sm);
+  k_seg_sort<P, NT><<<blocks, NT, bytes, ctx().stream>>>(segs, nseg, off, hist, ek, ev);
+  KMP_LAUNCHED("seg_sort");
+}
+
 // sorted entries back into their rows (rank r's entries fill [boff[r], boff[r + 1]))
 __global__ void k_large_place(int64_t N, const uint64_t *ek, const int32_t *ev, int bits, const int32_t *rows,
                               const int64_t *boff, const int64_t *toff, int32_t *tadj, int32_t *tw) {
@@ -727,8 +805,8 @@ Graph contract_graph(const Graph &g, const int32_t *label, int32_t *map) {
     // large rows: every member inserts in parallel into its coarse node's global
     // table; each row's distinct entries are compacted into its temporary row
     // and sorted there by neighbour: in shared memory by one CTA per row when
-    // they fit, else by one key-value radix sort of (row rank, neighbour) over
-    // all such rows
+    // they fit; the longer rows' entries by a key-value radix sort of (row
+    // rank, neighbour's high bits) and then per segment in shared memory
     int bits = 1;
     while ((1ll << bits) < (int64_t)nc) ++bits;
     DBuf<int64_t> tsz(nc), ltoff(nc), ltot(1);
@@ -774,15 +852,43 @@ Graph contract_graph(const Graph &g, const int32_t *label, int32_t *map) {
       KMP_LAUNCHED("gather_deg");
       scan_excl_i64(bdeg, boff, nbig, btot);
       const int64_t NE = read1(btot.p);
-      int rbits = 1;
-      while ((1ll << rbits) < (int64_t)nbig) ++rbits;
       DBuf<uint64_t> ek(NE), ektmp(NE);
       DBuf<int32_t> ev(NE), evtmp(NE);
       k_large_gather<<<grid_for((int64_t)nbig * 32, 256), 256, 0, s>>>(brows, nbig, boff, toff, tadj, tw, cdeg,
                                                                       bits, ek, ev);
       KMP_LAUNCHED("large_gather");
-      radix_sort_kv(ek, ev, ektmp, evtmp, NE, rbits + bits);
-      k_large_place<<<grid_for(NE, 256), 256, 0, s>>>(NE, ek, ev, bits, brows, boff, toff, tadj, tw);
+      // counting sort by (rank, neighbour >> SEG_LO), then every segment by the
+      // low bits in shared memory (a row above SORT_L entries has more than
+      // 2^SEG_LO distinct neighbours, so bits > SEG_LO here)
+      const int hb = bits - SEG_LO;
+      const int64_t X = (int64_t)nbig << hb;
+      if (X > (int64_t)INT32_MAX / 2) {
+        // counters beyond int32 indexing (coarse graphs near 2^31 nodes): one
+        // key-value radix sort of (rank, neighbour) instead
+        int rbits = 1;
+        while ((1ll << rbits) < (int64_t)nbig) ++rbits;
+        radix_sort_kv(ek, ev, ektmp, evtmp, NE, rbits + bits);
+        KMP_CUDA(cudaMemcpyAsync(ektmp, ek, NE * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        KMP_CUDA(cudaMemcpyAsync(evtmp, ev, NE * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+      } else {
+        DBuf<int32_t> hist(X), off(X), cur(X), htot(1);
+        hist.zero();
+        cur.zero();
+        k_seg_hist<<<grid_for(NE, 256), 256, 0, s>>>(NE, ek, bits, hist);
+        KMP_LAUNCHED("seg_hist");
+        scan_excl_i32(hist, off, X, htot);
+        k_seg_scatter<<<grid_for(NE, 256), 256, 0, s>>>(NE, ek, ev, bits, off, cur, ektmp, evtmp);
+        KMP_LAUNCHED("seg_scatter");
+        DBuf<int32_t> slists(2 * X), scnt(2);
+        scnt.zero();
+        k_seg_split<<<grid_for(X, 256), 256, 0, s>>>(X, hist, slists, scnt, X);
+        KMP_LAUNCHED("seg_split");
+        int32_t sc2[2];
+        to_host(sc2, scnt.p, 2);
+        if (sc2[0] > 0) launch_seg_sort<SORT_S, 256>(slists.p, sc2[0], off, hist, ektmp, evtmp);
+        if (sc2[1] > 0) launch_seg_sort<SORT_L, 1024>(slists.p + X, sc2[1], off, hist, ektmp, evtmp);
+      }
+      k_large_place<<<grid_for(NE, 256), 256, 0, s>>>(NE, ektmp, evtmp, bits, brows, boff, toff, tadj, tw);
       KMP_LAUNCHED("large_place");
     }
   }

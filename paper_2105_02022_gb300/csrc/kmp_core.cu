@@ -309,7 +309,8 @@ void radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t n, int bits, int lo_b
   if (a != keys) KMP_CUDA(cudaMemcpyAsync(keys, a, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
 }
 
-void radix_sort_kv(uint64_t *keys, int32_t *vals, uint64_t *tmpk, int32_t *tmpv, int64_t n, int bits) {
+void radix_sort_kv(uint64_t *keys, int32_t *vals, uint64_t *tmpk, int32_t *tmpv, int64_t n, int bits,
+                   int lo_bit) {
   if (n <= 1 || bits <= 0) return;
   int64_t ntiles = ceil_div(n, RS_TILE);
   DBuf<int32_t> cnt(256 * ntiles), off(256 * ntiles);
@@ -318,7 +319,7 @@ void radix_sort_kv(uint64_t *keys, int32_t *vals, uint64_t *tmpk, int32_t *tmpv,
   int32_t *va = vals, *vb = tmpv;
   int passes = (bits + 7) / 8;
   for (int p = 0; p < passes; ++p) {
-    int sh = 8 * p;
+    int sh = lo_bit + 8 * p;
     k_rs_hist<<<(unsigned)ntiles, RS_T, 0, s>>>(a, n, sh, cnt, ntiles);
     KMP_LAUNCHED("rs_hist");
     scan_excl_i32(cnt, off, 256 * ntiles, nullptr);

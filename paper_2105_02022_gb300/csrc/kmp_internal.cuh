@@ -247,7 +247,8 @@ void scan_excl_u8_to_i32(const uint8_t *in, int32_t *out, int64_t n, int32_t *to
 // keys equal in those bits keep their order
 void radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t n, int bits, int lo_bit = 0);
 // same with an int32 payload moved along with each key
-void radix_sort_kv(uint64_t *keys, int32_t *vals, uint64_t *tmpk, int32_t *tmpv, int64_t n, int bits);
+void radix_sort_kv(uint64_t *keys, int32_t *vals, uint64_t *tmpk, int32_t *tmpv, int64_t n, int bits,
+                   int lo_bit = 0);
 int grid_for(int64_t work, int per_block, int max_blocks_per_sm = 8);
 
 // -------------------------------------------------------------- components
