@@ -287,11 +287,12 @@ __global__ void __launch_bounds__(BAL_T) k_bal_sort(BalArgs A) {
 
 // Moves in candidate order, evaluated in batches of up to 32.  A batch holds
 // the shortest prefix of the remaining candidates whose weights cover the
-// overload (it may need more moves, never fewer).  The whole CTA walks the
-// batch's adjacency rows at once, building one connectivity table per member
-// and marking which members are neighbours of each other; warp j then picks
-// member j's target from the state at the start of the batch, and thread 0
-// commits in order.  While a block is emptied, every other block only gains
+// overload (it may need more moves, never fewer).  The batch's adjacency
+// rows are walked at once (by warp 0 alone for a small batch, else by the
+// whole CTA), building one connectivity table per member and marking which
+// members are neighbours of each other; each member's target is picked from
+// the state at the start of the batch, and one thread commits in order.
+// While a block is emptied, every other block only gains
 // weight, so a target that is still admissible is still the best (or still
 // the lowest-id admissible one), and "no admissible target" stays true; only
 // a move of a neighbour changes connectivity.  A member passes iff its target
